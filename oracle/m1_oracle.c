@@ -1,0 +1,774 @@
+/*
+ * m1_oracle.c -- plain, slow, FP64 CPU oracle of one radiation step of the
+ * gray M1 module of Scepi & Lesur, "A nonrelativistic radiative transfer
+ * module for Idefix" (arxiv 2606.26268).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the judge of the CUDA path: only the
+ * test suite, the smoke check and the benchmark's CPU-baseline leg may load
+ * it.  It shares no code, header, table or helper with the CUDA library.
+ *
+ * What it computes (one explicit Euler step, Sect. 2.4 "Integration scheme",
+ * items 1-10, followed literally and cell by cell):
+ *   1. boundary values by index mapping (outflow = copy of the nearest
+ *      interior cell, periodic = wrap);
+ *   3. PLM reconstruction with the van Leer limiter (Sect. 2.5);
+ *   4. the f-preserving face fix, Eq. (f_reconstruct) (Sect. 2.5);
+ *   5. signal speeds lambda_{1,3}, Sect. 2.6, with the optically thick
+ *      correction of the same section;
+ *   6. the HLL flux (Sect. 2.5 names HLL; the standard two-wave form);
+ *   7. finite-volume flux divergence with Cartesian, cylindrical or spherical
+ *      metric (orthonormal components);
+ *   8. the implicit matter-radiation coupling of Sect. 2.8, Eqs.
+ *      (source_discrete2) and (implicit_matrix), optionally iterated to
+ *      convergence (Newton mode), and the gas energy / momentum from the
+ *      rescaled conservation laws of Sect. 2.7;
+ *  10. the CFL time step.
+ * Primitive and conservative radiation variables are identical (Sect. 2.4),
+ * so items 2 and 9 are the identity.
+ *
+ * Readings where the paper is silent (each is restated in the design notes):
+ *   - f-fix: keep the reconstructed face flux iff f_face <= 1 and
+ *     f_face > f_center (the inequality of Eq. f_reconstruct), else
+ *     F_face = F_center * (E_face / E_center).
+ *   - PLM on stretched grids: one-sided differences divided by centre
+ *     distances, van Leer harmonic mean, face = u_c + s (x_face - x_c),
+ *     cell centre = midpoint of its faces.
+ *   - tau at a face: mean of rho*chi*dx of the two adjacent cells, dx = the
+ *     largest physical width of the cell over the active directions.
+ *   - transport is unsplit (every direction sees U^n).
+ *   - dt = cfl / max_cells sum_d (chat / h_d).
+ *   - metric terms: well-balanced finite-volume forms, angular-momentum
+ *     conserving form for the phi component.  An inactive direction is one
+ *     cell whose two faces carry the cell's own physical flux.
+ *   - C_v = rho / (mu (Gamma - 1)) per unit volume; e = C_v T.
+ *   - opacities frozen at (rho, T^n) for the whole step.
+ *   - E floor after transport and after the coupling; |F| <= E clip after
+ *     the coupling; gas bookkeeping uses the final E and F.
+ * Parity status: every step above is pinned by the oracle tests (closed
+ * forms, invariants, brute force and printed values of the paper); the whole
+ * step has no printed reference values, so end-to-end parity of full configs
+ * rests on those pins.
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+enum { ORC_CART = 0, ORC_CYL = 1, ORC_SPH = 2 };
+enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1 };
+enum { ORC_OPAC_CONST = 0, ORC_OPAC_POWERLAW = 1, ORC_OPAC_TABLE = 2 };
+enum { ORC_ONCE = 0, ORC_NEWTON = 1 };
+
+/* Problem description.  Face coordinates xf[d] hold n[d]+1 values; for an
+ * inactive direction n[d] = 1 and xf[d] gives its extent. */
+typedef struct {
+  int ndim;
+  int n[3];
+  int geom;
+  int bc_lo[3], bc_hi[3];
+  const double *xf[3];
+  /* physics, code units */
+  double chat, c, a_rad, gamma_gas, mu, cfl, e_floor;
+  /* opacity */
+  int opac_kind;
+  double kappa_p, kappa_r, sigma;             /* CONST, per unit mass */
+  double k0, a_rho, b_T, kmin, kmax;          /* POWERLAW */
+  double sigma_ratio;                         /* POWERLAW and TABLE */
+  int nrho, nT;
+  double lrho0, lrho1, lT0, lT1;
+  const double *ltable;                       /* log10 kappa, [iT][irho] */
+  /* implicit step */
+  int implicit_mode;
+  double newton_rtol;
+  int newton_maxit;
+  int nthreads;
+} orc_problem;
+
+/* State: SoA arrays of N = n0 n1 n2 cells, x fastest.  Three flux and three
+ * momentum components are always carried. */
+typedef struct {
+  double *E, *F0, *F1, *F2, *rho, *e, *m0, *m1, *m2;
+} orc_state;
+
+/* Counters, summed over cells and steps. */
+enum {
+  ORC_ST_FIX = 0,      /* face states where the f-fix recomputed F */
+  ORC_ST_EFLOOR = 1,   /* E floor applications */
+  ORC_ST_FCLIP = 2,    /* |F| <= E clips after the coupling */
+  ORC_ST_ITERS = 3,    /* coupling iterations (sum) */
+  ORC_ST_ITMAX = 4,    /* coupling iterations (max) */
+  ORC_ST_FALLBACK = 5, /* Newton restarts from T^n */
+  ORC_ST_NOCONV = 6,   /* cells that did not converge */
+  ORC_NSTATS = 8
+};
+
+/* ------------------------------------------------------------------------ */
+/* Closure and signal speeds (Sect. 2.1, Sect. 2.6)                          */
+/* ------------------------------------------------------------------------ */
+
+/* Levermore Eddington factor xi(f), Sect. 2.1. */
+double orc_xi(double f) {
+  return (3.0 + 4.0 * f * f) / (5.0 + 2.0 * sqrt(4.0 - 3.0 * f * f));
+}
+
+static double norm3(const double F[3]) {
+  return sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+}
+
+/* Eddington tensor D (row-major 3x3) and reduced flux f of a state (E, F),
+ * Sect. 2.1: D = (1-xi)/2 delta + (3 xi - 1)/2 n n, n = F/|F|, f = |F|/E
+ * capped at 1. */
+void orc_closure(double E, const double F[3], double D[9], double *f_out) {
+  double nF = norm3(F);
+  double f = nF / E;
+  if (f > 1.0) f = 1.0;
+  double xi = orc_xi(f);
+  double nvec[3] = {0.0, 0.0, 0.0};
+  if (nF > 0.0) {
+    nvec[0] = F[0] / nF;
+    nvec[1] = F[1] / nF;
+    nvec[2] = F[2] / nF;
+  }
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j)
+      D[3 * i + j] = (i == j ? 0.5 * (1.0 - xi) : 0.0) + 0.5 * (3.0 * xi - 1.0) * nvec[i] * nvec[j];
+  if (f_out) *f_out = f;
+}
+
+/* Physical flux of (E, F) along direction d: (chat F_d, chat D_{d j} E). */
+void orc_phys_flux(double chat, double E, const double F[3], int d, double out[4]) {
+  double D[9];
+  orc_closure(E, F, D, NULL);
+  out[0] = chat * F[d];
+  for (int j = 0; j < 3; ++j) out[1 + j] = chat * D[3 * d + j] * E;
+}
+
+/* Eigenvalues lambda_{1,3} (units of chat) along direction d, Sect. 2.6:
+ * lambda = (f cos(theta) +/- zeta) / sqrt(4 - 3 f^2), theta = angle between F
+ * and the direction.  zeta^2 is clamped at zero against rounding. */
+void orc_lambda(double E, const double F[3], int d, double *lm, double *lp) {
+  double nF = norm3(F);
+  double f = nF / E;
+  if (f > 1.0) f = 1.0;
+  double cth = (nF > 0.0) ? F[d] / nF : 0.0;
+  double s = sqrt(4.0 - 3.0 * f * f);
+  double z2 = (2.0 / 3.0) * (4.0 - 3.0 * f * f - s) + 2.0 * cth * cth * (2.0 - f * f - s);
+  if (z2 < 0.0) z2 = 0.0;
+  double z = sqrt(z2);
+  *lp = (f * cth + z) / s;
+  *lm = (f * cth - z) / s;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Reconstruction (Sect. 2.5)                                                */
+/* ------------------------------------------------------------------------ */
+
+/* van Leer limited slope from left and right one-sided slopes. */
+double orc_vanleer(double dl, double dr) {
+  if (dl * dr > 0.0) return 2.0 * dl * dr / (dl + dr);
+  return 0.0;
+}
+
+/* f-preserving face fix, Eq. (f_reconstruct).  (Ef, Ff) is the reconstructed
+ * face state, (Ec, Fc) the centre of the cell it was reconstructed from.
+ * Returns 1 when F was recomputed. */
+int orc_fix_face(double Ef, double Ff[3], double Ec, const double Fc[3]) {
+  double rf = norm3(Ff) / Ef;
+  double rc = norm3(Fc) / Ec;
+  if (rf <= 1.0 && rf > rc) return 0;
+  double scale = Ef / Ec;
+  Ff[0] = Fc[0] * scale;
+  Ff[1] = Fc[1] * scale;
+  Ff[2] = Fc[2] * scale;
+  return 1;
+}
+
+/* HLL flux from left/right states and their physical fluxes with signal
+ * speeds sl <= sr. */
+void orc_hll(double sl, double sr, const double uL[4], const double uR[4], const double fL[4],
+             const double fR[4], double out[4]) {
+  if (sl >= 0.0) {
+    for (int q = 0; q < 4; ++q) out[q] = fL[q];
+  } else if (sr <= 0.0) {
+    for (int q = 0; q < 4; ++q) out[q] = fR[q];
+  } else {
+    for (int q = 0; q < 4; ++q)
+      out[q] = (sr * fL[q] - sl * fR[q] + sl * sr * (uR[q] - uL[q])) / (sr - sl);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Opacities                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Absorption (Planck, Rosseland) and scattering opacities per unit mass at
+ * (rho, T): constant, a clipped power law (the Kramers-like form of
+ * Sect. 3.3 is k0 rho T^-3.5), or a table bilinear in log space. */
+void orc_opacity(const orc_problem *p, double rho, double T, double *kp, double *kr,
+                 double *sg) {
+  if (p->opac_kind == ORC_OPAC_CONST) {
+    *kp = p->kappa_p;
+    *kr = p->kappa_r;
+    *sg = p->sigma;
+    return;
+  }
+  double k;
+  if (p->opac_kind == ORC_OPAC_POWERLAW) {
+    k = p->k0 * pow(rho, p->a_rho) * pow(T, p->b_T);
+    if (k < p->kmin) k = p->kmin;
+    if (k > p->kmax) k = p->kmax;
+  } else {
+    /* bilinear interpolation of log10 kappa in (log10 rho, log10 T), clamped
+     * at the table edges */
+    double xr = (log10(rho) - p->lrho0) / (p->lrho1 - p->lrho0) * (p->nrho - 1);
+    double xt = (log10(T) - p->lT0) / (p->lT1 - p->lT0) * (p->nT - 1);
+    if (xr < 0.0) xr = 0.0;
+    if (xr > p->nrho - 1) xr = p->nrho - 1;
+    if (xt < 0.0) xt = 0.0;
+    if (xt > p->nT - 1) xt = p->nT - 1;
+    int ir = (int)floor(xr), it = (int)floor(xt);
+    if (ir > p->nrho - 2) ir = p->nrho - 2;
+    if (it > p->nT - 2) it = p->nT - 2;
+    double wr = xr - ir, wt = xt - it;
+    const double *t = p->ltable;
+    double l00 = t[it * p->nrho + ir], l10 = t[it * p->nrho + ir + 1];
+    double l01 = t[(it + 1) * p->nrho + ir], l11 = t[(it + 1) * p->nrho + ir + 1];
+    double lk = (1.0 - wr) * (1.0 - wt) * l00 + wr * (1.0 - wt) * l10 + (1.0 - wr) * wt * l01 +
+                wr * wt * l11;
+    k = pow(10.0, lk);
+  }
+  *kp = k;
+  *kr = k;
+  *sg = p->sigma_ratio * k;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Grid geometry                                                             */
+/* ------------------------------------------------------------------------ */
+
+static int map_index(const orc_problem *p, int d, int i) {
+  int n = p->n[d];
+  if (i < 0) return (p->bc_lo[d] == ORC_BC_PERIODIC) ? ((i % n) + n) % n : 0;
+  if (i >= n) return (p->bc_hi[d] == ORC_BC_PERIODIC) ? i % n : n - 1;
+  return i;
+}
+
+/* Centre coordinate of cell i along d, for i in [-2, n+1].  Ghost centres
+ * mirror the boundary cells (outflow) or are shifted by the period. */
+static double centre(const orc_problem *p, int d, int i) {
+  int n = p->n[d];
+  const double *x = p->xf[d];
+  if (i >= 0 && i < n) return 0.5 * (x[i] + x[i + 1]);
+  double L = x[n] - x[0];
+  if (i < 0) {
+    if (p->bc_lo[d] == ORC_BC_PERIODIC) return centre(p, d, i + n) - L;
+    return 2.0 * x[0] - centre(p, d, -1 - i);
+  }
+  if (p->bc_hi[d] == ORC_BC_PERIODIC) return centre(p, d, i - n) + L;
+  return 2.0 * x[n] - centre(p, d, 2 * n - 1 - i);
+}
+
+static size_t lin(const orc_problem *p, int i, int j, int k) {
+  return (size_t)i + (size_t)p->n[0] * ((size_t)j + (size_t)p->n[1] * (size_t)k);
+}
+
+/* Physical widths h_d of cell (i,j,k) (used by tau and the CFL condition). */
+static void widths(const orc_problem *p, int i, int j, int k, double h[3]) {
+  const double *x0 = p->xf[0], *x1 = p->xf[1], *x2 = p->xf[2];
+  double d0 = x0[i + 1] - x0[i], d1 = x1[j + 1] - x1[j], d2 = x2[k + 1] - x2[k];
+  if (p->geom == ORC_CART) {
+    h[0] = d0; h[1] = d1; h[2] = d2;
+  } else if (p->geom == ORC_CYL) {
+    double Rc = 0.5 * (x0[i] + x0[i + 1]);
+    h[0] = d0; h[1] = Rc * d1; h[2] = d2;
+  } else {
+    double rc = 0.5 * (x0[i] + x0[i + 1]);
+    double thc = 0.5 * (x1[j] + x1[j + 1]);
+    h[0] = d0; h[1] = rc * d1; h[2] = rc * sin(thc) * d2;
+  }
+}
+
+static double max_active_width(const orc_problem *p, int i, int j, int k) {
+  double h[3];
+  widths(p, i, j, k, h);
+  double m = h[0];
+  for (int d = 1; d < p->ndim; ++d)
+    if (h[d] > m) m = h[d];
+  return m;
+}
+
+/* Time step from the CFL condition (Sect. 2.4 item 10): cfl over the largest
+ * sum over active directions of chat / h_d. */
+double orc_dt(const orc_problem *p) {
+  double worst = 0.0;
+  for (int k = 0; k < p->n[2]; ++k)
+    for (int j = 0; j < p->n[1]; ++j)
+      for (int i = 0; i < p->n[0]; ++i) {
+        double h[3];
+        widths(p, i, j, k, h);
+        double s = 0.0;
+        for (int d = 0; d < p->ndim; ++d) s += p->chat / h[d];
+        if (s > worst) worst = s;
+      }
+  return p->cfl / worst;
+}
+
+/* Cell volume and face areas (lower/upper face along each direction). */
+static void vol_area(const orc_problem *p, int i, int j, int k, double *V, double Alo[3],
+                     double Ahi[3]) {
+  const double *x0 = p->xf[0], *x1 = p->xf[1], *x2 = p->xf[2];
+  double a0 = x0[i], b0 = x0[i + 1], a1 = x1[j], b1 = x1[j + 1], a2 = x2[k], b2 = x2[k + 1];
+  if (p->geom == ORC_CART) {
+    *V = (b0 - a0) * (b1 - a1) * (b2 - a2);
+    Alo[0] = Ahi[0] = (b1 - a1) * (b2 - a2);
+    Alo[1] = Ahi[1] = (b0 - a0) * (b2 - a2);
+    Alo[2] = Ahi[2] = (b0 - a0) * (b1 - a1);
+  } else if (p->geom == ORC_CYL) { /* (R, phi, z) */
+    *V = 0.5 * (b0 * b0 - a0 * a0) * (b1 - a1) * (b2 - a2);
+    Alo[0] = a0 * (b1 - a1) * (b2 - a2);
+    Ahi[0] = b0 * (b1 - a1) * (b2 - a2);
+    Alo[1] = Ahi[1] = (b0 - a0) * (b2 - a2);
+    Alo[2] = Ahi[2] = 0.5 * (b0 * b0 - a0 * a0) * (b1 - a1);
+  } else { /* (r, theta, phi) */
+    double dcos = cos(a1) - cos(b1);
+    *V = (b0 * b0 * b0 - a0 * a0 * a0) / 3.0 * dcos * (b2 - a2);
+    Alo[0] = a0 * a0 * dcos * (b2 - a2);
+    Ahi[0] = b0 * b0 * dcos * (b2 - a2);
+    Alo[1] = 0.5 * (b0 * b0 - a0 * a0) * sin(a1) * (b2 - a2);
+    Ahi[1] = 0.5 * (b0 * b0 - a0 * a0) * sin(b1) * (b2 - a2);
+    Alo[2] = Ahi[2] = 0.5 * (b0 * b0 - a0 * a0) * (b1 - a1);
+  }
+}
+
+/* ------------------------------------------------------------------------ */
+/* One face                                                                  */
+/* ------------------------------------------------------------------------ */
+
+static void load_u(const orc_state *s, size_t c, double *E, double F[3]) {
+  *E = s->E[c];
+  F[0] = s->F0[c];
+  F[1] = s->F1[c];
+  F[2] = s->F2[c];
+}
+
+static double temperature(const orc_problem *p, double rho, double e) {
+  double Cv = rho / (p->mu * (p->gamma_gas - 1.0));
+  return e / Cv;
+}
+
+/* rho * chi * dx of a cell, with chi = kappa_R + sigma at (rho, T^n). */
+static double tau_cell(const orc_problem *p, const orc_state *s, int i, int j, int k) {
+  size_t c = lin(p, i, j, k);
+  double rho = s->rho[c];
+  double T = temperature(p, rho, s->e[c]);
+  double kp, kr, sg;
+  orc_opacity(p, rho, T, &kp, &kr, &sg);
+  return rho * (kr + sg) * max_active_width(p, i, j, k);
+}
+
+/* Right face state (side = +1) or left face state (side = -1) of cell ic
+ * along d, the other two indices of the cell being those of idx. */
+static void face_state(const orc_problem *p, const orc_state *s, const int idx[3], int d, int ic,
+                       int side, double *Ef, double Ff[3], double *Ec, double Fc[3]) {
+  int a[3] = {idx[0], idx[1], idx[2]};
+  double u[3][4];
+  for (int q = -1; q <= 1; ++q) {
+    a[d] = map_index(p, d, ic + q);
+    double E, F[3];
+    load_u(s, lin(p, a[0], a[1], a[2]), &E, F);
+    u[q + 1][0] = E;
+    u[q + 1][1] = F[0];
+    u[q + 1][2] = F[1];
+    u[q + 1][3] = F[2];
+  }
+  double xm = centre(p, d, ic - 1), x0 = centre(p, d, ic), xp = centre(p, d, ic + 1);
+  /* face coordinate: the ghost cells -1 and n are only asked for the face
+   * they share with the domain, so the index stays in [0, n] */
+  double xface = (side > 0) ? p->xf[d][ic + 1] : p->xf[d][ic];
+  double uf[4];
+  for (int q = 0; q < 4; ++q) {
+    double dl = (u[1][q] - u[0][q]) / (x0 - xm);
+    double dr = (u[2][q] - u[1][q]) / (xp - x0);
+    uf[q] = u[1][q] + orc_vanleer(dl, dr) * (xface - x0);
+  }
+  *Ef = uf[0];
+  Ff[0] = uf[1];
+  Ff[1] = uf[2];
+  Ff[2] = uf[3];
+  *Ec = u[1][0];
+  Fc[0] = u[1][1];
+  Fc[1] = u[1][2];
+  Fc[2] = u[1][3];
+}
+
+/* HLL flux through the lower face (between cells i_d - 1 and i_d) of the
+ * cell idx along active direction d.  Returns the number of f-fix events. */
+static int face_flux(const orc_problem *p, const orc_state *s, const int idx[3], int d,
+                     double out[4]) {
+  int i = idx[d];
+  double EL, FL[3], EcL, FcL[3], ER, FR[3], EcR, FcR[3];
+  face_state(p, s, idx, d, i - 1, +1, &EL, FL, &EcL, FcL);
+  face_state(p, s, idx, d, i, -1, &ER, FR, &EcR, FcR);
+  int nfix = orc_fix_face(EL, FL, EcL, FcL) + orc_fix_face(ER, FR, EcR, FcR);
+
+  double fL[4], fR[4];
+  orc_phys_flux(p->chat, EL, FL, d, fL);
+  orc_phys_flux(p->chat, ER, FR, d, fR);
+  double lmL, lpL, lmR, lpR;
+  orc_lambda(EL, FL, d, &lmL, &lpL);
+  orc_lambda(ER, FR, d, &lmR, &lpR);
+  double sl = p->chat * (lmL < lmR ? lmL : lmR);
+  double sr = p->chat * (lpL > lpR ? lpL : lpR);
+
+  /* optically thick correction (Sect. 2.6), tau = mean of the two cells */
+  int a[3] = {idx[0], idx[1], idx[2]};
+  a[d] = map_index(p, d, i - 1);
+  double tL = tau_cell(p, s, a[0], a[1], a[2]);
+  a[d] = map_index(p, d, i);
+  double tR = tau_cell(p, s, a[0], a[1], a[2]);
+  double tau = 0.5 * (tL + tR);
+  if (tau > 0.0) {
+    double bound = 4.0 * p->chat / (3.0 * tau);
+    if (sl < -bound) sl = -bound;
+    if (sr > bound) sr = bound;
+  }
+  double uL[4] = {EL, FL[0], FL[1], FL[2]}, uR[4] = {ER, FR[0], FR[1], FR[2]};
+  orc_hll(sl, sr, uL, uR, fL, fR, out);
+  return nfix;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Implicit coupling (Sect. 2.8) and gas bookkeeping (Sect. 2.7)             */
+/* ------------------------------------------------------------------------ */
+
+/* Solves the 2x2 system of Eq. (implicit_matrix) with T^4 linearised about
+ * Tk.  Written out by Cramer's rule; the determinant
+ *   (1+g_r)(C_v + 4 g a Tk^3) - (4 g_r a Tk^3) g
+ * simplifies exactly to (1+g_r) C_v + 4 g a Tk^3, and the T numerator to
+ * (1+g_r) C_v T^n + 3 g a Tk^4 + g E*, which are used as such.  Tn enters only
+ * through C_v T^n on the right-hand side. */
+void orc_solve2x2(double Estar, double Tn, double Tk, double Cv, double g, double gr, double a,
+                  double *Enew, double *Tnew) {
+  double aT3 = a * Tk * Tk * Tk;
+  double aT4 = aT3 * Tk;
+  double det = (1.0 + gr) * Cv + 4.0 * g * aT3;
+  double T = ((1.0 + gr) * Cv * Tn + 3.0 * g * aT4 + g * Estar) / det;
+  double E = (Estar + gr * aT3 * (4.0 * T - 3.0 * Tk)) / (1.0 + gr);
+  *Enew = E;
+  *Tnew = T;
+}
+
+/* The coupling step of one cell.  In ORC_ONCE mode this is the paper's
+ * single solve about T^n; in ORC_NEWTON mode the same solve is repeated about
+ * the latest temperature until |T_{k+1} - T_k| <= rtol T_{k+1} (Newton's
+ * method on C_v (T - T^n) + g/(1+g_r) (a T^4 - E*) = 0).  T0 is the starting
+ * point of the iteration (T^n when no other guess is given). */
+static void couple(const orc_problem *p, double dt, double rho, double Tn, double T0, double kp,
+                   double Estar, double *Enew, double *Tnew, int64_t st[ORC_NSTATS]) {
+  double Cv = rho / (p->mu * (p->gamma_gas - 1.0));
+  double g = dt * p->c * kp * rho;
+  double gr = dt * p->chat * kp * rho;
+  if (p->implicit_mode == ORC_ONCE) {
+    orc_solve2x2(Estar, Tn, Tn, Cv, g, gr, p->a_rad, Enew, Tnew);
+    st[ORC_ST_ITERS] += 1;
+    if (st[ORC_ST_ITMAX] < 1) st[ORC_ST_ITMAX] = 1;
+    return;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    double Tk = (attempt == 0) ? T0 : Tn;
+    double E = Estar, T = Tk;
+    int it, ok = 0;
+    for (it = 1; it <= p->newton_maxit; ++it) {
+      orc_solve2x2(Estar, Tn, Tk, Cv, g, gr, p->a_rad, &E, &T);
+      if (!(T > 0.0)) break;
+      if (fabs(T - Tk) <= p->newton_rtol * T) {
+        ok = 1;
+        break;
+      }
+      Tk = T;
+    }
+    int used = ok ? it : (it > p->newton_maxit ? p->newton_maxit : it);
+    st[ORC_ST_ITERS] += used;
+    if (st[ORC_ST_ITMAX] < used) st[ORC_ST_ITMAX] = used;
+    if (ok) {
+      *Enew = E;
+      *Tnew = T;
+      return;
+    }
+    if (attempt == 0) st[ORC_ST_FALLBACK] += 1;
+    else {
+      st[ORC_ST_NOCONV] += 1;
+      *Enew = E;
+      *Tnew = T;
+    }
+  }
+}
+
+/* One full step of one cell, reading the old state `s` and writing the new
+ * values into out[9] = (E, F0, F1, F2, e, m0, m1, m2, T).  T0 is the start of
+ * the Newton iteration (<= 0: T^n). */
+static void cell_step(const orc_problem *p, const orc_state *s, double dt, int i, int j, int k,
+                      double T0, double out[9], int64_t st[ORC_NSTATS]) {
+  int idx[3] = {i, j, k};
+  size_t c = lin(p, i, j, k);
+  double E0, F0v[3];
+  load_u(s, c, &E0, F0v);
+
+  /* items 3-7: face fluxes and their divergence */
+  double V, Alo[3], Ahi[3];
+  vol_area(p, i, j, k, &V, Alo, Ahi);
+  const double *x0 = p->xf[0], *x1 = p->xf[1];
+  double dE = 0.0, dF[3] = {0.0, 0.0, 0.0};
+  for (int d = 0; d < 3; ++d) {
+    double flo[4], fhi[4];
+    if (d < p->ndim) {
+      st[ORC_ST_FIX] += face_flux(p, s, idx, d, flo);
+      int up[3] = {i, j, k};
+      up[d] += 1; /* upper face of this cell = lower face of index i_d + 1 */
+      st[ORC_ST_FIX] += face_flux(p, s, up, d, fhi);
+    } else {
+      /* inactive direction: one cell whose faces carry its own flux */
+      orc_phys_flux(p->chat, E0, F0v, d, flo);
+      orc_phys_flux(p->chat, E0, F0v, d, fhi);
+    }
+    /* weights of the angular-momentum-conserving phi component */
+    double wlo[3] = {1, 1, 1}, whi[3] = {1, 1, 1}, wc[3] = {1, 1, 1};
+    if (p->geom == ORC_CYL && d == 0) {
+      wlo[1] = x0[i];
+      whi[1] = x0[i + 1];
+      wc[1] = 0.5 * (x0[i] + x0[i + 1]);
+    }
+    if (p->geom == ORC_SPH && d == 0) {
+      double a = x0[i], b = x0[i + 1];
+      wlo[2] = a;
+      whi[2] = b;
+      wc[2] = 2.0 * (b * b * b - a * a * a) / (3.0 * (b * b - a * a));
+    }
+    if (p->geom == ORC_SPH && d == 1) {
+      wlo[2] = sin(x1[j]);
+      whi[2] = sin(x1[j + 1]);
+      wc[2] = sin(0.5 * (x1[j] + x1[j + 1]));
+    }
+    dE -= (Ahi[d] * fhi[0] - Alo[d] * flo[0]) / V;
+    for (int q = 0; q < 3; ++q)
+      dF[q] -= (whi[q] * Ahi[d] * fhi[1 + q] - wlo[q] * Alo[d] * flo[1 + q]) / (wc[q] * V);
+  }
+  /* geometric sources from the cell-centred pressure tensor of U^n */
+  if (p->geom != ORC_CART) {
+    double D[9];
+    orc_closure(E0, F0v, D, NULL);
+    double P[9];
+    for (int q = 0; q < 9; ++q) P[q] = D[q] * E0;
+    if (p->geom == ORC_CYL) {
+      double Rc = 0.5 * (x0[i] + x0[i + 1]);
+      dF[0] += p->chat * P[4] / Rc; /* P_phiphi / R */
+    } else {
+      double a = x0[i], b = x0[i + 1];
+      double rt = 2.0 * (b * b * b - a * a * a) / (3.0 * (b * b - a * a));
+      double cott = (sin(x1[j + 1]) - sin(x1[j])) / (cos(x1[j]) - cos(x1[j + 1]));
+      dF[0] += p->chat * (P[4] + P[8]) / rt;          /* (P_thth + P_phph) / r */
+      dF[1] += p->chat * (-P[1] + cott * P[8]) / rt;  /* -P_rth / r + cot P_phph / r */
+    }
+  }
+  double Es = E0 + dt * dE;
+  double Fs[3] = {F0v[0] + dt * dF[0], F0v[1] + dt * dF[1], F0v[2] + dt * dF[2]};
+  if (Es < p->e_floor) {
+    Es = p->e_floor;
+    st[ORC_ST_EFLOOR] += 1;
+  }
+
+  /* item 8: local sources */
+  double rho = s->rho[c];
+  double e0 = s->e[c];
+  double m0[3] = {s->m0[c], s->m1[c], s->m2[c]};
+  double Tn = temperature(p, rho, e0);
+  double kp, kr, sg;
+  orc_opacity(p, rho, Tn, &kp, &kr, &sg);
+  double En, Tnew;
+  couple(p, dt, rho, Tn, T0 > 0.0 ? T0 : Tn, kp, Es, &En, &Tnew, st);
+  if (En < p->e_floor) {
+    En = p->e_floor;
+    st[ORC_ST_EFLOOR] += 1;
+  }
+  /* Eq. (source_discrete2): F^{n+1} (1 + dt chat chi rho) = F* */
+  double sc = 1.0 + dt * p->chat * (kr + sg) * rho;
+  double Fn[3] = {Fs[0] / sc, Fs[1] / sc, Fs[2] / sc};
+  double nF = norm3(Fn);
+  if (nF > En) {
+    double r = En / nF;
+    Fn[0] *= r;
+    Fn[1] *= r;
+    Fn[2] *= r;
+    st[ORC_ST_FCLIP] += 1;
+  }
+  /* Sect. 2.7: E_gas + (c/chat) E_r and m + F/chat are conserved by the
+   * coupling; the internal energy absorbs the kinetic-energy change. */
+  double ke0 = (m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2]) / (2.0 * rho);
+  double Egas = e0 + ke0 - (p->c / p->chat) * (En - Es);
+  double mn[3];
+  for (int q = 0; q < 3; ++q) mn[q] = m0[q] - (Fn[q] - Fs[q]) / p->chat;
+  double ke1 = (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / (2.0 * rho);
+  out[0] = En;
+  out[1] = Fn[0];
+  out[2] = Fn[1];
+  out[3] = Fn[2];
+  out[4] = Egas - ke1;
+  out[5] = mn[0];
+  out[6] = mn[1];
+  out[7] = mn[2];
+  out[8] = Tnew;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Public entry points                                                       */
+/* ------------------------------------------------------------------------ */
+
+static void set_threads(const orc_problem *p) {
+#ifdef _OPENMP
+  if (p->nthreads > 0) omp_set_num_threads(p->nthreads);
+#else
+  (void)p;
+#endif
+}
+
+int orc_max_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
+
+/* Advances `s` by nsteps steps of size dt, using `w` (same shape) as the
+ * second buffer; on return the result is in `s`.  stats[ORC_NSTATS] is
+ * accumulated. */
+int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int nsteps,
+             int64_t *stats) {
+  set_threads(p);
+  size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  for (int step = 0; step < nsteps; ++step) {
+    int64_t tot[ORC_NSTATS] = {0};
+#pragma omp parallel
+    {
+      int64_t loc[ORC_NSTATS] = {0};
+#pragma omp for schedule(static)
+      for (long long cc = 0; cc < (long long)N; ++cc) {
+        int i = (int)(cc % p->n[0]);
+        int j = (int)((cc / p->n[0]) % p->n[1]);
+        int k = (int)(cc / ((long long)p->n[0] * p->n[1]));
+        double o[9];
+        cell_step(p, s, dt, i, j, k, -1.0, o, loc);
+        w->E[cc] = o[0];
+        w->F0[cc] = o[1];
+        w->F1[cc] = o[2];
+        w->F2[cc] = o[3];
+        w->e[cc] = o[4];
+        w->m0[cc] = o[5];
+        w->m1[cc] = o[6];
+        w->m2[cc] = o[7];
+      }
+#pragma omp critical
+      {
+        for (int q = 0; q < ORC_NSTATS; ++q) {
+          if (q == ORC_ST_ITMAX) {
+            if (loc[q] > tot[q]) tot[q] = loc[q];
+          } else {
+            tot[q] += loc[q];
+          }
+        }
+      }
+    }
+    memcpy(s->E, w->E, N * sizeof(double));
+    memcpy(s->F0, w->F0, N * sizeof(double));
+    memcpy(s->F1, w->F1, N * sizeof(double));
+    memcpy(s->F2, w->F2, N * sizeof(double));
+    memcpy(s->e, w->e, N * sizeof(double));
+    memcpy(s->m0, w->m0, N * sizeof(double));
+    memcpy(s->m1, w->m1, N * sizeof(double));
+    memcpy(s->m2, w->m2, N * sizeof(double));
+    if (stats) {
+      for (int q = 0; q < ORC_NSTATS; ++q) {
+        if (q == ORC_ST_ITMAX) {
+          if (tot[q] > stats[q]) stats[q] = tot[q];
+        } else {
+          stats[q] += tot[q];
+        }
+      }
+    }
+  }
+  return 0;
+}
+
+/* One step for a list of cells only (each computed from its own stencil of
+ * the old state): out has 9 values per cell, see cell_step. */
+int orc_step_cells(const orc_problem *p, const orc_state *s, double dt, long long ncells,
+                   const long long *cells, double *out) {
+  set_threads(p);
+#pragma omp parallel for schedule(dynamic, 64)
+  for (long long q = 0; q < ncells; ++q) {
+    long long cc = cells[q];
+    int i = (int)(cc % p->n[0]);
+    int j = (int)((cc / p->n[0]) % p->n[1]);
+    int k = (int)(cc / ((long long)p->n[0] * p->n[1]));
+    int64_t st[ORC_NSTATS] = {0};
+    cell_step(p, s, dt, i, j, k, -1.0, out + 9 * q, st);
+  }
+  return 0;
+}
+
+/* The coupling step alone for arrays of cells (tests of Sect. 2.8):
+ * inputs rho, Tn, kp, Estar, T0 (<= 0: T^n); outputs Enew, Tnew, iters. */
+int orc_couple_cells(const orc_problem *p, double dt, long long n, const double *rho,
+                     const double *Tn, const double *kp, const double *Estar, const double *T0,
+                     double *Enew, double *Tnew, int *iters, int *status) {
+  for (long long q = 0; q < n; ++q) {
+    int64_t st[ORC_NSTATS] = {0};
+    double t0 = (T0 && T0[q] > 0.0) ? T0[q] : Tn[q];
+    couple(p, dt, rho[q], Tn[q], t0, kp[q], Estar[q], &Enew[q], &Tnew[q], st);
+    if (iters) iters[q] = (int)st[ORC_ST_ITERS];
+    if (status) status[q] = st[ORC_ST_NOCONV] ? 2 : (st[ORC_ST_FALLBACK] ? 1 : 0);
+  }
+  return 0;
+}
+
+/* HLL face flux between two given states (tests): (EL, FL) and (ER, FR) are
+ * face states already fixed; tau < 0 disables the thick correction. */
+void orc_face_flux_states(double chat, int d, double EL, const double FL[3], double ER,
+                          const double FR[3], double tau, double out[4]) {
+  double fL[4], fR[4], lmL, lpL, lmR, lpR;
+  orc_phys_flux(chat, EL, FL, d, fL);
+  orc_phys_flux(chat, ER, FR, d, fR);
+  orc_lambda(EL, FL, d, &lmL, &lpL);
+  orc_lambda(ER, FR, d, &lmR, &lpR);
+  double sl = chat * (lmL < lmR ? lmL : lmR);
+  double sr = chat * (lpL > lpR ? lpL : lpR);
+  if (tau > 0.0) {
+    double bound = 4.0 * chat / (3.0 * tau);
+    if (sl < -bound) sl = -bound;
+    if (sr > bound) sr = bound;
+  }
+  double uL[4] = {EL, FL[0], FL[1], FL[2]}, uR[4] = {ER, FR[0], FR[1], FR[2]};
+  orc_hll(sl, sr, uL, uR, fL, fR, out);
+}
+
+/* Reconstructed face states at the lower face of cell (i,j,k) along d,
+ * before (raw) and after (fixed) the f-fix: out = (EL, FL0..2, ER, FR0..2)
+ * raw, then the same fixed (16 values).  For the tests of Sect. 2.5. */
+void orc_face_states(const orc_problem *p, const orc_state *s, int i, int j, int k, int d,
+                     double out[16]) {
+  int idx[3] = {i, j, k};
+  double EL, FL[3], EcL, FcL[3], ER, FR[3], EcR, FcR[3];
+  face_state(p, s, idx, d, idx[d] - 1, +1, &EL, FL, &EcL, FcL);
+  face_state(p, s, idx, d, idx[d], -1, &ER, FR, &EcR, FcR);
+  double raw[8] = {EL, FL[0], FL[1], FL[2], ER, FR[0], FR[1], FR[2]};
+  orc_fix_face(EL, FL, EcL, FcL);
+  orc_fix_face(ER, FR, EcR, FcR);
+  double fixed[8] = {EL, FL[0], FL[1], FL[2], ER, FR[0], FR[1], FR[2]};
+  for (int q = 0; q < 8; ++q) {
+    out[q] = raw[q];
+    out[8 + q] = fixed[q];
+  }
+}

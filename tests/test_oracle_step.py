@@ -1,0 +1,306 @@
+"""Whole-step pins of the oracle: invariants, conservation laws, analytic
+special cases and the convergence behaviour printed in the paper.  CPU only."""
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def volumes(p):
+    """Cell volumes from the face coordinates (flat, x fastest)."""
+    a = [p.xfaces[d] for d in range(3)]
+    if p.geometry == "cartesian":
+        f = [np.diff(a[0]), np.diff(a[1]), np.diff(a[2])]
+    elif p.geometry == "cylindrical":
+        f = [0.5 * np.diff(a[0] ** 2), np.diff(a[1]), np.diff(a[2])]
+    else:
+        f = [np.diff(a[0] ** 3) / 3.0, -np.diff(np.cos(a[1])), np.diff(a[2])]
+    z, y, x = np.meshgrid(f[2], f[1], f[0], indexing="ij")
+    return (x * y * z).ravel()
+
+
+# ---------------------------------------------------------------------------
+# uniform states stay uniform (well-balanced metric terms)
+# ---------------------------------------------------------------------------
+
+CASES = [("cartesian", 1, False), ("cartesian", 2, False), ("cartesian", 3, False),
+         ("cylindrical", 1, False), ("cylindrical", 2, False), ("cylindrical", 3, False),
+         ("spherical", 1, False), ("spherical", 2, False), ("spherical", 3, False),
+         ("spherical", 1, True), ("spherical", 3, True)]
+
+
+@pytest.mark.parametrize("geom,ndim,logr", CASES)
+def test_uniform_equilibrium_state_stays_uniform(geom, ndim, logr):
+    p = W.uniform_state(geom, (12, 10, 8), ndim, log_r=logr)
+    o = oracle.Oracle(p)
+    e0 = o.e.copy()
+    o.step(3)
+    assert np.max(np.abs(o.E - 2.0)) / 2.0 < 1e-13
+    assert np.max(np.abs(o.F)) / 2.0 < 1e-13
+    assert np.max(np.abs(o.e - e0) / e0) < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# free streaming and conservation of the transport
+# ---------------------------------------------------------------------------
+
+def test_free_streaming_pulse_moves_at_chat_and_conserves_energy():
+    n = 400
+    xf = W.uniform_faces(n, 0.0, 1.0)
+    p = W.Problem(name="fs", ndim=1, n=(n, 1, 1), geometry="cartesian",
+                  bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3,
+                  xfaces=[xf, W.uniform_faces(1, 0, 1), W.uniform_faces(1, 0, 1)], chat=2.0,
+                  c=2.0, ncomp=1)
+    x = W.cell_centres(xf)
+    p.E = 1e-6 + np.exp(-(x - 0.3) ** 2 / (2 * 0.04 ** 2))
+    p.F = np.zeros((3, n))
+    p.F[0] = p.E  # f = 1 along +x
+    p.rho, p.T, p.v = np.ones(n), np.full(n, 1e-3), np.zeros((3, n))
+    o = oracle.Oracle(p)
+    dt = o.dt()
+    c0 = np.sum(x * (o.E - 1e-6)) / np.sum(o.E - 1e-6)
+    tot0 = o.E.sum()
+    nst = 150
+    o.step(nst)
+    c1 = np.sum(x * (o.E - 1e-6)) / np.sum(o.E - 1e-6)
+    assert (c1 - c0) == pytest.approx(p.chat * dt * nst, abs=1.0 / n)
+    assert abs(o.E.sum() - tot0) / tot0 < 1e-13
+    # f stays 1 and the flux stays along +x
+    assert np.max(np.abs(o.F[0] - o.E) / o.E) < 1e-12
+
+
+def test_transport_conserves_energy_and_momentum_on_a_periodic_box():
+    p = W.random_smooth("cartesian", (14, 12, 10), 3, seed=11, bc="periodic", fmax=0.6,
+                        opacity={"kind": "const", "kappa_p": 0.0, "kappa_r": 0.0, "sigma": 0.0})
+    o = oracle.Oracle(p)
+    V = volumes(p)
+    E0 = np.sum(V * o.E)
+    F0 = (o.F * V).sum(axis=1)
+    o.step(4)
+    assert abs(np.sum(V * o.E) - E0) / E0 < 1e-13
+    np.testing.assert_allclose((o.F * V).sum(axis=1), F0, atol=1e-13 * E0)
+
+
+@pytest.mark.parametrize("ratio", [1.0, 100.0])
+def test_total_energy_and_momentum_conserved_with_coupling(ratio):
+    """Sect. 2.7: E_gas + (c/chat) E_r and rho v + F/chat are conserved; the
+    transport conserves sum E and sum F on a periodic Cartesian box."""
+    p = W.random_smooth("cartesian", (12, 10, 1), 2, seed=12, bc="periodic", fmax=0.3,
+                        chat=2.0, c=2.0 * ratio,
+                        opacity={"kind": "const", "kappa_p": 3.0, "kappa_r": 2.0, "sigma": 1.0})
+    o = oracle.Oracle(p)
+    V = volumes(p)
+
+    def totals():
+        ke = np.sum(o.m * o.m, axis=0) / (2 * o.rho)
+        egas = np.sum(V * (o.e + ke))
+        erad = np.sum(V * o.E)
+        mom = (V * (o.m + o.F / p.chat)).sum(axis=1)
+        return egas, erad, mom
+
+    g0, r0, m0 = totals()
+    o.step(5)
+    g1, r1, m1 = totals()
+    assert o.stats[2] == 0 and o.stats[1] == 0  # no clip or floor (not conservative)
+    tot = g0 + ratio * r0
+    assert abs((g1 + ratio * r1) - tot) / tot < 1e-13
+    np.testing.assert_allclose(m1, m0, atol=1e-13 * np.abs(m0).max() + 1e-15)
+    # the energy-loss identity of Sect. 3.5 in the form fixed by Sect. 2.7:
+    # d(E_gas + E_r) = (1 - c/chat) dE_r = (1 - chat/c) dE_gas
+    dgas, drad = g1 - g0, r1 - r0
+    assert (dgas + drad) == pytest.approx((1 - ratio) * drad, rel=1e-9, abs=1e-12 * tot)
+    if ratio != 1.0:
+        assert (dgas + drad) == pytest.approx((1 - 1 / ratio) * dgas, rel=1e-9)
+
+
+def test_uniform_cells_relax_exactly_like_the_single_cell_coupling():
+    """A uniform non-equilibrium box has no transport: the step reduces to the
+    coupling of Sect. 2.8, cell by cell."""
+    p = W.uniform_state("cartesian", (6, 5, 1), 2, E=3.0, kappa=2.0)
+    p.T = np.full(p.N, 0.7)
+    o = oracle.Oracle(p)
+    dt = o.dt()
+    E1, T1, _, _ = o.couple_cells(dt, o.rho[:1], o.temperature()[:1], np.array([2.0]),
+                                  o.E[:1])
+    o.step(1)
+    np.testing.assert_allclose(o.E, E1[0], rtol=1e-14)
+    np.testing.assert_allclose(o.temperature(), T1[0], rtol=1e-13)
+
+
+# ---------------------------------------------------------------------------
+# curvilinear geometry
+# ---------------------------------------------------------------------------
+
+def test_spherical_pulse_conserves_energy_and_decays_as_inverse_square():
+    """Sect. 3.4: 1D spherical pulse; total energy conserved to rounding and
+    the front amplitude decays as 1/r^2 at late times."""
+    n = 600
+    xf = [W.uniform_faces(n, 0.0, 60.0), W.uniform_faces(1, 0.0, math.pi),
+          W.uniform_faces(1, 0.0, 2 * math.pi)]
+    p = W.Problem(name="sphpulse", ndim=1, n=(n, 1, 1), geometry="spherical",
+                  bc_lo=("outflow",) * 3, bc_hi=("outflow",) * 3, xfaces=xf, chat=1.0, c=1.0,
+                  ncomp=1)
+    r = W.cell_centres(xf[0])
+    bg = 1e-8
+    p.E = bg + np.exp(-(r / 2.0) ** 2)
+    p.F = np.zeros((3, n))
+    p.rho, p.v = np.ones(n), np.zeros((3, n))
+    p.T = p.E ** 0.25
+    p.opacity = {"kind": "const", "kappa_p": 0.0, "kappa_r": 0.0, "sigma": 1e-4}
+    o = oracle.Oracle(p)
+    V = volumes(p)
+    tot0 = np.sum(V * o.E)
+    dt = o.dt()
+    peaks = []
+    t = 0.0
+    for t_target in (25.0, 40.0):
+        nst = int(round((t_target - t) / dt))
+        o.step(nst)
+        t += nst * dt
+        i = int(np.argmax(o.E))
+        peaks.append((r[i], o.E[i] - bg))
+    assert abs(np.sum(V * o.E) - tot0) / tot0 < 1e-12
+    (r1, e1), (r2, e2) = peaks
+    assert r2 > r1 + 10
+    assert (r2 ** 2 * e2) / (r1 ** 2 * e1) == pytest.approx(1.0, abs=0.15)
+
+
+@pytest.mark.parametrize("geom", ["cylindrical", "spherical"])
+def test_angular_momentum_of_the_phi_flux_is_conserved(geom):
+    """The phi component uses the angular-momentum form: sum of
+    (R_c | r~ sin(theta_c)) V F_phi is conserved by the transport while the
+    radiation stays away from the open boundaries."""
+    if geom == "cylindrical":
+        n, ext = (32, 20, 1), [(1.0, 3.0), (0.0, 2 * math.pi), None]
+        ndim, bc = 2, ("outflow", "periodic", "outflow")
+    else:
+        n, ext = (32, 28, 12), [(1.0, 3.0), (0.6, math.pi - 0.6), (0.0, 2 * math.pi)]
+        ndim, bc = 3, ("outflow", "outflow", "periodic")
+    p = W.random_smooth(geom, n, ndim, seed=13, extents=ext, fmax=0.5,
+                        opacity={"kind": "const", "kappa_p": 0.0, "kappa_r": 0.0, "sigma": 0.0})
+    p.bc_lo = p.bc_hi = bc
+    # compact support: background plus a blob in the middle of the r (and
+    # theta) range, so that nothing reaches the open boundaries in a few steps
+    x, y, z = W.mesh(p)
+    r0 = 0.5 * (ext[0][0] + ext[0][1])
+    blob = np.exp(-((x - r0) / 0.15) ** 2)
+    if geom == "spherical":
+        blob *= np.exp(-((y - 0.5 * math.pi) / 0.15) ** 2)
+    p.E = 1e-12 + blob
+    p.F = p.F / np.maximum(np.linalg.norm(p.F, axis=0), 1e-300) * 0.5 * p.E
+    o = oracle.Oracle(p)
+    V = volumes(p)
+    xf = p.xfaces
+    if geom == "cylindrical":
+        Rc = 0.5 * (xf[0][1:] + xf[0][:-1])
+        lever = np.tile(Rc, n[1] * n[2])
+        comp = 1
+    else:
+        a, b = xf[0][:-1], xf[0][1:]
+        rt = 2 * (b ** 3 - a ** 3) / (3 * (b ** 2 - a ** 2))
+        sc = np.sin(0.5 * (xf[1][1:] + xf[1][:-1]))
+        zz, yy, xx = np.meshgrid(np.ones(n[2]), sc, rt, indexing="ij")
+        lever = (xx * yy).ravel()
+        comp = 2
+    L0 = np.sum(lever * V * o.F[comp])
+    scale = np.sum(lever * V * np.abs(o.F[comp]))
+    o.step(3)
+    assert abs(np.sum(lever * V * o.F[comp]) - L0) / scale < 1e-13
+
+
+# ---------------------------------------------------------------------------
+# diffusion limit
+# ---------------------------------------------------------------------------
+
+def test_optically_thick_gaussian_spreads_at_the_diffusion_rate():
+    """Pure scattering, chi rho dx = 5: the variance of a Gaussian grows as
+    s0^2 + 2 D t with D = chat / (3 chi rho), and F tends to Fick's law
+    F = -dE/dx / (3 chi rho) (Eqs. rad1, rad2 with the sources of Sect. 2.1)."""
+    n, sig = 400, 1000.0
+    xf = W.uniform_faces(n, 0.0, 2.0)
+    p = W.Problem(name="diff", ndim=1, n=(n, 1, 1), geometry="cartesian",
+                  bc_lo=("periodic",) * 3, bc_hi=("periodic",) * 3,
+                  xfaces=[xf, W.uniform_faces(1, 0, 1), W.uniform_faces(1, 0, 1)], chat=1.0,
+                  c=1.0, ncomp=1)
+    x = W.cell_centres(xf)
+    s0 = 0.06
+    bg = 1e-8
+    p.E = bg + np.exp(-(x - 1.0) ** 2 / (2 * s0 ** 2))
+    p.F = np.zeros((3, n))
+    p.rho, p.T, p.v = np.ones(n), np.full(n, 1e-2), np.zeros((3, n))
+    p.opacity = {"kind": "const", "kappa_p": 0.0, "kappa_r": 0.0, "sigma": sig}
+    o = oracle.Oracle(p)
+    dt = o.dt()
+    nst = 3000
+    o.step(nst)
+    t = nst * dt
+    w = o.E - bg
+    mean = np.sum(x * w) / np.sum(w)
+    var = np.sum((x - mean) ** 2 * w) / np.sum(w)
+    D = p.chat / (3 * sig)
+    assert var - s0 ** 2 == pytest.approx(2 * D * t, rel=0.05)
+    core = np.abs(x - 1.0) < 1.5 * math.sqrt(var)
+    dEdx = np.gradient(o.E, x)
+    fick = -dEdx / (3 * sig)
+    err = np.max(np.abs(o.F[0][core] - fick[core])) / np.max(np.abs(fick[core]))
+    assert err < 0.05
+
+
+# ---------------------------------------------------------------------------
+# Riemann problems (Sect. 3.1)
+# ---------------------------------------------------------------------------
+
+def golden_tubes():
+    states, slope = {}, None
+    for line in open(os.path.join(GOLD, "riemann_problems.txt")):
+        line = line.split("#")[0].strip()
+        if not line:
+            continue
+        parts = line.split()
+        if parts[0] == "slope":
+            slope = float(parts[1])
+        else:
+            states[(int(parts[0]), parts[1])] = tuple(float(v) for v in parts[2:])
+    return states, slope
+
+
+def run_tube(which, n, t_end=20.0):
+    p = W.shock_tube(which, n, t_end)
+    states, _ = golden_tubes()
+    x, _, _ = W.mesh(p)
+    for side, mask in (("L", x < 0), ("R", x >= 0)):
+        E, Fx, Fy = states[(which, side)]
+        p.E[mask], p.F[0][mask], p.F[1][mask] = E, Fx, Fy
+    o = oracle.Oracle(p, nthreads=0)
+    dt = o.dt()
+    nst = int(math.ceil(t_end / dt))
+    o.step(nst, dt=t_end / nst)
+    return x, o
+
+
+def test_shock_tube_1_contact_has_constant_velocity_and_pressure_analogs():
+    """Sect. 3.1: the velocity analog beta_x and the pressure analog
+    Pi = (1 - xi) E / 2 are constant across the contact-like discontinuity
+    while E and F_y jump.  beta_x is read as the contact speed lambda_2 of
+    Sect. 2.6, (3 xi - 1) F_x E / (2 |F|^2): the typeset formula lacks the
+    square on |F| (it is not constant across the contact, lambda_2 is)."""
+    x, o = run_tube(1, 2048)
+    E, Fx, Fy = o.E, o.F[0], o.F[1]
+    nF = np.sqrt(Fx ** 2 + Fy ** 2)
+    f = nF / E
+    xi = (3 + 4 * f * f) / (5 + 2 * np.sqrt(4 - 3 * f * f))
+    beta = (3 * xi - 1) * Fx * E / (2 * nF * nF)
+    Pi = (1 - xi) * E / 2
+    # locate the contact: largest jump of F_y away from the outer waves
+    window = (x > -6) & (x < 6)
+    j = np.argmax(np.abs(np.diff(Fy)) * window[:-1])
+    lo, hi = slice(j - 60, j - 20), slice(j + 20, j + 60)
+    assert abs(np.mean(E[lo]) - np.mean(E[hi])) > 0.02  # E does jump
+    assert np.mean(beta[lo]) == pytest.approx(np.mean(beta[hi]), rel=3e-2)
+    assert np.mean(Pi[lo]) == pytest.approx(np.mean(Pi[hi]), rel=5e-3)
