@@ -1,0 +1,210 @@
+/*
+ * rad.h -- C ABI of the B300 (sm_103a) M1 radiation step.
+ *
+ * One call of rad_step advances the gray M1 radiation field by one explicit
+ * transport step followed by the cell-local implicit matter-radiation
+ * coupling, as described in Scepi & Lesur, "A nonrelativistic radiative
+ * transfer module for Idefix":
+ *   - transport: Sect. 2.4 (items 1-7 of the Euler step), Sect. 2.5 (PLM
+ *     reconstruction, f-preserving face fix, Eq. f_reconstruct, HLL), Sect. 2.6
+ *     (signal speeds lambda_{1,3} and the optically thick correction), Eqs.
+ *     (rad1)-(rad2) with the Levermore closure of Sect. 2.1;
+ *   - coupling: Sect. 2.8, Eqs. (source_discrete2) and (implicit_matrix),
+ *     with the gas energy and momentum from the conservation laws of
+ *     Sect. 2.7, Eq. (conservation_energy);
+ *   - reduced speed of light c_hat of Sect. 2.7 and the CFL step of Sect. 2.4
+ *     item 10.
+ * The gas density and velocity are inputs; the step updates the gas internal
+ * energy and momentum.
+ *
+ * Conventions for every function:
+ *   - Fields are structure-of-arrays of N = n[0]*n[1]*n[2] cells, x fastest
+ *     (cell (i,j,k) at i + n0*(j + n1*k)).  Vector fields (F, v, m) are
+ *     `ncomp` consecutive N-arrays in the geometry's orthonormal components:
+ *     (x,y,z), (R,phi,z) or (r,theta,phi).
+ *   - The element type of every field buffer is double for RAD_FP64 and float
+ *     for RAD_FP32_SPLIT (rad_params.precision).
+ *   - Pointers marked "host" are read or written only during the call.
+ *     Pointers marked "device" must be device memory of the context's device;
+ *     the call enqueues work on the context's stream and returns.
+ *   - Functions return RAD_OK or an error code and never abort the process.
+ *     Device-side failures of an enqueued step (no convergence of the
+ *     iteration, non-physical state, bounded waits that ran out) are recorded
+ *     in a status word that rad_sync and rad_read return.
+ */
+#ifndef RAD_H_
+#define RAD_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RAD_ABI_VERSION 1
+
+typedef enum {
+  RAD_OK = 0,
+  RAD_EINVAL = 1,       /* invalid argument (pointer, size, value) */
+  RAD_ENOMEM = 2,       /* workspace missing or too small, host allocation failed */
+  RAD_ECUDA = 3,        /* a CUDA runtime call failed */
+  RAD_ENONPHYS = 4,     /* non-physical input or state (E <= 0, |F| > E, NaN) */
+  RAD_ENOCONV = 5,      /* the coupling iteration did not converge in some cell */
+  RAD_ETIMEOUT = 6,     /* a bounded device wait ran out */
+  RAD_EUNSUPPORTED = 7  /* valid request this build does not implement */
+} rad_status;
+
+typedef enum { RAD_CARTESIAN = 0, RAD_CYLINDRICAL = 1, RAD_SPHERICAL = 2 } rad_geometry;
+typedef enum { RAD_BC_OUTFLOW = 0, RAD_BC_PERIODIC = 1 } rad_bc;
+typedef enum { RAD_OPAC_CONST = 0, RAD_OPAC_POWERLAW = 1, RAD_OPAC_TABLE = 2 } rad_opac_kind;
+typedef enum { RAD_FP64 = 0, RAD_FP32_SPLIT = 1 } rad_precision;
+typedef enum { RAD_LINEARIZED_ONCE = 0, RAD_NEWTON = 1 } rad_implicit;
+
+/* Fields for rad_read. */
+typedef enum {
+  RAD_FIELD_E = 0,    /* radiation energy density E_r, N values */
+  RAD_FIELD_F = 1,    /* radiation flux F_r (with the 1/c of Eq. def_flux), ncomp*N */
+  RAD_FIELD_EINT = 2, /* gas internal energy density e, N */
+  RAD_FIELD_M = 3,    /* gas momentum density rho v, ncomp*N */
+  RAD_FIELD_T = 4,    /* gas temperature e / C_v, N */
+  RAD_FIELD_RHO = 5   /* gas density, N */
+} rad_field;
+
+/* Grid.  Active directions are the first `ndim`; inactive ones have n = 1
+ * and their two face coordinates give the extent (e.g. theta in [0, pi]).
+ * Angles are in radians.  Face coordinates must increase strictly; radii
+ * must be >= 0. */
+typedef struct {
+  int ndim;                /* 1, 2 or 3 */
+  int n[3];                /* cells per direction, >= 1; n[d] = 1 for d >= ndim */
+  const double *xface[3];  /* host, n[d]+1 face coordinates each, copied */
+  int bc_lo[3], bc_hi[3];  /* rad_bc per active direction; periodic needs both */
+} rad_grid;
+
+/* Opacity model (per unit mass); the absorption coefficient is kappa*rho.
+ * CONST:    kappa_P, kappa_R and sigma as given.
+ * POWERLAW: kappa = clip(k0 rho^a_rho T^b_T, kmin, kmax) (Kramers-like,
+ *           Sect. 3.3), kappa_P = kappa_R = kappa, sigma = sigma_ratio kappa.
+ * TABLE:    log10 kappa on a uniform (log10 rho, log10 T) grid, bilinear in
+ *           log space and clamped at the edges; kappa_P = kappa_R = kappa,
+ *           sigma = sigma_ratio kappa.  The table is nT rows of nrho values
+ *           (rho fastest), host memory, copied. */
+typedef struct {
+  int kind;
+  double kappa_p, kappa_r, sigma;
+  double k0, a_rho, b_T, kmin, kmax;
+  double sigma_ratio;
+  int nrho, nT;
+  double lrho0, lrho1, lT0, lT1;
+  const float *table_log10_kappa;
+} rad_opacity;
+
+/* Physical and numerical parameters (code units, k_B / m_u = 1). */
+typedef struct {
+  double chat;          /* reduced speed of light, > 0 (Sect. 2.7) */
+  double c;             /* speed of light, >= chat */
+  double a_rad;         /* radiation constant a_R, > 0 */
+  double gamma_gas;     /* adiabatic index, > 1; C_v = rho / (mu (gamma - 1)) */
+  double mu;            /* mean molecular weight, > 0 */
+  double cfl;           /* Courant number of the fixed CFL step, in (0, 1] */
+  double e_floor;       /* floor of E_r, > 0 */
+  int precision;        /* rad_precision */
+  int implicit_mode;    /* rad_implicit */
+  double newton_rtol;   /* RAD_NEWTON: stop when |T_{k+1}-T_k| <= rtol T_{k+1} */
+  int newton_maxit;     /* RAD_NEWTON: iteration cap, >= 1 */
+  int ncomp;            /* vector components in the caller's F, v and m arrays, 1..3 */
+} rad_params;
+
+/* Counters accumulated by rad_step since the last rad_reset_stats. */
+typedef struct {
+  uint64_t fix;         /* face states whose flux the f-fix recomputed */
+  uint64_t efloor;      /* applications of the E floor */
+  uint64_t fclip;       /* |F| <= E clips after the coupling */
+  uint64_t iters;       /* coupling iterations summed over cells */
+  uint64_t itmax;       /* largest iteration count of one cell */
+  uint64_t fallback;    /* Newton restarts from T^n */
+  uint64_t noconv;      /* cells that did not converge */
+  uint64_t steps;       /* steps taken */
+} rad_stats;
+
+typedef struct rad_ctx rad_ctx;
+
+/* Fills *p with defaults: chat = c = 1, a_rad = 1, gamma = 5/3, mu = 1,
+ * cfl = 0.4, e_floor = 1e-30, RAD_FP64, RAD_LINEARIZED_ONCE, rtol = 1e-12,
+ * maxit = 50, ncomp = 3.  Returns RAD_EINVAL if p is NULL. */
+rad_status rad_default_params(rad_params *p);
+
+/* Validates the description, precomputes the geometry (face areas, volumes,
+ * metric factors, the CFL step of Sect. 2.4 item 10) on the host and
+ * returns a context that owns no device memory yet.  Host arrays are copied.
+ * Errors: RAD_EINVAL for any invalid field, RAD_ENOMEM if host allocation
+ * fails.  *out is set only on success. */
+rad_status rad_create(const rad_grid *grid, int geometry, const rad_opacity *opacity,
+                      const rad_params *params, rad_ctx **out);
+
+/* Device bytes the context needs (double-buffered state with ghost layers,
+ * geometry tables, opacity table, counters, staging for host copies). */
+rad_status rad_workspace_size(const rad_ctx *ctx, size_t *bytes);
+
+/* Binds caller-owned device memory of at least rad_workspace_size bytes,
+ * 256-byte aligned, on the current device; the caller keeps it alive until
+ * rad_destroy.  Errors: RAD_EINVAL (NULL, misaligned), RAD_ENOMEM (too
+ * small), RAD_ECUDA. */
+rad_status rad_bind_workspace(rad_ctx *ctx, void *device_ptr, size_t bytes);
+
+/* Convenience for C callers: allocates the workspace with cudaMalloc (freed
+ * by rad_destroy).  Errors: RAD_ENOMEM, RAD_ECUDA. */
+rad_status rad_alloc_workspace(rad_ctx *ctx);
+
+/* Sets the CUDA stream (a cudaStream_t) on which all work is enqueued;
+ * NULL selects the legacy default stream. */
+rad_status rad_set_stream(rad_ctx *ctx, void *cuda_stream);
+
+/* Sets the gas: rho (N), v (ncomp*N) and T (N), all host (on_device = 0)
+ * or all device (on_device = 1).  Stores rho, m = rho v and e = C_v T.
+ * Errors: RAD_EINVAL (NULL, no workspace), RAD_ECUDA.  With host pointers
+ * the call returns after the copies completed. */
+rad_status rad_set_gas(rad_ctx *ctx, const void *rho, const void *v, const void *T,
+                       int on_device);
+
+/* Sets the radiation field: E (N) and F (ncomp*N), host or device. */
+rad_status rad_set_rad(rad_ctx *ctx, const void *E, const void *F, int on_device);
+
+/* Enqueues nsteps steps of size dt (dt <= 0: the CFL step of rad_dt).
+ * Asynchronous on the context's stream.  Errors: RAD_EINVAL (nsteps < 0, no
+ * state set), RAD_ECUDA (launch failure). */
+rad_status rad_step(rad_ctx *ctx, double dt, int nsteps);
+
+/* Copies a field (rad_field) into dst of `bytes` bytes (host or device).
+ * Synchronises the stream for host destinations and returns the device
+ * status word (RAD_ENOCONV, RAD_ENONPHYS, ...) if a step recorded one.
+ * Errors: RAD_EINVAL (unknown field, bytes too small). */
+rad_status rad_read(rad_ctx *ctx, int field, void *dst, size_t bytes, int on_device);
+
+/* Waits for the stream and returns the device status word (RAD_OK if no
+ * step recorded a failure); the word is cleared by the read. */
+rad_status rad_sync(rad_ctx *ctx);
+
+/* The CFL step dt = cfl / max_cells sum_d (chat / h_d), h_d the physical
+ * cell widths. */
+rad_status rad_dt(const rad_ctx *ctx, double *dt);
+
+/* Reads (synchronising) and resets the counters. */
+rad_status rad_get_stats(rad_ctx *ctx, rad_stats *out);
+rad_status rad_reset_stats(rad_ctx *ctx);
+
+/* Number of kernel launches rad_step enqueues per step (for launch
+ * accounting by callers). */
+int rad_launches_per_step(const rad_ctx *ctx);
+
+/* Releases the context (and the workspace if rad_alloc_workspace made it). */
+void rad_destroy(rad_ctx *ctx);
+
+/* Static description of a status code. */
+const char *rad_strerror(rad_status s);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAD_H_ */

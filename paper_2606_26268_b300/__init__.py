@@ -1,0 +1,286 @@
+"""B300-native M1 radiation step (transport + implicit coupling).
+
+Python binding of the C ABI in include/rad.h (librad.so, hand-written sm_103a
+CUDA).  This module only marshals arguments: every step of the method runs in
+the library's kernels.  PyTorch supplies device memory (the workspace) and the
+stream.  There is no CPU fallback: importing the binding without the built
+library raises.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "librad.so")
+
+RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ENONPHYS, RAD_ENOCONV, RAD_ETIMEOUT, \
+    RAD_EUNSUPPORTED = range(8)
+RAD_CARTESIAN, RAD_CYLINDRICAL, RAD_SPHERICAL = range(3)
+RAD_BC_OUTFLOW, RAD_BC_PERIODIC = range(2)
+RAD_OPAC_CONST, RAD_OPAC_POWERLAW, RAD_OPAC_TABLE = range(3)
+RAD_FP64, RAD_FP32_SPLIT = range(2)
+RAD_LINEARIZED_ONCE, RAD_NEWTON = range(2)
+RAD_FIELD_E, RAD_FIELD_F, RAD_FIELD_EINT, RAD_FIELD_M, RAD_FIELD_T, RAD_FIELD_RHO = range(6)
+
+GEOMETRY = {"cartesian": RAD_CARTESIAN, "cylindrical": RAD_CYLINDRICAL,
+            "spherical": RAD_SPHERICAL}
+BC = {"outflow": RAD_BC_OUTFLOW, "periodic": RAD_BC_PERIODIC}
+OPACITY = {"const": RAD_OPAC_CONST, "powerlaw": RAD_OPAC_POWERLAW, "table": RAD_OPAC_TABLE}
+PRECISION = {"fp64": RAD_FP64, "split": RAD_FP32_SPLIT}
+IMPLICIT = {"once": RAD_LINEARIZED_ONCE, "newton": RAD_NEWTON}
+FIELDS = {"E": RAD_FIELD_E, "F": RAD_FIELD_F, "e": RAD_FIELD_EINT, "m": RAD_FIELD_M,
+          "T": RAD_FIELD_T, "rho": RAD_FIELD_RHO}
+
+
+class rad_grid(C.Structure):
+    _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("xface", C.c_void_p * 3),
+                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3)]
+
+
+class rad_opacity(C.Structure):
+    _fields_ = [("kind", C.c_int), ("kappa_p", C.c_double), ("kappa_r", C.c_double),
+                ("sigma", C.c_double), ("k0", C.c_double), ("a_rho", C.c_double),
+                ("b_T", C.c_double), ("kmin", C.c_double), ("kmax", C.c_double),
+                ("sigma_ratio", C.c_double), ("nrho", C.c_int), ("nT", C.c_int),
+                ("lrho0", C.c_double), ("lrho1", C.c_double), ("lT0", C.c_double),
+                ("lT1", C.c_double), ("table_log10_kappa", C.c_void_p)]
+
+
+class rad_params(C.Structure):
+    _fields_ = [("chat", C.c_double), ("c", C.c_double), ("a_rad", C.c_double),
+                ("gamma_gas", C.c_double), ("mu", C.c_double), ("cfl", C.c_double),
+                ("e_floor", C.c_double), ("precision", C.c_int), ("implicit_mode", C.c_int),
+                ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int)]
+
+
+class rad_stats(C.Structure):
+    _fields_ = [(k, C.c_uint64) for k in ("fix", "efloor", "fclip", "iters", "itmax",
+                                          "fallback", "noconv", "steps")]
+
+
+EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_workspace",
+           "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad", "rad_step",
+           "rad_read", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
+           "rad_launches_per_step", "rad_destroy", "rad_strerror"]
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    """Loads librad.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError("librad.so is missing (%s): build it with "
+                           "`python -m paper_2606_26268_b300.build`" % LIB_PATH)
+    L = C.CDLL(LIB_PATH)
+    P = C.POINTER
+    vp = C.c_void_p
+    L.rad_default_params.argtypes = [P(rad_params)]
+    L.rad_create.argtypes = [P(rad_grid), C.c_int, P(rad_opacity), P(rad_params), P(vp)]
+    L.rad_workspace_size.argtypes = [vp, P(C.c_size_t)]
+    L.rad_bind_workspace.argtypes = [vp, vp, C.c_size_t]
+    L.rad_alloc_workspace.argtypes = [vp]
+    L.rad_set_stream.argtypes = [vp, vp]
+    L.rad_set_gas.argtypes = [vp, vp, vp, vp, C.c_int]
+    L.rad_set_rad.argtypes = [vp, vp, vp, C.c_int]
+    L.rad_step.argtypes = [vp, C.c_double, C.c_int]
+    L.rad_read.argtypes = [vp, C.c_int, vp, C.c_size_t, C.c_int]
+    L.rad_sync.argtypes = [vp]
+    L.rad_dt.argtypes = [vp, P(C.c_double)]
+    L.rad_get_stats.argtypes = [vp, P(rad_stats)]
+    L.rad_reset_stats.argtypes = [vp]
+    L.rad_launches_per_step.argtypes = [vp]
+    L.rad_launches_per_step.restype = C.c_int
+    L.rad_destroy.argtypes = [vp]
+    L.rad_destroy.restype = None
+    L.rad_strerror.argtypes = [C.c_int]
+    L.rad_strerror.restype = C.c_char_p
+    _lib = L
+    return L
+
+
+class RadError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        msg = lib().rad_strerror(status).decode()
+        super().__init__("%s failed: %s (status %d)" % (where, msg, status))
+
+
+def check(status: int, where: str) -> None:
+    if status != RAD_OK:
+        raise RadError(status, where)
+
+
+def default_params() -> rad_params:
+    p = rad_params()
+    check(lib().rad_default_params(C.byref(p)), "rad_default_params")
+    return p
+
+
+class Rad:
+    """One radiation problem on one GPU.
+
+    grid: dict(ndim, n=(n0,n1,n2), xfaces=[3 arrays], bc_lo=(...), bc_hi=(...))
+    with bc names 'outflow' / 'periodic'; opacity: dict with 'kind' and the
+    fields of rad_opacity; params: rad_params field values, with precision
+    'fp64' | 'split' and implicit_mode 'once' | 'newton'.
+    """
+
+    def __init__(self, grid: dict, geometry: str, opacity: dict, params: dict,
+                 device: Optional[object] = None, workspace: str = "torch"):
+        import torch
+        self.torch = torch
+        L = lib()
+        g = rad_grid()
+        g.ndim = int(grid["ndim"])
+        self._xf = [np.ascontiguousarray(np.asarray(x, dtype=np.float64)) for x in grid["xfaces"]]
+        for d in range(3):
+            g.n[d] = int(grid["n"][d])
+            g.xface[d] = self._xf[d].ctypes.data
+            g.bc_lo[d] = BC[grid["bc_lo"][d]]
+            g.bc_hi[d] = BC[grid["bc_hi"][d]]
+        o = rad_opacity()
+        o.kind = OPACITY[opacity["kind"]]
+        for k in ("kappa_p", "kappa_r", "sigma", "k0", "a_rho", "b_T", "kmin", "sigma_ratio",
+                  "lrho0", "lT0"):
+            setattr(o, k, float(opacity.get(k, 0.0)))
+        o.kmax = float(opacity.get("kmax", 1e300))
+        o.lrho1 = float(opacity.get("lrho1", 1.0))
+        o.lT1 = float(opacity.get("lT1", 1.0))
+        o.nrho = int(opacity.get("nrho", 2))
+        o.nT = int(opacity.get("nT", 2))
+        self._table = None
+        if opacity["kind"] == "table":
+            self._table = np.ascontiguousarray(np.asarray(opacity["table"], dtype=np.float32))
+            o.table_log10_kappa = self._table.ctypes.data
+        p = default_params()
+        for k, v in params.items():
+            if k == "precision":
+                v = PRECISION[v] if isinstance(v, str) else v
+            elif k == "implicit_mode":
+                v = IMPLICIT[v] if isinstance(v, str) else v
+            setattr(p, k, v)
+        self.params = p
+        self.ncomp = int(p.ncomp)
+        self.N = int(np.prod([int(x) for x in grid["n"]]))
+        self.dtype = np.float64 if p.precision == RAD_FP64 else np.float32
+        ctx = C.c_void_p()
+        check(L.rad_create(C.byref(g), GEOMETRY[geometry], C.byref(o), C.byref(p),
+                           C.byref(ctx)), "rad_create")
+        self.ctx = ctx
+        self.device = torch.device(device if device is not None else "cuda")
+        nbytes = C.c_size_t()
+        check(L.rad_workspace_size(ctx, C.byref(nbytes)), "rad_workspace_size")
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            check(L.rad_set_stream(ctx, C.c_void_p(self.stream.cuda_stream)), "rad_set_stream")
+            if workspace == "torch":
+                self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
+                                       device=self.device)
+                base = self._ws.data_ptr()
+                aligned = (base + 255) // 256 * 256
+                check(L.rad_bind_workspace(ctx, C.c_void_p(aligned), self.workspace_bytes),
+                      "rad_bind_workspace")
+            else:
+                self._ws = None
+                check(L.rad_alloc_workspace(ctx), "rad_alloc_workspace")
+
+    # -- marshalling ---------------------------------------------------------
+    def _arg(self, a, count):
+        torch = self.torch
+        if isinstance(a, torch.Tensor):
+            assert a.is_cuda and a.is_contiguous() and a.numel() == count, "bad device tensor"
+            assert a.dtype == (torch.float64 if self.dtype == np.float64 else torch.float32)
+            return C.c_void_p(a.data_ptr()), 1, a
+        arr = np.ascontiguousarray(np.asarray(a, dtype=self.dtype)).reshape(-1)
+        assert arr.size == count, "expected %d values, got %d" % (count, arr.size)
+        return C.c_void_p(arr.ctypes.data), 0, arr
+
+    def set_gas(self, rho, v, T):
+        r, dr, kr = self._arg(rho, self.N)
+        vv, dv, kv = self._arg(v, self.N * self.ncomp)
+        t, dt_, kt = self._arg(T, self.N)
+        assert dr == dv == dt_, "all host or all device"
+        check(lib().rad_set_gas(self.ctx, r, vv, t, dr), "rad_set_gas")
+
+    def set_rad(self, E, F):
+        e, de, ke = self._arg(E, self.N)
+        f, df, kf = self._arg(F, self.N * self.ncomp)
+        assert de == df, "all host or all device"
+        check(lib().rad_set_rad(self.ctx, e, f, de), "rad_set_rad")
+
+    def step(self, nsteps: int = 1, dt: Optional[float] = None):
+        check(lib().rad_step(self.ctx, float(dt) if dt else 0.0, int(nsteps)), "rad_step")
+
+    def dt(self) -> float:
+        v = C.c_double()
+        check(lib().rad_dt(self.ctx, C.byref(v)), "rad_dt")
+        return v.value
+
+    def read(self, field: str, out=None, host: bool = True):
+        """Field as a numpy array (host=True) or into/as a device tensor."""
+        fid = FIELDS[field]
+        count = self.N * (self.ncomp if field in ("F", "m") else 1)
+        itemsize = np.dtype(self.dtype).itemsize
+        if host:
+            arr = np.empty(count, dtype=self.dtype) if out is None else out
+            check(lib().rad_read(self.ctx, fid, C.c_void_p(arr.ctypes.data), count * itemsize, 0),
+                  "rad_read")
+            return arr.reshape(self.ncomp, self.N) if field in ("F", "m") else arr
+        torch = self.torch
+        t = out if out is not None else torch.empty(
+            count, dtype=torch.float64 if self.dtype == np.float64 else torch.float32,
+            device=self.device)
+        check(lib().rad_read(self.ctx, fid, C.c_void_p(t.data_ptr()), count * itemsize, 1),
+              "rad_read")
+        return t
+
+    def sync(self) -> int:
+        return lib().rad_sync(self.ctx)
+
+    def stats(self) -> dict:
+        s = rad_stats()
+        check(lib().rad_get_stats(self.ctx, C.byref(s)), "rad_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in rad_stats._fields_}
+
+    def reset_stats(self):
+        check(lib().rad_reset_stats(self.ctx), "rad_reset_stats")
+
+    def launches_per_step(self) -> int:
+        return lib().rad_launches_per_step(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().rad_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def from_problem(prob, precision: str = "fp64", device=None, **overrides) -> "Rad":
+    """Builds a Rad from any object with the attributes of a problem
+    description (ndim, n, geometry, bc_lo, bc_hi, xfaces, chat, c, a_rad,
+    gamma_gas, mu, cfl, e_floor, opacity, implicit_mode, newton_rtol,
+    newton_maxit, ncomp) and uploads its fields (rho, v, T, E, F)."""
+    params = dict(chat=prob.chat, c=prob.c, a_rad=prob.a_rad, gamma_gas=prob.gamma_gas,
+                  mu=prob.mu, cfl=prob.cfl, e_floor=prob.e_floor, precision=precision,
+                  implicit_mode=prob.implicit_mode, newton_rtol=prob.newton_rtol,
+                  newton_maxit=prob.newton_maxit, ncomp=prob.ncomp)
+    params.update(overrides)
+    grid = dict(ndim=prob.ndim, n=prob.n, xfaces=prob.xfaces, bc_lo=prob.bc_lo, bc_hi=prob.bc_hi)
+    r = Rad(grid, prob.geometry, prob.opacity, params, device=device)
+    nc = prob.ncomp
+    r.set_gas(prob.rho, np.asarray(prob.v)[:nc], prob.T)
+    r.set_rad(prob.E, np.asarray(prob.F)[:nc])
+    return r

@@ -1,0 +1,88 @@
+// m1_internal.h -- structures shared by the host library and the step
+// kernels.  Not part of the public ABI.
+#pragma once
+#include <cstdint>
+
+#include "m1_math.cuh"
+
+namespace m1 {
+
+enum { kCart = 0, kCyl = 1, kSph = 2 };
+
+// Per-direction geometry tables, indexed by the padded index ip = i + g
+// (g = 2 ghost cells on active directions, 0 on inactive ones); each table
+// has len = n + 2 g entries.  Ghost entries describe the cell the ghost
+// copies (its width, radius) except TAB_IDXC/TAB_HLO/TAB_HHI, which use the
+// extended centre coordinates of the ghost itself.
+enum {
+  TAB_IDXC = 0,  // 1 / (xc[ip+1] - xc[ip])
+  TAB_HLO,       // x_face_lo - xc  (<= 0)
+  TAB_HHI,       // x_face_hi - xc  (>= 0)
+  TAB_ALO,       // lower-face area / volume factor of this direction
+  TAB_AHI,       // upper-face area / volume factor
+  TAB_WID,       // coordinate width (dx, dR, dr, dphi, dtheta, dz)
+  TAB_MET,       // dir 0: 1/R_c (cyl) or 1/r~ (sph); dir 1 (sph): cot~theta
+  TAB_AMLO,      // area/volume factors of the phi component (angular-momentum form)
+  TAB_AMHI,
+  TAB_RC,        // dir 0: centre radius; dir 1 (sph): sin(theta_c)
+  TAB_PHF,       // dir 1 (sph): dtheta / (cos theta_lo - cos theta_hi)
+  TAB_N
+};
+
+template <class T>
+struct GeomDev {
+  const T* tab[3];  // tab[d][slot * len[d] + ip]
+  int len[3];
+};
+
+struct StepDims {
+  int ndim;
+  int n[3];         // cells per direction
+  int g[3];         // ghost depth per direction
+  int pn[3];        // padded extents (pn[0] may be rounded up for alignment)
+  long long sy, sz; // padded strides of directions 1 and 2
+  int bc_lo[3], bc_hi[3];
+};
+
+template <class S>
+struct Fields {
+  S* E;
+  S* F[3];
+  S* e;
+  S* m[3];
+};
+
+enum {
+  ST_FIX = 0,
+  ST_EFLOOR,
+  ST_FCLIP,
+  ST_ITERS,
+  ST_ITMAX,
+  ST_FALLBACK,
+  ST_NOCONV,
+  ST_STEPS,
+  ST_N
+};
+
+enum { STATUS_NOCONV = 1, STATUS_NONPHYS = 2, STATUS_TIMEOUT = 4 };
+
+template <class P>
+struct StepArgs {
+  using S = typename P::S;
+  using T = typename P::T;
+  StepDims dim;
+  Fields<S> in;   // U^n (read only)
+  Fields<S> out;  // U^{n+1}
+  const S* rho;
+  GeomDev<T> geo;
+  OpacityDev opac;
+  CoupleParams cp;
+  T chat, dt, efloor;
+  T ratio;        // c / chat
+  T inv_chat;
+  unsigned long long* stats;
+  int* status;
+  int chunk;      // cells along the march axis per CTA
+};
+
+}  // namespace m1

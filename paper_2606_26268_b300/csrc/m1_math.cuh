@@ -1,0 +1,445 @@
+// m1_math.cuh -- per-state and per-cell arithmetic of the M1 radiation step
+// (device code, sm_103a).  Two precision policies:
+//   Fp64  : storage, transport and coupling in double, IEEE division/sqrt;
+//   Split : float storage and transport (MUFU approximations of rcp, rsqrt,
+//           sqrt, ex2, lg2), the coupling's T^4 term and E - a T^4 residual
+//           in double, the remaining well-conditioned coupling products in
+//           float.
+#pragma once
+#include <cstdint>
+
+namespace m1 {
+
+// ---------------------------------------------------------------------------
+// scalar helpers
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_approx(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sqrt_approx(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_approx(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float lg2_approx(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
+template <class T> struct Ops;
+
+template <> struct Ops<double> {
+  static __device__ __forceinline__ double div(double a, double b) { return a / b; }
+  static __device__ __forceinline__ double rcp(double a) { return 1.0 / a; }
+  static __device__ __forceinline__ double sqrt_(double a) { return sqrt(a); }
+};
+
+template <> struct Ops<float> {
+  static __device__ __forceinline__ float div(float a, float b) { return a * rcp_approx(b); }
+  static __device__ __forceinline__ float rcp(float a) { return rcp_approx(a); }
+  static __device__ __forceinline__ float sqrt_(float a) { return sqrt_approx(a); }
+};
+
+struct Fp64 {
+  using S = double;  // storage
+  using T = double;  // transport arithmetic
+  static constexpr bool kSplit = false;
+};
+struct Split {
+  using S = float;
+  using T = float;
+  static constexpr bool kSplit = true;
+};
+
+// ---------------------------------------------------------------------------
+// PLM with the van Leer limiter (Sect. 2.5)
+// ---------------------------------------------------------------------------
+
+// Limited slope from the two one-sided slopes: the harmonic mean
+// 2 dl dr / (dl + dr) when they have the same sign, else zero.
+template <class T>
+__device__ __forceinline__ T vanleer(T dl, T dr) {
+  T p = dl * dr;
+  return p > T(0) ? Ops<T>::div(T(2) * p, dl + dr) : T(0);
+}
+
+// ---------------------------------------------------------------------------
+// f-preserving face fix, Eq. (f_reconstruct)
+// ---------------------------------------------------------------------------
+
+// uf = (Ef, Ff) is the reconstructed face state of the cell uc = (Ec, Fc)
+// with nc2 = |Fc|^2.  The reconstructed flux is kept iff f_face <= 1 and
+// f_face > f_centre (compared without division: Ef, Ec > 0); otherwise
+// F_face = F_centre * E_face / E_centre.  Returns true when recomputed.
+template <class T, int NC>
+__device__ __forceinline__ bool fix_face(T (&uf)[4], const T (&uc)[4], T nc2, T inv_Ec) {
+  T nf2 = uf[1] * uf[1];
+  if (NC > 1) nf2 += uf[2] * uf[2];
+  if (NC > 2) nf2 += uf[3] * uf[3];
+  const T Ef = uf[0], Ec = uc[0];
+  bool keep = (nf2 <= Ef * Ef) && (nf2 * (Ec * Ec) > nc2 * (Ef * Ef));
+  if (!keep) {
+    T r = (sizeof(T) == 8) ? Ef / Ec : Ef * inv_Ec;
+    uf[1] = uc[1] * r;
+    if (NC > 1) uf[2] = uc[2] * r;
+    if (NC > 2) uf[3] = uc[3] * r;
+  }
+  return !keep;
+}
+
+// ---------------------------------------------------------------------------
+// Closure (Sect. 2.1) and signal speeds (Sect. 2.6) of one state along D
+// ---------------------------------------------------------------------------
+
+// Physical flux (chat F_D, chat D_{D j} E) and the eigenvalues lambda_{1,3}
+// (units of chat) of the state (E, F) along direction D.
+//   f = min(|F|/E, 1), s = sqrt(4 - 3 f^2), xi = (3 + 4 f^2) / (5 + 2 s),
+//   D E = a delta + b F F  with a = (1 - xi) E / 2, b = (3 xi - 1) E / (2 |F|^2),
+//   lambda = (f cos(theta) +/- zeta) / s.
+// zeta^2 of Sect. 2.6 is evaluated in the algebraically identical form
+//   zeta^2 = 2 (1 - f^2) (s (1 + c^2) - 2 c^2) / (s + 1),  c = cos(theta),
+// which is non-negative term by term and free of the cancellation of
+// 4 - 3 f^2 - s as f -> 1.
+template <class T, int NC, int D>
+__device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4], T& lm,
+                                           T& lp) {
+  const T E = u[0];
+  const T F[3] = {u[1], u[2], u[3]};
+  T nF2 = F[0] * F[0];
+  if (NC > 1) nF2 += F[1] * F[1];
+  if (NC > 2) nF2 += F[2] * F[2];
+  const T Fd = (D < NC) ? F[D] : T(0);
+  T f, fc, c2, b;
+  T invE = Ops<T>::rcp(E);
+  if constexpr (sizeof(T) == 8) {
+    T nF = sqrt(nF2);
+    f = nF / E;
+    if (f > T(1)) f = T(1);
+    T cth = (nF > T(0)) ? Fd / nF : T(0);
+    fc = f * cth;
+    c2 = cth * cth;
+    b = T(0);
+    T f2 = f * f;
+    T s = sqrt(T(4) - T(3) * f2);
+    T xi = (T(3) + T(4) * f2) / (T(5) + T(2) * s);
+    T a = T(0.5) * (T(1) - xi) * E;
+    if (nF > T(0)) b = T(0.5) * (T(3) * xi - T(1)) * E / nF2;
+    flux[0] = chat * Fd;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T Fj = (j < NC) ? F[j] : T(0);
+      T dj = (j == D ? a : T(0)) + b * Fd * Fj;
+      if (j < NC) flux[1 + j] = chat * dj;
+    }
+    T z2 = T(2) * (T(1) - f2) * (s * (T(1) + c2) - T(2) * c2) / (s + T(1));
+    T z = sqrt(z2 > T(0) ? z2 : T(0));
+    lp = (fc + z) / s;
+    lm = (fc - z) / s;
+  } else {
+    T rn = nF2 > T(0) ? rsqrt_approx(nF2) : T(0);
+    T nF = nF2 * rn;
+    f = nF * invE;
+    f = f > T(1) ? T(1) : f;
+    T cth = Fd * rn;
+    fc = f * cth;
+    c2 = cth * cth;
+    T f2 = f * f;
+    T q = T(4) - T(3) * f2;
+    T rs = rsqrt_approx(q);
+    T s = q * rs;
+    T xi = (T(3) + T(4) * f2) * rcp_approx(T(5) + T(2) * s);
+    T a = T(0.5) * (T(1) - xi) * E;
+    b = T(0.5) * (T(3) * xi - T(1)) * E * (rn * rn);
+    flux[0] = chat * Fd;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      T Fj = (j < NC) ? F[j] : T(0);
+      T dj = (j == D ? a : T(0)) + b * Fd * Fj;
+      if (j < NC) flux[1 + j] = chat * dj;
+    }
+    T z2 = T(2) * (T(1) - f2) * (s * (T(1) + c2) - T(2) * c2) * rcp_approx(s + T(1));
+    T z = sqrt_approx(z2 > T(0) ? z2 : T(0));
+    lp = (fc + z) * rs;
+    lm = (fc - z) * rs;
+  }
+}
+
+// Pressure tensor P = D E of a cell-centred state (for the geometric
+// sources): P_ij = a delta_ij + b F_i F_j.
+template <class T, int NC>
+__device__ __forceinline__ void pressure(const T (&u)[4], T& a, T& b) {
+  const T E = u[0];
+  T nF2 = u[1] * u[1];
+  if (NC > 1) nF2 += u[2] * u[2];
+  if (NC > 2) nF2 += u[3] * u[3];
+  T nF = Ops<T>::sqrt_(nF2);
+  T f = Ops<T>::div(nF, E);
+  f = f > T(1) ? T(1) : f;
+  T f2 = f * f;
+  T s = Ops<T>::sqrt_(T(4) - T(3) * f2);
+  T xi = Ops<T>::div(T(3) + T(4) * f2, T(5) + T(2) * s);
+  a = T(0.5) * (T(1) - xi) * E;
+  b = nF2 > T(0) ? Ops<T>::div(T(0.5) * (T(3) * xi - T(1)) * E, nF2) : T(0);
+}
+
+// HLL flux (Sect. 2.5) with the signal speeds of Sect. 2.6:
+// S_L = chat min(lm_L, lm_R), S_R = chat max(lp_L, lp_R), limited to
+// -/+ 4 chat / (3 tau) when tau > 0.
+template <class T, int NV>
+__device__ __forceinline__ void hll(const T (&uL)[4], const T (&uR)[4], const T (&fL)[4],
+                                    const T (&fR)[4], T lmL, T lpL, T lmR, T lpR, T chat,
+                                    T tau, T (&out)[4]) {
+  T sl = chat * (lmL < lmR ? lmL : lmR);
+  T sr = chat * (lpL > lpR ? lpL : lpR);
+  if (tau > T(0)) {
+    T bound = Ops<T>::div(T(4) * chat, T(3) * tau);
+    if (sl < -bound) sl = -bound;
+    if (sr > bound) sr = bound;
+  }
+  if (sl >= T(0)) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = fL[q];
+  } else if (sr <= T(0)) {
+#pragma unroll
+    for (int q = 0; q < NV; ++q) out[q] = fR[q];
+  } else {
+    T inv = Ops<T>::rcp(sr - sl);
+#pragma unroll
+    for (int q = 0; q < NV; ++q) {
+      T num = sr * fL[q] - sl * fR[q] + sl * sr * (uR[q] - uL[q]);
+      out[q] = (sizeof(T) == 8) ? num / (sr - sl) : num * inv;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Opacities
+// ---------------------------------------------------------------------------
+
+struct OpacityDev {
+  int kind;                    // 0 const, 1 powerlaw, 2 table
+  double kappa_p, kappa_r, sigma;
+  double k0, a_rho, b_T, kmin, kmax, sigma_ratio;
+  int nrho, nT;
+  double lrho0, lT0, sr, sT;   // sr = (nrho-1)/(lrho1-lrho0), sT likewise
+  const double* tab64;         // log10 kappa, [iT][irho]
+  const float* tab32;
+  int linear_rho;              // powerlaw with a = 1, b = 0 (kappa = k0 rho)
+};
+
+// Opacities per unit mass at (rho, T): kp (Planck), chi = kappa_R + sigma.
+__device__ __forceinline__ void opacity(const OpacityDev& o, double rho, double T, double& kp,
+                                        double& chi) {
+  if (o.kind == 0) {
+    kp = o.kappa_p;
+    chi = o.kappa_r + o.sigma;
+    return;
+  }
+  double k;
+  if (o.kind == 1) {
+    k = o.k0 * pow(rho, o.a_rho) * pow(T, o.b_T);
+    k = k < o.kmin ? o.kmin : k;
+    k = k > o.kmax ? o.kmax : k;
+  } else {
+    double xr = (log10(rho) - o.lrho0) * o.sr;
+    double xt = (log10(T) - o.lT0) * o.sT;
+    xr = xr < 0.0 ? 0.0 : (xr > o.nrho - 1 ? double(o.nrho - 1) : xr);
+    xt = xt < 0.0 ? 0.0 : (xt > o.nT - 1 ? double(o.nT - 1) : xt);
+    int ir = int(floor(xr)), it = int(floor(xt));
+    ir = ir > o.nrho - 2 ? o.nrho - 2 : ir;
+    it = it > o.nT - 2 ? o.nT - 2 : it;
+    double wr = xr - ir, wt = xt - it;
+    const double* t = o.tab64 + it * o.nrho + ir;
+    double l00 = __ldg(t), l10 = __ldg(t + 1), l01 = __ldg(t + o.nrho), l11 = __ldg(t + o.nrho + 1);
+    double lk = (1.0 - wr) * (1.0 - wt) * l00 + wr * (1.0 - wt) * l10 + (1.0 - wr) * wt * l01 +
+                wr * wt * l11;
+    k = pow(10.0, lk);
+  }
+  kp = k;
+  chi = k * (1.0 + o.sigma_ratio);
+}
+
+__device__ __forceinline__ void opacity(const OpacityDev& o, float rho, float T, float& kp,
+                                        float& chi) {
+  if (o.kind == 0) {
+    kp = float(o.kappa_p);
+    chi = float(o.kappa_r + o.sigma);
+    return;
+  }
+  float k;
+  if (o.kind == 1) {
+    if (o.linear_rho) {
+      k = float(o.k0) * rho;
+    } else {
+      k = float(o.k0) * ex2_approx(float(o.a_rho) * lg2_approx(rho) + float(o.b_T) * lg2_approx(T));
+    }
+    k = k < float(o.kmin) ? float(o.kmin) : k;
+    k = k > float(o.kmax) ? float(o.kmax) : k;
+  } else {
+    const float kLog10_2 = 0.30102999566398120f;
+    float xr = (lg2_approx(rho) * kLog10_2 - float(o.lrho0)) * float(o.sr);
+    float xt = (lg2_approx(T) * kLog10_2 - float(o.lT0)) * float(o.sT);
+    xr = fminf(fmaxf(xr, 0.f), float(o.nrho - 1));
+    xt = fminf(fmaxf(xt, 0.f), float(o.nT - 1));
+    int ir = min(int(xr), o.nrho - 2), it = min(int(xt), o.nT - 2);
+    float wr = xr - ir, wt = xt - it;
+    const float* t = o.tab32 + it * o.nrho + ir;
+    float l00 = __ldg(t), l10 = __ldg(t + 1), l01 = __ldg(t + o.nrho), l11 = __ldg(t + o.nrho + 1);
+    float lk = (1.f - wr) * ((1.f - wt) * l00 + wt * l01) + wr * ((1.f - wt) * l10 + wt * l11);
+    k = ex2_approx(lk * 3.32192809488736235f);
+  }
+  kp = k;
+  chi = k * (1.f + float(o.sigma_ratio));
+}
+
+// ---------------------------------------------------------------------------
+// Implicit coupling (Sect. 2.8)
+// ---------------------------------------------------------------------------
+
+struct CoupleParams {
+  double dt, chat, c, a_rad, cvfac;  // cvfac = 1 / (mu (gamma - 1)): C_v = rho cvfac
+  double rtol;
+  int maxit, newton;
+};
+
+struct CoupleOut {
+  double dE;     // E^{n+1} - E*
+  double Tnew;   // T^{n+1} of the solve
+  int iters;
+  int fallback;  // restarted from T^n
+  int noconv;
+};
+
+// Increments of the 2x2 system of Eq. (implicit_matrix) with T^4 linearised
+// about Tk.  With D = E* - a Tk^4, det = (1 + g_r) C_v + 4 g a Tk^3 and
+// G = (1 + g_r) C_v (T^n - Tk), Cramer's rule gives exactly
+//   T^{n+1} - Tk = (G + g D) / det,
+//   E^{n+1} - E* = g_r C_v (4 a Tk^3 (T^n - Tk) - D) / det,
+// which for Tk = T^n is the paper's single solve.  Newton mode repeats it
+// with Tk <- T^{n+1} until |T^{n+1} - Tk| <= rtol T^{n+1}.
+__device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double rho, double e,
+                                                 double kp, double Es, double T0) {
+  CoupleOut o{};
+  double Cv = rho * p.cvfac;
+  double Tn = e / Cv;
+  double gr = p.dt * p.chat * kp * rho;
+  double g = p.dt * p.c * kp * rho;
+  double c1 = (1.0 + gr) * Cv;
+  if (T0 <= 0.0) T0 = Tn;
+  if (!p.newton) {
+    double aT3 = p.a_rad * Tn * Tn * Tn;
+    double D = Es - aT3 * Tn;
+    double det = c1 + 4.0 * g * aT3;
+    double q = D / det;
+    o.Tnew = Tn + g * q;
+    o.dE = -gr * Cv * q;
+    o.iters = 1;
+    return o;
+  }
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    double Tk = attempt == 0 ? T0 : Tn;
+    bool ok = false;
+    int it;
+    double aT3 = 0.0, D = 0.0, det = 1.0, Tnew = Tk;
+    for (it = 1; it <= p.maxit; ++it) {
+      aT3 = p.a_rad * Tk * Tk * Tk;
+      D = Es - aT3 * Tk;
+      det = c1 + 4.0 * g * aT3;
+      double dT = (c1 * (Tn - Tk) + g * D) / det;
+      Tnew = Tk + dT;
+      if (!(Tnew > 0.0)) break;
+      if (fabs(dT) <= p.rtol * Tnew) {
+        ok = true;
+        break;
+      }
+      Tk = Tnew;
+    }
+    int used = ok ? it : (it > p.maxit ? p.maxit : it);
+    o.iters += used;
+    if (ok || attempt == 1) {
+      o.Tnew = Tnew;
+      o.dE = gr * Cv * (4.0 * aT3 * (Tn - Tk) - D) / det;
+      o.noconv = ok ? 0 : 1;
+      return o;
+    }
+    o.fallback = 1;
+  }
+  return o;
+}
+
+// Split precision: the T^4 emission term, the residual E* - a Tk^4 and the
+// Newton numerator are formed in double; det and the final products, whose
+// terms are all positive, in float.
+__device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
+                                                  float kp, float Es, float T0f) {
+  CoupleOut o{};
+  float Cv = rho * float(p.cvfac);
+  float invCv = rcp_approx(Cv);
+  double Tn = double(e) * double(invCv);
+  float gr = float(p.dt * p.chat) * kp * rho;
+  float g = float(p.dt * p.c) * kp * rho;
+  float c1 = (1.f + gr) * Cv;
+  if (!p.newton) {
+    double T2 = Tn * Tn;
+    double aT4 = (p.a_rad * T2) * T2;
+    float D = float(double(Es) - aT4);
+    float Tf = e * invCv;
+    float aT3 = float(p.a_rad) * Tf * Tf * Tf;
+    float det = c1 + 4.f * g * aT3;
+    float q = D * rcp_approx(det);
+    o.Tnew = Tn + double(g * q);
+    o.dE = double(-gr * Cv * q);
+    o.iters = 1;
+    return o;
+  }
+  double c1d = double(c1);
+  for (int attempt = 0; attempt < 2; ++attempt) {
+    double Tk = (attempt == 0 && T0f > 0.f) ? double(T0f) : Tn;
+    bool ok = false;
+    int it;
+    double aT3 = 0.0, D = 0.0;
+    float det = 1.f;
+    double Tnew = Tk;
+    for (it = 1; it <= p.maxit; ++it) {
+      aT3 = p.a_rad * Tk * Tk * Tk;
+      D = double(Es) - aT3 * Tk;
+      det = c1 + 4.f * g * float(aT3);
+      double num = c1d * (Tn - Tk) + double(g) * D;
+      double dT = num * double(rcp_approx(det));
+      Tnew = Tk + dT;
+      if (!(Tnew > 0.0)) break;
+      if (fabsf(float(dT)) <= float(p.rtol) * float(Tnew)) {
+        ok = true;
+        break;
+      }
+      Tk = Tnew;
+    }
+    int used = ok ? it : (it > p.maxit ? p.maxit : it);
+    o.iters += used;
+    if (ok || attempt == 1) {
+      o.Tnew = Tnew;
+      float inner = float(4.0 * aT3 * (Tn - Tk) - D);
+      o.dE = double(gr * Cv * inner * rcp_approx(det));
+      o.noconv = ok ? 0 : 1;
+      return o;
+    }
+    o.fallback = 1;
+  }
+  return o;
+}
+
+}  // namespace m1

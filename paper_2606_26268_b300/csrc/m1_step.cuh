@@ -1,0 +1,582 @@
+// m1_step.cuh -- the fused M1 radiation step kernel (sm_103a).
+//
+// One launch performs, for every cell, the whole Euler step of Sect. 2.4:
+// boundary values (ghost layers kept up to date by the previous launch),
+// PLM reconstruction, the f-preserving fix of Eq. (f_reconstruct), closure,
+// signal speeds with the optically thick limit (Sect. 2.6), HLL fluxes,
+// the unsplit flux divergence with the metric terms of the geometry, and
+// the implicit coupling of Sect. 2.8 with the gas bookkeeping of Sect. 2.7.
+//
+// Work decomposition.  A CTA of TX x TY threads owns an x (and, in 3D, y)
+// tile and marches along the slowest active axis (y in 2D, z in 3D).  Thread
+// (tx, ty) computes the lower face of its own column in every tile direction;
+// tiles overlap by one cell, so each CTA updates (TX-1) x (TY-1) columns.  The
+// march direction keeps the column's states, its reconstructed upper face
+// state and the lower face flux in registers, so each march face is computed
+// once.  The tile directions read a shared-memory plane holding the current
+// march plane with a 2-cell halo; the face fluxes are exchanged through
+// shared memory.  Optical depths of the halo cells needed by the tile faces
+// are computed by the threads that load the halo.
+#pragma once
+#include "m1_internal.h"
+
+namespace m1 {
+
+template <class T>
+__device__ __forceinline__ T tabv(const GeomDev<T>& G, int d, int slot, int ip) {
+  return __ldg(G.tab[d] + slot * G.len[d] + ip);
+}
+
+// Largest physical width of a cell over the active directions (tau and CFL).
+template <class T, int NDIM, int GEOM>
+__device__ __forceinline__ T cell_hmax(const GeomDev<T>& G, int p0, int p1, int p2) {
+  T h = tabv(G, 0, TAB_WID, p0);
+  if (NDIM >= 2) {
+    T w = tabv(G, 1, TAB_WID, p1);
+    if (GEOM != kCart) w *= tabv(G, 0, TAB_RC, p0);
+    h = w > h ? w : h;
+  }
+  if (NDIM >= 3) {
+    T w = tabv(G, 2, TAB_WID, p2);
+    if (GEOM == kSph) w *= tabv(G, 0, TAB_RC, p0) * tabv(G, 1, TAB_RC, p1);
+    h = w > h ? w : h;
+  }
+  return h;
+}
+
+// Opacities and optical depth rho chi h of a cell from its (rho, e).
+template <class P, int NDIM, int GEOM>
+__device__ __forceinline__ typename P::T cell_tau(const StepArgs<P>& a, typename P::S rho,
+                                                  typename P::S e, int p0, int p1, int p2,
+                                                  typename P::T& kp, typename P::T& chi) {
+  using T = typename P::T;
+  T r = T(rho);
+  T Cv = r * T(a.cp.cvfac);
+  T Temp = (sizeof(T) == 8) ? T(e) / Cv : T(e) * rcp_approx(float(Cv));
+  opacity(a.opac, r, Temp, kp, chi);
+  return r * chi * cell_hmax<T, NDIM, GEOM>(a.geo, p0, p1, p2);
+}
+
+// Reconstructed state at the face of cell uc at offset h from its centre,
+// from the one-sided differences dl = (uc - um) ixl and dr = (up - uc) ixr.
+template <class T, int NV>
+__device__ __forceinline__ void plm_state(const T (&dl)[4], const T (&dr)[4], const T (&uc)[4],
+                                          T h, T (&out)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) out[q] = (q < NV) ? uc[q] + vanleer(dl[q], dr[q]) * h : T(0);
+}
+
+template <class T, int NC>
+__device__ __forceinline__ T flux2(const T (&u)[4]) {
+  T s = u[1] * u[1];
+  if (NC > 1) s += u[2] * u[2];
+  if (NC > 2) s += u[3] * u[3];
+  return s;
+}
+
+// HLL flux from two fixed face states along D.
+template <class T, int NC, int D>
+__device__ __forceinline__ void riemann(const T (&uL)[4], const T (&uR)[4], T chat, T tau,
+                                        T (&out)[4]) {
+  T fL[4] = {0, 0, 0, 0}, fR[4] = {0, 0, 0, 0};
+  T lmL, lpL, lmR, lpR;
+  state_flux<T, NC, D>(uL, chat, fL, lmL, lpL);
+  state_flux<T, NC, D>(uR, chat, fR, lmR, lpR);
+  hll<T, 1 + NC>(uL, uR, fL, fR, lmL, lpL, lmR, lpR, chat, tau, out);
+}
+
+// Face flux from four consecutive cells um2, um1 | u0, up1 along D (the
+// face between um1 and u0).  ix_k = 1 / (centre distance) of the pairs
+// (um2, um1), (um1, u0), (u0, up1); hh = offset of the upper face of um1,
+// hl = offset of the lower face of u0.  Returns the number of fixed states.
+template <class T, int NC, int D>
+__device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const T (&u0)[4],
+                                     const T (&up1)[4], T ix0, T ix1, T ix2, T hh, T hl, T tau,
+                                     T chat, T (&out)[4]) {
+  constexpr int NV = 1 + NC;
+  T d0[4], d1[4], d2[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    d0[q] = (um1[q] - um2[q]) * ix0;
+    d1[q] = (u0[q] - um1[q]) * ix1;
+    d2[q] = (up1[q] - u0[q]) * ix2;
+  }
+  T uL[4], uR[4];
+  plm_state<T, NV>(d0, d1, um1, hh, uL);
+  plm_state<T, NV>(d1, d2, u0, hl, uR);
+  int nfix = fix_face<T, NC>(uL, um1, flux2<T, NC>(um1), Ops<T>::rcp(um1[0]));
+  nfix += fix_face<T, NC>(uR, u0, flux2<T, NC>(u0), Ops<T>::rcp(u0[0]));
+  riemann<T, NC, D>(uL, uR, chat, tau, out);
+  return nfix;
+}
+
+template <class S, int NC, class T>
+__device__ __forceinline__ void load_state(const Fields<S>& f, long long i, T (&u)[4]) {
+  u[0] = T(__ldg(f.E + i));
+#pragma unroll
+  for (int q = 0; q < 3; ++q) u[1 + q] = (q < NC) ? T(__ldg(f.F[q] + i)) : T(0);
+}
+
+template <class P, int NDIM, int GEOM, int NC, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ StepArgs<P> a) {
+  using S = typename P::S;
+  using T = typename P::T;
+  constexpr int NV = 1 + NC;
+  constexpr bool TILE_Y = (NDIM == 3);
+  constexpr bool MARCH = (NDIM >= 2);
+  constexpr int MA = (NDIM == 3) ? 2 : 1;  // march axis
+  constexpr int SX = TX + 3;
+  constexpr int SY = TILE_Y ? TY + 3 : 1;
+  constexpr int OY = TILE_Y ? 2 : 0;
+  constexpr int NT = TX * TY;
+  constexpr int NHALO = TILE_Y ? 3 * (TX + TY) : 3;
+
+  __shared__ T s_u[NV][SY][SX];
+  __shared__ T s_tau[TILE_Y ? TY + 1 : 1][TX + 1];
+  __shared__ T s_fx[NV][TY][TX];
+  __shared__ T s_fy[TILE_Y ? NV : 1][TILE_Y ? TY : 1][TX];
+  __shared__ unsigned long long s_red[ST_N];
+
+  const StepDims& Dm = a.dim;
+  const GeomDev<T>& G = a.geo;
+  const int tx = threadIdx.x;
+  const int ty = TILE_Y ? threadIdx.y : 0;
+  const int tid = tx + TX * ty;
+  const int x0 = blockIdx.x * (TX - 1);
+  const int y0 = TILE_Y ? blockIdx.y * (TY - 1) : 0;
+  const int mblk = MARCH ? (TILE_Y ? blockIdx.z : blockIdx.y) : 0;
+  const int m0 = MARCH ? mblk * a.chunk : 0;
+  const int m1 = MARCH ? min(m0 + a.chunk, Dm.n[MA]) : 1;
+
+  if (tid < ST_N) s_red[tid] = 0ull;
+
+  const int cx = x0 + tx;
+  const int cy = TILE_Y ? y0 + ty : 0;
+  const int px = min(cx + Dm.g[0], G.len[0] - 1);                 // table / array x
+  const int pxa = min(cx + Dm.g[0], Dm.pn[0] - 1);
+  const int py = TILE_Y ? min(cy + Dm.g[1], G.len[1] - 1) : 0;
+  const long long base = (long long)pxa + (TILE_Y ? (long long)py * Dm.sy : 0ll);
+  const long long ms = MARCH ? (MA == 2 ? Dm.sz : Dm.sy) : 0ll;
+  const int gm = MARCH ? Dm.g[MA] : 0;
+  const bool in_col = cx < Dm.n[0] && (!TILE_Y || cy < Dm.n[1]);
+  const bool upd_col = in_col && tx <= TX - 2 && (!TILE_Y || ty <= TY - 2);
+  const T chat = a.chat;
+
+  // march-plane coordinates for tables: p1 (2D: march; 3D: tile y), p2
+  auto p1_of = [&](int m) { return TILE_Y ? py : (MARCH ? m + gm : 0); };
+  auto p2_of = [&](int m) { return TILE_Y ? m + gm : 0; };
+
+  unsigned int c_fix = 0, c_efloor = 0, c_fclip = 0, c_fallback = 0, c_noconv = 0, c_itmax = 0;
+  unsigned long long c_iters = 0;
+  int status = 0;
+
+  // column queue: q[0..3] = states at m-1, m, m+1, m+2
+  T q[4][4];
+  T hiS[4];         // fixed upper face state of cell m along the march axis
+  T zlo[4], zhi[4]; // march-face fluxes m-1/2 and m+1/2
+  T tau_m = 0, tau_n = 0, kp_m = 0, chi_m = 0, kp_n = 0, chi_n = 0;
+  S rho_m = 0, e_m = 0, rho_n = 0, e_n = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) zlo[v] = zhi[v] = hiS[v] = T(0);
+
+  if constexpr (MARCH) {
+    T qm2[4];
+    load_state<S, NC>(a.in, base + (long long)(m0 - 2 + gm) * ms, qm2);
+    load_state<S, NC>(a.in, base + (long long)(m0 - 1 + gm) * ms, q[0]);
+    load_state<S, NC>(a.in, base + (long long)(m0 + gm) * ms, q[1]);
+    load_state<S, NC>(a.in, base + (long long)(m0 + 1 + gm) * ms, q[2]);
+    {
+      long long i = base + (long long)(m0 - 1 + gm) * ms;
+      S r = __ldg(a.rho + i), e = __ldg(a.in.e + i);
+      T kp, chi;
+      tau_m = cell_tau<P, NDIM, GEOM>(a, r, e, px, p1_of(m0 - 1), p2_of(m0 - 1), kp, chi);
+    }
+    T tau_prev = tau_m;
+    {
+      long long i = base + (long long)(m0 + gm) * ms;
+      rho_m = __ldg(a.rho + i);
+      e_m = __ldg(a.in.e + i);
+      tau_m = cell_tau<P, NDIM, GEOM>(a, rho_m, e_m, px, p1_of(m0), p2_of(m0), kp_m, chi_m);
+    }
+    const int pm = m0 + gm;
+    T ix0 = tabv(G, MA, TAB_IDXC, pm - 2), ix1 = tabv(G, MA, TAB_IDXC, pm - 1);
+    T ix2 = tabv(G, MA, TAB_IDXC, pm);
+    int nf = face4<T, NC, MA>(qm2, q[0], q[1], q[2], ix0, ix1, ix2, tabv(G, MA, TAB_HHI, pm - 1),
+                              tabv(G, MA, TAB_HLO, pm), T(0.5) * (tau_prev + tau_m), chat, zlo);
+    if (upd_col && m0 == 0) c_fix += nf;
+    // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
+    T d1[4], d2[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      d1[v] = (q[1][v] - q[0][v]) * ix1;
+      d2[v] = (q[2][v] - q[1][v]) * ix2;
+    }
+    plm_state<T, NV>(d1, d2, q[1], tabv(G, MA, TAB_HHI, pm), hiS);
+    int nfh = fix_face<T, NC>(hiS, q[1], flux2<T, NC>(q[1]), Ops<T>::rcp(q[1][0]));
+    if (upd_col) c_fix += nfh;
+  } else {
+    load_state<S, NC>(a.in, base, q[1]);
+    rho_m = __ldg(a.rho + base);
+    e_m = __ldg(a.in.e + base);
+    tau_m = cell_tau<P, NDIM, GEOM>(a, rho_m, e_m, px, 0, 0, kp_m, chi_m);
+  }
+
+  for (int m = m0; m < m1; ++m) {
+    const long long ic = base + (long long)(m + gm) * ms;  // own cell
+    T mom[3] = {0, 0, 0};
+    if constexpr (MARCH) {
+      load_state<S, NC>(a.in, ic + 2 * ms, q[3]);
+      long long i1 = ic + ms;
+      rho_n = __ldg(a.rho + i1);
+      e_n = __ldg(a.in.e + i1);
+      tau_n = cell_tau<P, NDIM, GEOM>(a, rho_n, e_n, px, p1_of(m + 1), p2_of(m + 1), kp_n, chi_n);
+    }
+    if (upd_col) {
+#pragma unroll
+      for (int v = 0; v < NC; ++v) mom[v] = T(__ldg(a.in.m[v] + ic));
+    }
+    // own state and tau into the shared plane
+#pragma unroll
+    for (int v = 0; v < NV; ++v) s_u[v][ty + OY][tx + 2] = q[1][v];
+    s_tau[TILE_Y ? ty + 1 : 0][tx + 1] = tau_m;
+    // halo of the plane
+    for (int h = tid; h < NHALO; h += NT) {
+      int xs, ys;
+      if (TILE_Y) {
+        if (h < 3 * TY) {
+          int c = h / TY;
+          xs = c == 0 ? -2 : (c == 1 ? -1 : TX);
+          ys = h - c * TY;
+        } else {
+          int hh = h - 3 * TY;
+          int c = hh / TX;
+          ys = c == 0 ? -2 : (c == 1 ? -1 : TY);
+          xs = hh - c * TX;
+        }
+      } else {
+        xs = h == 0 ? -2 : (h == 1 ? -1 : TX);
+        ys = 0;
+      }
+      int hx = min(max(x0 + xs + Dm.g[0], 0), Dm.pn[0] - 1);
+      int hy = TILE_Y ? min(max(y0 + ys + Dm.g[1], 0), Dm.pn[1] - 1) : 0;
+      long long ih = (long long)hx + (TILE_Y ? (long long)hy * Dm.sy : 0ll) +
+                     (long long)(m + gm) * ms;
+      T u[4];
+      load_state<S, NC>(a.in, ih, u);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s_u[v][ys + OY][xs + 2] = u[v];
+      bool need_tau = TILE_Y ? ((xs == -1 && ys >= 0 && ys < TY) || (ys == -1 && xs >= 0 && xs < TX))
+                             : (xs == -1);
+      if (need_tau) {
+        T kp, chi;
+        int tx_ = min(hx, G.len[0] - 1);
+        int ty_ = TILE_Y ? min(hy, G.len[1] - 1) : p1_of(m);
+        T t = cell_tau<P, NDIM, GEOM>(a, __ldg(a.rho + ih), __ldg(a.in.e + ih), tx_, ty_, p2_of(m),
+                                      kp, chi);
+        s_tau[TILE_Y ? ys + 1 : 0][xs + 1] = t;
+      }
+    }
+    __syncthreads();
+
+    // x face (tx - 1/2)
+    {
+      T um2[4], um1[4], u0[4], up1[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        um2[v] = v < NV ? s_u[v][ty + OY][tx] : T(0);
+        um1[v] = v < NV ? s_u[v][ty + OY][tx + 1] : T(0);
+        u0[v] = v < NV ? s_u[v][ty + OY][tx + 2] : T(0);
+        up1[v] = v < NV ? s_u[v][ty + OY][tx + 3] : T(0);
+      }
+      T tau = T(0.5) * (s_tau[TILE_Y ? ty + 1 : 0][tx] + s_tau[TILE_Y ? ty + 1 : 0][tx + 1]);
+      T fx[4];
+      int nf = face4<T, NC, 0>(um2, um1, u0, up1, tabv(G, 0, TAB_IDXC, px - 2),
+                               tabv(G, 0, TAB_IDXC, px - 1), tabv(G, 0, TAB_IDXC, px),
+                               tabv(G, 0, TAB_HHI, px - 1), tabv(G, 0, TAB_HLO, px), tau, chat, fx);
+      bool own = (tx >= 1 || x0 == 0) && cx <= Dm.n[0] && (!TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]));
+      if (own) c_fix += nf;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = fx[v];
+    }
+    // y face (ty - 1/2), 3D only
+    if constexpr (TILE_Y) {
+      T um2[4], um1[4], u0[4], up1[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        um2[v] = v < NV ? s_u[v][ty][tx + 2] : T(0);
+        um1[v] = v < NV ? s_u[v][ty + 1][tx + 2] : T(0);
+        u0[v] = v < NV ? s_u[v][ty + 2][tx + 2] : T(0);
+        up1[v] = v < NV ? s_u[v][ty + 3][tx + 2] : T(0);
+      }
+      T tau = T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]);
+      T fy[4];
+      int nf = face4<T, NC, 1>(um2, um1, u0, up1, tabv(G, 1, TAB_IDXC, py - 2),
+                               tabv(G, 1, TAB_IDXC, py - 1), tabv(G, 1, TAB_IDXC, py),
+                               tabv(G, 1, TAB_HHI, py - 1), tabv(G, 1, TAB_HLO, py), tau, chat, fy);
+      bool own = (ty >= 1 || y0 == 0) && cy <= Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0];
+      if (own) c_fix += nf;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = fy[v];
+    }
+    // march face m + 1/2 from the column registers
+    T hiN[4];
+    if constexpr (MARCH) {
+      const int pm = m + 1 + gm;  // padded index of cell m+1
+      T ix1 = tabv(G, MA, TAB_IDXC, pm - 1), ix2 = tabv(G, MA, TAB_IDXC, pm);
+      T d1[4], d2[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        d1[v] = (q[2][v] - q[1][v]) * ix1;
+        d2[v] = (q[3][v] - q[2][v]) * ix2;
+      }
+      T loN[4];
+      plm_state<T, NV>(d1, d2, q[2], tabv(G, MA, TAB_HLO, pm), loN);
+      plm_state<T, NV>(d1, d2, q[2], tabv(G, MA, TAB_HHI, pm), hiN);
+      T inv2 = Ops<T>::rcp(q[2][0]);
+      T n2 = flux2<T, NC>(q[2]);
+      int nf = fix_face<T, NC>(loN, q[2], n2, inv2);
+      int nf2 = fix_face<T, NC>(hiN, q[2], n2, inv2);
+      riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
+      if (upd_col) c_fix += nf + (m + 1 < m1 ? nf2 : 0);
+    }
+    __syncthreads();
+
+    // update of the own cell
+    if (upd_col && m < (MARCH ? Dm.n[MA] : 1)) {
+      T dU[4] = {0, 0, 0, 0};
+      // direction 0
+      {
+        T flo[4], fhi[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          flo[v] = v < NV ? s_fx[v][ty][tx] : T(0);
+          fhi[v] = v < NV ? s_fx[v][ty][tx + 1] : T(0);
+        }
+        T alo = tabv(G, 0, TAB_ALO, px), ahi = tabv(G, 0, TAB_AHI, px);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= ahi * fhi[v] - alo * flo[v];
+        if (GEOM == kCyl && NC >= 2) {
+          dU[2] += ahi * fhi[2] - alo * flo[2];
+          dU[2] -= tabv(G, 0, TAB_AMHI, px) * fhi[2] - tabv(G, 0, TAB_AMLO, px) * flo[2];
+        }
+        if (GEOM == kSph && NC >= 3) {
+          dU[3] += ahi * fhi[3] - alo * flo[3];
+          dU[3] -= tabv(G, 0, TAB_AMHI, px) * fhi[3] - tabv(G, 0, TAB_AMLO, px) * flo[3];
+        }
+      }
+      const int p1 = p1_of(m), p2 = p2_of(m);
+      T met0 = (GEOM != kCart) ? tabv(G, 0, TAB_MET, px) : T(1);
+      // direction 1
+      if constexpr (NDIM >= 2) {
+        T flo[4], fhi[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          if constexpr (TILE_Y) {
+            flo[v] = v < NV ? s_fy[v][ty][tx] : T(0);
+            fhi[v] = v < NV ? s_fy[v][ty + 1][tx] : T(0);
+          } else {
+            flo[v] = zlo[v];
+            fhi[v] = zhi[v];
+          }
+        }
+        T alo = tabv(G, 1, TAB_ALO, p1), ahi = tabv(G, 1, TAB_AHI, p1);
+        if (GEOM != kCart) {
+          alo *= met0;
+          ahi *= met0;
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= ahi * fhi[v] - alo * flo[v];
+        if (GEOM == kSph && NC >= 3) {
+          dU[3] += ahi * fhi[3] - alo * flo[3];
+          dU[3] -= met0 * (tabv(G, 1, TAB_AMHI, p1) * fhi[3] - tabv(G, 1, TAB_AMLO, p1) * flo[3]);
+        }
+      }
+      // direction 2
+      if constexpr (NDIM >= 3) {
+        T alo = tabv(G, 2, TAB_ALO, p2), ahi = tabv(G, 2, TAB_AHI, p2);
+        if (GEOM == kSph) {
+          T f = met0 * tabv(G, 1, TAB_PHF, p1);
+          alo *= f;
+          ahi *= f;
+        }
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= ahi * zhi[v] - alo * zlo[v];
+      }
+      const T (&u)[4] = q[1];
+      // inactive theta of a 1D spherical grid: one cell whose faces carry the
+      // cell's own physical flux
+      if constexpr (GEOM == kSph && NDIM == 1) {
+        T fl[4] = {0, 0, 0, 0}, lm, lp;
+        state_flux<T, NC, 1>(u, chat, fl, lm, lp);
+        T alo = met0 * tabv(G, 1, TAB_ALO, 0), ahi = met0 * tabv(G, 1, TAB_AHI, 0);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= (ahi - alo) * fl[v];
+        if (NC >= 3) {
+          dU[3] += (ahi - alo) * fl[3];
+          dU[3] -= met0 * (tabv(G, 1, TAB_AMHI, 0) - tabv(G, 1, TAB_AMLO, 0)) * fl[3];
+        }
+      }
+      // geometric sources of the cell-centred pressure tensor of U^n
+      if constexpr (GEOM != kCart) {
+        T pa, pb;
+        pressure<T, NC>(u, pa, pb);
+        if constexpr (GEOM == kCyl) {
+          T Fp = NC >= 2 ? u[2] : T(0);
+          dU[1] += chat * met0 * (pa + pb * Fp * Fp);
+        } else {
+          T Ft = NC >= 2 ? u[2] : T(0), Fp = NC >= 3 ? u[3] : T(0);
+          T Ptt = pa + pb * Ft * Ft, Ppp = pa + pb * Fp * Fp, Prt = pb * u[1] * Ft;
+          dU[1] += chat * met0 * (Ptt + Ppp);
+          if (NC >= 2) dU[2] += chat * met0 * (tabv(G, 1, TAB_MET, p1) * Ppp - Prt);
+        }
+      }
+      T Us[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+      if (Us[0] < a.efloor) {
+        Us[0] = a.efloor;
+        ++c_efloor;
+      }
+      // implicit coupling (Sect. 2.8)
+      CoupleOut co;
+      if constexpr (P::kSplit)
+        co = couple_split(a.cp, float(rho_m), float(e_m), float(kp_m), float(Us[0]), 0.f);
+      else
+        co = couple_fp64(a.cp, double(rho_m), double(e_m), double(kp_m), double(Us[0]), 0.0);
+      c_iters += co.iters;
+      c_itmax = max(c_itmax, (unsigned)co.iters);
+      c_fallback += co.fallback;
+      c_noconv += co.noconv;
+      if (co.noconv) status |= STATUS_NOCONV;
+      T En = Us[0] + T(co.dE);
+      T dE = T(co.dE);
+      if (En < a.efloor) {
+        En = a.efloor;
+        dE = En - Us[0];
+        ++c_efloor;
+      }
+      // Eq. (source_discrete2): F^{n+1} (1 + dt chat chi rho) = F*
+      T x = a.dt * chat * chi_m * T(rho_m);
+      T Fn[3], dF[3];
+      T inv = Ops<T>::rcp(T(1) + x);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        if (v < NC) {
+          if constexpr (sizeof(T) == 8) {
+            Fn[v] = Us[1 + v] / (T(1) + x);
+            dF[v] = Fn[v] - Us[1 + v];
+          } else {
+            dF[v] = -Us[1 + v] * x * inv;
+            Fn[v] = Us[1 + v] + dF[v];
+          }
+        } else {
+          Fn[v] = dF[v] = T(0);
+        }
+      }
+      T nF2 = Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2];
+      if (nF2 > En * En) {
+        T r = Ops<T>::div(En, Ops<T>::sqrt_(nF2));
+#pragma unroll
+        for (int v = 0; v < NC; ++v) {
+          Fn[v] *= r;
+          dF[v] = Fn[v] - Us[1 + v];
+        }
+        ++c_fclip;
+      }
+      // Sect. 2.7: E_gas + (c/chat) E_r and m + F/chat are conserved; the
+      // internal energy takes the kinetic-energy change.
+      T mn[3], dke = T(0);
+#pragma unroll
+      for (int v = 0; v < 3; ++v) {
+        T dm = -dF[v] * a.inv_chat;
+        mn[v] = mom[v] + dm;
+        dke += dm * (T(2) * mom[v] + dm);
+      }
+      T rr = T(rho_m);
+      T en;
+      if constexpr (sizeof(T) == 8)
+        en = T(e_m) - a.ratio * dE - dke / (T(2) * rr);
+      else
+        en = T(e_m) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
+      if (!(En > T(0)) || !(en == en) || !(en > T(0))) status |= STATUS_NONPHYS;
+      // stores: own cell and the ghost copies it feeds
+      a.out.E[ic] = S(En);
+#pragma unroll
+      for (int v = 0; v < NC; ++v) {
+        a.out.F[v][ic] = S(Fn[v]);
+        a.out.m[v][ic] = S(mn[v]);
+      }
+      a.out.e[ic] = S(en);
+      const int ci[3] = {cx, TILE_Y ? cy : (MARCH ? m : 0), TILE_Y ? m : 0};
+#pragma unroll
+      for (int d = 0; d < NDIM; ++d) {
+        const int n = Dm.n[d];
+        const int i = ci[d];
+        if (i >= 2 && i < n - 2) continue;
+        const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
+#pragma unroll
+        for (int gslot = 0; gslot < 4; ++gslot) {
+          int gpos = gslot < 2 ? gslot - 2 : n + gslot - 2;  // -2, -1, n, n+1
+          int src;
+          if (gslot < 2)
+            src = Dm.bc_lo[d] ? ((gpos % n) + n) % n : 0;
+          else
+            src = Dm.bc_hi[d] ? gpos % n : n - 1;
+          if (src != i) continue;
+          long long ig = ic + (long long)(gpos - i) * stride;
+          a.out.E[ig] = S(En);
+#pragma unroll
+          for (int v = 0; v < NC; ++v) a.out.F[v][ig] = S(Fn[v]);
+          a.out.e[ig] = S(en);
+        }
+      }
+    }
+    if constexpr (MARCH) {
+#pragma unroll
+      for (int v = 0; v < 4; ++v) {
+        q[0][v] = q[1][v];
+        q[1][v] = q[2][v];
+        q[2][v] = q[3][v];
+        hiS[v] = hiN[v];
+        zlo[v] = zhi[v];
+      }
+      tau_m = tau_n;
+      kp_m = kp_n;
+      chi_m = chi_n;
+      rho_m = rho_n;
+      e_m = e_n;
+    }
+  }
+
+  // block reduction of the counters, one atomic per counter per CTA
+  unsigned long long v[ST_N] = {c_fix, c_efloor, c_fclip, c_iters, c_itmax, c_fallback, c_noconv, 0};
+#pragma unroll
+  for (int k = 0; k < ST_N; ++k) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+      unsigned long long o = __shfl_down_sync(0xffffffffu, v[k], off);
+      v[k] = (k == ST_ITMAX) ? (o > v[k] ? o : v[k]) : v[k] + o;
+    }
+  }
+  __syncthreads();
+  if ((tid & 31) == 0) {
+#pragma unroll
+    for (int k = 0; k < ST_N; ++k) {
+      if (k == ST_ITMAX)
+        atomicMax(&s_red[k], v[k]);
+      else if (v[k])
+        atomicAdd(&s_red[k], v[k]);
+    }
+  }
+  if (status) atomicOr(a.status, status);
+  __syncthreads();
+  if (tid < ST_N && s_red[tid]) {
+    if (tid == ST_ITMAX)
+      atomicMax(a.stats + tid, s_red[tid]);
+    else
+      atomicAdd(a.stats + tid, s_red[tid]);
+  }
+}
+
+}  // namespace m1

@@ -1,0 +1,755 @@
+// rad_api.cu -- host side of the C ABI declared in include/rad.h: argument
+// validation, geometry tables, workspace layout, host<->device transfers
+// (pack/unpack kernels between the caller's flat arrays and the padded
+// ghost-layer layout) and the step dispatch.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "m1_internal.h"
+#include "rad.h"
+#include "step_launch.h"
+
+using namespace m1;
+
+struct rad_ctx {
+  // description
+  int ndim = 1, n[3] = {1, 1, 1}, geom = 0;
+  int bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
+  std::vector<double> xf[3];
+  rad_opacity opac{};
+  std::vector<float> table32;
+  std::vector<double> table64;
+  rad_params par{};
+  int nc = 3;            // flux/momentum components carried internally
+  double dt_cfl = 0.0;
+  // layout
+  StepDims dims{};
+  size_t pcells = 0;     // padded cells per array
+  size_t N = 0;          // interior cells
+  size_t esize = 8;      // bytes per stored value
+  std::vector<double> tab64[3];
+  std::vector<float> tab32[3];
+  int len[3] = {1, 1, 1};
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  size_t off_state[2][8] = {};  // E, F0..F2, e, m0..m2 per buffer
+  size_t off_rho = 0, off_tab = 0, off_tab_dir[3] = {}, off_op32 = 0, off_op64 = 0;
+  size_t off_stats = 0, off_status = 0, off_stage = 0;
+  size_t total = 0;
+  cudaStream_t stream = nullptr;
+  int cur = 0;
+  bool have_gas = false, have_rad = false;
+  uint64_t steps = 0;
+  LaunchFn launch = nullptr;
+};
+
+static const char* kMsg[] = {"ok",
+                             "invalid argument",
+                             "workspace missing or too small / out of memory",
+                             "CUDA runtime error",
+                             "non-physical input or state",
+                             "coupling iteration did not converge",
+                             "bounded device wait ran out",
+                             "unsupported request"};
+
+extern "C" const char* rad_strerror(rad_status s) {
+  int i = int(s);
+  if (i < 0 || i > 7) return "unknown status";
+  return kMsg[i];
+}
+
+extern "C" rad_status rad_default_params(rad_params* p) {
+  if (!p) return RAD_EINVAL;
+  std::memset(p, 0, sizeof(*p));
+  p->chat = 1.0;
+  p->c = 1.0;
+  p->a_rad = 1.0;
+  p->gamma_gas = 5.0 / 3.0;
+  p->mu = 1.0;
+  p->cfl = 0.4;
+  p->e_floor = 1e-30;
+  p->precision = RAD_FP64;
+  p->implicit_mode = RAD_LINEARIZED_ONCE;
+  p->newton_rtol = 1e-12;
+  p->newton_maxit = 50;
+  p->ncomp = 3;
+  return RAD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// geometry tables
+// ---------------------------------------------------------------------------
+
+static int map_index(int i, int n, int lo_periodic, int hi_periodic) {
+  if (i < 0) return lo_periodic ? ((i % n) + n) % n : 0;
+  if (i >= n) return hi_periodic ? i % n : n - 1;
+  return i;
+}
+
+// Centre of cell i (ghosts: mirrored for outflow, shifted by the period).
+static double centre_ext(const std::vector<double>& x, int n, int i, int lo_p, int hi_p) {
+  if (i >= 0 && i < n) return 0.5 * (x[i] + x[i + 1]);
+  double L = x[n] - x[0];
+  if (i < 0) return lo_p ? centre_ext(x, n, i + n, lo_p, hi_p) - L
+                         : 2.0 * x[0] - centre_ext(x, n, -1 - i, lo_p, hi_p);
+  return hi_p ? centre_ext(x, n, i - n, lo_p, hi_p) + L
+              : 2.0 * x[n] - centre_ext(x, n, 2 * n - 1 - i, lo_p, hi_p);
+}
+
+static void build_tables(rad_ctx* c) {
+  for (int d = 0; d < 3; ++d) {
+    const int n = c->n[d];
+    const int g = d < c->ndim ? 2 : 0;
+    const int len = n + 2 * g;
+    c->len[d] = len;
+    const std::vector<double>& x = c->xf[d];
+    const int lp = c->bc_lo[d] == RAD_BC_PERIODIC, hp = c->bc_hi[d] == RAD_BC_PERIODIC;
+    std::vector<double>& T = c->tab64[d];
+    T.assign(size_t(TAB_N) * len, 0.0);
+    auto at = [&](int slot, int ip) -> double& { return T[size_t(slot) * len + ip]; };
+    for (int ip = 0; ip < len; ++ip) {
+      const int i = ip - g;
+      const int mi = map_index(i, n, lp, hp);
+      const double xc = centre_ext(x, n, i, lp, hp);
+      if (ip + 1 < len) at(TAB_IDXC, ip) = 1.0 / (centre_ext(x, n, i + 1, lp, hp) - xc);
+      if (i >= 0 && i <= n) at(TAB_HLO, ip) = x[i] - xc;
+      if (i + 1 >= 0 && i + 1 <= n) at(TAB_HHI, ip) = x[i + 1] - xc;
+      const double a = x[mi], b = x[mi + 1];
+      at(TAB_WID, ip) = b - a;
+      if (d == 0) at(TAB_RC, ip) = 0.5 * (a + b);
+      if (d == 1 && c->geom == RAD_SPHERICAL) at(TAB_RC, ip) = std::sin(0.5 * (a + b));
+      if (i < 0 || i >= n) continue;
+      // interior: area/volume factors
+      if (c->geom == RAD_CARTESIAN || (c->geom == RAD_CYLINDRICAL && d != 0) ||
+          (c->geom == RAD_SPHERICAL && d == 2)) {
+        at(TAB_ALO, ip) = at(TAB_AHI, ip) = 1.0 / (b - a);
+      } else if (c->geom == RAD_CYLINDRICAL) {  // d == 0, radius R
+        double den = b * b - a * a;
+        at(TAB_ALO, ip) = 2.0 * a / den;
+        at(TAB_AHI, ip) = 2.0 * b / den;
+        double invRc = 2.0 / (a + b);
+        at(TAB_MET, ip) = invRc;
+        at(TAB_AMLO, ip) = at(TAB_ALO, ip) * a * invRc;
+        at(TAB_AMHI, ip) = at(TAB_AHI, ip) * b * invRc;
+      } else if (d == 0) {  // spherical radius
+        double den = b * b * b - a * a * a;
+        at(TAB_ALO, ip) = 3.0 * a * a / den;
+        at(TAB_AHI, ip) = 3.0 * b * b / den;
+        double invrt = 3.0 * (b * b - a * a) / (2.0 * den);
+        at(TAB_MET, ip) = invrt;
+        at(TAB_AMLO, ip) = at(TAB_ALO, ip) * a * invrt;
+        at(TAB_AMHI, ip) = at(TAB_AHI, ip) * b * invrt;
+      } else {  // spherical theta
+        double dcos = std::cos(a) - std::cos(b);
+        double sc = std::sin(0.5 * (a + b));
+        at(TAB_ALO, ip) = std::sin(a) / dcos;
+        at(TAB_AHI, ip) = std::sin(b) / dcos;
+        at(TAB_MET, ip) = (std::sin(b) - std::sin(a)) / dcos;
+        at(TAB_AMLO, ip) = at(TAB_ALO, ip) * std::sin(a) / sc;
+        at(TAB_AMHI, ip) = at(TAB_AHI, ip) * std::sin(b) / sc;
+        at(TAB_PHF, ip) = (b - a) / dcos;
+      }
+    }
+    c->tab32[d].resize(T.size());
+    for (size_t k = 0; k < T.size(); ++k) c->tab32[d][k] = float(T[k]);
+  }
+}
+
+// dt = cfl / max over cells of sum_d chat / h_d (Sect. 2.4 item 10).
+static double cfl_dt(const rad_ctx* c) {
+  const std::vector<double>*x = c->xf;
+  double worst = 0.0;
+  for (int k = 0; k < c->n[2]; ++k) {
+    double w2 = x[2][k + 1] - x[2][k];
+    for (int j = 0; j < c->n[1]; ++j) {
+      double w1 = x[1][j + 1] - x[1][j];
+      double sth = std::sin(0.5 * (x[1][j] + x[1][j + 1]));
+      for (int i = 0; i < c->n[0]; ++i) {
+        double w0 = x[0][i + 1] - x[0][i];
+        double rc = 0.5 * (x[0][i] + x[0][i + 1]);
+        double h[3] = {w0, w1, w2};
+        if (c->geom == RAD_CYLINDRICAL) h[1] = rc * w1;
+        if (c->geom == RAD_SPHERICAL) {
+          h[1] = rc * w1;
+          h[2] = rc * sth * w2;
+        }
+        double s = 0.0;
+        for (int d = 0; d < c->ndim; ++d) s += c->par.chat / h[d];
+        worst = std::max(worst, s);
+      }
+    }
+  }
+  return c->par.cfl / worst;
+}
+
+// ---------------------------------------------------------------------------
+// creation and workspace
+// ---------------------------------------------------------------------------
+
+static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_opacity* opacity,
+                                 const rad_params* params, rad_ctx** out) {
+  if (!grid || !opacity || !params || !out) return RAD_EINVAL;
+  if (grid->ndim < 1 || grid->ndim > 3) return RAD_EINVAL;
+  if (geometry < 0 || geometry > 2) return RAD_EINVAL;
+  const rad_params& p = *params;
+  if (!finite_pos(p.chat) || !(p.c >= p.chat) || !std::isfinite(p.c) || !finite_pos(p.a_rad) ||
+      !(p.gamma_gas > 1.0) || !finite_pos(p.mu) || !(p.cfl > 0.0 && p.cfl <= 1.0) ||
+      !finite_pos(p.e_floor))
+    return RAD_EINVAL;
+  if (p.precision != RAD_FP64 && p.precision != RAD_FP32_SPLIT) return RAD_EINVAL;
+  if (p.implicit_mode != RAD_LINEARIZED_ONCE && p.implicit_mode != RAD_NEWTON) return RAD_EINVAL;
+  if (p.implicit_mode == RAD_NEWTON && (!(p.newton_rtol > 0.0) || p.newton_maxit < 1))
+    return RAD_EINVAL;
+  if (p.ncomp < 1 || p.ncomp > 3) return RAD_EINVAL;
+  size_t N = 1;
+  for (int d = 0; d < 3; ++d) {
+    int n = grid->n[d];
+    if (n < 1 || (d >= grid->ndim && n != 1) || !grid->xface[d]) return RAD_EINVAL;
+    if (n > (1 << 24)) return RAD_EINVAL;
+    for (int i = 0; i < n; ++i)
+      if (!(grid->xface[d][i + 1] > grid->xface[d][i]) || !std::isfinite(grid->xface[d][i + 1]))
+        return RAD_EINVAL;
+    if (d < grid->ndim) {
+      int lo = grid->bc_lo[d], hi = grid->bc_hi[d];
+      if (lo < 0 || lo > 1 || hi < 0 || hi > 1 || lo != hi) return RAD_EINVAL;
+    }
+    N *= size_t(n);
+  }
+  if (N > (size_t(1) << 34)) return RAD_EINVAL;
+  if (geometry != RAD_CARTESIAN && grid->xface[0][0] < 0.0) return RAD_EINVAL;
+  if (geometry == RAD_SPHERICAL && (grid->xface[1][0] < 0.0 || grid->xface[1][grid->n[1]] > M_PI + 1e-12))
+    return RAD_EINVAL;
+  const rad_opacity& o = *opacity;
+  if (o.kind < 0 || o.kind > 2) return RAD_EINVAL;
+  if (o.kind == RAD_OPAC_CONST && !(o.kappa_p >= 0 && o.kappa_r >= 0 && o.sigma >= 0))
+    return RAD_EINVAL;
+  if (o.kind == RAD_OPAC_POWERLAW &&
+      !(o.k0 >= 0 && o.kmin >= 0 && o.kmax >= o.kmin && o.sigma_ratio >= 0))
+    return RAD_EINVAL;
+  if (o.kind == RAD_OPAC_TABLE &&
+      (o.nrho < 2 || o.nT < 2 || !o.table_log10_kappa || !(o.lrho1 > o.lrho0) ||
+       !(o.lT1 > o.lT0) || !(o.sigma_ratio >= 0)))
+    return RAD_EINVAL;
+
+  rad_ctx* c = new (std::nothrow) rad_ctx();
+  if (!c) return RAD_ENOMEM;
+  c->ndim = grid->ndim;
+  c->geom = geometry;
+  for (int d = 0; d < 3; ++d) {
+    c->n[d] = grid->n[d];
+    c->bc_lo[d] = d < grid->ndim ? grid->bc_lo[d] : 0;
+    c->bc_hi[d] = d < grid->ndim ? grid->bc_hi[d] : 0;
+    c->xf[d].assign(grid->xface[d], grid->xface[d] + grid->n[d] + 1);
+  }
+  c->opac = o;
+  if (o.kind == RAD_OPAC_TABLE) {
+    c->table32.assign(o.table_log10_kappa, o.table_log10_kappa + size_t(o.nrho) * o.nT);
+    c->table64.assign(c->table32.begin(), c->table32.end());
+  } else {
+    c->table32.assign(4, 0.f);
+    c->table64.assign(4, 0.0);
+  }
+  c->opac.table_log10_kappa = nullptr;
+  c->par = p;
+  c->N = N;
+  c->nc = (geometry == RAD_CARTESIAN) ? std::max(p.ncomp, grid->ndim) : 3;
+  c->esize = p.precision == RAD_FP64 ? 8 : 4;
+  build_tables(c);
+  c->dt_cfl = cfl_dt(c);
+  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc);
+  if (!c->launch) {
+    delete c;
+    return RAD_EUNSUPPORTED;
+  }
+  // padded layout
+  StepDims& D = c->dims;
+  D.ndim = c->ndim;
+  for (int d = 0; d < 3; ++d) {
+    D.n[d] = c->n[d];
+    D.g[d] = d < c->ndim ? 2 : 0;
+    D.pn[d] = c->n[d] + 2 * D.g[d];
+    D.bc_lo[d] = c->bc_lo[d];
+    D.bc_hi[d] = c->bc_hi[d];
+  }
+  const int align_elems = int(16 / c->esize);
+  D.pn[0] = (D.pn[0] + align_elems - 1) / align_elems * align_elems;
+  D.sy = D.pn[0];
+  D.sz = (long long)D.pn[0] * D.pn[1];
+  c->pcells = size_t(D.pn[0]) * D.pn[1] * D.pn[2];
+  // workspace offsets (256-byte aligned pieces)
+  size_t off = 0;
+  auto take = [&](size_t bytes) {
+    size_t o2 = off;
+    off += (bytes + 255) / 256 * 256;
+    return o2;
+  };
+  const size_t arr = c->pcells * c->esize;
+  for (int b = 0; b < 2; ++b)
+    for (int k = 0; k < 8; ++k) {
+      int comp = (k >= 1 && k <= 3) ? k - 1 : (k >= 5 ? k - 5 : 0);
+      bool used = (k == 0 || k == 4) || comp < c->nc;
+      c->off_state[b][k] = used ? take(arr) : size_t(-1);
+    }
+  c->off_rho = take(arr);
+  const size_t tsz = c->esize;
+  for (int d = 0; d < 3; ++d) c->off_tab_dir[d] = take(size_t(TAB_N) * c->len[d] * tsz);
+  c->off_op32 = take(c->table32.size() * 4);
+  c->off_op64 = take(c->table64.size() * 8);
+  c->off_stats = take(sizeof(unsigned long long) * ST_N);
+  c->off_status = take(sizeof(int) * 4);
+  c->off_stage = take(3 * N * c->esize);
+  c->total = off;
+  *out = c;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_workspace_size(const rad_ctx* c, size_t* bytes) {
+  if (!c || !bytes) return RAD_EINVAL;
+  *bytes = c->total;
+  return RAD_OK;
+}
+
+static rad_status cuda_err(cudaError_t e) { return e == cudaSuccess ? RAD_OK : RAD_ECUDA; }
+
+static rad_status upload_static(rad_ctx* c) {
+  cudaError_t e;
+  for (int d = 0; d < 3; ++d) {
+    const void* src = c->esize == 8 ? (const void*)c->tab64[d].data() : (const void*)c->tab32[d].data();
+    e = cudaMemcpyAsync(c->ws + c->off_tab_dir[d], src, size_t(TAB_N) * c->len[d] * c->esize,
+                        cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return RAD_ECUDA;
+  }
+  e = cudaMemcpyAsync(c->ws + c->off_op32, c->table32.data(), c->table32.size() * 4,
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return RAD_ECUDA;
+  e = cudaMemcpyAsync(c->ws + c->off_op64, c->table64.data(), c->table64.size() * 8,
+                      cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return RAD_ECUDA;
+  e = cudaMemsetAsync(c->ws + c->off_stats, 0, sizeof(unsigned long long) * ST_N + 256, c->stream);
+  if (e != cudaSuccess) return RAD_ECUDA;
+  e = cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(int) * 4, c->stream);
+  if (e != cudaSuccess) return RAD_ECUDA;
+  return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
+extern "C" rad_status rad_bind_workspace(rad_ctx* c, void* ptr, size_t bytes) {
+  if (!c || !ptr) return RAD_EINVAL;
+  if (reinterpret_cast<uintptr_t>(ptr) % 256) return RAD_EINVAL;
+  if (bytes < c->total) return RAD_ENOMEM;
+  if (c->ws_owned) {
+    cudaFree(c->ws);
+    c->ws_owned = false;
+  }
+  c->ws = static_cast<char*>(ptr);
+  c->ws_bytes = bytes;
+  c->have_gas = c->have_rad = false;
+  return upload_static(c);
+}
+
+extern "C" rad_status rad_alloc_workspace(rad_ctx* c) {
+  if (!c) return RAD_EINVAL;
+  void* p = nullptr;
+  if (cudaMalloc(&p, c->total) != cudaSuccess) return RAD_ENOMEM;
+  rad_status s = rad_bind_workspace(c, p, c->total);
+  if (s != RAD_OK) {
+    cudaFree(p);
+    return s;
+  }
+  c->ws_owned = true;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_set_stream(rad_ctx* c, void* stream) {
+  if (!c) return RAD_EINVAL;
+  c->stream = static_cast<cudaStream_t>(stream);
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_dt(const rad_ctx* c, double* dt) {
+  if (!c || !dt) return RAD_EINVAL;
+  *dt = c->dt_cfl;
+  return RAD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// pack / unpack kernels
+// ---------------------------------------------------------------------------
+
+enum { PK_COPY = 0, PK_MOM = 1, PK_EINT = 2 };
+
+// Fills every padded cell (ghosts included) of dst from the flat array src
+// (x fastest) through the boundary mapping; PK_MOM multiplies by rho (flat),
+// PK_EINT by rho * cvfac.
+template <class S>
+__global__ void pack_kernel(S* __restrict__ dst, const S* __restrict__ src,
+                            const S* __restrict__ rho, StepDims D, int mode, double cvfac) {
+  const long long total = (long long)D.pn[0] * D.pn[1] * D.pn[2];
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    int c[3];
+    long long r = p;
+    c[0] = int(r % D.pn[0]);
+    r /= D.pn[0];
+    c[1] = int(r % D.pn[1]);
+    c[2] = int(r / D.pn[1]);
+    long long lin = 0, mul = 1;
+    for (int d = 0; d < 3; ++d) {
+      int i = c[d] - D.g[d];
+      int n = D.n[d];
+      if (i < 0) i = D.bc_lo[d] ? ((i % n) + n) % n : 0;
+      if (i >= n) i = D.bc_hi[d] ? i % n : n - 1;
+      lin += (long long)i * mul;
+      mul *= n;
+    }
+    S v = src[lin];
+    if (mode == PK_MOM) v = v * rho[lin];
+    if (mode == PK_EINT) v = S(double(v) * double(rho[lin]) * cvfac);
+    dst[p] = v;
+  }
+}
+
+enum { UN_COPY = 0, UN_TEMP = 1 };
+
+template <class S>
+__global__ void unpack_kernel(S* __restrict__ dst, const S* __restrict__ src,
+                              const S* __restrict__ rho, StepDims D, int mode, double cvfac) {
+  const long long N = (long long)D.n[0] * D.n[1] * D.n[2];
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long r = q;
+    int i = int(r % D.n[0]);
+    r /= D.n[0];
+    int j = int(r % D.n[1]);
+    int k = int(r / D.n[1]);
+    long long p = (long long)(i + D.g[0]) + D.sy * (j + D.g[1]) + D.sz * (k + D.g[2]);
+    S v = src[p];
+    if (mode == UN_TEMP) v = S(double(v) / (double(rho[p]) * cvfac));
+    dst[q] = v;
+  }
+}
+
+static int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  return int(std::min<long long>(std::max<long long>(b, 1), 148 * 32));
+}
+
+template <class S>
+static rad_status pack(rad_ctx* c, S* dst, const S* src, const S* rho, int mode) {
+  double cvfac = 1.0 / (c->par.mu * (c->par.gamma_gas - 1.0));
+  pack_kernel<S><<<grid_for((long long)c->pcells), 256, 0, c->stream>>>(dst, src, rho, c->dims, mode,
+                                                                    cvfac);
+  return cuda_err(cudaGetLastError());
+}
+
+static void* state_ptr(rad_ctx* c, int b, int k) {
+  size_t o = c->off_state[b][k];
+  return o == size_t(-1) ? nullptr : c->ws + o;
+}
+
+// Copies `count` values from the caller (host or device) to a device flat
+// array and returns it: the staging area for host input, else the pointer.
+static const void* stage_in(rad_ctx* c, const void* src, size_t count, int slot, int on_device,
+                            rad_status* st) {
+  *st = RAD_OK;
+  if (on_device) return src;
+  char* dst = c->ws + c->off_stage + size_t(slot) * c->N * c->esize;
+  if (cudaMemcpyAsync(dst, src, count * c->esize, cudaMemcpyHostToDevice, c->stream) !=
+      cudaSuccess)
+    *st = RAD_ECUDA;
+  return dst;
+}
+
+template <class S>
+static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const void* T, int dev) {
+  rad_status st;
+  // rho first (flat copy kept in stage slot 0 while m and e are built)
+  const S* r = static_cast<const S*>(stage_in(c, rho, c->N, 0, dev, &st));
+  if (st) return st;
+  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_rho), r, r, PK_COPY))) return st;
+  // v: ncomp arrays (host input goes through stage slot 1 one component at a
+  // time); internal components beyond ncomp are zero
+  for (int comp = 0; comp < c->nc; ++comp) {
+    const S* src = nullptr;
+    if (comp < c->par.ncomp) {
+      if (dev) {
+        src = static_cast<const S*>(v) + comp * c->N;
+      } else {
+        char* slot = c->ws + c->off_stage + c->N * c->esize;
+        if (cudaMemcpyAsync(slot, static_cast<const char*>(v) + comp * c->N * c->esize,
+                            c->N * c->esize, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+          return RAD_ECUDA;
+        src = reinterpret_cast<const S*>(slot);
+      }
+    }
+    for (int b = 0; b < 2; ++b) {
+      S* dst = static_cast<S*>(state_ptr(c, b, 5 + comp));
+      if (src) {
+        if ((st = pack<S>(c, dst, src, r, PK_MOM))) return st;
+      } else if (cudaMemsetAsync(dst, 0, c->pcells * c->esize, c->stream) != cudaSuccess) {
+        return RAD_ECUDA;
+      }
+    }
+  }
+  const S* t = static_cast<const S*>(stage_in(c, T, c->N, 2, dev, &st));
+  if (st) return st;
+  for (int b = 0; b < 2; ++b)
+    if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 4)), t, r, PK_EINT))) return st;
+  c->have_gas = true;
+  return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
+extern "C" rad_status rad_set_gas(rad_ctx* c, const void* rho, const void* v, const void* T,
+                                  int on_device) {
+  if (!c || !rho || !v || !T) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  return c->esize == 8 ? set_gas_t<double>(c, rho, v, T, on_device)
+                       : set_gas_t<float>(c, rho, v, T, on_device);
+}
+
+template <class S>
+static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
+  rad_status st;
+  const S* e = static_cast<const S*>(stage_in(c, E, c->N, 0, dev, &st));
+  if (st) return st;
+  for (int b = 0; b < 2; ++b)
+    if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 0)), e, e, PK_COPY))) return st;
+  for (int comp = 0; comp < c->nc; ++comp) {
+    for (int b = 0; b < 2; ++b) {
+      S* dst = static_cast<S*>(state_ptr(c, b, 1 + comp));
+      if (comp < c->par.ncomp) {
+        const S* src;
+        if (dev) {
+          src = static_cast<const S*>(F) + comp * c->N;
+        } else {
+          char* slot = c->ws + c->off_stage + c->N * c->esize;
+          if (b == 0 && cudaMemcpyAsync(slot, static_cast<const char*>(F) + comp * c->N * c->esize,
+                                        c->N * c->esize, cudaMemcpyHostToDevice,
+                                        c->stream) != cudaSuccess)
+            return RAD_ECUDA;
+          src = reinterpret_cast<const S*>(slot);
+        }
+        if ((st = pack<S>(c, dst, src, src, PK_COPY))) return st;
+      } else if (cudaMemsetAsync(dst, 0, c->pcells * c->esize, c->stream) != cudaSuccess) {
+        return RAD_ECUDA;
+      }
+    }
+  }
+  c->have_rad = true;
+  return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
+extern "C" rad_status rad_set_rad(rad_ctx* c, const void* E, const void* F, int on_device) {
+  if (!c || !E || !F) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  return c->esize == 8 ? set_rad_t<double>(c, E, F, on_device)
+                       : set_rad_t<float>(c, E, F, on_device);
+}
+
+// ---------------------------------------------------------------------------
+// stepping
+// ---------------------------------------------------------------------------
+
+template <class S>
+static void fill_fields(rad_ctx* c, int b, Fields<S>& f) {
+  f.E = static_cast<S*>(state_ptr(c, b, 0));
+  for (int q = 0; q < 3; ++q) {
+    f.F[q] = static_cast<S*>(state_ptr(c, b, 1 + q));
+    f.m[q] = static_cast<S*>(state_ptr(c, b, 5 + q));
+  }
+  f.e = static_cast<S*>(state_ptr(c, b, 4));
+}
+
+template <class P>
+static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
+  using S = typename P::S;
+  using T = typename P::T;
+  a.dim = c->dims;
+  fill_fields<S>(c, c->cur, a.in);
+  fill_fields<S>(c, 1 - c->cur, a.out);
+  a.rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
+  for (int d = 0; d < 3; ++d) {
+    a.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
+    a.geo.len[d] = c->len[d];
+  }
+  const rad_opacity& o = c->opac;
+  OpacityDev& od = a.opac;
+  od.kind = o.kind;
+  od.kappa_p = o.kappa_p;
+  od.kappa_r = o.kappa_r;
+  od.sigma = o.sigma;
+  od.k0 = o.k0;
+  od.a_rho = o.a_rho;
+  od.b_T = o.b_T;
+  od.kmin = o.kmin;
+  od.kmax = o.kmax;
+  od.sigma_ratio = o.sigma_ratio;
+  od.nrho = o.nrho;
+  od.nT = o.nT;
+  od.lrho0 = o.lrho0;
+  od.lT0 = o.lT0;
+  od.sr = o.kind == RAD_OPAC_TABLE ? (o.nrho - 1) / (o.lrho1 - o.lrho0) : 0.0;
+  od.sT = o.kind == RAD_OPAC_TABLE ? (o.nT - 1) / (o.lT1 - o.lT0) : 0.0;
+  od.tab64 = reinterpret_cast<const double*>(c->ws + c->off_op64);
+  od.tab32 = reinterpret_cast<const float*>(c->ws + c->off_op32);
+  od.linear_rho = (o.kind == RAD_OPAC_POWERLAW && o.a_rho == 1.0 && o.b_T == 0.0);
+  CoupleParams& cp = a.cp;
+  cp.dt = dt;
+  cp.chat = c->par.chat;
+  cp.c = c->par.c;
+  cp.a_rad = c->par.a_rad;
+  cp.cvfac = 1.0 / (c->par.mu * (c->par.gamma_gas - 1.0));
+  cp.rtol = c->par.newton_rtol;
+  cp.maxit = c->par.newton_maxit;
+  cp.newton = c->par.implicit_mode == RAD_NEWTON;
+  a.chat = T(c->par.chat);
+  a.dt = T(dt);
+  a.efloor = T(c->par.e_floor);
+  a.ratio = T(c->par.c / c->par.chat);
+  a.inv_chat = T(1.0 / c->par.chat);
+  a.stats = reinterpret_cast<unsigned long long*>(c->ws + c->off_stats);
+  a.status = reinterpret_cast<int*>(c->ws + c->off_status);
+  a.chunk = 0;
+}
+
+extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
+  if (!c || nsteps < 0) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
+  if (!(dt > 0.0)) dt = c->dt_cfl;
+  if (!std::isfinite(dt)) return RAD_EINVAL;
+  for (int s = 0; s < nsteps; ++s) {
+    cudaError_t e;
+    if (c->esize == 8) {
+      StepArgs<Fp64> a{};
+      fill_args<Fp64>(c, a, dt);
+      e = c->launch(&a, c->stream);
+    } else {
+      StepArgs<Split> a{};
+      fill_args<Split>(c, a, dt);
+      e = c->launch(&a, c->stream);
+    }
+    if (e != cudaSuccess) return RAD_ECUDA;
+    c->cur = 1 - c->cur;
+    ++c->steps;
+  }
+  return RAD_OK;
+}
+
+extern "C" int rad_launches_per_step(const rad_ctx* c) { return c ? 1 : 0; }
+
+// ---------------------------------------------------------------------------
+// reads, status, counters
+// ---------------------------------------------------------------------------
+
+static rad_status take_status(rad_ctx* c) {
+  int st = 0;
+  if (cudaMemcpyAsync(&st, c->ws + c->off_status, sizeof(int), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
+  if (st) cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(int), c->stream);
+  if (st & STATUS_TIMEOUT) return RAD_ETIMEOUT;
+  if (st & STATUS_NONPHYS) return RAD_ENONPHYS;
+  if (st & STATUS_NOCONV) return RAD_ENOCONV;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_sync(rad_ctx* c) {
+  if (!c) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
+  return take_status(c);
+}
+
+template <class S>
+static rad_status read_t(rad_ctx* c, int field, void* dst, int dev) {
+  const double cvfac = 1.0 / (c->par.mu * (c->par.gamma_gas - 1.0));
+  const S* rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
+  int ncomp = (field == RAD_FIELD_F || field == RAD_FIELD_M) ? c->par.ncomp : 1;
+  for (int comp = 0; comp < ncomp; ++comp) {
+    const S* src;
+    int mode = UN_COPY;
+    switch (field) {
+      case RAD_FIELD_E: src = static_cast<const S*>(state_ptr(c, c->cur, 0)); break;
+      case RAD_FIELD_F: src = static_cast<const S*>(state_ptr(c, c->cur, 1 + comp)); break;
+      case RAD_FIELD_EINT: src = static_cast<const S*>(state_ptr(c, c->cur, 4)); break;
+      case RAD_FIELD_M: src = static_cast<const S*>(state_ptr(c, c->cur, 5 + comp)); break;
+      case RAD_FIELD_T:
+        src = static_cast<const S*>(state_ptr(c, c->cur, 4));
+        mode = UN_TEMP;
+        break;
+      default: src = rho; break;
+    }
+    S* out = dev ? static_cast<S*>(dst) + comp * c->N
+                 : reinterpret_cast<S*>(c->ws + c->off_stage);
+    unpack_kernel<S><<<grid_for((long long)c->N), 256, 0, c->stream>>>(out, src, rho, c->dims, mode,
+                                                                   cvfac);
+    if (cudaGetLastError() != cudaSuccess) return RAD_ECUDA;
+    if (!dev) {
+      if (cudaMemcpyAsync(static_cast<char*>(dst) + comp * c->N * c->esize, out, c->N * c->esize,
+                          cudaMemcpyDeviceToHost, c->stream) != cudaSuccess)
+        return RAD_ECUDA;
+      if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
+    }
+  }
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_read(rad_ctx* c, int field, void* dst, size_t bytes, int on_device) {
+  if (!c || !dst || field < 0 || field > 5) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  int ncomp = (field == RAD_FIELD_F || field == RAD_FIELD_M) ? c->par.ncomp : 1;
+  if (bytes < size_t(ncomp) * c->N * c->esize) return RAD_EINVAL;
+  if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
+  rad_status s = c->esize == 8 ? read_t<double>(c, field, dst, on_device)
+                               : read_t<float>(c, field, dst, on_device);
+  if (s != RAD_OK) return s;
+  if (on_device) return RAD_OK;
+  return take_status(c);
+}
+
+extern "C" rad_status rad_get_stats(rad_ctx* c, rad_stats* out) {
+  if (!c || !out) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  unsigned long long v[ST_N] = {};
+  if (cudaMemcpyAsync(v, c->ws + c->off_stats, sizeof(v), cudaMemcpyDeviceToHost, c->stream) !=
+      cudaSuccess)
+    return RAD_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
+  out->fix = v[ST_FIX];
+  out->efloor = v[ST_EFLOOR];
+  out->fclip = v[ST_FCLIP];
+  out->iters = v[ST_ITERS];
+  out->itmax = v[ST_ITMAX];
+  out->fallback = v[ST_FALLBACK];
+  out->noconv = v[ST_NOCONV];
+  out->steps = c->steps;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_reset_stats(rad_ctx* c) {
+  if (!c) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  c->steps = 0;
+  return cuda_err(
+      cudaMemsetAsync(c->ws + c->off_stats, 0, sizeof(unsigned long long) * ST_N, c->stream));
+}
+
+extern "C" void rad_destroy(rad_ctx* c) {
+  if (!c) return;
+  if (c->ws_owned && c->ws) {
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->ws);
+  }
+  delete c;
+}

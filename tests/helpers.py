@@ -1,0 +1,49 @@
+"""Shared helpers of the parity tests: run a problem on the GPU through the
+C ABI and on the CPU oracle, and compare them with the per-cell error metric
+(|dE|/|E|, |dF|/E, |de|/|e|, |dm|/(|m| + E/chat))."""
+import numpy as np
+
+import oracle
+import workloads as W
+
+
+def rounded(p, dtype):
+    """Copy of the problem with every field rounded to the storage dtype."""
+    q = p.copy()
+    for k in ("rho", "v", "T", "E", "F"):
+        setattr(q, k, np.asarray(getattr(q, k)).astype(dtype).astype(np.float64))
+    return q
+
+
+def run_gpu(p, nsteps, precision="fp64", dt=None, **overrides):
+    import paper_2606_26268_b300 as R
+    r = R.from_problem(p, precision=precision, **overrides)
+    if dt is None:
+        dt = r.dt()
+    r.step(nsteps, dt)
+    st = r.sync()
+    out = {k: np.asarray(r.read(k), dtype=np.float64) for k in ("E", "F", "e", "m", "T")}
+    out["stats"] = r.stats()
+    out["status"] = st
+    out["dt"] = dt
+    r.close()
+    return out
+
+
+def run_oracle(p, nsteps, dt=None, nthreads=0):
+    o = oracle.Oracle(p, nthreads=nthreads)
+    if dt is None:
+        dt = o.dt()
+    o.step(nsteps, dt)
+    return {"E": o.E, "F": o.F, "e": o.e, "m": o.m, "T": o.temperature(), "stats": o.stats,
+            "dt": dt}
+
+
+def errors(g, o, ncomp, chat):
+    E = o["E"]
+    out = {"E": np.max(np.abs(g["E"] - E) / np.abs(E)),
+           "e": np.max(np.abs(g["e"] - o["e"]) / np.abs(o["e"]))}
+    out["F"] = max(np.max(np.abs(g["F"][q] - o["F"][q]) / E) for q in range(ncomp))
+    scale = np.sqrt(np.sum(o["m"] ** 2, axis=0)) + E / chat
+    out["m"] = max(np.max(np.abs(g["m"][q] - o["m"][q]) / scale) for q in range(ncomp))
+    return out

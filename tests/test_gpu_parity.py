@@ -1,0 +1,185 @@
+"""Parity of the CUDA step (through the C ABI) with the FP64 CPU oracle.
+
+FP64 runs must match the oracle to <= 1e-11 per cell (|dE|/|E|, |dF|/E,
+|de|/|e|); the split FP32-transport form is held to the error bounds stated
+in each test.  Sizes span several CTA tiles with ragged tails.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads as W
+from helpers import errors, rounded, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_26268_b300 import build
+    build.build()
+
+
+def check64(p, nsteps, tol=TOL64, **kw):
+    g = run_gpu(p, nsteps, "fp64", **kw)
+    o = run_oracle(p, nsteps, dt=g["dt"])
+    err = errors(g, o, p.ncomp, p.chat)
+    assert g["status"] == 0, g["status"]
+    for k, v in err.items():
+        assert v <= tol, (p.name, k, v, err)
+    # third components the GPU does not carry stay zero in the oracle
+    for q in range(p.ncomp, 3):
+        assert np.max(np.abs(o["F"][q])) <= 1e-14 * np.max(o["E"])
+    return g, o, err
+
+
+def test_pulse_1d_fp64_matches_oracle():
+    """1D Cartesian pulse, 512 cells, 200 steps of transport + coupling."""
+    p = W.pulse_1d(512, 200)
+    g, o, err = check64(p, 200)
+    assert g["stats"]["efloor"] == o["stats"][1]
+    assert g["stats"]["iters"] == o["stats"][3]
+
+
+CASES = [
+    # geometry, n, ndim, bc, ncomp, log_r, opacity
+    ("cartesian", (300, 1, 1), 1, "outflow", 3, False, None),
+    ("cartesian", (257, 1, 1), 1, "periodic", 1, False, None),
+    ("cartesian", (131, 70, 1), 2, "periodic", 2, False, None),
+    ("cartesian", (140, 45, 1), 2, "outflow", 3, False, "powerlaw"),
+    ("cartesian", (40, 23, 37), 3, "periodic", 3, False, "table"),
+    ("cartesian", (33, 20, 9), 3, "outflow", 3, False, "powerlaw"),
+    ("cylindrical", (150, 1, 1), 1, "outflow", 3, False, None),
+    ("cylindrical", (70, 33, 1), 2, "outflow", 3, False, "powerlaw"),
+    ("cylindrical", (35, 16, 20), 3, "outflow", 3, False, None),
+    ("spherical", (200, 1, 1), 1, "outflow", 3, True, None),
+    ("spherical", (64, 40, 1), 2, "outflow", 3, True, "table"),
+    ("spherical", (40, 18, 26), 3, "outflow", 3, True, "powerlaw"),
+]
+
+
+def _opacity(kind):
+    if kind is None:
+        return None
+    if kind == "powerlaw":
+        return {"kind": "powerlaw", "k0": 2.0, "a_rho": 1.0, "b_T": -3.5, "kmin": 1e-3,
+                "kmax": 1e3, "sigma_ratio": 0.3}
+    t = W.opacity_table(24, 20, seed=3)
+    t.update(lrho0=-3.0, lrho1=2.0, lT0=-1.0, lT1=1.5)
+    return t
+
+
+@pytest.mark.parametrize("geom,n,ndim,bc,nc,logr,opac", CASES)
+def test_random_states_fp64_match_oracle(geom, n, ndim, bc, nc, logr, opac):
+    p = W.random_smooth(geom, n, ndim, seed=sum(n) + ndim, bc=bc, opacity=_opacity(opac),
+                        log_r=logr, ncomp=nc, fmax=0.8)
+    check64(p, 6)
+
+
+@pytest.mark.parametrize("ratio", [1.0, 1e3])
+def test_newton_mode_fp64_matches_oracle(ratio):
+    p = W.random_smooth("cartesian", (90, 50, 1), 2, seed=21, bc="periodic", ncomp=2,
+                        chat=2.0, c=2.0 * ratio,
+                        opacity={"kind": "const", "kappa_p": 30.0, "kappa_r": 5.0, "sigma": 1.0})
+    p.implicit_mode = "newton"
+    p.T = p.T * np.exp(0.5 * np.random.default_rng(3).standard_normal(p.N))
+    g, o, err = check64(p, 4)
+    assert g["stats"]["iters"] == o["stats"][3]
+    assert g["stats"]["itmax"] == o["stats"][4]
+    assert g["stats"]["noconv"] == 0
+
+
+def test_free_streaming_and_floors_fp64():
+    """f = 1 beam in 2D, zero opacity, with E floors hit at the trailing edge."""
+    n = (96, 80, 1)
+    p = W.random_smooth("cartesian", n, 2, seed=5, bc="outflow", ncomp=2,
+                        opacity={"kind": "const", "kappa_p": 0.0, "kappa_r": 0.0, "sigma": 0.0})
+    x, y, _ = W.mesh(p)
+    p.E = 1e-12 + np.where((np.abs(x - 0.3) < 0.08) & (np.abs(y - 0.3) < 0.08), 1.0, 0.0)
+    p.F = np.zeros((3, p.N))
+    p.F[0] = p.E / math.sqrt(2)
+    p.F[1] = p.E / math.sqrt(2)
+    p.e_floor = 1e-12
+    check64(p, 30)
+
+
+def test_checkpoint_restart():
+    """N steps, read the state, restart from it, M steps == N + M steps.  The
+    restart goes through (rho, v, T), which reproduce m and e to rounding, so
+    the comparison is at 1e-12 rather than bitwise."""
+    import paper_2606_26268_b300 as R
+    p = W.random_smooth("cartesian", (60, 31, 17), 3, seed=8, bc="periodic")
+    r = R.from_problem(p, "fp64")
+    r.step(9)
+    ref = {k: r.read(k).copy() for k in ("E", "F", "e")}
+    r.close()
+    r1 = R.from_problem(p, "fp64")
+    r1.step(5)
+    q = p.copy()
+    q.E, q.F, q.rho, q.T = (r1.read(k).copy() for k in ("E", "F", "rho", "T"))
+    q.v = r1.read("m") / q.rho
+    r1.close()
+    r2 = R.from_problem(q, "fp64")
+    r2.step(4)
+    for k in ("E", "F", "e"):
+        np.testing.assert_allclose(r2.read(k), ref[k], rtol=1e-12, atol=1e-14)
+    r2.close()
+
+
+def test_invalid_states_and_sizes_are_reported():
+    import paper_2606_26268_b300 as R
+    p = W.random_smooth("cartesian", (16, 1, 1), 1, seed=2)
+    r = R.from_problem(p, "fp64")
+    with pytest.raises(R.RadError):
+        r.step(-1)
+    with pytest.raises(AssertionError):
+        r.set_rad(np.ones(5), np.zeros(5))
+    r.step(0)
+    assert r.sync() == R.RAD_OK
+    bad = p.copy()
+    bad.T = -np.ones(p.N)  # negative temperature: flagged as non-physical
+    r2 = R.from_problem(bad, "fp64")
+    r2.step(1)
+    assert r2.sync() == R.RAD_ENONPHYS
+    r.close()
+    r2.close()
+
+
+def test_single_cell_and_tiny_grids():
+    for n, ndim in (((1, 1, 1), 1), ((2, 1, 1), 1), ((3, 2, 1), 2), ((2, 3, 2), 3)):
+        for bc in ("outflow", "periodic"):
+            p = W.random_smooth("cartesian", n, ndim, seed=7, bc=bc)
+            check64(p, 3)
+
+
+# ---------------------------------------------------------------------------
+# split precision (FP32 transport, FP64 emission term)
+# ---------------------------------------------------------------------------
+
+def check_split(p, nsteps, tol):
+    q = rounded(p, np.float32)
+    g = run_gpu(q, nsteps, "split")
+    o = run_oracle(q, nsteps, dt=g["dt"])
+    err = errors(g, o, p.ncomp, p.chat)
+    assert g["status"] == 0
+    for k in ("E", "F", "e"):
+        assert err[k] <= tol, (p.name, k, err)
+    return err
+
+
+def test_split_turbulent_box_100_steps():
+    """The 2D turbulent recipe (log-normal density, tau spanning decades) at
+    160 x 96, non-equilibrium radiation, 100 steps."""
+    p = W.turbulent_2d((160, 96), nsteps=100, nonequilibrium=True)
+    check_split(p, 100, 1e-5)
+
+
+def test_split_hot_sphere_100_steps():
+    p = W.hot_sphere_3d(ns=(40, 36, 34), nsteps=100)
+    check_split(p, 100, 1e-5)

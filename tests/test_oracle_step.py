@@ -304,3 +304,22 @@ def test_shock_tube_1_contact_has_constant_velocity_and_pressure_analogs():
     assert abs(np.mean(E[lo]) - np.mean(E[hi])) > 0.02  # E does jump
     assert np.mean(beta[lo]) == pytest.approx(np.mean(beta[hi]), rel=3e-2)
     assert np.mean(Pi[lo]) == pytest.approx(np.mean(Pi[hi]), rel=5e-3)
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_shock_tube_l1_error_converges_at_the_printed_rate(which):
+    """Sect. 3.1: the L1 error of E_r against a fine reference falls as
+    N^-1/2 for both tubes.  The paper integrates with RK2; this step is forward
+    Euler, and the rate is checked over the coarse end of the paper's range
+    against a reference 8x finer than the finest run."""
+    _, slope_printed = golden_tubes()
+    nref = 2048
+    _, oref = run_tube(which, nref)
+    ns = [64, 128, 256]
+    errs = []
+    for n in ns:
+        _, o = run_tube(which, n)
+        ref = oref.E.reshape(n, nref // n).mean(axis=1)
+        errs.append(np.mean(np.abs(o.E - ref)) * 40.0)
+    slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+    assert slope == pytest.approx(slope_printed, abs=0.2)
