@@ -1,0 +1,380 @@
+#!/usr/bin/env python
+"""Benchmark of the M1 radiation step on B300: cell updates per second.
+
+Default workload: the 3D Cartesian hot-sphere box, 256^3 cells, FP32
+transport with the FP64 emission term, Kramers-like opacity, chat = 30
+(seeded synthetic inputs, see workloads.hot_sphere_3d).  One benchmark step is
+one full radiation step (transport + implicit coupling) over all cells.  The
+plain FP64 form is timed on the same grid for comparison.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --gpus N > 1 (launched by
+torch.distributed.run) every rank advances its own replica of the grid
+(weak scaling, no collective on the data path) and `value` counts the cell
+updates of all ranks over the slowest rank's time.  `--impl reference` times
+the CPU oracle on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "radiation cell updates/s on 1 B300 + % HBM roofline; FP32+MLP vs FP64 plain"
+UNIT = "cell updates/s"
+# algorithmic bytes per cell update of the fused step (each field read once and
+# written once; halos, tables and ghost layers excluded)
+BYTES_PER_CELL = {("split", 3): 68, ("fp64", 3): 136, ("split", 2): 52, ("fp64", 2): 104}
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6400.0, "fallback"
+
+
+def kernel_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2606_26268_b300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(workload, precision):
+    """DRAM bytes per launch from a committed ncu summary of the same kernel
+    source (null if the kernel changed since the capture)."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        e = d.get("%s/%s" % (workload, precision))
+        if e and e.get("kernel_hash") == kernel_hash():
+            return float(e["dram_bytes_per_launch"])
+    except Exception:
+        pass
+    return None
+
+
+class Clocks:
+    """Samples SM clocks and throttle reasons with nvidia-smi while running."""
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            for line in open(self.path):
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 7:
+                    rows.append(parts)
+        except Exception:
+            pass
+        finally:
+            if self.path and os.path.exists(self.path):
+                os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        sm = [float(r[0]) for r in rows if r[0].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = [n for i, n in enumerate(names) if any(r[3 + i] == "Active" for r in rows)]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": float(rows[0][1]) if rows[0][1].replace(".", "").isdigit() else None,
+                "samples": len(rows), "reasons": reasons}
+
+
+def make_workload(name):
+    import workloads as W
+    if name.startswith("hotsphere3d"):
+        n = int(name.split("_")[1]) if "_" in name else 256
+        return W.hot_sphere_3d(n)
+    if name.startswith("turb2d"):
+        n = int(name.split("_")[1]) if "_" in name else 1024
+        return W.turbulent_2d((n, n))
+    raise SystemExit("unknown workload %s" % name)
+
+
+def time_steps(r, torch, steps, warmup, dt):
+    """Device time of `steps` steps (events on the library's stream), after
+    `warmup` steps, with synchronisation on both sides; also the per-launch
+    kernel times."""
+    s = r.stream
+    r.step(warmup, dt)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+    with torch.cuda.stream(s):
+        ev[0].record(s)
+        for k in range(steps):
+            r.step(1, dt)
+            ev[k + 1].record(s)
+    torch.cuda.synchronize()
+    per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
+    return sum(per), per
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+    import paper_2606_26268_b300 as R
+    from paper_2606_26268_b300 import build as B
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", local)
+    if rank == 0 or not os.path.exists(B.LIB):
+        B.build()
+    if world > 1:
+        dist.barrier()
+
+    prob = make_workload(args.workload)
+    N = prob.N
+    ndim = prob.ndim
+    hbm, peak_kind = peaks()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    # --- headline form -----------------------------------------------------
+    r = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
+    dt = r.dt()
+    barrier()
+    with Clocks(local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        total_ms, per = time_steps(r, torch, args.steps, args.warmup, dt)
+        barrier()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    status = r.sync()
+    st = r.stats()
+    launches = args.steps * r.launches_per_step()
+    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * N * args.steps / (ms_max * 1e-3)
+    kernel_ms = statistics.mean(per)
+    bpc = BYTES_PER_CELL[(args.precision, ndim)]
+    achieved = bpc * N / (kernel_ms * 1e-3) / 1e9
+    r.close()
+
+    # --- end to end through the C ABI with host buffers --------------------
+    e2e = None
+    if rank == 0 or True:
+        nc = prob.ncomp
+        dtype = np.float64 if args.precision == "fp64" else np.float32
+        tdt = torch.float64 if dtype == np.float64 else torch.float32
+
+        def pinned(a):
+            t_ = torch.empty(a.size, dtype=tdt, pin_memory=True)
+            t_.numpy()[:] = a.ravel()
+            return t_.numpy()
+
+        h_rho, h_T, h_E = pinned(prob.rho), pinned(prob.T), pinned(prob.E)
+        h_v, h_F = pinned(np.asarray(prob.v)[:nc]), pinned(np.asarray(prob.F)[:nc])
+        outs = {k: pinned(np.zeros(N * (nc if k in ("F", "m") else 1))) for k in ("E", "F", "e", "m")}
+        r2 = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
+        ksteps = max(1, min(args.steps, 3))
+        for _ in range(1):
+            r2.set_gas(h_rho, h_v, h_T)
+            r2.set_rad(h_E, h_F)
+            r2.step(1, dt)
+            for k in outs:
+                r2.read(k, out=outs[k])
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(ksteps):
+            r2.set_gas(h_rho, h_v, h_T)
+            r2.set_rad(h_E, h_F)
+            r2.step(1, dt)
+            for k in outs:
+                r2.read(k, out=outs[k])
+        torch.cuda.synchronize()
+        e2e_s = time.perf_counter() - t0
+        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        isz = np.dtype(dtype).itemsize
+        e2e = {"value": world * N * ksteps / float(tt.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int((3 + 2 * nc) * N * isz),
+               "d2h_bytes_per_step": int((2 + 2 * nc) * N * isz), "steps": ksteps}
+        r2.close()
+
+    # --- plain FP64 form on the same grid -----------------------------------
+    fp64 = None
+    if args.precision != "fp64" and not args.skip_fp64:
+        r3 = R.from_problem(prob, "fp64", device=dev, implicit_mode=args.implicit)
+        k64 = max(2, args.steps // 4)
+        ms64, per64 = time_steps(r3, torch, k64, 2, dt)
+        r3.close()
+        t64 = torch.tensor([ms64], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t64, op=dist.ReduceOp.MAX)
+        b64 = BYTES_PER_CELL[("fp64", ndim)]
+        km64 = statistics.mean(per64)
+        fp64 = {"value": world * N * k64 / (float(t64.item()) * 1e-3), "unit": UNIT,
+                "steps": k64, "ms_per_step": float(t64.item()) / k64,
+                "hbm_frac": b64 * N / (km64 * 1e-3) / 1e9 / hbm}
+
+    # --- CPU baseline: the oracle on the host cores, bounded sample ---------
+    cpu = None
+    if rank == 0 and not args.skip_cpu:
+        cpu = cpu_baseline(prob, dt, args.cpu_seconds)
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": ms_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "split" else "f64",
+            "data": "synthetic (seeded hot-sphere box: log-normal density, Kramers opacity)",
+            "config": {"workload": prob.name, "cells": N, "precision": args.precision,
+                       "implicit": args.implicit, "chat": prob.chat, "dt": dt,
+                       "parallelism": "replicas" if world > 1 else "single",
+                       "l2": "state larger than L2 (%.2f GB per buffer)" % (
+                           (3 + 2 * prob.ncomp) * N * (4 if args.precision == "split" else 8) / 1e9)},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm, "unit": "GB/s",
+                         "frac": achieved / hbm, "peak_kind": peak_kind,
+                         "bytes_per_cell": bpc, "kernel_ms": kernel_ms,
+                         "traffic": profiled_traffic(prob.name, args.precision)},
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+            "fp64_plain": fp64,
+            "gpu_launches": launches,
+            "clocks": clocks,
+            "status": int(status),
+            "stats": st,
+            "wall_s": wall,
+        }
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def cpu_baseline(prob, dt, seconds):
+    """The oracle, as it stands, timed on the host cores on a random sample of
+    the workload's cells (one step of each sampled cell from the same initial
+    state); rate = sampled cell updates per second."""
+    import oracle
+    o = oracle.Oracle(prob, nthreads=0)
+    threads = oracle.max_threads()
+    rng = np.random.default_rng(0)
+    n = 20000
+    cells = rng.choice(prob.N, size=n, replace=False)
+    t0 = time.perf_counter()
+    o.step_cells(cells, dt)
+    t1 = time.perf_counter() - t0
+    n2 = int(min(prob.N, max(n, n * seconds / max(t1, 1e-6))))
+    cells = rng.choice(prob.N, size=n2, replace=False)
+    t0 = time.perf_counter()
+    o.step_cells(cells, dt)
+    t2 = time.perf_counter() - t0
+    return {"value": n2 / t2, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": "%d random cells of %s, one step each from the initial state "
+                      "(%.1f s)" % (n2, prob.name, t2)}
+
+
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    prob = make_workload(args.workload)
+    o = oracle.Oracle(prob, nthreads=0)
+    dt = o.dt()
+    rng = np.random.default_rng(1)
+    sample = int(min(prob.N, args.ref_cells))
+    cells = rng.choice(prob.N, size=sample, replace=False)
+    for _ in range(args.warmup):
+        o.step_cells(cells[: max(1, sample // 10)], dt)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        o.step_cells(cells, dt)
+    el = time.perf_counter() - t0
+    value = sample * args.steps / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": el / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": prob.name, "cells": prob.N, "precision": "fp64 (oracle)"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.max_threads(),
+                             "kind": "oracle",
+                             "sample": "%d random cells per step of %s" % (sample, prob.name)},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="hotsphere3d_256")
+    ap.add_argument("--precision", default="split", choices=["split", "fp64"])
+    ap.add_argument("--implicit", default="once", choices=["once", "newton"])
+    ap.add_argument("--cpu-seconds", type=float, default=10.0)
+    ap.add_argument("--ref-cells", type=int, default=200000)
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3 and args.impl == "ours":
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

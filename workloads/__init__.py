@@ -137,7 +137,7 @@ def gaussian_random_field(shape: Sequence[int], seed: int, slope: float = -11.0 
     amp = np.zeros_like(k2)
     nz = k2 > 0
     amp[nz] = k2[nz] ** (slope / 4.0)  # |k|^(slope/2) on the amplitude
-    g = np.fft.irfftn(spec * amp, s=shape)
+    g = np.fft.irfftn(spec * amp, s=shape, axes=tuple(range(len(shape))))
     g -= g.mean()
     g /= g.std()
     return g.ravel().astype(np.float64)
