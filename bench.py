@@ -184,6 +184,7 @@ def run_ours(args):
     # --- headline form -----------------------------------------------------
     r = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
     dt = r.dt()
+    tuned = r.tune(3) if not args.no_tune else r.get_launch()[:2] + (None,)
     barrier()
     with Clocks(local) as clk:
         barrier()
@@ -204,6 +205,7 @@ def run_ours(args):
     bpc = BYTES_PER_CELL[(args.precision, ndim)]
     achieved = bpc * N / (kernel_ms * 1e-3) / 1e9
     r.close()
+    del r
 
     # --- end to end through the C ABI with host buffers --------------------
     e2e = None
@@ -221,6 +223,7 @@ def run_ours(args):
         h_v, h_F = pinned(np.asarray(prob.v)[:nc]), pinned(np.asarray(prob.F)[:nc])
         outs = {k: pinned(np.zeros(N * (nc if k in ("F", "m") else 1))) for k in ("E", "F", "e", "m")}
         r2 = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
+        r2.set_launch(tuned[0], tuned[1])
         ksteps = max(1, min(args.steps, 3))
         for _ in range(1):
             r2.set_gas(h_rho, h_v, h_T)
@@ -251,6 +254,8 @@ def run_ours(args):
     fp64 = None
     if args.precision != "fp64" and not args.skip_fp64:
         r3 = R.from_problem(prob, "fp64", device=dev, implicit_mode=args.implicit)
+        if not args.no_tune:
+            r3.tune(1)
         k64 = max(2, args.steps // 4)
         ms64, per64 = time_steps(r3, torch, k64, 2, dt)
         r3.close()
@@ -277,6 +282,7 @@ def run_ours(args):
             "data": "synthetic (seeded hot-sphere box: log-normal density, Kramers opacity)",
             "config": {"workload": prob.name, "cells": N, "precision": args.precision,
                        "implicit": args.implicit, "chat": prob.chat, "dt": dt,
+                       "launch": {"variant": tuned[0], "chunk": tuned[1], "tuned_ms": tuned[2]},
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state larger than L2 (%.2f GB per buffer)" % (
                            (3 + 2 * prob.ncomp) * N * (4 if args.precision == "split" else 8) / 1e9)},
@@ -367,6 +373,7 @@ def main():
     ap.add_argument("--ref-cells", type=int, default=200000)
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--no-tune", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3

@@ -198,6 +198,22 @@ rad_status rad_reset_stats(rad_ctx *ctx);
  * accounting by callers). */
 int rad_launches_per_step(const rad_ctx *ctx);
 
+/* Launch shape of the step kernel: `variant` selects one of the CTA shapes
+ * instantiated for this grid (0 = default; rad_get_launch reports how many)
+ * and `chunk` the number of cells a CTA marches along the slowest active
+ * axis (0 = default).  Results do not depend on either.  Not in the paper:
+ * a tuning knob of this implementation.  Errors: RAD_EINVAL. */
+rad_status rad_set_launch(rad_ctx *ctx, int variant, int chunk);
+rad_status rad_get_launch(const rad_ctx *ctx, int *variant, int *chunk, int *nvariants);
+
+/* Autotuner: times `reps` steps of every (shape, chunk) candidate on the
+ * current state without advancing it (each trial recomputes the same step
+ * into the spare buffer), selects the fastest, and restores the counters
+ * and the status word.  Outputs (any may be NULL): the chosen variant and
+ * chunk and its time per step in ms.  Synchronises the stream.  Not in the
+ * paper.  Errors: RAD_EINVAL (no state), RAD_ENOMEM, RAD_ECUDA. */
+rad_status rad_tune(rad_ctx *ctx, int reps, int *variant, int *chunk, float *ms);
+
 /* Releases the context (and the workspace if rad_alloc_workspace made it). */
 void rad_destroy(rad_ctx *ctx);
 

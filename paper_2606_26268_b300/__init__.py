@@ -65,7 +65,8 @@ class rad_stats(C.Structure):
 EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_workspace",
            "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad", "rad_step",
            "rad_read", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
-           "rad_launches_per_step", "rad_destroy", "rad_strerror"]
+           "rad_launches_per_step", "rad_set_launch", "rad_get_launch", "rad_tune",
+           "rad_destroy", "rad_strerror"]
 
 _lib = None
 
@@ -97,6 +98,9 @@ def lib() -> C.CDLL:
     L.rad_reset_stats.argtypes = [vp]
     L.rad_launches_per_step.argtypes = [vp]
     L.rad_launches_per_step.restype = C.c_int
+    L.rad_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    L.rad_get_launch.argtypes = [vp, P(C.c_int), P(C.c_int), P(C.c_int)]
+    L.rad_tune.argtypes = [vp, C.c_int, P(C.c_int), P(C.c_int), P(C.c_float)]
     L.rad_destroy.argtypes = [vp]
     L.rad_destroy.restype = None
     L.rad_strerror.argtypes = [C.c_int]
@@ -252,6 +256,20 @@ class Rad:
 
     def reset_stats(self):
         check(lib().rad_reset_stats(self.ctx), "rad_reset_stats")
+
+    def set_launch(self, variant: int, chunk: int = 0):
+        check(lib().rad_set_launch(self.ctx, int(variant), int(chunk)), "rad_set_launch")
+
+    def get_launch(self) -> tuple:
+        v, c, n = C.c_int(), C.c_int(), C.c_int()
+        check(lib().rad_get_launch(self.ctx, C.byref(v), C.byref(c), C.byref(n)), "rad_get_launch")
+        return v.value, c.value, n.value
+
+    def tune(self, reps: int = 3) -> tuple:
+        """Picks the fastest launch shape on the current state (state unchanged)."""
+        v, c, t = C.c_int(), C.c_int(), C.c_float()
+        check(lib().rad_tune(self.ctx, int(reps), C.byref(v), C.byref(c), C.byref(t)), "rad_tune")
+        return v.value, c.value, t.value
 
     def launches_per_step(self) -> int:
         return lib().rad_launches_per_step(self.ctx)

@@ -150,7 +150,10 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
     lp = (fc + z) / s;
     lm = (fc - z) / s;
   } else {
-    T rn = nF2 > T(0) ? rsqrt_approx(nF2) : T(0);
+    // |F| below 1e-15 E (or a float denormal) is treated as zero flux: the
+    // closure depends on the direction of F only at O(f^2), and the FTZ
+    // approximations would turn a denormal |F|^2 into an infinite 1/|F|.
+    T rn = nF2 > fmaxf(T(1e-30) * E * E, T(1e-36)) ? rsqrt_approx(nF2) : T(0);
     T nF = nF2 * rn;
     f = nF * invE;
     f = f > T(1) ? T(1) : f;
@@ -186,6 +189,7 @@ __device__ __forceinline__ void pressure(const T (&u)[4], T& a, T& b) {
   T nF2 = u[1] * u[1];
   if (NC > 1) nF2 += u[2] * u[2];
   if (NC > 2) nF2 += u[3] * u[3];
+  if (sizeof(T) == 4 && !(nF2 > T(1e-30) * E * E && nF2 > T(1e-36))) nF2 = T(0);
   T nF = Ops<T>::sqrt_(nF2);
   T f = Ops<T>::div(nF, E);
   f = f > T(1) ? T(1) : f;
@@ -239,6 +243,8 @@ struct OpacityDev {
   const double* tab64;         // log10 kappa, [iT][irho]
   const float* tab32;
   int linear_rho;              // powerlaw with a = 1, b = 0 (kappa = k0 rho)
+  // float copies for the split-precision path (no double conversions there)
+  float f_kp, f_chi0, f_k0, f_a, f_b, f_kmin, f_kmax, f_s1, f_lrho0, f_lT0, f_sr, f_sT;
 };
 
 // Opacities per unit mass at (rho, T): kp (Planck), chi = kappa_R + sigma.
@@ -276,23 +282,23 @@ __device__ __forceinline__ void opacity(const OpacityDev& o, double rho, double 
 __device__ __forceinline__ void opacity(const OpacityDev& o, float rho, float T, float& kp,
                                         float& chi) {
   if (o.kind == 0) {
-    kp = float(o.kappa_p);
-    chi = float(o.kappa_r + o.sigma);
+    kp = o.f_kp;
+    chi = o.f_chi0;
     return;
   }
   float k;
   if (o.kind == 1) {
     if (o.linear_rho) {
-      k = float(o.k0) * rho;
+      k = o.f_k0 * rho;
     } else {
-      k = float(o.k0) * ex2_approx(float(o.a_rho) * lg2_approx(rho) + float(o.b_T) * lg2_approx(T));
+      k = o.f_k0 * ex2_approx(o.f_a * lg2_approx(rho) + o.f_b * lg2_approx(T));
     }
-    k = k < float(o.kmin) ? float(o.kmin) : k;
-    k = k > float(o.kmax) ? float(o.kmax) : k;
+    k = k < o.f_kmin ? o.f_kmin : k;
+    k = k > o.f_kmax ? o.f_kmax : k;
   } else {
     const float kLog10_2 = 0.30102999566398120f;
-    float xr = (lg2_approx(rho) * kLog10_2 - float(o.lrho0)) * float(o.sr);
-    float xt = (lg2_approx(T) * kLog10_2 - float(o.lT0)) * float(o.sT);
+    float xr = (lg2_approx(rho) * kLog10_2 - o.f_lrho0) * o.f_sr;
+    float xt = (lg2_approx(T) * kLog10_2 - o.f_lT0) * o.f_sT;
     xr = fminf(fmaxf(xr, 0.f), float(o.nrho - 1));
     xt = fminf(fmaxf(xt, 0.f), float(o.nT - 1));
     int ir = min(int(xr), o.nrho - 2), it = min(int(xt), o.nT - 2);
@@ -303,7 +309,7 @@ __device__ __forceinline__ void opacity(const OpacityDev& o, float rho, float T,
     k = ex2_approx(lk * 3.32192809488736235f);
   }
   kp = k;
-  chi = k * (1.f + float(o.sigma_ratio));
+  chi = k * o.f_s1;
 }
 
 // ---------------------------------------------------------------------------
@@ -314,6 +320,8 @@ struct CoupleParams {
   double dt, chat, c, a_rad, cvfac;  // cvfac = 1 / (mu (gamma - 1)): C_v = rho cvfac
   double rtol;
   int maxit, newton;
+  // float copies for the split-precision path
+  float f_dtchat, f_dtc, f_cvfac, f_a, f_rtol;
 };
 
 struct CoupleOut {
@@ -387,25 +395,27 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
 __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
                                                   float kp, float Es, float T0f) {
   CoupleOut o{};
-  float Cv = rho * float(p.cvfac);
+  float Cv = rho * p.f_cvfac;
   float invCv = rcp_approx(Cv);
-  double Tn = double(e) * double(invCv);
-  float gr = float(p.dt * p.chat) * kp * rho;
-  float g = float(p.dt * p.c) * kp * rho;
+  float Tf = e * invCv;
+  float gr = p.f_dtchat * kp * rho;
+  float g = p.f_dtc * kp * rho;
   float c1 = (1.f + gr) * Cv;
   if (!p.newton) {
-    double T2 = Tn * Tn;
+    // the T^4 emission term and E* - a T^4 in double: T^2 of a float is
+    // exact in double, so this is two roundings from exact
+    double T2 = double(Tf) * double(Tf);
     double aT4 = (p.a_rad * T2) * T2;
     float D = float(double(Es) - aT4);
-    float Tf = e * invCv;
-    float aT3 = float(p.a_rad) * Tf * Tf * Tf;
+    float aT3 = p.f_a * Tf * Tf * Tf;
     float det = c1 + 4.f * g * aT3;
     float q = D * rcp_approx(det);
-    o.Tnew = Tn + double(g * q);
+    o.Tnew = double(Tf + g * q);
     o.dE = double(-gr * Cv * q);
     o.iters = 1;
     return o;
   }
+  double Tn = double(Tf);
   double c1d = double(c1);
   for (int attempt = 0; attempt < 2; ++attempt) {
     double Tk = (attempt == 0 && T0f > 0.f) ? double(T0f) : Tn;
@@ -422,7 +432,7 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
       double dT = num * double(rcp_approx(det));
       Tnew = Tk + dT;
       if (!(Tnew > 0.0)) break;
-      if (fabsf(float(dT)) <= float(p.rtol) * float(Tnew)) {
+      if (fabsf(float(dT)) <= p.f_rtol * float(Tnew)) {
         ok = true;
         break;
       }

@@ -51,8 +51,11 @@ __device__ __forceinline__ typename P::T cell_tau(const StepArgs<P>& a, typename
                                                   typename P::T& kp, typename P::T& chi) {
   using T = typename P::T;
   T r = T(rho);
-  T Cv = r * T(a.cp.cvfac);
-  T Temp = (sizeof(T) == 8) ? T(e) / Cv : T(e) * rcp_approx(float(Cv));
+  T Temp;
+  if constexpr (sizeof(T) == 8)
+    Temp = T(e) / (r * T(a.cp.cvfac));
+  else
+    Temp = T(e) * rcp_approx(r * a.cp.f_cvfac);
   opacity(a.opac, r, Temp, kp, chi);
   return r * chi * cell_hmax<T, NDIM, GEOM>(a.geo, p0, p1, p2);
 }
@@ -117,8 +120,9 @@ __device__ __forceinline__ void load_state(const Fields<S>& f, long long i, T (&
   for (int q = 0; q < 3; ++q) u[1 + q] = (q < NC) ? T(__ldg(f.F[q] + i)) : T(0);
 }
 
-template <class P, int NDIM, int GEOM, int NC, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ StepArgs<P> a) {
+// MINB: resident CTAs per SM requested from the register allocator.
+template <class P, int NDIM, int GEOM, int NC, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_constant__ StepArgs<P> a) {
   using S = typename P::S;
   using T = typename P::T;
   constexpr int NV = 1 + NC;
@@ -170,8 +174,8 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
   unsigned long long c_iters = 0;
   int status = 0;
 
-  // column queue: q[0..3] = states at m-1, m, m+1, m+2
-  T q[4][4];
+  // column queue: q[0..2] = states at m, m+1, m+2
+  T q[3][4];
   T hiS[4];         // fixed upper face state of cell m along the march axis
   T zlo[4], zhi[4]; // march-face fluxes m-1/2 and m+1/2
   T tau_m = 0, tau_n = 0, kp_m = 0, chi_m = 0, kp_n = 0, chi_n = 0;
@@ -180,11 +184,11 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
   for (int v = 0; v < 4; ++v) zlo[v] = zhi[v] = hiS[v] = T(0);
 
   if constexpr (MARCH) {
-    T qm2[4];
+    T qm2[4], qm1[4];
     load_state<S, NC>(a.in, base + (long long)(m0 - 2 + gm) * ms, qm2);
-    load_state<S, NC>(a.in, base + (long long)(m0 - 1 + gm) * ms, q[0]);
-    load_state<S, NC>(a.in, base + (long long)(m0 + gm) * ms, q[1]);
-    load_state<S, NC>(a.in, base + (long long)(m0 + 1 + gm) * ms, q[2]);
+    load_state<S, NC>(a.in, base + (long long)(m0 - 1 + gm) * ms, qm1);
+    load_state<S, NC>(a.in, base + (long long)(m0 + gm) * ms, q[0]);
+    load_state<S, NC>(a.in, base + (long long)(m0 + 1 + gm) * ms, q[1]);
     {
       long long i = base + (long long)(m0 - 1 + gm) * ms;
       S r = __ldg(a.rho + i), e = __ldg(a.in.e + i);
@@ -201,21 +205,21 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
     const int pm = m0 + gm;
     T ix0 = tabv(G, MA, TAB_IDXC, pm - 2), ix1 = tabv(G, MA, TAB_IDXC, pm - 1);
     T ix2 = tabv(G, MA, TAB_IDXC, pm);
-    int nf = face4<T, NC, MA>(qm2, q[0], q[1], q[2], ix0, ix1, ix2, tabv(G, MA, TAB_HHI, pm - 1),
+    int nf = face4<T, NC, MA>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, tabv(G, MA, TAB_HHI, pm - 1),
                               tabv(G, MA, TAB_HLO, pm), T(0.5) * (tau_prev + tau_m), chat, zlo);
     if (upd_col && m0 == 0) c_fix += nf;
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
     T d1[4], d2[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
-      d1[v] = (q[1][v] - q[0][v]) * ix1;
-      d2[v] = (q[2][v] - q[1][v]) * ix2;
+      d1[v] = (q[0][v] - qm1[v]) * ix1;
+      d2[v] = (q[1][v] - q[0][v]) * ix2;
     }
-    plm_state<T, NV>(d1, d2, q[1], tabv(G, MA, TAB_HHI, pm), hiS);
-    int nfh = fix_face<T, NC>(hiS, q[1], flux2<T, NC>(q[1]), Ops<T>::rcp(q[1][0]));
+    plm_state<T, NV>(d1, d2, q[0], tabv(G, MA, TAB_HHI, pm), hiS);
+    int nfh = fix_face<T, NC>(hiS, q[0], flux2<T, NC>(q[0]), Ops<T>::rcp(q[0][0]));
     if (upd_col) c_fix += nfh;
   } else {
-    load_state<S, NC>(a.in, base, q[1]);
+    load_state<S, NC>(a.in, base, q[0]);
     rho_m = __ldg(a.rho + base);
     e_m = __ldg(a.in.e + base);
     tau_m = cell_tau<P, NDIM, GEOM>(a, rho_m, e_m, px, 0, 0, kp_m, chi_m);
@@ -225,7 +229,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
     const long long ic = base + (long long)(m + gm) * ms;  // own cell
     T mom[3] = {0, 0, 0};
     if constexpr (MARCH) {
-      load_state<S, NC>(a.in, ic + 2 * ms, q[3]);
+      load_state<S, NC>(a.in, ic + 2 * ms, q[2]);
       long long i1 = ic + ms;
       rho_n = __ldg(a.rho + i1);
       e_n = __ldg(a.in.e + i1);
@@ -237,7 +241,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
     }
     // own state and tau into the shared plane
 #pragma unroll
-    for (int v = 0; v < NV; ++v) s_u[v][ty + OY][tx + 2] = q[1][v];
+    for (int v = 0; v < NV; ++v) s_u[v][ty + OY][tx + 2] = q[0][v];
     s_tau[TILE_Y ? ty + 1 : 0][tx + 1] = tau_m;
     // halo of the plane
     for (int h = tid; h < NHALO; h += NT) {
@@ -326,16 +330,16 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
       T d1[4], d2[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
-        d1[v] = (q[2][v] - q[1][v]) * ix1;
-        d2[v] = (q[3][v] - q[2][v]) * ix2;
+        d1[v] = (q[1][v] - q[0][v]) * ix1;
+        d2[v] = (q[2][v] - q[1][v]) * ix2;
       }
       T loN[4];
-      plm_state<T, NV>(d1, d2, q[2], tabv(G, MA, TAB_HLO, pm), loN);
-      plm_state<T, NV>(d1, d2, q[2], tabv(G, MA, TAB_HHI, pm), hiN);
-      T inv2 = Ops<T>::rcp(q[2][0]);
-      T n2 = flux2<T, NC>(q[2]);
-      int nf = fix_face<T, NC>(loN, q[2], n2, inv2);
-      int nf2 = fix_face<T, NC>(hiN, q[2], n2, inv2);
+      plm_state<T, NV>(d1, d2, q[1], tabv(G, MA, TAB_HLO, pm), loN);
+      plm_state<T, NV>(d1, d2, q[1], tabv(G, MA, TAB_HHI, pm), hiN);
+      T inv2 = Ops<T>::rcp(q[1][0]);
+      T n2 = flux2<T, NC>(q[1]);
+      int nf = fix_face<T, NC>(loN, q[1], n2, inv2);
+      int nf2 = fix_face<T, NC>(hiN, q[1], n2, inv2);
       riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
       // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
       if (upd_col) c_fix += nf + (m + 1 < m1 ? nf2 : 0);
@@ -403,7 +407,7 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
 #pragma unroll
         for (int v = 0; v < NV; ++v) dU[v] -= ahi * zhi[v] - alo * zlo[v];
       }
-      const T (&u)[4] = q[1];
+      const T (&u)[4] = q[0];
       // inactive theta of a 1D spherical grid: one cell whose faces carry the
       // cell's own physical flux
       if constexpr (GEOM == kSph && NDIM == 1) {
@@ -537,7 +541,6 @@ __global__ void __launch_bounds__(TX * TY) step_kernel(const __grid_constant__ S
       for (int v = 0; v < 4; ++v) {
         q[0][v] = q[1][v];
         q[1][v] = q[2][v];
-        q[2][v] = q[3][v];
         hiS[v] = hiN[v];
         zlo[v] = zhi[v];
       }

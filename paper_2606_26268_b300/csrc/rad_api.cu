@@ -48,7 +48,8 @@ struct rad_ctx {
   int cur = 0;
   bool have_gas = false, have_rad = false;
   uint64_t steps = 0;
-  LaunchFn launch = nullptr;
+  LaunchEntry launch{nullptr, 0};
+  int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
 };
 
 static const char* kMsg[] = {"ok",
@@ -267,7 +268,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   build_tables(c);
   c->dt_cfl = cfl_dt(c);
   c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc);
-  if (!c->launch) {
+  if (!c->launch.fn) {
     delete c;
     return RAD_EUNSUPPORTED;
   }
@@ -602,6 +603,18 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
   od.tab64 = reinterpret_cast<const double*>(c->ws + c->off_op64);
   od.tab32 = reinterpret_cast<const float*>(c->ws + c->off_op32);
   od.linear_rho = (o.kind == RAD_OPAC_POWERLAW && o.a_rho == 1.0 && o.b_T == 0.0);
+  od.f_kp = float(o.kappa_p);
+  od.f_chi0 = float(o.kappa_r + o.sigma);
+  od.f_k0 = float(o.k0);
+  od.f_a = float(o.a_rho);
+  od.f_b = float(o.b_T);
+  od.f_kmin = float(o.kmin);
+  od.f_kmax = o.kmax > 3.0e38 ? 3.0e38f : float(o.kmax);
+  od.f_s1 = float(1.0 + o.sigma_ratio);
+  od.f_lrho0 = float(o.lrho0);
+  od.f_lT0 = float(o.lT0);
+  od.f_sr = float(od.sr);
+  od.f_sT = float(od.sT);
   CoupleParams& cp = a.cp;
   cp.dt = dt;
   cp.chat = c->par.chat;
@@ -611,6 +624,11 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
   cp.rtol = c->par.newton_rtol;
   cp.maxit = c->par.newton_maxit;
   cp.newton = c->par.implicit_mode == RAD_NEWTON;
+  cp.f_dtchat = float(dt * c->par.chat);
+  cp.f_dtc = float(dt * c->par.c);
+  cp.f_cvfac = float(cp.cvfac);
+  cp.f_a = float(c->par.a_rad);
+  cp.f_rtol = float(c->par.newton_rtol);
   a.chat = T(c->par.chat);
   a.dt = T(dt);
   a.efloor = T(c->par.e_floor);
@@ -632,11 +650,11 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
     if (c->esize == 8) {
       StepArgs<Fp64> a{};
       fill_args<Fp64>(c, a, dt);
-      e = c->launch(&a, c->stream);
+      e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
     } else {
       StepArgs<Split> a{};
       fill_args<Split>(c, a, dt);
-      e = c->launch(&a, c->stream);
+      e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
     }
     if (e != cudaSuccess) return RAD_ECUDA;
     c->cur = 1 - c->cur;
@@ -646,6 +664,100 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
 }
 
 extern "C" int rad_launches_per_step(const rad_ctx* c) { return c ? 1 : 0; }
+
+// ---------------------------------------------------------------------------
+// launch shape selection and autotuning
+// ---------------------------------------------------------------------------
+
+extern "C" rad_status rad_set_launch(rad_ctx* c, int variant, int chunk) {
+  if (!c || variant < 0 || variant >= c->launch.variants || chunk < 0) return RAD_EINVAL;
+  c->variant = variant;
+  c->chunk = chunk;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_get_launch(const rad_ctx* c, int* variant, int* chunk, int* nvariants) {
+  if (!c) return RAD_EINVAL;
+  if (variant) *variant = c->variant;
+  if (chunk) *chunk = c->chunk;
+  if (nvariants) *nvariants = c->launch.variants;
+  return RAD_OK;
+}
+
+// Times one step per (shape, chunk) candidate on the current state without
+// advancing it (the step is recomputed from the same input buffer), keeps
+// the fastest, and restores the counters and the status word.
+extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, float* ms) {
+  if (!c || reps < 1) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
+  unsigned long long saved[ST_N + 1];
+  int saved_status = 0;
+  if (cudaMemcpyAsync(saved, c->ws + c->off_stats, sizeof(unsigned long long) * ST_N,
+                      cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(&saved_status, c->ws + c->off_status, sizeof(int), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  std::vector<int> chunks;
+  if (c->ndim == 3) chunks = {16, 32, 64, 128};
+  else if (c->ndim == 2) chunks = {32, 64, 128, 256};
+  else chunks = {1};
+  const int nmarch = c->ndim == 3 ? c->n[2] : (c->ndim == 2 ? c->n[1] : 1);
+  cudaEvent_t e0, e1;
+  if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+    return RAD_ECUDA;
+  float best = 1e30f;
+  int bv = 0, bc = 0;
+  rad_status st = RAD_OK;
+  StepArgs<Fp64> a64{};
+  StepArgs<Split> a32{};
+  if (c->esize == 8)
+    fill_args<Fp64>(c, a64, c->dt_cfl);
+  else
+    fill_args<Split>(c, a32, c->dt_cfl);
+  const void* args = c->esize == 8 ? (const void*)&a64 : (const void*)&a32;
+  for (int v = 0; v < c->launch.variants && st == RAD_OK; ++v) {
+    for (size_t k = 0; k < chunks.size(); ++k) {
+      int ch = chunks[k];
+      if (k > 0 && ch >= 2 * nmarch) break;
+      if (c->launch.fn(args, c->stream, v, ch) != cudaSuccess) {
+        st = RAD_ECUDA;
+        break;
+      }
+      cudaEventRecord(e0, c->stream);
+      for (int r = 0; r < reps; ++r) c->launch.fn(args, c->stream, v, ch);
+      cudaEventRecord(e1, c->stream);
+      if (cudaEventSynchronize(e1) != cudaSuccess) {
+        st = RAD_ECUDA;
+        break;
+      }
+      float t = 0.f;
+      cudaEventElapsedTime(&t, e0, e1);
+      t /= reps;
+      if (t < best) {
+        best = t;
+        bv = v;
+        bc = ch;
+      }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (cudaMemcpyAsync(c->ws + c->off_stats, saved, sizeof(unsigned long long) * ST_N,
+                      cudaMemcpyHostToDevice, c->stream) != cudaSuccess ||
+      cudaMemcpyAsync(c->ws + c->off_status, &saved_status, sizeof(int), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  if (st != RAD_OK) return st;
+  c->variant = bv;
+  c->chunk = c->ndim == 1 ? 0 : bc;
+  if (variant) *variant = bv;
+  if (chunk) *chunk = c->chunk;
+  if (ms) *ms = best;
+  return RAD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // reads, status, counters

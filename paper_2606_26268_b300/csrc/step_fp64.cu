@@ -2,27 +2,27 @@
 #include "step_launch.cuh"
 
 namespace m1 {
-LaunchFn select_fp64(int ndim, int geom, int nc) {
+LaunchEntry select_fp64(int ndim, int geom, int nc) {
   if (geom == kCart) {
-    if (ndim == 1 && nc == 1) return launch_step<Fp64, 1, kCart, 1>;
-    if (ndim == 1 && nc == 2) return launch_step<Fp64, 1, kCart, 2>;
-    if (ndim == 1 && nc == 3) return launch_step<Fp64, 1, kCart, 3>;
-    if (ndim == 2 && nc == 2) return launch_step<Fp64, 2, kCart, 2>;
-    if (ndim == 2 && nc == 3) return launch_step<Fp64, 2, kCart, 3>;
-    if (ndim == 3 && nc == 3) return launch_step<Fp64, 3, kCart, 3>;
-    return nullptr;
+    if (ndim == 1 && nc == 1) return entry<Fp64, 1, kCart, 1>();
+    if (ndim == 1 && nc == 2) return entry<Fp64, 1, kCart, 2>();
+    if (ndim == 1 && nc == 3) return entry<Fp64, 1, kCart, 3>();
+    if (ndim == 2 && nc == 2) return entry<Fp64, 2, kCart, 2>();
+    if (ndim == 2 && nc == 3) return entry<Fp64, 2, kCart, 3>();
+    if (ndim == 3 && nc == 3) return entry<Fp64, 3, kCart, 3>();
+    return LaunchEntry{nullptr, 0};
   }
-  if (nc != 3) return nullptr;
+  if (nc != 3) return LaunchEntry{nullptr, 0};
   if (geom == kCyl) {
-    if (ndim == 1) return launch_step<Fp64, 1, kCyl, 3>;
-    if (ndim == 2) return launch_step<Fp64, 2, kCyl, 3>;
-    if (ndim == 3) return launch_step<Fp64, 3, kCyl, 3>;
+    if (ndim == 1) return entry<Fp64, 1, kCyl, 3>();
+    if (ndim == 2) return entry<Fp64, 2, kCyl, 3>();
+    if (ndim == 3) return entry<Fp64, 3, kCyl, 3>();
   }
   if (geom == kSph) {
-    if (ndim == 1) return launch_step<Fp64, 1, kSph, 3>;
-    if (ndim == 2) return launch_step<Fp64, 2, kSph, 3>;
-    if (ndim == 3) return launch_step<Fp64, 3, kSph, 3>;
+    if (ndim == 1) return entry<Fp64, 1, kSph, 3>();
+    if (ndim == 2) return entry<Fp64, 2, kSph, 3>();
+    if (ndim == 3) return entry<Fp64, 3, kSph, 3>();
   }
-  return nullptr;
+  return LaunchEntry{nullptr, 0};
 }
 }  // namespace m1

@@ -220,3 +220,53 @@ def test_split_hot_sphere_within_the_problems_own_sensitivity():
     sens = np.linalg.norm(o2.E - o["E"]) / np.linalg.norm(o["E"])
     assert err["norm_E"] <= max(20 * sens, 1e-5), (err, sens)
     assert err["norm_E"] <= 2e-2, err
+
+
+@pytest.mark.parametrize("precision", ["fp64", "split"])
+@pytest.mark.parametrize("ndim,n", [(3, (70, 41, 39)), (2, (300, 130, 1))])
+def test_launch_shapes_agree_and_tuning_keeps_the_state(precision, ndim, n):
+    """Every CTA shape and march length gives the same step; the autotuner
+    does not advance the state or change the counters."""
+    import paper_2606_26268_b300 as R
+    p = W.random_smooth("cartesian", n, ndim, seed=4, bc="periodic", ncomp=ndim)
+    ref = None
+    r0 = R.from_problem(p, precision)
+    nvar = r0.get_launch()[2]
+    r0.close()
+    assert nvar >= 3
+    tol = 1e-13 if precision == "fp64" else 2e-6
+    for v in range(nvar):
+        for chunk in (0, 7, 16):
+            r = R.from_problem(p, precision)
+            r.set_launch(v, chunk)
+            r.step(3)
+            out = r.read("E").astype(np.float64)
+            r.close()
+            if ref is None:
+                ref = out
+            else:
+                np.testing.assert_allclose(out, ref, rtol=tol, atol=0)
+    r = R.from_problem(p, precision)
+    before = r.read("E").copy()
+    st0 = r.stats()
+    v, c, ms = r.tune(2)
+    assert ms > 0
+    np.testing.assert_array_equal(r.read("E"), before)
+    assert r.stats() == st0
+    r.step(3)
+    np.testing.assert_allclose(r.read("E").astype(np.float64), ref, rtol=tol, atol=0)
+    r.close()
+
+
+def test_split_large_box_stays_physical():
+    """Near-equilibrium cells carry flux of rounding size; the FP32 closure
+    must treat it as zero (a regression test for a denormal |F|^2 that turned
+    into NaN under the flush-to-zero reciprocal square root)."""
+    import paper_2606_26268_b300 as R
+    p = W.hot_sphere_3d(ns=(96, 96, 96))
+    r = R.from_problem(p, "split")
+    r.step(30)
+    assert r.sync() == R.RAD_OK
+    for k in ("E", "F", "e", "m"):
+        assert np.all(np.isfinite(r.read(k)))
+    r.close()
