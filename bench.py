@@ -184,7 +184,12 @@ def run_ours(args):
     # --- headline form -----------------------------------------------------
     r = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
     dt = r.dt()
-    tuned = r.tune(3) if not args.no_tune else r.get_launch()[:2] + (None,)
+    if args.launch:
+        v_, c_ = (int(x) for x in args.launch.split(","))
+        r.set_launch(v_, c_)
+        tuned = (v_, c_, None)
+    else:
+        tuned = r.tune(3) if not args.no_tune else r.get_launch()[:2] + (None,)
     barrier()
     with Clocks(local) as clk:
         barrier()
@@ -374,6 +379,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
