@@ -83,6 +83,9 @@ struct StepArgs {
   unsigned long long* stats;
   int* status;
   int chunk;      // cells along the march axis per CTA
+  // uniform Cartesian grids: 1 / width per direction and the largest width
+  T uni_inv[3];
+  T uni_h;
 };
 
 }  // namespace m1

@@ -150,10 +150,10 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
     lp = (fc + z) / s;
     lm = (fc - z) / s;
   } else {
-    // |F| below 1e-15 E (or a float denormal) is treated as zero flux: the
-    // closure depends on the direction of F only at O(f^2), and the FTZ
-    // approximations would turn a denormal |F|^2 into an infinite 1/|F|.
-    T rn = nF2 > fmaxf(T(1e-30) * E * E, T(1e-36)) ? rsqrt_approx(nF2) : T(0);
+    // A denormal |F|^2 is treated as zero flux: the flush-to-zero rsqrt would
+    // turn it into an infinite 1/|F|, and the closure depends on the
+    // direction of F only at O(f^2).
+    T rn = nF2 > T(1e-37) ? rsqrt_approx(nF2) : T(0);
     T nF = nF2 * rn;
     f = nF * invE;
     f = f > T(1) ? T(1) : f;
@@ -174,7 +174,8 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
       T dj = (j == D ? a : T(0)) + b * Fd * Fj;
       if (j < NC) flux[1 + j] = chat * dj;
     }
-    T z2 = T(2) * (T(1) - f2) * (s * (T(1) + c2) - T(2) * c2) * rcp_approx(s + T(1));
+    // (1 - f^2) / (s + 1) = (s - 1) / 3 since s^2 - 1 = 3 (1 - f^2)
+    T z2 = T(2.0 / 3.0) * (s - T(1)) * (s * (T(1) + c2) - T(2) * c2);
     T z = sqrt_approx(z2 > T(0) ? z2 : T(0));
     lp = (fc + z) * rs;
     lm = (fc - z) * rs;
@@ -189,7 +190,7 @@ __device__ __forceinline__ void pressure(const T (&u)[4], T& a, T& b) {
   T nF2 = u[1] * u[1];
   if (NC > 1) nF2 += u[2] * u[2];
   if (NC > 2) nF2 += u[3] * u[3];
-  if (sizeof(T) == 4 && !(nF2 > T(1e-30) * E * E && nF2 > T(1e-36))) nF2 = T(0);
+  if (sizeof(T) == 4 && !(nF2 > T(1e-37))) nF2 = T(0);
   T nF = Ops<T>::sqrt_(nF2);
   T f = Ops<T>::div(nF, E);
   f = f > T(1) ? T(1) : f;
@@ -322,6 +323,7 @@ struct CoupleParams {
   int maxit, newton;
   // float copies for the split-precision path
   float f_dtchat, f_dtc, f_cvfac, f_a, f_rtol;
+  int a_is_one;  // a_R == 1 (code units): the emission term needs no scaling
 };
 
 struct CoupleOut {
@@ -405,8 +407,8 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
     // the T^4 emission term and E* - a T^4 in double: T^2 of a float is
     // exact in double, so this is two roundings from exact
     double T2 = double(Tf) * double(Tf);
-    double aT4 = (p.a_rad * T2) * T2;
-    float D = float(double(Es) - aT4);
+    double aT2 = p.a_is_one ? T2 : p.a_rad * T2;
+    float D = float(fma(-aT2, T2, double(Es)));
     float aT3 = p.f_a * Tf * Tf * Tf;
     float det = c1 + 4.f * g * aT3;
     float q = D * rcp_approx(det);

@@ -45,7 +45,7 @@ __device__ __forceinline__ T cell_hmax(const GeomDev<T>& G, int p0, int p1, int 
 }
 
 // Opacities and optical depth rho chi h of a cell from its (rho, e).
-template <class P, int NDIM, int GEOM>
+template <class P, int NDIM, int GEOM, bool UNI = false>
 __device__ __forceinline__ typename P::T cell_tau(const StepArgs<P>& a, typename P::S rho,
                                                   typename P::S e, int p0, int p1, int p2,
                                                   typename P::T& kp, typename P::T& chi) {
@@ -57,6 +57,7 @@ __device__ __forceinline__ typename P::T cell_tau(const StepArgs<P>& a, typename
   else
     Temp = T(e) * rcp_approx(r * a.cp.f_cvfac);
   opacity(a.opac, r, Temp, kp, chi);
+  if constexpr (UNI) return r * chi * a.uni_h;
   return r * chi * cell_hmax<T, NDIM, GEOM>(a.geo, p0, p1, p2);
 }
 
@@ -121,7 +122,10 @@ __device__ __forceinline__ void load_state(const Fields<S>& f, long long i, T (&
 }
 
 // MINB: resident CTAs per SM requested from the register allocator.
-template <class P, int NDIM, int GEOM, int NC, int TX, int TY, int MINB>
+// UNI: uniform Cartesian grid (spacing from constants instead of tables; the
+// slopes use raw differences, the 1/dx factor cancelling in the van Leer
+// mean, and faces sit at -/+ 1/2 in units of the difference).
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>
 __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_constant__ StepArgs<P> a) {
   using S = typename P::S;
   using T = typename P::T;
@@ -169,6 +173,12 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
   // march-plane coordinates for tables: p1 (2D: march; 3D: tile y), p2
   auto p1_of = [&](int m) { return TILE_Y ? py : (MARCH ? m + gm : 0); };
   auto p2_of = [&](int m) { return TILE_Y ? m + gm : 0; };
+  // spacing tables, or their constant values on a uniform grid
+  auto IXC = [&](int d, int ip) -> T { return UNI ? T(1) : tabv(G, d, TAB_IDXC, ip); };
+  auto HHI = [&](int d, int ip) -> T { return UNI ? T(0.5) : tabv(G, d, TAB_HHI, ip); };
+  auto HLO = [&](int d, int ip) -> T { return UNI ? T(-0.5) : tabv(G, d, TAB_HLO, ip); };
+  auto ALO = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_ALO, ip); };
+  auto AHI = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_AHI, ip); };
 
   unsigned int c_fix = 0, c_efloor = 0, c_fclip = 0, c_fallback = 0, c_noconv = 0, c_itmax = 0;
   unsigned long long c_iters = 0;
@@ -193,20 +203,20 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       long long i = base + (long long)(m0 - 1 + gm) * ms;
       S r = __ldg(a.rho + i), e = __ldg(a.in.e + i);
       T kp, chi;
-      tau_m = cell_tau<P, NDIM, GEOM>(a, r, e, px, p1_of(m0 - 1), p2_of(m0 - 1), kp, chi);
+      tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, r, e, px, p1_of(m0 - 1), p2_of(m0 - 1), kp, chi);
     }
     T tau_prev = tau_m;
     {
       long long i = base + (long long)(m0 + gm) * ms;
       rho_m = __ldg(a.rho + i);
       e_m = __ldg(a.in.e + i);
-      tau_m = cell_tau<P, NDIM, GEOM>(a, rho_m, e_m, px, p1_of(m0), p2_of(m0), kp_m, chi_m);
+      tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, rho_m, e_m, px, p1_of(m0), p2_of(m0), kp_m, chi_m);
     }
     const int pm = m0 + gm;
-    T ix0 = tabv(G, MA, TAB_IDXC, pm - 2), ix1 = tabv(G, MA, TAB_IDXC, pm - 1);
-    T ix2 = tabv(G, MA, TAB_IDXC, pm);
-    int nf = face4<T, NC, MA>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, tabv(G, MA, TAB_HHI, pm - 1),
-                              tabv(G, MA, TAB_HLO, pm), T(0.5) * (tau_prev + tau_m), chat, zlo);
+    T ix0 = IXC(MA, pm - 2), ix1 = IXC(MA, pm - 1);
+    T ix2 = IXC(MA, pm);
+    int nf = face4<T, NC, MA>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
+                              HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat, zlo);
     if (upd_col && m0 == 0) c_fix += nf;
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
     T d1[4], d2[4];
@@ -215,14 +225,14 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       d1[v] = (q[0][v] - qm1[v]) * ix1;
       d2[v] = (q[1][v] - q[0][v]) * ix2;
     }
-    plm_state<T, NV>(d1, d2, q[0], tabv(G, MA, TAB_HHI, pm), hiS);
+    plm_state<T, NV>(d1, d2, q[0], HHI(MA, pm), hiS);
     int nfh = fix_face<T, NC>(hiS, q[0], flux2<T, NC>(q[0]), Ops<T>::rcp(q[0][0]));
     if (upd_col) c_fix += nfh;
   } else {
     load_state<S, NC>(a.in, base, q[0]);
     rho_m = __ldg(a.rho + base);
     e_m = __ldg(a.in.e + base);
-    tau_m = cell_tau<P, NDIM, GEOM>(a, rho_m, e_m, px, 0, 0, kp_m, chi_m);
+    tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, rho_m, e_m, px, 0, 0, kp_m, chi_m);
   }
 
   for (int m = m0; m < m1; ++m) {
@@ -233,7 +243,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       long long i1 = ic + ms;
       rho_n = __ldg(a.rho + i1);
       e_n = __ldg(a.in.e + i1);
-      tau_n = cell_tau<P, NDIM, GEOM>(a, rho_n, e_n, px, p1_of(m + 1), p2_of(m + 1), kp_n, chi_n);
+      tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, rho_n, e_n, px, p1_of(m + 1), p2_of(m + 1), kp_n, chi_n);
     }
     if (upd_col) {
 #pragma unroll
@@ -275,7 +285,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
         T kp, chi;
         int tx_ = min(hx, G.len[0] - 1);
         int ty_ = TILE_Y ? min(hy, G.len[1] - 1) : p1_of(m);
-        T t = cell_tau<P, NDIM, GEOM>(a, __ldg(a.rho + ih), __ldg(a.in.e + ih), tx_, ty_, p2_of(m),
+        T t = cell_tau<P, NDIM, GEOM, UNI>(a, __ldg(a.rho + ih), __ldg(a.in.e + ih), tx_, ty_, p2_of(m),
                                       kp, chi);
         s_tau[TILE_Y ? ys + 1 : 0][xs + 1] = t;
       }
@@ -294,9 +304,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       }
       T tau = T(0.5) * (s_tau[TILE_Y ? ty + 1 : 0][tx] + s_tau[TILE_Y ? ty + 1 : 0][tx + 1]);
       T fx[4];
-      int nf = face4<T, NC, 0>(um2, um1, u0, up1, tabv(G, 0, TAB_IDXC, px - 2),
-                               tabv(G, 0, TAB_IDXC, px - 1), tabv(G, 0, TAB_IDXC, px),
-                               tabv(G, 0, TAB_HHI, px - 1), tabv(G, 0, TAB_HLO, px), tau, chat, fx);
+      int nf = face4<T, NC, 0>(um2, um1, u0, up1, IXC(0, px - 2),
+                               IXC(0, px - 1), IXC(0, px),
+                               HHI(0, px - 1), HLO(0, px), tau, chat, fx);
       bool own = (tx >= 1 || x0 == 0) && cx <= Dm.n[0] && (!TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]));
       if (own) c_fix += nf;
 #pragma unroll
@@ -314,9 +324,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       }
       T tau = T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]);
       T fy[4];
-      int nf = face4<T, NC, 1>(um2, um1, u0, up1, tabv(G, 1, TAB_IDXC, py - 2),
-                               tabv(G, 1, TAB_IDXC, py - 1), tabv(G, 1, TAB_IDXC, py),
-                               tabv(G, 1, TAB_HHI, py - 1), tabv(G, 1, TAB_HLO, py), tau, chat, fy);
+      int nf = face4<T, NC, 1>(um2, um1, u0, up1, IXC(1, py - 2),
+                               IXC(1, py - 1), IXC(1, py),
+                               HHI(1, py - 1), HLO(1, py), tau, chat, fy);
       bool own = (ty >= 1 || y0 == 0) && cy <= Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0];
       if (own) c_fix += nf;
 #pragma unroll
@@ -326,7 +336,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     T hiN[4];
     if constexpr (MARCH) {
       const int pm = m + 1 + gm;  // padded index of cell m+1
-      T ix1 = tabv(G, MA, TAB_IDXC, pm - 1), ix2 = tabv(G, MA, TAB_IDXC, pm);
+      T ix1 = IXC(MA, pm - 1), ix2 = IXC(MA, pm);
       T d1[4], d2[4];
 #pragma unroll
       for (int v = 0; v < 4; ++v) {
@@ -334,8 +344,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
         d2[v] = (q[2][v] - q[1][v]) * ix2;
       }
       T loN[4];
-      plm_state<T, NV>(d1, d2, q[1], tabv(G, MA, TAB_HLO, pm), loN);
-      plm_state<T, NV>(d1, d2, q[1], tabv(G, MA, TAB_HHI, pm), hiN);
+      plm_state<T, NV>(d1, d2, q[1], HLO(MA, pm), loN);
+      plm_state<T, NV>(d1, d2, q[1], HHI(MA, pm), hiN);
       T inv2 = Ops<T>::rcp(q[1][0]);
       T n2 = flux2<T, NC>(q[1]);
       int nf = fix_face<T, NC>(loN, q[1], n2, inv2);
@@ -357,7 +367,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
           flo[v] = v < NV ? s_fx[v][ty][tx] : T(0);
           fhi[v] = v < NV ? s_fx[v][ty][tx + 1] : T(0);
         }
-        T alo = tabv(G, 0, TAB_ALO, px), ahi = tabv(G, 0, TAB_AHI, px);
+        T alo = ALO(0, px), ahi = AHI(0, px);
 #pragma unroll
         for (int v = 0; v < NV; ++v) dU[v] -= ahi * fhi[v] - alo * flo[v];
         if (GEOM == kCyl && NC >= 2) {
@@ -384,7 +394,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
             fhi[v] = zhi[v];
           }
         }
-        T alo = tabv(G, 1, TAB_ALO, p1), ahi = tabv(G, 1, TAB_AHI, p1);
+        T alo = ALO(1, p1), ahi = AHI(1, p1);
         if (GEOM != kCart) {
           alo *= met0;
           ahi *= met0;
@@ -398,7 +408,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       }
       // direction 2
       if constexpr (NDIM >= 3) {
-        T alo = tabv(G, 2, TAB_ALO, p2), ahi = tabv(G, 2, TAB_AHI, p2);
+        T alo = ALO(2, p2), ahi = AHI(2, p2);
         if (GEOM == kSph) {
           T f = met0 * tabv(G, 1, TAB_PHF, p1);
           alo *= f;
@@ -413,7 +423,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       if constexpr (GEOM == kSph && NDIM == 1) {
         T fl[4] = {0, 0, 0, 0}, lm, lp;
         state_flux<T, NC, 1>(u, chat, fl, lm, lp);
-        T alo = met0 * tabv(G, 1, TAB_ALO, 0), ahi = met0 * tabv(G, 1, TAB_AHI, 0);
+        T alo = met0 * ALO(1, 0), ahi = met0 * AHI(1, 0);
 #pragma unroll
         for (int v = 0; v < NV; ++v) dU[v] -= (ahi - alo) * fl[v];
         if (NC >= 3) {

@@ -50,6 +50,7 @@ struct rad_ctx {
   uint64_t steps = 0;
   LaunchEntry launch{nullptr, 0};
   int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
+  bool uniform = false;         // Cartesian with equal widths in every direction
 };
 
 static const char* kMsg[] = {"ok",
@@ -267,7 +268,17 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   c->esize = p.precision == RAD_FP64 ? 8 : 4;
   build_tables(c);
   c->dt_cfl = cfl_dt(c);
-  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc);
+  c->uniform = geometry == RAD_CARTESIAN;
+  for (int d = 0; d < c->ndim && c->uniform; ++d) {
+    const std::vector<double>& x = c->xf[d];
+    double w0 = x[1] - x[0];
+    for (int i = 1; i < c->n[d]; ++i)
+      if (std::fabs((x[i + 1] - x[i]) - w0) > 1e-12 * w0) {
+        c->uniform = false;
+        break;
+      }
+  }
+  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform);
   if (!c->launch.fn) {
     delete c;
     return RAD_EUNSUPPORTED;
@@ -629,6 +640,7 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
   cp.f_cvfac = float(cp.cvfac);
   cp.f_a = float(c->par.a_rad);
   cp.f_rtol = float(c->par.newton_rtol);
+  cp.a_is_one = c->par.a_rad == 1.0;
   a.chat = T(c->par.chat);
   a.dt = T(dt);
   a.efloor = T(c->par.e_floor);
@@ -637,6 +649,13 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
   a.stats = reinterpret_cast<unsigned long long*>(c->ws + c->off_stats);
   a.status = reinterpret_cast<int*>(c->ws + c->off_status);
   a.chunk = 0;
+  double hmax = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    double w = c->xf[d][1] - c->xf[d][0];
+    a.uni_inv[d] = T(1.0 / w);
+    if (d < c->ndim) hmax = std::max(hmax, w);
+  }
+  a.uni_h = T(hmax);
 }
 
 extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {

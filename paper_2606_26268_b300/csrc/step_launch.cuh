@@ -5,30 +5,30 @@
 
 namespace m1 {
 
-template <class P, int NDIM, int GEOM, int NC, int TX, int TY, int MINB>
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>
 cudaError_t launch_shape(StepArgs<P> a, cudaStream_t s, int chunk) {
   const int* n = a.dim.n;
   if constexpr (NDIM == 3) {
     a.chunk = chunk > 0 ? chunk : 32;
     if (a.chunk > n[2]) a.chunk = n[2];
     dim3 grid((n[0] + TX - 2) / (TX - 1), (n[1] + TY - 2) / (TY - 1), (n[2] + a.chunk - 1) / a.chunk);
-    step_kernel<P, 3, GEOM, NC, TX, TY, MINB><<<grid, dim3(TX, TY), 0, s>>>(a);
+    step_kernel<P, 3, GEOM, NC, UNI, TX, TY, MINB><<<grid, dim3(TX, TY), 0, s>>>(a);
   } else if constexpr (NDIM == 2) {
     a.chunk = chunk > 0 ? chunk : 64;
     if (a.chunk > n[1]) a.chunk = n[1];
     dim3 grid((n[0] + TX - 2) / (TX - 1), (n[1] + a.chunk - 1) / a.chunk);
-    step_kernel<P, 2, GEOM, NC, TX, 1, MINB><<<grid, dim3(TX, 1), 0, s>>>(a);
+    step_kernel<P, 2, GEOM, NC, UNI, TX, 1, MINB><<<grid, dim3(TX, 1), 0, s>>>(a);
   } else {
     a.chunk = 1;
     dim3 grid((n[0] + TX - 2) / (TX - 1));
-    step_kernel<P, 1, GEOM, NC, TX, 1, MINB><<<grid, dim3(TX, 1), 0, s>>>(a);
+    step_kernel<P, 1, GEOM, NC, UNI, TX, 1, MINB><<<grid, dim3(TX, 1), 0, s>>>(a);
   }
   return cudaGetLastError();
 }
 
 // CTA shapes.  3D: 32x8 (2 or 3 CTAs/SM), 32x16, 64x8; 2D rows of 128, 256
 // or 64 threads; 1D: 128.  Curvilinear grids get the default shape only.
-template <class P, int NDIM, int GEOM, int NC>
+template <class P, int NDIM, int GEOM, int NC, bool UNI>
 struct Shapes {
   static constexpr int count = (GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? 4 : 3);
   static cudaError_t launch(const void* vargs, cudaStream_t s, int variant, int chunk) {
@@ -36,26 +36,26 @@ struct Shapes {
     if (variant < 0 || variant >= count) variant = 0;
     if constexpr (NDIM == 3) {
       if constexpr (count > 1) {
-        if (variant == 1) return launch_shape<P, 3, GEOM, NC, 32, 8, 3>(a, s, chunk);
-        if (variant == 2) return launch_shape<P, 3, GEOM, NC, 32, 16, 1>(a, s, chunk);
-        if (variant == 3) return launch_shape<P, 3, GEOM, NC, 64, 8, 1>(a, s, chunk);
+        if (variant == 1) return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 3>(a, s, chunk);
+        if (variant == 2) return launch_shape<P, 3, GEOM, NC, UNI, 32, 16, 1>(a, s, chunk);
+        if (variant == 3) return launch_shape<P, 3, GEOM, NC, UNI, 64, 8, 1>(a, s, chunk);
       }
-      return launch_shape<P, 3, GEOM, NC, 32, 8, 2>(a, s, chunk);
+      return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2>(a, s, chunk);
     } else if constexpr (NDIM == 2) {
       if constexpr (count > 1) {
-        if (variant == 1) return launch_shape<P, 2, GEOM, NC, 256, 1, 1>(a, s, chunk);
-        if (variant == 2) return launch_shape<P, 2, GEOM, NC, 64, 1, 1>(a, s, chunk);
+        if (variant == 1) return launch_shape<P, 2, GEOM, NC, UNI, 256, 1, 1>(a, s, chunk);
+        if (variant == 2) return launch_shape<P, 2, GEOM, NC, UNI, 64, 1, 1>(a, s, chunk);
       }
-      return launch_shape<P, 2, GEOM, NC, 128, 1, 1>(a, s, chunk);
+      return launch_shape<P, 2, GEOM, NC, UNI, 128, 1, 1>(a, s, chunk);
     } else {
-      return launch_shape<P, 1, GEOM, NC, 128, 1, 1>(a, s, chunk);
+      return launch_shape<P, 1, GEOM, NC, UNI, 128, 1, 1>(a, s, chunk);
     }
   }
 };
 
-template <class P, int NDIM, int GEOM, int NC>
+template <class P, int NDIM, int GEOM, int NC, bool UNI = false>
 LaunchEntry entry() {
-  return LaunchEntry{&Shapes<P, NDIM, GEOM, NC>::launch, Shapes<P, NDIM, GEOM, NC>::count};
+  return LaunchEntry{&Shapes<P, NDIM, GEOM, NC, UNI>::launch, Shapes<P, NDIM, GEOM, NC, UNI>::count};
 }
 
 }  // namespace m1

@@ -13,5 +13,6 @@ struct LaunchEntry {
 };
 
 // The launcher for (precision, active directions, geometry, carried flux
-// components); fn == nullptr when that combination is not instantiated.
-LaunchEntry select_launch(bool split, int ndim, int geom, int nc);
+// components, uniform Cartesian spacing); fn == nullptr when that
+// combination is not instantiated.
+LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform);

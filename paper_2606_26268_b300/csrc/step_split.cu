@@ -2,7 +2,16 @@
 #include "step_launch.cuh"
 
 namespace m1 {
-LaunchEntry select_split(int ndim, int geom, int nc) {
+LaunchEntry select_split(int ndim, int geom, int nc, bool uni) {
+  if (geom == kCart && uni) {
+    if (ndim == 1 && nc == 1) return entry<Split, 1, kCart, 1, true>();
+    if (ndim == 1 && nc == 2) return entry<Split, 1, kCart, 2, true>();
+    if (ndim == 1 && nc == 3) return entry<Split, 1, kCart, 3, true>();
+    if (ndim == 2 && nc == 2) return entry<Split, 2, kCart, 2, true>();
+    if (ndim == 2 && nc == 3) return entry<Split, 2, kCart, 3, true>();
+    if (ndim == 3 && nc == 3) return entry<Split, 3, kCart, 3, true>();
+    return LaunchEntry{nullptr, 0};
+  }
   if (geom == kCart) {
     if (ndim == 1 && nc == 1) return entry<Split, 1, kCart, 1>();
     if (ndim == 1 && nc == 2) return entry<Split, 1, kCart, 2>();

@@ -270,3 +270,16 @@ def test_split_large_box_stays_physical():
     for k in ("E", "F", "e", "m"):
         assert np.all(np.isfinite(r.read(k)))
     r.close()
+
+
+@pytest.mark.parametrize("ndim", [2, 3])
+def test_stretched_cartesian_grid_fp64(ndim):
+    """Non-uniform Cartesian spacing (the table path of the kernel)."""
+    n = (50, 37, 21) if ndim == 3 else (120, 61, 1)
+    p = W.random_smooth("cartesian", n, ndim, seed=31, bc="outflow",
+                        opacity={"kind": "powerlaw", "k0": 3.0, "a_rho": 1.0, "b_T": -1.0,
+                                 "kmin": 1e-3, "kmax": 1e3, "sigma_ratio": 0.2})
+    for d in range(ndim):
+        w = 1.03 ** np.arange(n[d])
+        p.xfaces[d] = np.r_[0.0, np.cumsum(w / w.sum())]
+    check64(p, 5)
