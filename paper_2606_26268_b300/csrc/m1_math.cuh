@@ -165,14 +165,16 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
     T rs = rsqrt_approx(q);
     T s = q * rs;
     T xi = (T(3) + T(4) * f2) * rcp_approx(T(5) + T(2) * s);
-    T a = T(0.5) * (T(1) - xi) * E;
-    b = T(0.5) * (T(3) * xi - T(1)) * E * (rn * rn);
+    T Ec = E * chat;
+    T ac = (T(0.5) - T(0.5) * xi) * Ec;
+    T bFd = ((T(1.5) * xi - T(0.5)) * Ec) * (rn * rn) * Fd;
     flux[0] = chat * Fd;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      T Fj = (j < NC) ? F[j] : T(0);
-      T dj = (j == D ? a : T(0)) + b * Fd * Fj;
-      if (j < NC) flux[1 + j] = chat * dj;
+      if (j < NC) {
+        T v = bFd * F[j];
+        flux[1 + j] = (j == D) ? v + ac : v;
+      }
     }
     // (1 - f^2) / (s + 1) = (s - 1) / 3 since s^2 - 1 = 3 (1 - f^2)
     T z2 = T(2.0 / 3.0) * (s - T(1)) * (s * (T(1) + c2) - T(2) * c2);
@@ -208,26 +210,37 @@ template <class T, int NV>
 __device__ __forceinline__ void hll(const T (&uL)[4], const T (&uR)[4], const T (&fL)[4],
                                     const T (&fR)[4], T lmL, T lpL, T lmR, T lpR, T chat,
                                     T tau, T (&out)[4]) {
-  T sl = chat * (lmL < lmR ? lmL : lmR);
-  T sr = chat * (lpL > lpR ? lpL : lpR);
-  if (tau > T(0)) {
-    T bound = Ops<T>::div(T(4) * chat, T(3) * tau);
-    if (sl < -bound) sl = -bound;
-    if (sr > bound) sr = bound;
-  }
-  if (sl >= T(0)) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = fL[q];
-  } else if (sr <= T(0)) {
-#pragma unroll
-    for (int q = 0; q < NV; ++q) out[q] = fR[q];
-  } else {
-    T inv = Ops<T>::rcp(sr - sl);
-#pragma unroll
-    for (int q = 0; q < NV; ++q) {
-      T num = sr * fL[q] - sl * fR[q] + sl * sr * (uR[q] - uL[q]);
-      out[q] = (sizeof(T) == 8) ? num / (sr - sl) : num * inv;
+  if constexpr (sizeof(T) == 8) {
+    T sl = chat * (lmL < lmR ? lmL : lmR);
+    T sr = chat * (lpL > lpR ? lpL : lpR);
+    if (tau > T(0)) {
+      T bound = T(4) * chat / (T(3) * tau);
+      if (sl < -bound) sl = -bound;
+      if (sr > bound) sr = bound;
     }
+    if (sl >= T(0)) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) out[q] = fL[q];
+    } else if (sr <= T(0)) {
+#pragma unroll
+      for (int q = 0; q < NV; ++q) out[q] = fR[q];
+    } else {
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        out[q] = (sr * fL[q] - sl * fR[q] + sl * sr * (uR[q] - uL[q])) / (sr - sl);
+    }
+  } else {
+    // Branch-free form: with S_L <= 0 <= S_R enforced the same expression
+    // gives the two upwind cases (S_L = 0 -> F_L, S_R = 0 -> F_R); the
+    // thick-limit bound 4 chat / (3 tau) is +inf when tau = 0.
+    T bound = (T(4.0 / 3.0) * chat) * rcp_approx(tau);
+    T sl = fmaxf(fminf(chat * fminf(lmL, lmR), T(0)), -bound);
+    T sr = fminf(fmaxf(chat * fmaxf(lpL, lpR), T(0)), bound);
+    T inv = rcp_approx(fmaxf(sr - sl, T(1e-30)));
+    T slsr = sl * sr;
+#pragma unroll
+    for (int q = 0; q < NV; ++q)
+      out[q] = (sr * fL[q] - sl * fR[q] + slsr * (uR[q] - uL[q])) * inv;
   }
 }
 

@@ -93,23 +93,44 @@ __device__ __forceinline__ void riemann(const T (&uL)[4], const T (&uR)[4], T ch
 // face between um1 and u0).  ix_k = 1 / (centre distance) of the pairs
 // (um2, um1), (um1, u0), (u0, up1); hh = offset of the upper face of um1,
 // hl = offset of the lower face of u0.  Returns the number of fixed states.
-template <class T, int NC, int D>
+// Half of the van Leer limited slope on a uniform grid, in units of the
+// cell difference: vl(dl, dr) / 2 = dl dr / (dl + dr) when dl dr > 0.
+template <class T>
+__device__ __forceinline__ T half_vanleer(T dl, T dr) {
+  T p = dl * dr;
+  return p > T(0) ? p * rcp_approx(dl + dr) : T(0);
+}
+
+template <class T, int NC, int D, bool UNI>
 __device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const T (&u0)[4],
                                      const T (&up1)[4], T ix0, T ix1, T ix2, T hh, T hl, T tau,
-                                     T chat, T (&out)[4]) {
+                                     T chat, T inv_u0, T n2_u0, T (&out)[4]) {
   constexpr int NV = 1 + NC;
-  T d0[4], d1[4], d2[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) {
-    d0[q] = (um1[q] - um2[q]) * ix0;
-    d1[q] = (u0[q] - um1[q]) * ix1;
-    d2[q] = (up1[q] - u0[q]) * ix2;
-  }
   T uL[4], uR[4];
-  plm_state<T, NV>(d0, d1, um1, hh, uL);
-  plm_state<T, NV>(d1, d2, u0, hl, uR);
+  if constexpr (UNI && sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      if (q < NV) {
+        T d0 = um1[q] - um2[q], d1 = u0[q] - um1[q], d2 = up1[q] - u0[q];
+        uL[q] = um1[q] + half_vanleer(d0, d1);
+        uR[q] = u0[q] - half_vanleer(d1, d2);
+      } else {
+        uL[q] = uR[q] = T(0);
+      }
+    }
+  } else {
+    T d0[4], d1[4], d2[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      d0[q] = (um1[q] - um2[q]) * ix0;
+      d1[q] = (u0[q] - um1[q]) * ix1;
+      d2[q] = (up1[q] - u0[q]) * ix2;
+    }
+    plm_state<T, NV>(d0, d1, um1, hh, uL);
+    plm_state<T, NV>(d1, d2, u0, hl, uR);
+  }
   int nfix = fix_face<T, NC>(uL, um1, flux2<T, NC>(um1), Ops<T>::rcp(um1[0]));
-  nfix += fix_face<T, NC>(uR, u0, flux2<T, NC>(u0), Ops<T>::rcp(u0[0]));
+  nfix += fix_face<T, NC>(uR, u0, n2_u0, inv_u0);
   riemann<T, NC, D>(uL, uR, chat, tau, out);
   return nfix;
 }
@@ -188,6 +209,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
   T q[3][4];
   T hiS[4];         // fixed upper face state of cell m along the march axis
   T zlo[4], zhi[4]; // march-face fluxes m-1/2 and m+1/2
+  T inv_own = 0, n2_own = 0;  // 1/E and |F|^2 of the own cell (fix of its face states)
   T tau_m = 0, tau_n = 0, kp_m = 0, chi_m = 0, kp_n = 0, chi_n = 0;
   S rho_m = 0, e_m = 0, rho_n = 0, e_n = 0;
 #pragma unroll
@@ -215,8 +237,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     const int pm = m0 + gm;
     T ix0 = IXC(MA, pm - 2), ix1 = IXC(MA, pm - 1);
     T ix2 = IXC(MA, pm);
-    int nf = face4<T, NC, MA>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
-                              HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat, zlo);
+    int nf = face4<T, NC, MA, UNI>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
+                                   HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat,
+                                   Ops<T>::rcp(q[0][0]), flux2<T, NC>(q[0]), zlo);
     if (upd_col && m0 == 0) c_fix += nf;
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
     T d1[4], d2[4];
@@ -226,13 +249,65 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       d2[v] = (q[1][v] - q[0][v]) * ix2;
     }
     plm_state<T, NV>(d1, d2, q[0], HHI(MA, pm), hiS);
-    int nfh = fix_face<T, NC>(hiS, q[0], flux2<T, NC>(q[0]), Ops<T>::rcp(q[0][0]));
+    inv_own = Ops<T>::rcp(q[0][0]);
+    n2_own = flux2<T, NC>(q[0]);
+    int nfh = fix_face<T, NC>(hiS, q[0], n2_own, inv_own);
     if (upd_col) c_fix += nfh;
   } else {
     load_state<S, NC>(a.in, base, q[0]);
+    inv_own = Ops<T>::rcp(q[0][0]);
+    n2_own = flux2<T, NC>(q[0]);
     rho_m = __ldg(a.rho + base);
     e_m = __ldg(a.in.e + base);
     tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, rho_m, e_m, px, 0, 0, kp_m, chi_m);
+  }
+
+  // Halo cell of this thread (each thread owns at most one), decoded once;
+  // its values for plane m are loaded one iteration ahead.
+  static_assert(NHALO <= NT, "one halo cell per thread");
+  const bool has_halo = tid < NHALO;
+  int hxs = 0, hys = 0;
+  if (has_halo) {
+    const int h = tid;
+    if (TILE_Y) {
+      if (h < 3 * TY) {
+        int c = h / TY;
+        hxs = c == 0 ? -2 : (c == 1 ? -1 : TX);
+        hys = h - c * TY;
+      } else {
+        int hh = h - 3 * TY;
+        int c = hh / TX;
+        hys = c == 0 ? -2 : (c == 1 ? -1 : TY);
+        hxs = hh - c * TX;
+      }
+    } else {
+      hxs = h == 0 ? -2 : (h == 1 ? -1 : TX);
+    }
+  }
+  const bool halo_tau = has_halo && (TILE_Y ? ((hxs == -1 && hys >= 0 && hys < TY) ||
+                                               (hys == -1 && hxs >= 0 && hxs < TX))
+                                            : (hxs == -1));
+  const int hx = min(max(x0 + hxs + Dm.g[0], 0), Dm.pn[0] - 1);
+  const int hy = TILE_Y ? min(max(y0 + hys + Dm.g[1], 0), Dm.pn[1] - 1) : 0;
+  const long long hbase = (long long)hx + (TILE_Y ? (long long)hy * Dm.sy : 0ll);
+  T hu[4] = {0, 0, 0, 0};
+  S hrho = S(1), he = S(1);
+  auto load_halo = [&](int m) {
+    if (has_halo) {
+      long long ih = hbase + (long long)(m + gm) * ms;
+      load_state<S, NC>(a.in, ih, hu);
+      if (halo_tau) {
+        hrho = __ldg(a.rho + ih);
+        he = __ldg(a.in.e + ih);
+      }
+    }
+  };
+  load_halo(m0);
+  // (rho, e) of the cell m + 1 of the own column, loaded one iteration ahead
+  S rho_p = S(1), e_p = S(1);
+  if constexpr (MARCH) {
+    rho_p = __ldg(a.rho + base + (long long)(m0 + 1 + gm) * ms);
+    e_p = __ldg(a.in.e + base + (long long)(m0 + 1 + gm) * ms);
   }
 
   for (int m = m0; m < m1; ++m) {
@@ -240,10 +315,10 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     T mom[3] = {0, 0, 0};
     if constexpr (MARCH) {
       load_state<S, NC>(a.in, ic + 2 * ms, q[2]);
-      long long i1 = ic + ms;
-      rho_n = __ldg(a.rho + i1);
-      e_n = __ldg(a.in.e + i1);
-      tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, rho_n, e_n, px, p1_of(m + 1), p2_of(m + 1), kp_n, chi_n);
+      rho_n = rho_p;
+      e_n = e_p;
+      rho_p = __ldg(a.rho + ic + 2 * ms);
+      e_p = __ldg(a.in.e + ic + 2 * ms);
     }
     if (upd_col) {
 #pragma unroll
@@ -253,43 +328,21 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
 #pragma unroll
     for (int v = 0; v < NV; ++v) s_u[v][ty + OY][tx + 2] = q[0][v];
     s_tau[TILE_Y ? ty + 1 : 0][tx + 1] = tau_m;
-    // halo of the plane
-    for (int h = tid; h < NHALO; h += NT) {
-      int xs, ys;
-      if (TILE_Y) {
-        if (h < 3 * TY) {
-          int c = h / TY;
-          xs = c == 0 ? -2 : (c == 1 ? -1 : TX);
-          ys = h - c * TY;
-        } else {
-          int hh = h - 3 * TY;
-          int c = hh / TX;
-          ys = c == 0 ? -2 : (c == 1 ? -1 : TY);
-          xs = hh - c * TX;
-        }
-      } else {
-        xs = h == 0 ? -2 : (h == 1 ? -1 : TX);
-        ys = 0;
-      }
-      int hx = min(max(x0 + xs + Dm.g[0], 0), Dm.pn[0] - 1);
-      int hy = TILE_Y ? min(max(y0 + ys + Dm.g[1], 0), Dm.pn[1] - 1) : 0;
-      long long ih = (long long)hx + (TILE_Y ? (long long)hy * Dm.sy : 0ll) +
-                     (long long)(m + gm) * ms;
-      T u[4];
-      load_state<S, NC>(a.in, ih, u);
+    // halo of the plane (values loaded in the previous iteration)
+    if (has_halo) {
 #pragma unroll
-      for (int v = 0; v < NV; ++v) s_u[v][ys + OY][xs + 2] = u[v];
-      bool need_tau = TILE_Y ? ((xs == -1 && ys >= 0 && ys < TY) || (ys == -1 && xs >= 0 && xs < TX))
-                             : (xs == -1);
-      if (need_tau) {
+      for (int v = 0; v < NV; ++v) s_u[v][hys + OY][hxs + 2] = hu[v];
+      if (halo_tau) {
         T kp, chi;
         int tx_ = min(hx, G.len[0] - 1);
         int ty_ = TILE_Y ? min(hy, G.len[1] - 1) : p1_of(m);
-        T t = cell_tau<P, NDIM, GEOM, UNI>(a, __ldg(a.rho + ih), __ldg(a.in.e + ih), tx_, ty_, p2_of(m),
-                                      kp, chi);
-        s_tau[TILE_Y ? ys + 1 : 0][xs + 1] = t;
+        s_tau[TILE_Y ? hys + 1 : 0][hxs + 1] =
+            cell_tau<P, NDIM, GEOM, UNI>(a, hrho, he, tx_, ty_, p2_of(m), kp, chi);
       }
     }
+    if (MARCH && m + 1 < m1) load_halo(m + 1);
+    if constexpr (MARCH)
+      tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, rho_n, e_n, px, p1_of(m + 1), p2_of(m + 1), kp_n, chi_n);
     __syncthreads();
 
     // x face (tx - 1/2)
@@ -304,9 +357,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       }
       T tau = T(0.5) * (s_tau[TILE_Y ? ty + 1 : 0][tx] + s_tau[TILE_Y ? ty + 1 : 0][tx + 1]);
       T fx[4];
-      int nf = face4<T, NC, 0>(um2, um1, u0, up1, IXC(0, px - 2),
+      int nf = face4<T, NC, 0, UNI>(um2, um1, u0, up1, IXC(0, px - 2),
                                IXC(0, px - 1), IXC(0, px),
-                               HHI(0, px - 1), HLO(0, px), tau, chat, fx);
+                               HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx);
       bool own = (tx >= 1 || x0 == 0) && cx <= Dm.n[0] && (!TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]));
       if (own) c_fix += nf;
 #pragma unroll
@@ -324,9 +377,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       }
       T tau = T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]);
       T fy[4];
-      int nf = face4<T, NC, 1>(um2, um1, u0, up1, IXC(1, py - 2),
+      int nf = face4<T, NC, 1, UNI>(um2, um1, u0, up1, IXC(1, py - 2),
                                IXC(1, py - 1), IXC(1, py),
-                               HHI(1, py - 1), HLO(1, py), tau, chat, fy);
+                               HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy);
       bool own = (ty >= 1 || y0 == 0) && cy <= Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0];
       if (own) c_fix += nf;
 #pragma unroll
@@ -334,22 +387,32 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     }
     // march face m + 1/2 from the column registers
     T hiN[4];
+    T inv_n = 0, n2_n = 0;
     if constexpr (MARCH) {
       const int pm = m + 1 + gm;  // padded index of cell m+1
-      T ix1 = IXC(MA, pm - 1), ix2 = IXC(MA, pm);
-      T d1[4], d2[4];
-#pragma unroll
-      for (int v = 0; v < 4; ++v) {
-        d1[v] = (q[1][v] - q[0][v]) * ix1;
-        d2[v] = (q[2][v] - q[1][v]) * ix2;
-      }
       T loN[4];
-      plm_state<T, NV>(d1, d2, q[1], HLO(MA, pm), loN);
-      plm_state<T, NV>(d1, d2, q[1], HHI(MA, pm), hiN);
-      T inv2 = Ops<T>::rcp(q[1][0]);
-      T n2 = flux2<T, NC>(q[1]);
-      int nf = fix_face<T, NC>(loN, q[1], n2, inv2);
-      int nf2 = fix_face<T, NC>(hiN, q[1], n2, inv2);
+      if constexpr (UNI && sizeof(T) == 4) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T hs = v < NV ? half_vanleer(q[1][v] - q[0][v], q[2][v] - q[1][v]) : T(0);
+          loN[v] = q[1][v] - hs;
+          hiN[v] = q[1][v] + hs;
+        }
+      } else {
+        T ix1 = IXC(MA, pm - 1), ix2 = IXC(MA, pm);
+        T d1[4], d2[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          d1[v] = (q[1][v] - q[0][v]) * ix1;
+          d2[v] = (q[2][v] - q[1][v]) * ix2;
+        }
+        plm_state<T, NV>(d1, d2, q[1], HLO(MA, pm), loN);
+        plm_state<T, NV>(d1, d2, q[1], HHI(MA, pm), hiN);
+      }
+      inv_n = Ops<T>::rcp(q[1][0]);
+      n2_n = flux2<T, NC>(q[1]);
+      int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
+      int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
       riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
       // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
       if (upd_col) c_fix += nf + (m + 1 < m1 ? nf2 : 0);
@@ -555,6 +618,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
         zlo[v] = zhi[v];
       }
       tau_m = tau_n;
+      inv_own = inv_n;
+      n2_own = n2_n;
       kp_m = kp_n;
       chi_m = chi_n;
       rho_m = rho_n;
