@@ -114,6 +114,10 @@ typedef struct {
   double newton_rtol;   /* RAD_NEWTON: stop when |T_{k+1}-T_k| <= rtol T_{k+1} */
   int newton_maxit;     /* RAD_NEWTON: iteration cap, >= 1 */
   int ncomp;            /* vector components in the caller's F, v and m arrays, 1..3 */
+  int use_mlp;          /* RAD_NEWTON only: start the iteration from the learned guess
+                           (once rad_mlp_set/init/train has given it parameters) in cells
+                           whose first linearised solve changes T by more than mlp_gate */
+  double mlp_gate;      /* relative change of T above which the learned guess is used */
 } rad_params;
 
 /* Counters accumulated by rad_step since the last rad_reset_stats. */
@@ -132,7 +136,8 @@ typedef struct rad_ctx rad_ctx;
 
 /* Fills *p with defaults: chat = c = 1, a_rad = 1, gamma = 5/3, mu = 1,
  * cfl = 0.4, e_floor = 1e-30, RAD_FP64, RAD_LINEARIZED_ONCE, rtol = 1e-12,
- * maxit = 50, ncomp = 3.  Returns RAD_EINVAL if p is NULL. */
+ * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2.  Returns RAD_EINVAL if
+ * p is NULL. */
 rad_status rad_default_params(rad_params *p);
 
 /* Validates the description, precomputes the geometry (face areas, volumes,
@@ -213,6 +218,52 @@ rad_status rad_get_launch(const rad_ctx *ctx, int *variant, int *chunk, int *nva
  * chunk and its time per step in ms.  Synchronises the stream.  Not in the
  * paper.  Errors: RAD_EINVAL (no state), RAD_ENOMEM, RAD_ECUDA. */
 rad_status rad_tune(rad_ctx *ctx, int reps, int *variant, int *chunk, float *ms);
+
+/* --------------------------------------------------------------------------
+ * Learned starting guess of the coupling iteration (not in the paper: an
+ * extension of this implementation).  In RAD_NEWTON mode the root T^{n+1}
+ * of the cell's coupling depends only on alpha = g a T^n^3/((1+g_r) C_v) and
+ * eps = E* / (a T^n^4) (Sect. 2.8 with T^4 kept exact).  A network with three
+ * tanh layers of 64 units maps (log10 alpha / 4, log10 eps / 4) to
+ * log(T^{n+1}/T^n); the iteration starts from T^n exp(output) and keeps its
+ * convergence test, so results agree with starting from T^n to that test.
+ * Records are float4 (x1, x2, log(T^{n+1}/T^n), gate value), device memory.
+ * Parameters: rad_mlp_nparam() floats, laid out W1 (64x2, row-major), b1,
+ * W2 (64x64), b2, W3 (64x64), b3, w4 (64), b4.
+ * -------------------------------------------------------------------------- */
+int rad_mlp_nparam(void);
+
+/* Host copies of the parameters in and out (n == rad_mlp_nparam()); set
+ * also clears the Adam moments.  Errors: RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA. */
+rad_status rad_mlp_set(rad_ctx *ctx, const float *host_params, size_t n);
+rad_status rad_mlp_get(rad_ctx *ctx, float *host_params, size_t n);
+
+/* Glorot-uniform weights, zero biases, from a seeded splitmix64 stream. */
+rad_status rad_mlp_init(rad_ctx *ctx, uint64_t seed);
+
+/* Trains on n device records: `epochs` passes over a seeded permutation of
+ * the records in mini-batches of `batch`, mean-squared error, Adam with step
+ * lr.  Runs forward/backward/update kernels on the context's stream and
+ * synchronises; *final_loss (may be NULL) is the mean loss of the last epoch.
+ * Initialises the parameters first if none were given. */
+rad_status rad_mlp_train(rad_ctx *ctx, const float *dev_records, size_t n, int epochs, int batch,
+                         float lr, uint64_t seed, float *final_loss);
+
+/* Gradient of the mean-squared error over n device records with the current
+ * parameters (host_grad: rad_mlp_nparam() floats, may be NULL) and the loss;
+ * synchronises.  For checking the training kernels. */
+rad_status rad_mlp_grad(rad_ctx *ctx, const float *dev_records, size_t n, float *host_grad,
+                        float *host_loss);
+
+/* Network output for n device records into dev_out (n floats). */
+rad_status rad_mlp_predict(rad_ctx *ctx, const float *dev_records, size_t n, float *dev_out);
+
+/* Logging of converged RAD_NEWTON solves for training: cells whose linear
+ * index is a multiple of `stride` append one record to dev_records (up to
+ * `capacity`); NULL unbinds.  rad_log_count returns the records written
+ * (synchronising). */
+rad_status rad_log_bind(rad_ctx *ctx, float *dev_records, size_t capacity, long long stride);
+rad_status rad_log_count(rad_ctx *ctx, size_t *n);
 
 /* Releases the context (and the workspace if rad_alloc_workspace made it). */
 void rad_destroy(rad_ctx *ctx);

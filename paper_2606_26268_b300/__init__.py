@@ -54,7 +54,8 @@ class rad_params(C.Structure):
     _fields_ = [("chat", C.c_double), ("c", C.c_double), ("a_rad", C.c_double),
                 ("gamma_gas", C.c_double), ("mu", C.c_double), ("cfl", C.c_double),
                 ("e_floor", C.c_double), ("precision", C.c_int), ("implicit_mode", C.c_int),
-                ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int)]
+                ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int),
+                ("use_mlp", C.c_int), ("mlp_gate", C.c_double)]
 
 
 class rad_stats(C.Structure):
@@ -66,6 +67,8 @@ EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_w
            "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad", "rad_step",
            "rad_read", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
            "rad_launches_per_step", "rad_set_launch", "rad_get_launch", "rad_tune",
+           "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
+           "rad_mlp_grad", "rad_mlp_predict", "rad_log_bind", "rad_log_count",
            "rad_destroy", "rad_strerror"]
 
 _lib = None
@@ -101,6 +104,17 @@ def lib() -> C.CDLL:
     L.rad_set_launch.argtypes = [vp, C.c_int, C.c_int]
     L.rad_get_launch.argtypes = [vp, P(C.c_int), P(C.c_int), P(C.c_int)]
     L.rad_tune.argtypes = [vp, C.c_int, P(C.c_int), P(C.c_int), P(C.c_float)]
+    L.rad_mlp_nparam.argtypes = []
+    L.rad_mlp_nparam.restype = C.c_int
+    fp = P(C.c_float)
+    L.rad_mlp_set.argtypes = [vp, vp, C.c_size_t]
+    L.rad_mlp_get.argtypes = [vp, vp, C.c_size_t]
+    L.rad_mlp_init.argtypes = [vp, C.c_uint64]
+    L.rad_mlp_train.argtypes = [vp, vp, C.c_size_t, C.c_int, C.c_int, C.c_float, C.c_uint64, fp]
+    L.rad_mlp_grad.argtypes = [vp, vp, C.c_size_t, vp, fp]
+    L.rad_mlp_predict.argtypes = [vp, vp, C.c_size_t, vp]
+    L.rad_log_bind.argtypes = [vp, vp, C.c_size_t, C.c_longlong]
+    L.rad_log_count.argtypes = [vp, P(C.c_size_t)]
     L.rad_destroy.argtypes = [vp]
     L.rad_destroy.restype = None
     L.rad_strerror.argtypes = [C.c_int]
@@ -270,6 +284,61 @@ class Rad:
         v, c, t = C.c_int(), C.c_int(), C.c_float()
         check(lib().rad_tune(self.ctx, int(reps), C.byref(v), C.byref(c), C.byref(t)), "rad_tune")
         return v.value, c.value, t.value
+
+    # -- learned starting guess ------------------------------------------------
+    def mlp_nparam(self) -> int:
+        return lib().rad_mlp_nparam()
+
+    def mlp_set(self, params):
+        arr = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        check(lib().rad_mlp_set(self.ctx, C.c_void_p(arr.ctypes.data), arr.size), "rad_mlp_set")
+
+    def mlp_get(self) -> np.ndarray:
+        arr = np.empty(self.mlp_nparam(), dtype=np.float32)
+        check(lib().rad_mlp_get(self.ctx, C.c_void_p(arr.ctypes.data), arr.size), "rad_mlp_get")
+        return arr
+
+    def mlp_init(self, seed: int = 0):
+        check(lib().rad_mlp_init(self.ctx, int(seed)), "rad_mlp_init")
+
+    def mlp_train(self, records, epochs: int, batch: int = 1024, lr: float = 1e-3,
+                  seed: int = 0) -> float:
+        """records: a (n, 4) float32 device tensor of (x1, x2, target, gate)."""
+        assert records.is_cuda and records.dtype == self.torch.float32 and records.is_contiguous()
+        loss = C.c_float()
+        check(lib().rad_mlp_train(self.ctx, C.c_void_p(records.data_ptr()), records.shape[0],
+                                  int(epochs), int(batch), float(lr), int(seed), C.byref(loss)),
+              "rad_mlp_train")
+        return loss.value
+
+    def mlp_grad(self, records):
+        assert records.is_cuda and records.dtype == self.torch.float32 and records.is_contiguous()
+        g = np.empty(self.mlp_nparam(), dtype=np.float32)
+        loss = C.c_float()
+        check(lib().rad_mlp_grad(self.ctx, C.c_void_p(records.data_ptr()), records.shape[0],
+                                 C.c_void_p(g.ctypes.data), C.byref(loss)), "rad_mlp_grad")
+        return loss.value, g
+
+    def mlp_predict(self, records):
+        out = self.torch.empty(records.shape[0], dtype=self.torch.float32, device=records.device)
+        check(lib().rad_mlp_predict(self.ctx, C.c_void_p(records.data_ptr()), records.shape[0],
+                                    C.c_void_p(out.data_ptr())), "rad_mlp_predict")
+        return out
+
+    def log_bind(self, records, stride: int = 1):
+        """records: (capacity, 4) float32 device tensor, or None to unbind."""
+        if records is None:
+            check(lib().rad_log_bind(self.ctx, None, 0, 1), "rad_log_bind")
+            self._log = None
+            return
+        self._log = records
+        check(lib().rad_log_bind(self.ctx, C.c_void_p(records.data_ptr()), records.shape[0],
+                                 int(stride)), "rad_log_bind")
+
+    def log_count(self) -> int:
+        n = C.c_size_t()
+        check(lib().rad_log_count(self.ctx, C.byref(n)), "rad_log_count")
+        return n.value
 
     def launches_per_step(self) -> int:
         return lib().rad_launches_per_step(self.ctx)

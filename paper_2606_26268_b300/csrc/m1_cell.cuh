@@ -1,0 +1,156 @@
+// m1_cell.cuh -- per-cell end of the step, shared by the fused step kernel
+// and the learned-guess queue pass: implicit coupling (Sect. 2.8), E floor,
+// scattering update of F (Eq. source_discrete2), |F| <= E, gas bookkeeping
+// (Sect. 2.7), stores of the cell and of the ghost copies it feeds, and the
+// optional record of the solve for training the learned guess.
+#pragma once
+#include "m1_internal.h"
+
+namespace m1 {
+
+struct Counters {
+  unsigned int fix = 0, efloor = 0, fclip = 0, fallback = 0, noconv = 0, itmax = 0;
+  unsigned long long iters = 0;
+  int status = 0;
+};
+
+// Dimensionless inputs of the converged coupling: the root y = T/T^n of
+// (y - 1) + alpha (y^4 - eps) = 0 depends only on
+//   alpha = g a T^n^3 / ((1 + g_r) C_v),  eps = E* / (a T^n^4),
+// returned as x1 = log10(alpha) / 4 and x2 = log10(eps) / 4, clamped to
+// [-2, 2].  lin = alpha |eps - 1| / (1 + 4 alpha) is the relative change of T
+// of the first linearised solve (the gate of the learned guess).
+__device__ __forceinline__ void coupling_features(const CoupleParams& p, float rho, float e,
+                                                  float kp, float Es, float& x1, float& x2,
+                                                  float& lin, float& Tn) {
+  float Cv = rho * p.f_cvfac;
+  Tn = e * rcp_approx(Cv);
+  float gr = p.f_dtchat * kp * rho;
+  float g = p.f_dtc * kp * rho;
+  float aT3 = p.f_a * Tn * Tn * Tn;
+  float alpha = g * aT3 * rcp_approx((1.f + gr) * Cv);
+  float eps = Es * rcp_approx(aT3 * Tn);
+  const float kQ = 0.25f * 0.30102999566398120f;  // log10(x) / 4 = lg2(x) * log10(2) / 4
+  x1 = fminf(fmaxf(lg2_approx(fmaxf(alpha, 1e-30f)) * kQ, -2.f), 2.f);
+  x2 = fminf(fmaxf(lg2_approx(fmaxf(eps, 1e-30f)) * kQ, -2.f), 2.f);
+  lin = alpha * fabsf(eps - 1.f) * rcp_approx(1.f + 4.f * alpha);
+}
+
+// Coupling and stores of the cell at padded index ic with unpadded
+// coordinates ci.  Us = (E*, F*) after transport (E* already floored).
+// T0 > 0 starts the Newton iteration there (learned guess).
+template <class P, int NDIM, int NC>
+__device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, const int (&ci)[3],
+                                            typename P::T (&Us)[4], typename P::S rho_s,
+                                            typename P::S e_s, typename P::T kp,
+                                            typename P::T chi, const typename P::T (&mom)[3],
+                                            float T0, Counters& c) {
+  using S = typename P::S;
+  using T = typename P::T;
+  const StepDims& Dm = a.dim;
+  CoupleOut co;
+  if constexpr (P::kSplit)
+    co = couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Us[0]), T0);
+  else
+    co = couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Us[0]), double(T0));
+  c.iters += co.iters;
+  c.itmax = max(c.itmax, (unsigned)co.iters);
+  c.fallback += co.fallback;
+  c.noconv += co.noconv;
+  if (co.noconv) c.status |= STATUS_NOCONV;
+  // record (features, converged log(T/T^n)) for training the learned guess
+  if (a.log_cap && a.cp.newton && !co.noconv) {
+    long long lin_idx = ci[0] + (long long)Dm.n[0] * (ci[1] + (long long)Dm.n[1] * ci[2]);
+    if (lin_idx % a.log_stride == 0) {
+      float x1, x2, glin, Tn;
+      coupling_features(a.cp, float(rho_s), float(e_s), float(kp), float(Us[0]), x1, x2, glin, Tn);
+      unsigned int slot = atomicAdd(a.log_count, 1u);
+      if (slot < a.log_cap)
+        reinterpret_cast<float4*>(a.log)[slot] =
+            make_float4(x1, x2, float(log(co.Tnew / double(Tn))), glin);
+    }
+  }
+  T En = Us[0] + T(co.dE);
+  T dE = T(co.dE);
+  if (En < a.efloor) {
+    En = a.efloor;
+    dE = En - Us[0];
+    ++c.efloor;
+  }
+  // Eq. (source_discrete2): F^{n+1} (1 + dt chat chi rho) = F*
+  T x = a.dt * a.chat * chi * T(rho_s);
+  T Fn[3], dF[3];
+  T inv = Ops<T>::rcp(T(1) + x);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    if (v < NC) {
+      if constexpr (sizeof(T) == 8) {
+        Fn[v] = Us[1 + v] / (T(1) + x);
+        dF[v] = Fn[v] - Us[1 + v];
+      } else {
+        dF[v] = -Us[1 + v] * x * inv;
+        Fn[v] = Us[1 + v] + dF[v];
+      }
+    } else {
+      Fn[v] = dF[v] = T(0);
+    }
+  }
+  T nF2 = Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2];
+  if (nF2 > En * En) {
+    T r = Ops<T>::div(En, Ops<T>::sqrt_(nF2));
+#pragma unroll
+    for (int v = 0; v < NC; ++v) {
+      Fn[v] *= r;
+      dF[v] = Fn[v] - Us[1 + v];
+    }
+    ++c.fclip;
+  }
+  // Sect. 2.7: E_gas + (c/chat) E_r and m + F/chat are conserved; the
+  // internal energy takes the kinetic-energy change.
+  T mn[3], dke = T(0);
+#pragma unroll
+  for (int v = 0; v < 3; ++v) {
+    T dm = -dF[v] * a.inv_chat;
+    mn[v] = mom[v] + dm;
+    dke += dm * (T(2) * mom[v] + dm);
+  }
+  T rr = T(rho_s);
+  T en;
+  if constexpr (sizeof(T) == 8)
+    en = T(e_s) - a.ratio * dE - dke / (T(2) * rr);
+  else
+    en = T(e_s) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
+  if (!(En > T(0)) || !(en == en) || !(en > T(0))) c.status |= STATUS_NONPHYS;
+  // stores: own cell and the ghost copies it feeds
+  a.out.E[ic] = S(En);
+#pragma unroll
+  for (int v = 0; v < NC; ++v) {
+    a.out.F[v][ic] = S(Fn[v]);
+    a.out.m[v][ic] = S(mn[v]);
+  }
+  a.out.e[ic] = S(en);
+#pragma unroll
+  for (int d = 0; d < NDIM; ++d) {
+    const int n = Dm.n[d];
+    const int i = ci[d];
+    if (i >= 2 && i < n - 2) continue;
+    const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
+#pragma unroll
+    for (int gslot = 0; gslot < 4; ++gslot) {
+      int gpos = gslot < 2 ? gslot - 2 : n + gslot - 2;  // -2, -1, n, n+1
+      int src;
+      if (gslot < 2)
+        src = Dm.bc_lo[d] ? ((gpos % n) + n) % n : 0;
+      else
+        src = Dm.bc_hi[d] ? gpos % n : n - 1;
+      if (src != i) continue;
+      long long ig = ic + (long long)(gpos - i) * stride;
+      a.out.E[ig] = S(En);
+#pragma unroll
+      for (int v = 0; v < NC; ++v) a.out.F[v][ig] = S(Fn[v]);
+      a.out.e[ig] = S(en);
+    }
+  }
+}
+
+}  // namespace m1

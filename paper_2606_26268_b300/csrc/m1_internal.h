@@ -86,6 +86,18 @@ struct StepArgs {
   // uniform Cartesian grids: 1 / width per direction and the largest width
   T uni_inv[3];
   T uni_h;
+  // learned guess (Newton mode): cells whose first linearised solve changes T
+  // by more than mlp_gate go to a queue solved by the queue pass
+  long long* queue;
+  unsigned int* queue_count;
+  unsigned int queue_cap;  // 0: no learned guess
+  float mlp_gate;
+  const float* mlp_w;      // parameters of the network (MLP_NPARAM floats)
+  // training records of converged solves: float4 (x1, x2, log(T/T^n), gate)
+  float* log;
+  unsigned int* log_count;
+  unsigned int log_cap;    // 0: no logging
+  long long log_stride;
 };
 
 }  // namespace m1

@@ -18,6 +18,7 @@
 // shared memory.  Optical depths of the halo cells needed by the tile faces
 // are computed by the threads that load the halo.
 #pragma once
+#include "m1_cell.cuh"
 #include "m1_internal.h"
 
 namespace m1 {
@@ -201,9 +202,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
   auto ALO = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_ALO, ip); };
   auto AHI = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_AHI, ip); };
 
-  unsigned int c_fix = 0, c_efloor = 0, c_fclip = 0, c_fallback = 0, c_noconv = 0, c_itmax = 0;
-  unsigned long long c_iters = 0;
-  int status = 0;
+  Counters cnt;
 
   // column queue: q[0..2] = states at m, m+1, m+2
   T q[3][4];
@@ -240,7 +239,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     int nf = face4<T, NC, MA, UNI>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
                                    HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat,
                                    Ops<T>::rcp(q[0][0]), flux2<T, NC>(q[0]), zlo);
-    if (upd_col && m0 == 0) c_fix += nf;
+    if (upd_col && m0 == 0) cnt.fix += nf;
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
     T d1[4], d2[4];
 #pragma unroll
@@ -252,7 +251,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     inv_own = Ops<T>::rcp(q[0][0]);
     n2_own = flux2<T, NC>(q[0]);
     int nfh = fix_face<T, NC>(hiS, q[0], n2_own, inv_own);
-    if (upd_col) c_fix += nfh;
+    if (upd_col) cnt.fix += nfh;
   } else {
     load_state<S, NC>(a.in, base, q[0]);
     inv_own = Ops<T>::rcp(q[0][0]);
@@ -361,7 +360,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
                                IXC(0, px - 1), IXC(0, px),
                                HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx);
       bool own = (tx >= 1 || x0 == 0) && cx <= Dm.n[0] && (!TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]));
-      if (own) c_fix += nf;
+      if (own) cnt.fix += nf;
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = fx[v];
     }
@@ -381,7 +380,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
                                IXC(1, py - 1), IXC(1, py),
                                HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy);
       bool own = (ty >= 1 || y0 == 0) && cy <= Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0];
-      if (own) c_fix += nf;
+      if (own) cnt.fix += nf;
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = fy[v];
     }
@@ -415,7 +414,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
       riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
       // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
-      if (upd_col) c_fix += nf + (m + 1 < m1 ? nf2 : 0);
+      if (upd_col) cnt.fix += nf + (m + 1 < m1 ? nf2 : 0);
     }
     __syncthreads();
 
@@ -513,101 +512,36 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
       for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
-        ++c_efloor;
+        ++cnt.efloor;
       }
-      // implicit coupling (Sect. 2.8)
-      CoupleOut co;
-      if constexpr (P::kSplit)
-        co = couple_split(a.cp, float(rho_m), float(e_m), float(kp_m), float(Us[0]), 0.f);
-      else
-        co = couple_fp64(a.cp, double(rho_m), double(e_m), double(kp_m), double(Us[0]), 0.0);
-      c_iters += co.iters;
-      c_itmax = max(c_itmax, (unsigned)co.iters);
-      c_fallback += co.fallback;
-      c_noconv += co.noconv;
-      if (co.noconv) status |= STATUS_NOCONV;
-      T En = Us[0] + T(co.dE);
-      T dE = T(co.dE);
-      if (En < a.efloor) {
-        En = a.efloor;
-        dE = En - Us[0];
-        ++c_efloor;
-      }
-      // Eq. (source_discrete2): F^{n+1} (1 + dt chat chi rho) = F*
-      T x = a.dt * chat * chi_m * T(rho_m);
-      T Fn[3], dF[3];
-      T inv = Ops<T>::rcp(T(1) + x);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        if (v < NC) {
-          if constexpr (sizeof(T) == 8) {
-            Fn[v] = Us[1 + v] / (T(1) + x);
-            dF[v] = Fn[v] - Us[1 + v];
-          } else {
-            dF[v] = -Us[1 + v] * x * inv;
-            Fn[v] = Us[1 + v] + dF[v];
-          }
-        } else {
-          Fn[v] = dF[v] = T(0);
-        }
-      }
-      T nF2 = Fn[0] * Fn[0] + Fn[1] * Fn[1] + Fn[2] * Fn[2];
-      if (nF2 > En * En) {
-        T r = Ops<T>::div(En, Ops<T>::sqrt_(nF2));
-#pragma unroll
-        for (int v = 0; v < NC; ++v) {
-          Fn[v] *= r;
-          dF[v] = Fn[v] - Us[1 + v];
-        }
-        ++c_fclip;
-      }
-      // Sect. 2.7: E_gas + (c/chat) E_r and m + F/chat are conserved; the
-      // internal energy takes the kinetic-energy change.
-      T mn[3], dke = T(0);
-#pragma unroll
-      for (int v = 0; v < 3; ++v) {
-        T dm = -dF[v] * a.inv_chat;
-        mn[v] = mom[v] + dm;
-        dke += dm * (T(2) * mom[v] + dm);
-      }
-      T rr = T(rho_m);
-      T en;
-      if constexpr (sizeof(T) == 8)
-        en = T(e_m) - a.ratio * dE - dke / (T(2) * rr);
-      else
-        en = T(e_m) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
-      if (!(En > T(0)) || !(en == en) || !(en > T(0))) status |= STATUS_NONPHYS;
-      // stores: own cell and the ghost copies it feeds
-      a.out.E[ic] = S(En);
-#pragma unroll
-      for (int v = 0; v < NC; ++v) {
-        a.out.F[v][ic] = S(Fn[v]);
-        a.out.m[v][ic] = S(mn[v]);
-      }
-      a.out.e[ic] = S(en);
       const int ci[3] = {cx, TILE_Y ? cy : (MARCH ? m : 0), TILE_Y ? m : 0};
+      // learned-guess mode: cells far from equilibrium go to the queue pass,
+      // which starts their Newton iteration from the network's guess
+      bool queued = false;
+      if (a.queue_cap) {
+        float x1, x2, lin, Tn;
+        coupling_features(a.cp, float(rho_m), float(e_m), float(kp_m), float(Us[0]), x1, x2, lin,
+                          Tn);
+        queued = lin > a.mlp_gate;
+        const unsigned int mask = __activemask();
+        const unsigned int want = __ballot_sync(mask, queued);
+        unsigned int base_slot = 0;
+        const int leader = __ffs(mask) - 1;
+        if ((tid & 31) == leader && want) base_slot = atomicAdd(a.queue_count, __popc(want));
+        base_slot = __shfl_sync(mask, base_slot, leader);
+        if (queued) {
+          unsigned int slot = base_slot + __popc(want & ((1u << (tid & 31)) - 1u));
+          if (slot < a.queue_cap) {
+            a.queue[slot] = ic;
+            a.out.E[ic] = S(Us[0]);
 #pragma unroll
-      for (int d = 0; d < NDIM; ++d) {
-        const int n = Dm.n[d];
-        const int i = ci[d];
-        if (i >= 2 && i < n - 2) continue;
-        const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
-#pragma unroll
-        for (int gslot = 0; gslot < 4; ++gslot) {
-          int gpos = gslot < 2 ? gslot - 2 : n + gslot - 2;  // -2, -1, n, n+1
-          int src;
-          if (gslot < 2)
-            src = Dm.bc_lo[d] ? ((gpos % n) + n) % n : 0;
-          else
-            src = Dm.bc_hi[d] ? gpos % n : n - 1;
-          if (src != i) continue;
-          long long ig = ic + (long long)(gpos - i) * stride;
-          a.out.E[ig] = S(En);
-#pragma unroll
-          for (int v = 0; v < NC; ++v) a.out.F[v][ig] = S(Fn[v]);
-          a.out.e[ig] = S(en);
+            for (int v = 0; v < NC; ++v) a.out.F[v][ic] = S(Us[1 + v]);
+          } else {
+            queued = false;  // queue full: solve here from T^n
+          }
         }
       }
+      if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, 0.f, cnt);
     }
     if constexpr (MARCH) {
 #pragma unroll
@@ -628,7 +562,8 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
   }
 
   // block reduction of the counters, one atomic per counter per CTA
-  unsigned long long v[ST_N] = {c_fix, c_efloor, c_fclip, c_iters, c_itmax, c_fallback, c_noconv, 0};
+  unsigned long long v[ST_N] = {cnt.fix, cnt.efloor, cnt.fclip, cnt.iters, cnt.itmax,
+                                cnt.fallback, cnt.noconv, 0};
 #pragma unroll
   for (int k = 0; k < ST_N; ++k) {
 #pragma unroll
@@ -647,7 +582,7 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
         atomicAdd(&s_red[k], v[k]);
     }
   }
-  if (status) atomicOr(a.status, status);
+  if (cnt.status) atomicOr(a.status, cnt.status);
   __syncthreads();
   if (tid < ST_N && s_red[tid]) {
     if (tid == ST_ITMAX)

@@ -9,9 +9,11 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <numeric>
 #include <vector>
 
 #include "m1_internal.h"
+#include "mlp_launch.h"
 #include "rad.h"
 #include "step_launch.h"
 
@@ -51,6 +53,15 @@ struct rad_ctx {
   LaunchEntry launch{nullptr, 0};
   int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
   bool uniform = false;         // Cartesian with equal widths in every direction
+  // learned guess
+  QueueFn qpass = nullptr;
+  size_t off_mlp = 0, off_grad = 0, off_m = 0, off_v = 0, off_loss = 0, off_queue = 0;
+  size_t off_qcount = 0, off_lcount = 0;
+  bool mlp_ready = false;
+  int adam_step = 0;
+  float* log_buf = nullptr;
+  unsigned int log_cap = 0;
+  long long log_stride = 1;
 };
 
 static const char* kMsg[] = {"ok",
@@ -83,6 +94,8 @@ extern "C" rad_status rad_default_params(rad_params* p) {
   p->newton_rtol = 1e-12;
   p->newton_maxit = 50;
   p->ncomp = 3;
+  p->use_mlp = 0;
+  p->mlp_gate = 1e-2;
   return RAD_OK;
 }
 
@@ -213,6 +226,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   if (p.implicit_mode == RAD_NEWTON && (!(p.newton_rtol > 0.0) || p.newton_maxit < 1))
     return RAD_EINVAL;
   if (p.ncomp < 1 || p.ncomp > 3) return RAD_EINVAL;
+  if (p.use_mlp && (p.implicit_mode != RAD_NEWTON || !(p.mlp_gate >= 0.0))) return RAD_EINVAL;
   size_t N = 1;
   for (int d = 0; d < 3; ++d) {
     int n = grid->n[d];
@@ -279,6 +293,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
       }
   }
   c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform);
+  c->qpass = select_queue_pass(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
   if (!c->launch.fn) {
     delete c;
     return RAD_EUNSUPPORTED;
@@ -320,6 +335,15 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   c->off_stats = take(sizeof(unsigned long long) * ST_N);
   c->off_status = take(sizeof(int) * 4);
   c->off_stage = take(3 * N * c->esize);
+  const size_t np = size_t(mlp_nparam()) * sizeof(float);
+  c->off_mlp = take(np);
+  c->off_grad = take(np);
+  c->off_m = take(np);
+  c->off_v = take(np);
+  c->off_loss = take(sizeof(double));
+  c->off_qcount = take(sizeof(unsigned int));
+  c->off_lcount = take(sizeof(unsigned int));
+  c->off_queue = p.use_mlp ? take(N * sizeof(long long)) : 0;
   c->total = off;
   *out = c;
   return RAD_OK;
@@ -351,6 +375,12 @@ static rad_status upload_static(rad_ctx* c) {
   if (e != cudaSuccess) return RAD_ECUDA;
   e = cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(int) * 4, c->stream);
   if (e != cudaSuccess) return RAD_ECUDA;
+  const size_t np = size_t(mlp_nparam()) * sizeof(float);
+  e = cudaMemsetAsync(c->ws + c->off_mlp, 0, c->off_qcount - c->off_mlp, c->stream);
+  if (e != cudaSuccess) return RAD_ECUDA;
+  (void)np;
+  c->mlp_ready = false;
+  c->adam_step = 0;
   return cuda_err(cudaStreamSynchronize(c->stream));
 }
 
@@ -656,6 +686,16 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
     if (d < c->ndim) hmax = std::max(hmax, w);
   }
   a.uni_h = T(hmax);
+  const bool q = c->par.use_mlp && c->par.implicit_mode == RAD_NEWTON && c->mlp_ready;
+  a.queue = q ? reinterpret_cast<long long*>(c->ws + c->off_queue) : nullptr;
+  a.queue_count = reinterpret_cast<unsigned int*>(c->ws + c->off_qcount);
+  a.queue_cap = q ? (unsigned int)std::min<size_t>(c->N, 0xffffffffu) : 0u;
+  a.mlp_gate = float(c->par.mlp_gate);
+  a.mlp_w = reinterpret_cast<const float*>(c->ws + c->off_mlp);
+  a.log = c->log_buf;
+  a.log_count = reinterpret_cast<unsigned int*>(c->ws + c->off_lcount);
+  a.log_cap = c->log_buf ? c->log_cap : 0u;
+  a.log_stride = c->log_stride;
 }
 
 extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
@@ -664,16 +704,22 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
   if (!(dt > 0.0)) dt = c->dt_cfl;
   if (!std::isfinite(dt)) return RAD_EINVAL;
+  const bool queue = c->par.use_mlp && c->par.implicit_mode == RAD_NEWTON && c->mlp_ready;
   for (int s = 0; s < nsteps; ++s) {
     cudaError_t e;
+    if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
+                     cudaSuccess)
+      return RAD_ECUDA;
     if (c->esize == 8) {
       StepArgs<Fp64> a{};
       fill_args<Fp64>(c, a, dt);
       e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
+      if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     } else {
       StepArgs<Split> a{};
       fill_args<Split>(c, a, dt);
       e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
+      if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     }
     if (e != cudaSuccess) return RAD_ECUDA;
     c->cur = 1 - c->cur;
@@ -682,7 +728,168 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   return RAD_OK;
 }
 
-extern "C" int rad_launches_per_step(const rad_ctx* c) { return c ? 1 : 0; }
+extern "C" int rad_launches_per_step(const rad_ctx* c) {
+  if (!c) return 0;
+  return (c->par.use_mlp && c->par.implicit_mode == RAD_NEWTON && c->mlp_ready) ? 2 : 1;
+}
+
+// ---------------------------------------------------------------------------
+// learned starting guess: parameters, training, logging
+// ---------------------------------------------------------------------------
+
+extern "C" int rad_mlp_nparam(void) { return mlp_nparam(); }
+
+extern "C" rad_status rad_mlp_set(rad_ctx* c, const float* host, size_t n) {
+  if (!c || !host || n != size_t(mlp_nparam())) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  if (cudaMemcpyAsync(c->ws + c->off_mlp, host, n * sizeof(float), cudaMemcpyHostToDevice,
+                      c->stream) != cudaSuccess ||
+      cudaMemsetAsync(c->ws + c->off_m, 0, 2 * (c->off_v - c->off_m), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  c->mlp_ready = true;
+  c->adam_step = 0;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_mlp_get(rad_ctx* c, float* host, size_t n) {
+  if (!c || !host || n != size_t(mlp_nparam())) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  if (cudaMemcpyAsync(host, c->ws + c->off_mlp, n * sizeof(float), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  return RAD_OK;
+}
+
+static uint64_t splitmix64(uint64_t& s) {
+  uint64_t z = (s += 0x9e3779b97f4a7c15ull);
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+// Glorot-uniform weights and zero biases from a seeded splitmix64 stream.
+extern "C" rad_status rad_mlp_init(rad_ctx* c, uint64_t seed) {
+  if (!c) return RAD_EINVAL;
+  const int H = 64;
+  std::vector<float> w(mlp_nparam(), 0.f);
+  uint64_t st = seed;
+  auto uni = [&](double lim) {
+    double u = (splitmix64(st) >> 11) * (1.0 / 9007199254740992.0);
+    return float((2.0 * u - 1.0) * lim);
+  };
+  size_t k = 0;
+  const int fan[4][2] = {{2, H}, {H, H}, {H, H}, {H, 1}};
+  for (int layer = 0; layer < 4; ++layer) {
+    int fin = fan[layer][0], fout = fan[layer][1];
+    double lim = std::sqrt(6.0 / (fin + fout));
+    for (int i = 0; i < fin * fout; ++i) w[k++] = uni(lim);
+    k += fout;  // biases stay zero
+  }
+  return rad_mlp_set(c, w.data(), w.size());
+}
+
+extern "C" rad_status rad_mlp_grad(rad_ctx* c, const float* dev_records, size_t n,
+                                   float* host_grad, float* host_loss) {
+  if (!c || !dev_records || n == 0 || n > (size_t(1) << 31)) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  float* w = reinterpret_cast<float*>(c->ws + c->off_mlp);
+  float* g = reinterpret_cast<float*>(c->ws + c->off_grad);
+  double* loss = reinterpret_cast<double*>(c->ws + c->off_loss);
+  const size_t np = size_t(mlp_nparam());
+  if (cudaMemsetAsync(g, 0, np * sizeof(float), c->stream) != cudaSuccess ||
+      cudaMemsetAsync(loss, 0, sizeof(double), c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  if (mlp_grad_launch(w, reinterpret_cast<const float4*>(dev_records), (long long)n, 1, 0, 0,
+                      int(n), g, loss, c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  double l = 0.0;
+  if ((host_grad && cudaMemcpyAsync(host_grad, g, np * sizeof(float), cudaMemcpyDeviceToHost,
+                                    c->stream) != cudaSuccess) ||
+      cudaMemcpyAsync(&l, loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaMemsetAsync(g, 0, np * sizeof(float), c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  if (host_loss) *host_loss = float(l / double(n));
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_mlp_train(rad_ctx* c, const float* dev_records, size_t n, int epochs,
+                                    int batch, float lr, uint64_t seed, float* final_loss) {
+  if (!c || !dev_records || n == 0 || epochs < 0 || batch < 1 || !(lr > 0.f) ||
+      n > (size_t(1) << 40))
+    return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  if (!c->mlp_ready) {
+    rad_status s = rad_mlp_init(c, seed ^ 0x5bd1e995ull);
+    if (s != RAD_OK) return s;
+  }
+  float* w = reinterpret_cast<float*>(c->ws + c->off_mlp);
+  float* g = reinterpret_cast<float*>(c->ws + c->off_grad);
+  float* m = reinterpret_cast<float*>(c->ws + c->off_m);
+  float* v = reinterpret_cast<float*>(c->ws + c->off_v);
+  double* loss = reinterpret_cast<double*>(c->ws + c->off_loss);
+  const float4* rec = reinterpret_cast<const float4*>(dev_records);
+  uint64_t st = seed;
+  double last = 0.0;
+  for (int ep = 0; ep < epochs; ++ep) {
+    // a random affine permutation k -> (a k + b) mod n of the records
+    unsigned long long a_perm, b_perm;
+    do {
+      a_perm = (splitmix64(st) % n) | 1ull;
+    } while (std::gcd(a_perm, (unsigned long long)n) != 1ull);
+    b_perm = splitmix64(st) % n;
+    if (cudaMemsetAsync(loss, 0, sizeof(double), c->stream) != cudaSuccess) return RAD_ECUDA;
+    for (size_t b0 = 0; b0 < n; b0 += size_t(batch)) {
+      int bs = int(std::min<size_t>(size_t(batch), n - b0));
+      if (mlp_grad_launch(w, rec, (long long)n, a_perm, b_perm, (long long)b0, bs, g, loss,
+                          c->stream) != cudaSuccess ||
+          mlp_adam_launch(w, g, m, v, lr, ++c->adam_step, c->stream) != cudaSuccess)
+        return RAD_ECUDA;
+    }
+    if (cudaMemcpyAsync(&last, loss, sizeof(double), cudaMemcpyDeviceToHost, c->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return RAD_ECUDA;
+  }
+  c->mlp_ready = true;
+  if (final_loss) *final_loss = float(last / double(n));
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_mlp_predict(rad_ctx* c, const float* dev_records, size_t n,
+                                      float* dev_out) {
+  if (!c || !dev_records || !dev_out || n == 0) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  return cuda_err(mlp_predict_launch(reinterpret_cast<const float*>(c->ws + c->off_mlp),
+                                     reinterpret_cast<const float4*>(dev_records), (long long)n,
+                                     dev_out, c->stream));
+}
+
+extern "C" rad_status rad_log_bind(rad_ctx* c, float* dev_records, size_t capacity,
+                                   long long stride) {
+  if (!c || (dev_records && (capacity == 0 || stride < 1)) || capacity > 0xffffffffull)
+    return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  c->log_buf = dev_records;
+  c->log_cap = (unsigned int)capacity;
+  c->log_stride = stride < 1 ? 1 : stride;
+  return cuda_err(cudaMemsetAsync(c->ws + c->off_lcount, 0, sizeof(unsigned int), c->stream));
+}
+
+extern "C" rad_status rad_log_count(rad_ctx* c, size_t* n) {
+  if (!c || !n) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  unsigned int k = 0;
+  if (cudaMemcpyAsync(&k, c->ws + c->off_lcount, sizeof(k), cudaMemcpyDeviceToHost, c->stream) !=
+          cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  *n = std::min<size_t>(k, c->log_cap);
+  return RAD_OK;
+}
 
 // ---------------------------------------------------------------------------
 // launch shape selection and autotuning
