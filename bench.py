@@ -136,6 +136,26 @@ def make_workload(name):
     raise SystemExit("unknown workload %s" % name)
 
 
+def train_guess(R, torch, dev, args):
+    """Logs converged Newton solves of the 2D non-equilibrium turbulent box and
+    trains the network on them with the library's training kernels."""
+    import workloads as W
+    t0 = time.perf_counter()
+    p = W.turbulent_2d((args.train_n, args.train_n), nonequilibrium=True)
+    p.implicit_mode = "newton"
+    r = R.from_problem(p, args.precision, device=dev)
+    cap = p.N * args.train_steps
+    buf = torch.zeros((cap, 4), dtype=torch.float32, device=dev)
+    r.log_bind(buf, stride=1)
+    r.step(args.train_steps)
+    n = r.log_count()
+    loss = r.mlp_train(buf[:n].contiguous(), epochs=args.train_epochs, batch=4096, lr=2e-3, seed=1)
+    theta = r.mlp_get()
+    r.close()
+    return theta, {"records": int(n), "epochs": args.train_epochs, "final_mse": loss,
+                   "source": p.name, "seconds": time.perf_counter() - t0}
+
+
 def time_steps(r, torch, steps, warmup, dt):
     """Device time of `steps` steps (events on the library's stream), after
     `warmup` steps, with synchronisation on both sides; also the per-launch
@@ -181,8 +201,18 @@ def run_ours(args):
             dist.barrier()
         torch.cuda.synchronize()
 
+    # --- learned guess: trained on solves logged from the 2D non-equilibrium
+    # turbulent box (FP32 transport, Newton coupling), before any timing
+    theta, train_info = None, None
+    if args.form == "mlp":
+        theta, train_info = train_guess(R, torch, dev, args)
+
     # --- headline form -----------------------------------------------------
-    r = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
+    implicit = "newton" if args.form in ("mlp", "newton") else args.implicit
+    extra = dict(use_mlp=1, mlp_gate=args.mlp_gate) if args.form == "mlp" else {}
+    r = R.from_problem(prob, args.precision, device=dev, implicit_mode=implicit, **extra)
+    if theta is not None:
+        r.mlp_set(theta)
     dt = r.dt()
     if args.launch:
         v_, c_ = (int(x) for x in args.launch.split(","))
@@ -227,7 +257,9 @@ def run_ours(args):
         h_rho, h_T, h_E = pinned(prob.rho), pinned(prob.T), pinned(prob.E)
         h_v, h_F = pinned(np.asarray(prob.v)[:nc]), pinned(np.asarray(prob.F)[:nc])
         outs = {k: pinned(np.zeros(N * (nc if k in ("F", "m") else 1))) for k in ("E", "F", "e", "m")}
-        r2 = R.from_problem(prob, args.precision, device=dev, implicit_mode=args.implicit)
+        r2 = R.from_problem(prob, args.precision, device=dev, implicit_mode=implicit, **extra)
+        if theta is not None:
+            r2.mlp_set(theta)
         r2.set_launch(tuned[0], tuned[1])
         ksteps = max(1, min(args.steps, 3))
         for _ in range(1):
@@ -254,6 +286,22 @@ def run_ours(args):
                "h2d_bytes_per_step": int((3 + 2 * nc) * N * isz),
                "d2h_bytes_per_step": int((2 + 2 * nc) * N * isz), "steps": ksteps}
         r2.close()
+
+    # --- comparison forms on the same grid ------------------------------------
+    forms = {}
+    if not args.skip_forms:
+        for name, prec, impl, ex in (("split_newton_no_guess", args.precision, "newton", {}),
+                                     ("split_once", args.precision, "once", {})):
+            if name == "split_newton_no_guess" and args.form != "mlp":
+                continue
+            rr = R.from_problem(prob, prec, device=dev, implicit_mode=impl, **ex)
+            rr.set_launch(tuned[0], tuned[1])
+            ms_, per_ = time_steps(rr, torch, args.steps, 3, dt)
+            st_ = rr.stats()
+            rr.close()
+            forms[name] = {"value": N * args.steps / (ms_ * 1e-3), "unit": UNIT,
+                           "ms_per_step": ms_ / args.steps, "iters": st_["iters"],
+                           "launches_per_step": 1}
 
     # --- plain FP64 form on the same grid -----------------------------------
     fp64 = None
@@ -286,7 +334,9 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "split" else "f64",
             "data": "synthetic (seeded hot-sphere box: log-normal density, Kramers opacity)",
             "config": {"workload": prob.name, "cells": N, "precision": args.precision,
-                       "implicit": args.implicit, "chat": prob.chat, "dt": dt,
+                       "form": args.form, "implicit": implicit, "chat": prob.chat, "dt": dt,
+                       "mlp_gate": args.mlp_gate if args.form == "mlp" else None,
+                       "guess_training": train_info,
                        "launch": {"variant": tuned[0], "chunk": tuned[1], "tuned_ms": tuned[2]},
                        "parallelism": "replicas" if world > 1 else "single",
                        "l2": "state larger than L2 (%.2f GB per buffer)" % (
@@ -298,6 +348,7 @@ def run_ours(args):
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64_plain": fp64,
+            "forms": forms,
             "gpu_launches": launches,
             "clocks": clocks,
             "status": int(status),
@@ -374,6 +425,13 @@ def main():
     ap.add_argument("--workload", default="hotsphere3d_256")
     ap.add_argument("--precision", default="split", choices=["split", "fp64"])
     ap.add_argument("--implicit", default="once", choices=["once", "newton"])
+    ap.add_argument("--form", default="mlp", choices=["mlp", "newton", "once"],
+                    help="mlp: FP32 transport + Newton coupling from the learned guess")
+    ap.add_argument("--mlp-gate", type=float, default=1e-2)
+    ap.add_argument("--train-n", type=int, default=512)
+    ap.add_argument("--train-steps", type=int, default=4)
+    ap.add_argument("--train-epochs", type=int, default=4)
+    ap.add_argument("--skip-forms", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=10.0)
     ap.add_argument("--ref-cells", type=int, default=200000)
     ap.add_argument("--skip-cpu", action="store_true")
