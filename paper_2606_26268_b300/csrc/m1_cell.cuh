@@ -36,23 +36,31 @@ __device__ __forceinline__ void coupling_features(const CoupleParams& p, float r
   lin = alpha * fabsf(eps - 1.f) * rcp_approx(1.f + 4.f * alpha);
 }
 
-// Coupling and stores of the cell at padded index ic with unpadded
-// coordinates ci.  Us = (E*, F*) after transport (E* already floored).
-// T0 > 0 starts the Newton iteration there (learned guess).
+// The implicit coupling of one cell (Sect. 2.8): the single linearised solve
+// when `once`, else the mode of the parameters (Newton from T0 > 0 or T^n).
+template <class P>
+__device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, typename P::S rho_s,
+                                                 typename P::S e_s, typename P::T kp,
+                                                 typename P::T Es, float T0, bool once) {
+  if constexpr (P::kSplit)
+    return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once);
+  else
+    return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
+                       once);
+}
+
+// Bookkeeping and stores of the cell at padded index ic with unpadded
+// coordinates ci, given its coupling result co.  Us = (E*, F*) after
+// transport (E* already floored).
 template <class P, int NDIM, int NC>
 __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, const int (&ci)[3],
                                             typename P::T (&Us)[4], typename P::S rho_s,
                                             typename P::S e_s, typename P::T kp,
                                             typename P::T chi, const typename P::T (&mom)[3],
-                                            float T0, Counters& c) {
+                                            const CoupleOut& co, Counters& c) {
   using S = typename P::S;
   using T = typename P::T;
   const StepDims& Dm = a.dim;
-  CoupleOut co;
-  if constexpr (P::kSplit)
-    co = couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Us[0]), T0);
-  else
-    co = couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Us[0]), double(T0));
   c.iters += co.iters;
   c.itmax = max(c.itmax, (unsigned)co.iters);
   c.fallback += co.fallback;

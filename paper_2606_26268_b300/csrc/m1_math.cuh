@@ -345,6 +345,7 @@ struct CoupleOut {
   int iters;
   int fallback;  // restarted from T^n
   int noconv;
+  int conv1;     // single solve only: it already passes the Newton convergence test
 };
 
 // Increments of the 2x2 system of Eq. (implicit_matrix) with T^4 linearised
@@ -355,7 +356,8 @@ struct CoupleOut {
 // which for Tk = T^n is the paper's single solve.  Newton mode repeats it
 // with Tk <- T^{n+1} until |T^{n+1} - Tk| <= rtol T^{n+1}.
 __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double rho, double e,
-                                                 double kp, double Es, double T0) {
+                                                 double kp, double Es, double T0,
+                                                 bool once = false) {
   CoupleOut o{};
   double Cv = rho * p.cvfac;
   double Tn = e / Cv;
@@ -363,7 +365,7 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
   double g = p.dt * p.c * kp * rho;
   double c1 = (1.0 + gr) * Cv;
   if (T0 <= 0.0) T0 = Tn;
-  if (!p.newton) {
+  if (!p.newton || once) {
     double aT3 = p.a_rad * Tn * Tn * Tn;
     double D = Es - aT3 * Tn;
     double det = c1 + 4.0 * g * aT3;
@@ -371,6 +373,7 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
     o.Tnew = Tn + g * q;
     o.dE = -gr * Cv * q;
     o.iters = 1;
+    o.conv1 = fabs(g * q) <= p.rtol * o.Tnew;
     return o;
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -408,7 +411,8 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
 // Newton numerator are formed in double; det and the final products, whose
 // terms are all positive, in float.
 __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
-                                                  float kp, float Es, float T0f) {
+                                                  float kp, float Es, float T0f,
+                                                  bool once = false) {
   CoupleOut o{};
   float Cv = rho * p.f_cvfac;
   float invCv = rcp_approx(Cv);
@@ -416,7 +420,7 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
   float gr = p.f_dtchat * kp * rho;
   float g = p.f_dtc * kp * rho;
   float c1 = (1.f + gr) * Cv;
-  if (!p.newton) {
+  if (!p.newton || once) {
     // the T^4 emission term and E* - a T^4 in double: T^2 of a float is
     // exact in double, so this is two roundings from exact
     double T2 = double(Tf) * double(Tf);
@@ -428,6 +432,7 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
     o.Tnew = double(Tf + g * q);
     o.dE = double(-gr * Cv * q);
     o.iters = 1;
+    o.conv1 = fabsf(g * q) <= p.f_rtol * float(o.Tnew);
     return o;
   }
   double Tn = double(Tf);

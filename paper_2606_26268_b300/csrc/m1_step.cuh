@@ -515,14 +515,14 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
         ++cnt.efloor;
       }
       const int ci[3] = {cx, TILE_Y ? cy : (MARCH ? m : 0), TILE_Y ? m : 0};
-      // learned-guess mode: cells far from equilibrium go to the queue pass,
-      // which starts their Newton iteration from the network's guess
+      // Newton mode with the queue: the single linearised solve here; cells
+      // it does not already converge go to the queue pass, which iterates
+      // (from T^n or the learned guess) without holding back this warp.
       bool queued = false;
+      CoupleOut co;
       if (a.queue_cap) {
-        float x1, x2, lin, Tn;
-        coupling_features(a.cp, float(rho_m), float(e_m), float(kp_m), float(Us[0]), x1, x2, lin,
-                          Tn);
-        queued = lin > a.mlp_gate;
+        co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, true);
+        queued = !co.conv1;
         const unsigned int mask = __activemask();
         const unsigned int want = __ballot_sync(mask, queued);
         unsigned int base_slot = 0;
@@ -537,11 +537,14 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
 #pragma unroll
             for (int v = 0; v < NC; ++v) a.out.F[v][ic] = S(Us[1 + v]);
           } else {
-            queued = false;  // queue full: solve here from T^n
+            queued = false;  // queue full: iterate here
+            co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);
           }
         }
+      } else {
+        co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
-      if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, 0.f, cnt);
+      if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
     }
     if constexpr (MARCH) {
 #pragma unroll

@@ -25,7 +25,8 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
   using S = typename P::S;
   using T = typename P::T;
   extern __shared__ float s_w[];
-  for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = a.mlp_w[i];
+  if (a.mlp_w)
+    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = a.mlp_w[i];
   __shared__ unsigned long long s_red[ST_N];
   if (threadIdx.x < ST_N) s_red[threadIdx.x] = 0ull;
   __syncthreads();
@@ -58,11 +59,17 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
         Temp = T(e) * rcp_approx(rr * a.cp.f_cvfac);
       opacity(a.opac, rr, Temp, kp, chi);
     }
-    float x1, x2, lin, Tn;
-    coupling_features(a.cp, float(rho), float(e), float(kp), float(Us[0]), x1, x2, lin, Tn);
-    const float guess = mlp_forward(s_w, x1, x2);
-    const float T0 = Tn * ex2_approx(fminf(fmaxf(guess, -20.f), 20.f) * 1.44269504088896341f);
-    finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho, e, kp, chi, mom, T0, cnt);
+    float T0 = 0.f;  // T^n
+    if (a.mlp_w) {
+      float x1, x2, lin, Tn;
+      coupling_features(a.cp, float(rho), float(e), float(kp), float(Us[0]), x1, x2, lin, Tn);
+      if (lin > a.mlp_gate) {
+        const float guess = mlp_forward(s_w, x1, x2);
+        T0 = Tn * ex2_approx(fminf(fmaxf(guess, -20.f), 20.f) * 1.44269504088896341f);
+      }
+    }
+    const CoupleOut co = couple_cell<P>(a, rho, e, kp, Us[0], T0, false);
+    finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho, e, kp, chi, mom, co, cnt);
   }
   unsigned long long v[ST_N] = {0, cnt.efloor, cnt.fclip, cnt.iters, cnt.itmax,
                                 cnt.fallback, cnt.noconv, 0};
@@ -96,11 +103,11 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
 template <class P, int NDIM, int NC>
 cudaError_t launch_queue_pass(const void* vargs, cudaStream_t s) {
   const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
-  const size_t smem = MLP_NPARAM * sizeof(float);
+  const size_t smem = a.mlp_w ? MLP_NPARAM * sizeof(float) : 0;
   static bool attr_set = false;
   if (!attr_set) {
     cudaFuncSetAttribute(queue_pass_kernel<P, NDIM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(smem));
+                         int(MLP_NPARAM * sizeof(float)));
     attr_set = true;
   }
   queue_pass_kernel<P, NDIM, NC><<<148 * 4, 128, smem, s>>>(a);

@@ -343,7 +343,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   c->off_loss = take(sizeof(double));
   c->off_qcount = take(sizeof(unsigned int));
   c->off_lcount = take(sizeof(unsigned int));
-  c->off_queue = p.use_mlp ? take(N * sizeof(long long)) : 0;
+  c->off_queue = p.implicit_mode == RAD_NEWTON ? take(N * sizeof(long long)) : 0;
   c->total = off;
   *out = c;
   return RAD_OK;
@@ -686,12 +686,13 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
     if (d < c->ndim) hmax = std::max(hmax, w);
   }
   a.uni_h = T(hmax);
-  const bool q = c->par.use_mlp && c->par.implicit_mode == RAD_NEWTON && c->mlp_ready;
+  const bool q = c->par.implicit_mode == RAD_NEWTON;
   a.queue = q ? reinterpret_cast<long long*>(c->ws + c->off_queue) : nullptr;
   a.queue_count = reinterpret_cast<unsigned int*>(c->ws + c->off_qcount);
   a.queue_cap = q ? (unsigned int)std::min<size_t>(c->N, 0xffffffffu) : 0u;
   a.mlp_gate = float(c->par.mlp_gate);
-  a.mlp_w = reinterpret_cast<const float*>(c->ws + c->off_mlp);
+  a.mlp_w = (c->par.use_mlp && c->mlp_ready) ? reinterpret_cast<const float*>(c->ws + c->off_mlp)
+                                             : nullptr;
   a.log = c->log_buf;
   a.log_count = reinterpret_cast<unsigned int*>(c->ws + c->off_lcount);
   a.log_cap = c->log_buf ? c->log_cap : 0u;
@@ -704,7 +705,7 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
   if (!(dt > 0.0)) dt = c->dt_cfl;
   if (!std::isfinite(dt)) return RAD_EINVAL;
-  const bool queue = c->par.use_mlp && c->par.implicit_mode == RAD_NEWTON && c->mlp_ready;
+  const bool queue = c->par.implicit_mode == RAD_NEWTON;
   for (int s = 0; s < nsteps; ++s) {
     cudaError_t e;
     if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
@@ -730,7 +731,7 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
 
 extern "C" int rad_launches_per_step(const rad_ctx* c) {
   if (!c) return 0;
-  return (c->par.use_mlp && c->par.implicit_mode == RAD_NEWTON && c->mlp_ready) ? 2 : 1;
+  return c->par.implicit_mode == RAD_NEWTON ? 2 : 1;
 }
 
 // ---------------------------------------------------------------------------
