@@ -143,6 +143,7 @@ def train_guess(R, torch, dev, args):
     t0 = time.perf_counter()
     p = W.turbulent_2d((args.train_n, args.train_n), nonequilibrium=True)
     p.implicit_mode = "newton"
+    p.newton_rtol = 1e-12
     r = R.from_problem(p, args.precision, device=dev)
     cap = p.N * args.train_steps
     buf = torch.zeros((cap, 4), dtype=torch.float32, device=dev)
@@ -210,6 +211,11 @@ def run_ours(args):
     # --- headline form -----------------------------------------------------
     implicit = "newton" if args.form in ("mlp", "newton") else args.implicit
     extra = dict(use_mlp=1, mlp_gate=args.mlp_gate) if args.form == "mlp" else {}
+    # Newton tolerance: FP64 1e-12; the split form stores T in float, so its
+    # iteration stops at the storage precision (same test with and without
+    # the learned guess)
+    rtol = args.rtol if args.rtol > 0 else (1e-7 if args.precision == "split" else 1e-12)
+    prob.newton_rtol = rtol
     r = R.from_problem(prob, args.precision, device=dev, implicit_mode=implicit, **extra)
     if theta is not None:
         r.mlp_set(theta)
@@ -336,6 +342,7 @@ def run_ours(args):
             "config": {"workload": prob.name, "cells": N, "precision": args.precision,
                        "form": args.form, "implicit": implicit, "chat": prob.chat, "dt": dt,
                        "mlp_gate": args.mlp_gate if args.form == "mlp" else None,
+                       "newton_rtol": rtol if implicit == "newton" else None,
                        "guess_training": train_info,
                        "launch": {"variant": tuned[0], "chunk": tuned[1], "tuned_ms": tuned[2]},
                        "parallelism": "replicas" if world > 1 else "single",
@@ -428,6 +435,7 @@ def main():
     ap.add_argument("--form", default="mlp", choices=["mlp", "newton", "once"],
                     help="mlp: FP32 transport + Newton coupling from the learned guess")
     ap.add_argument("--mlp-gate", type=float, default=1e-2)
+    ap.add_argument("--rtol", type=float, default=0.0, help="Newton tolerance (0: by precision)")
     ap.add_argument("--train-n", type=int, default=512)
     ap.add_argument("--train-steps", type=int, default=4)
     ap.add_argument("--train-epochs", type=int, default=4)
