@@ -265,6 +265,43 @@ rad_status rad_mlp_predict(rad_ctx *ctx, const float *dev_records, size_t n, flo
 rad_status rad_log_bind(rad_ctx *ctx, float *dev_records, size_t capacity, long long stride);
 rad_status rad_log_count(rad_ctx *ctx, size_t *n);
 
+/* --------------------------------------------------------------------------
+ * Gradient of the learned guess's training loss without device allocation.
+ * The paper has no counterpart: this is a convenience of this library.
+ *
+ * Same result as rad_mlp_grad (mean-squared-error gradient and mean loss over
+ * n records, for the parameters at dev_params), but it takes no context and
+ * allocates nothing.  It is meant for callers that cannot allocate device
+ * memory when they need the gradient: code whose framework owns all device
+ * memory through a pre-sized pool and forbids allocations after start-up, or
+ * code that must not let cudaMalloc/cudaFree synchronise the device.
+ *
+ * dev_params: rad_mlp_nparam() floats; dev_records: n float4 records (x1,
+ * x2, target, unused); dev_grad: rad_mlp_nparam() floats and dev_loss: one
+ * float, all device memory of the current device; the work is enqueued on
+ * `stream` (a cudaStream_t, NULL = legacy default stream) and the call
+ * returns without waiting.
+ *
+ * Scratch: a file-scope device array of RAD_NOALLOC_MAX_RECORDS /
+ * RAD_NOALLOC_ROW_RECORDS partial gradients (about 8.8 MB) that every GPU
+ * loading this library holds until the process exits.  Each call sums one
+ * partial per RAD_NOALLOC_ROW_RECORDS records in a fixed order, so the result
+ * is deterministic; every partial a call uses is fully rewritten, so nothing
+ * left by an earlier call leaks into it.  All calls share the array: calls
+ * that overlap on the GPU (other streams, other threads) race and give wrong
+ * results; order them on one stream.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current; make
+ * that first call before any stream capture.
+ *
+ * Errors: RAD_EINVAL for NULL pointers, n == 0 or n > RAD_NOALLOC_MAX_RECORDS
+ * (split larger sets and add the gradients, weighted by their counts);
+ * RAD_EUNSUPPORTED for device ordinals >= 64; RAD_ECUDA if the address lookup
+ * or a launch fails. */
+#define RAD_NOALLOC_ROW_RECORDS 64
+#define RAD_NOALLOC_MAX_RECORDS 16384
+rad_status rad_mlp_grad_noalloc(const float *dev_params, const float *dev_records, size_t n,
+                                float *dev_grad, float *dev_loss, void *stream);
+
 /* Releases the context (and the workspace if rad_alloc_workspace made it). */
 void rad_destroy(rad_ctx *ctx);
 

@@ -69,6 +69,7 @@ EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_w
            "rad_launches_per_step", "rad_set_launch", "rad_get_launch", "rad_tune",
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
            "rad_mlp_grad", "rad_mlp_predict", "rad_log_bind", "rad_log_count",
+           "rad_mlp_grad_noalloc",
            "rad_destroy", "rad_strerror"]
 
 _lib = None
@@ -115,6 +116,7 @@ def lib() -> C.CDLL:
     L.rad_mlp_predict.argtypes = [vp, vp, C.c_size_t, vp]
     L.rad_log_bind.argtypes = [vp, vp, C.c_size_t, C.c_longlong]
     L.rad_log_count.argtypes = [vp, P(C.c_size_t)]
+    L.rad_mlp_grad_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp, vp]
     L.rad_destroy.argtypes = [vp]
     L.rad_destroy.restype = None
     L.rad_strerror.argtypes = [C.c_int]
@@ -133,6 +135,23 @@ class RadError(RuntimeError):
 def check(status: int, where: str) -> None:
     if status != RAD_OK:
         raise RadError(status, where)
+
+
+NOALLOC_MAX_RECORDS = 16384
+
+
+def mlp_grad_noalloc(params, records, grad_out, loss_out, stream=None) -> int:
+    """rad_mlp_grad_noalloc on device tensors (float32, contiguous): params
+    (8577), records (n, 4), grad_out (8577), loss_out (1).  Enqueued on
+    `stream` (a torch stream; default: the current one); returns the status."""
+    import torch
+    for t in (params, records, grad_out, loss_out):
+        assert t.is_cuda and t.dtype == torch.float32 and t.is_contiguous()
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return lib().rad_mlp_grad_noalloc(C.c_void_p(params.data_ptr()),
+                                      C.c_void_p(records.data_ptr()), records.shape[0],
+                                      C.c_void_p(grad_out.data_ptr()),
+                                      C.c_void_p(loss_out.data_ptr()), C.c_void_p(s.cuda_stream))
 
 
 def default_params() -> rad_params:
