@@ -144,11 +144,14 @@ __device__ __forceinline__ void load_state(const Fields<S>& f, long long i, T (&
 }
 
 // MINB: resident CTAs per SM requested from the register allocator.
+// One tile of the step: the CTA's (bx, by, bz) block coordinates select the
+// x tile, the y tile (3D) and the march chunk.  Called by the single-grid
+// kernel below and by the batched kernel of many grids.
 // UNI: uniform Cartesian grid (spacing from constants instead of tables; the
 // slopes use raw differences, the 1/dx factor cancelling in the van Leer
 // mean, and faces sit at -/+ 1/2 in units of the difference).
-template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>
-__global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_constant__ StepArgs<P> a) {
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY>
+__device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, int bz) {
   using S = typename P::S;
   using T = typename P::T;
   constexpr int NV = 1 + NC;
@@ -172,9 +175,9 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
   const int tx = threadIdx.x;
   const int ty = TILE_Y ? threadIdx.y : 0;
   const int tid = tx + TX * ty;
-  const int x0 = blockIdx.x * (TX - 1);
-  const int y0 = TILE_Y ? blockIdx.y * (TY - 1) : 0;
-  const int mblk = MARCH ? (TILE_Y ? blockIdx.z : blockIdx.y) : 0;
+  const int x0 = bx * (TX - 1);
+  const int y0 = TILE_Y ? by * (TY - 1) : 0;
+  const int mblk = MARCH ? (TILE_Y ? bz : by) : 0;
   const int m0 = MARCH ? mblk * a.chunk : 0;
   const int m1 = MARCH ? min(m0 + a.chunk, Dm.n[MA]) : 1;
 
@@ -593,6 +596,11 @@ __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_consta
     else
       atomicAdd(a.stats + tid, s_red[tid]);
   }
+}
+
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_constant__ StepArgs<P> a) {
+  step_tile<P, NDIM, GEOM, NC, UNI, TX, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace m1

@@ -9,6 +9,7 @@
 
 #include "m1_cell.cuh"
 #include "mlp.cuh"
+#include "queue_cell.cuh"
 #include "mlp_launch.h"
 
 namespace m1 {
@@ -17,13 +18,8 @@ namespace m1 {
 // queue pass
 // ---------------------------------------------------------------------------
 
-// For every queued cell: (E*, F*) left in the output buffer by the step
-// kernel, gas state from the input buffer, opacities at (rho, T^n), network
-// guess T0 = T^n exp(net(x1, x2)), then the common end of the step.
 template <class P, int NDIM, int NC>
 __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__ StepArgs<P> a) {
-  using S = typename P::S;
-  using T = typename P::T;
   extern __shared__ float s_w[];
   if (a.mlp_w)
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = a.mlp_w[i];
@@ -31,73 +27,11 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
   if (threadIdx.x < ST_N) s_red[threadIdx.x] = 0ull;
   __syncthreads();
   const unsigned int count = min(*a.queue_count, a.queue_cap);
-  const StepDims& Dm = a.dim;
   Counters cnt;
   for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < count;
-       q += gridDim.x * blockDim.x) {
-    const long long ic = a.queue[q];
-    long long r = ic;
-    int ci[3];
-    ci[0] = int(r % Dm.pn[0]) - Dm.g[0];
-    r /= Dm.pn[0];
-    ci[1] = int(r % Dm.pn[1]) - Dm.g[1];
-    ci[2] = int(r / Dm.pn[1]) - Dm.g[2];
-    T Us[4] = {T(a.out.E[ic]), 0, 0, 0};
-#pragma unroll
-    for (int v = 0; v < NC; ++v) Us[1 + v] = T(a.out.F[v][ic]);
-    T mom[3] = {0, 0, 0};
-#pragma unroll
-    for (int v = 0; v < NC; ++v) mom[v] = T(a.in.m[v][ic]);
-    const S rho = a.rho[ic], e = a.in.e[ic];
-    T kp, chi;
-    {
-      T rr = T(rho);
-      T Temp;
-      if constexpr (sizeof(T) == 8)
-        Temp = T(e) / (rr * T(a.cp.cvfac));
-      else
-        Temp = T(e) * rcp_approx(rr * a.cp.f_cvfac);
-      opacity(a.opac, rr, Temp, kp, chi);
-    }
-    float T0 = 0.f;  // T^n
-    if (a.mlp_w) {
-      float x1, x2, lin, Tn;
-      coupling_features(a.cp, float(rho), float(e), float(kp), float(Us[0]), x1, x2, lin, Tn);
-      if (lin > a.mlp_gate) {
-        const float guess = mlp_forward(s_w, x1, x2);
-        T0 = Tn * ex2_approx(fminf(fmaxf(guess, -20.f), 20.f) * 1.44269504088896341f);
-      }
-    }
-    const CoupleOut co = couple_cell<P>(a, rho, e, kp, Us[0], T0, false);
-    finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho, e, kp, chi, mom, co, cnt);
-  }
-  unsigned long long v[ST_N] = {0, cnt.efloor, cnt.fclip, cnt.iters, cnt.itmax,
-                                cnt.fallback, cnt.noconv, 0};
-#pragma unroll
-  for (int k = 0; k < ST_N; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      unsigned long long o = __shfl_down_sync(0xffffffffu, v[k], off);
-      v[k] = (k == ST_ITMAX) ? (o > v[k] ? o : v[k]) : v[k] + o;
-    }
-  }
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int k = 0; k < ST_N; ++k) {
-      if (k == ST_ITMAX)
-        atomicMax(&s_red[k], v[k]);
-      else if (v[k])
-        atomicAdd(&s_red[k], v[k]);
-    }
-  }
-  if (cnt.status) atomicOr(a.status, cnt.status);
-  __syncthreads();
-  if (threadIdx.x < ST_N && s_red[threadIdx.x]) {
-    if (threadIdx.x == ST_ITMAX)
-      atomicMax(a.stats + threadIdx.x, s_red[threadIdx.x]);
-    else
-      atomicAdd(a.stats + threadIdx.x, s_red[threadIdx.x]);
-  }
+       q += gridDim.x * blockDim.x)
+    queue_cell<P, NDIM, NC>(a, a.queue[q], s_w, cnt);
+  flush_counters<P>(a, cnt, s_red);
 }
 
 template <class P, int NDIM, int NC>
