@@ -302,6 +302,86 @@ rad_status rad_log_count(rad_ctx *ctx, size_t *n);
 rad_status rad_mlp_grad_noalloc(const float *dev_params, const float *dev_records, size_t n,
                                 float *dev_grad, float *dev_loss, void *stream);
 
+/* --------------------------------------------------------------------------
+ * Batches: many independent grids advanced together (not in the paper: an
+ * extension of this implementation for serving many small problems).  Each
+ * step of every grid is one launch of a persistent kernel whose CTAs take
+ * tiles of any grid from a shared work list (largest grids first), so small
+ * grids do not leave the GPU idle; in RAD_NEWTON mode a second launch runs
+ * the queue pass over all grids.  A sequence of steps is captured once into a
+ * CUDA graph and replayed.  Each grid gets the values it gets from rad_step.
+ *
+ * Members are contexts made by rad_create with a bound workspace and their
+ * gas and radiation set; all are Cartesian with the same ndim (2 or 3),
+ * precision, ncomp, implicit mode and use_mlp, and all have constant widths
+ * along each direction or all do not.  The batch does not own them: they
+ * must outlive it, and rad_set_gas / rad_set_rad / rad_read on a member
+ * stay valid between batch steps (rad_batch_set_stream puts every member on
+ * the batch's stream).  Batch steps add to the batch's counters, not to the
+ * members'.
+ * -------------------------------------------------------------------------- */
+typedef struct rad_batch rad_batch;
+
+/* Validates the members (1..1024 distinct contexts) and returns a batch that
+ * owns no device memory yet.  Errors: RAD_EINVAL, RAD_EUNSUPPORTED (members
+ * that differ in kind, or a kind without batched kernels), RAD_ENOMEM. */
+rad_status rad_batch_create(rad_ctx *const *members, int count, rad_batch **out);
+
+/* Device memory the batch needs for its own state: the members' argument
+ * blocks, the tile work list, counters, queue lengths and the network
+ * parameters (the members keep their own workspaces).  Binding follows the
+ * rules of rad_bind_workspace (256-byte aligned, caller-owned). */
+rad_status rad_batch_workspace_size(const rad_batch *b, size_t *bytes);
+rad_status rad_batch_bind_workspace(rad_batch *b, void *dev_ptr, size_t bytes);
+rad_status rad_batch_alloc_workspace(rad_batch *b);
+
+/* Stream of the batch and of every member (NULL = legacy default stream). */
+rad_status rad_batch_set_stream(rad_batch *b, void *stream);
+
+/* use_graph != 0 (default): rad_batch_step captures its sequence of launches
+ * into a CUDA graph on a private stream the first time a given step count is
+ * asked for, and replays it on the batch's stream; 0: plain launches. */
+rad_status rad_batch_set_graph(rad_batch *b, int use_graph);
+
+/* Enqueues nsteps steps of every member.  dt: host array of one step length
+ * per member (entries <= 0, or dt == NULL, use the member's CFL step).
+ * Asynchronous; device failures land in the batch status word.  Errors:
+ * RAD_EINVAL (member without state, bad dt), RAD_ENOMEM, RAD_ECUDA. */
+rad_status rad_batch_step(rad_batch *b, const double *dt, int nsteps);
+
+/* Waits for the stream and returns (and clears) the batch status word. */
+rad_status rad_batch_sync(rad_batch *b);
+
+/* Counters summed over all members for the batch steps; steps counts batch
+ * steps.  Reading synchronises. */
+rad_status rad_batch_get_stats(rad_batch *b, rad_stats *out);
+rad_status rad_batch_reset_stats(rad_batch *b);
+
+/* Kernel launches per batch step (1, or 2 in RAD_NEWTON mode). */
+int rad_batch_launches_per_step(const rad_batch *b);
+
+/* CTA shape (`variant`, see rad_batch_get_launch for the count) and march
+ * length (`chunk`, 0 = default) of the persistent kernel; results do not
+ * depend on either.  rad_batch_get_launch also reports the CTAs of the last
+ * launch configuration (0 before the first step).  Errors: RAD_EINVAL. */
+rad_status rad_batch_set_launch(rad_batch *b, int variant, int chunk);
+rad_status rad_batch_get_launch(const rad_batch *b, int *variant, int *chunk, int *nvariants,
+                                int *blocks);
+
+/* Autotuner of the persistent launch: times `reps` launches of every
+ * (shape, chunk) pair on the current state without advancing it, keeps the
+ * fastest and restores the counters and the status word; synchronises.
+ * Outputs may be NULL. */
+rad_status rad_batch_tune(rad_batch *b, int reps, int *variant, int *chunk, float *ms);
+
+/* Parameters of the learned guess used by every member (use_mlp members;
+ * layout as for rad_mlp_set).  Errors: RAD_EINVAL (wrong n, members without
+ * use_mlp), RAD_ENOMEM, RAD_ECUDA. */
+rad_status rad_batch_mlp_set(rad_batch *b, const float *host_params, size_t n);
+
+/* Releases the batch (not the members). */
+void rad_batch_destroy(rad_batch *b);
+
 /* Releases the context (and the workspace if rad_alloc_workspace made it). */
 void rad_destroy(rad_ctx *ctx);
 

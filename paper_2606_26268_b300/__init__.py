@@ -70,6 +70,11 @@ EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_w
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
            "rad_mlp_grad", "rad_mlp_predict", "rad_log_bind", "rad_log_count",
            "rad_mlp_grad_noalloc",
+           "rad_batch_create", "rad_batch_workspace_size", "rad_batch_bind_workspace",
+           "rad_batch_alloc_workspace", "rad_batch_set_stream", "rad_batch_set_graph",
+           "rad_batch_step", "rad_batch_sync", "rad_batch_get_stats", "rad_batch_reset_stats",
+           "rad_batch_launches_per_step", "rad_batch_set_launch", "rad_batch_get_launch",
+           "rad_batch_tune", "rad_batch_mlp_set", "rad_batch_destroy",
            "rad_destroy", "rad_strerror"]
 
 _lib = None
@@ -117,6 +122,25 @@ def lib() -> C.CDLL:
     L.rad_log_bind.argtypes = [vp, vp, C.c_size_t, C.c_longlong]
     L.rad_log_count.argtypes = [vp, P(C.c_size_t)]
     L.rad_mlp_grad_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp, vp]
+    ip = P(C.c_int)
+    L.rad_batch_create.argtypes = [P(vp), C.c_int, P(vp)]
+    L.rad_batch_workspace_size.argtypes = [vp, P(C.c_size_t)]
+    L.rad_batch_bind_workspace.argtypes = [vp, vp, C.c_size_t]
+    L.rad_batch_alloc_workspace.argtypes = [vp]
+    L.rad_batch_set_stream.argtypes = [vp, vp]
+    L.rad_batch_set_graph.argtypes = [vp, C.c_int]
+    L.rad_batch_step.argtypes = [vp, vp, C.c_int]
+    L.rad_batch_sync.argtypes = [vp]
+    L.rad_batch_get_stats.argtypes = [vp, P(rad_stats)]
+    L.rad_batch_reset_stats.argtypes = [vp]
+    L.rad_batch_launches_per_step.argtypes = [vp]
+    L.rad_batch_launches_per_step.restype = C.c_int
+    L.rad_batch_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    L.rad_batch_get_launch.argtypes = [vp, ip, ip, ip, ip]
+    L.rad_batch_tune.argtypes = [vp, C.c_int, ip, ip, P(C.c_float)]
+    L.rad_batch_mlp_set.argtypes = [vp, vp, C.c_size_t]
+    L.rad_batch_destroy.argtypes = [vp]
+    L.rad_batch_destroy.restype = None
     L.rad_destroy.argtypes = [vp]
     L.rad_destroy.restype = None
     L.rad_strerror.argtypes = [C.c_int]
@@ -366,6 +390,96 @@ class Rad:
         if getattr(self, "ctx", None):
             lib().rad_destroy(self.ctx)
             self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class RadBatch:
+    """Many independent grids (Rad members of one kind) advanced together:
+    one persistent launch per step over a shared tile work list, replayed
+    from a captured CUDA graph.  The members stay usable for set_gas,
+    set_rad and read; they must outlive the batch."""
+
+    def __init__(self, members, use_graph: bool = True):
+        import torch
+        self.torch = torch
+        L = lib()
+        self.members = list(members)
+        assert self.members, "empty batch"
+        self.device = self.members[0].device
+        arr = (C.c_void_p * len(self.members))(*[m.ctx for m in self.members])
+        b = C.c_void_p()
+        check(L.rad_batch_create(arr, len(self.members), C.byref(b)), "rad_batch_create")
+        self.b = b
+        nbytes = C.c_size_t()
+        check(L.rad_batch_workspace_size(b, C.byref(nbytes)), "rad_batch_workspace_size")
+        self.workspace_bytes = int(nbytes.value)
+        with torch.cuda.device(self.device):
+            self.stream = torch.cuda.current_stream(self.device)
+            check(L.rad_batch_set_stream(b, C.c_void_p(self.stream.cuda_stream)),
+                  "rad_batch_set_stream")
+            self._ws = torch.empty(self.workspace_bytes + 256, dtype=torch.uint8,
+                                   device=self.device)
+            aligned = (self._ws.data_ptr() + 255) // 256 * 256
+            check(L.rad_batch_bind_workspace(b, C.c_void_p(aligned), self.workspace_bytes),
+                  "rad_batch_bind_workspace")
+        check(L.rad_batch_set_graph(b, int(bool(use_graph))), "rad_batch_set_graph")
+
+    def step(self, nsteps: int = 1, dt=None):
+        """dt: None (each member's CFL step) or one step length per member."""
+        if dt is None:
+            check(lib().rad_batch_step(self.b, None, int(nsteps)), "rad_batch_step")
+            return
+        d = np.ascontiguousarray(np.asarray(dt, dtype=np.float64)).reshape(-1)
+        assert d.size == len(self.members)
+        check(lib().rad_batch_step(self.b, C.c_void_p(d.ctypes.data), int(nsteps)),
+              "rad_batch_step")
+
+    def set_graph(self, use_graph: bool):
+        check(lib().rad_batch_set_graph(self.b, int(bool(use_graph))), "rad_batch_set_graph")
+
+    def sync(self) -> int:
+        return lib().rad_batch_sync(self.b)
+
+    def stats(self) -> dict:
+        s = rad_stats()
+        check(lib().rad_batch_get_stats(self.b, C.byref(s)), "rad_batch_get_stats")
+        return {k: int(getattr(s, k)) for k, _ in rad_stats._fields_}
+
+    def reset_stats(self):
+        check(lib().rad_batch_reset_stats(self.b), "rad_batch_reset_stats")
+
+    def launches_per_step(self) -> int:
+        return lib().rad_batch_launches_per_step(self.b)
+
+    def set_launch(self, variant: int, chunk: int = 0):
+        check(lib().rad_batch_set_launch(self.b, int(variant), int(chunk)), "rad_batch_set_launch")
+
+    def get_launch(self) -> tuple:
+        v, c, n, k = C.c_int(), C.c_int(), C.c_int(), C.c_int()
+        check(lib().rad_batch_get_launch(self.b, C.byref(v), C.byref(c), C.byref(n), C.byref(k)),
+              "rad_batch_get_launch")
+        return v.value, c.value, n.value, k.value
+
+    def tune(self, reps: int = 3) -> tuple:
+        v, c, t = C.c_int(), C.c_int(), C.c_float()
+        check(lib().rad_batch_tune(self.b, int(reps), C.byref(v), C.byref(c), C.byref(t)),
+              "rad_batch_tune")
+        return v.value, c.value, t.value
+
+    def mlp_set(self, params):
+        arr = np.ascontiguousarray(np.asarray(params, dtype=np.float32))
+        check(lib().rad_batch_mlp_set(self.b, C.c_void_p(arr.ctypes.data), arr.size),
+              "rad_batch_mlp_set")
+
+    def close(self):
+        if getattr(self, "b", None):
+            lib().rad_batch_destroy(self.b)
+            self.b = None
 
     def __del__(self):
         try:

@@ -1,0 +1,64 @@
+// ctx_internal.h -- the context behind the opaque rad_ctx handle, shared by
+// the single-grid host code (rad_api.cu) and the batched host code
+// (batch_api.cu).  Not part of the public ABI.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "m1_internal.h"
+#include "mlp_launch.h"
+#include "rad.h"
+#include "step_launch.h"
+
+struct rad_ctx {
+  // description
+  int ndim = 1, n[3] = {1, 1, 1}, geom = 0;
+  int bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
+  std::vector<double> xf[3];
+  rad_opacity opac{};
+  std::vector<float> table32;
+  std::vector<double> table64;
+  rad_params par{};
+  int nc = 3;            // flux/momentum components carried internally
+  double dt_cfl = 0.0;
+  // layout
+  m1::StepDims dims{};
+  size_t pcells = 0;     // padded cells per array
+  size_t N = 0;          // interior cells
+  size_t esize = 8;      // bytes per stored value
+  std::vector<double> tab64[3];
+  std::vector<float> tab32[3];
+  int len[3] = {1, 1, 1};
+  // workspace
+  char* ws = nullptr;
+  size_t ws_bytes = 0;
+  bool ws_owned = false;
+  size_t off_state[2][8] = {};  // E, F0..F2, e, m0..m2 per buffer
+  size_t off_rho = 0, off_tab = 0, off_tab_dir[3] = {}, off_op32 = 0, off_op64 = 0;
+  size_t off_stats = 0, off_status = 0, off_stage = 0;
+  size_t total = 0;
+  cudaStream_t stream = nullptr;
+  int cur = 0;
+  bool have_gas = false, have_rad = false;
+  uint64_t steps = 0;
+  LaunchEntry launch{nullptr, 0};
+  int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
+  bool uniform = false;         // Cartesian with a constant width along each direction
+  // learned guess
+  m1::QueueFn qpass = nullptr;
+  size_t off_mlp = 0, off_grad = 0, off_m = 0, off_v = 0, off_loss = 0, off_queue = 0;
+  size_t off_qcount = 0, off_lcount = 0;
+  bool mlp_ready = false;
+  int adam_step = 0;
+  float* log_buf = nullptr;
+  unsigned int log_cap = 0;
+  long long log_stride = 1;
+};
+
+// Size of the step-kernel argument block of this context (StepArgs of its
+// precision policy) and its filling for one step of length dt that reads
+// state buffer `in_buf` and writes the other one.
+size_t ctx_args_size(const rad_ctx* c);
+void ctx_fill_args(rad_ctx* c, void* out, double dt, int in_buf);

@@ -12,57 +12,10 @@
 #include <numeric>
 #include <vector>
 
-#include "m1_internal.h"
-#include "mlp_launch.h"
-#include "rad.h"
-#include "step_launch.h"
+#include "ctx_internal.h"
 
 using namespace m1;
 
-struct rad_ctx {
-  // description
-  int ndim = 1, n[3] = {1, 1, 1}, geom = 0;
-  int bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
-  std::vector<double> xf[3];
-  rad_opacity opac{};
-  std::vector<float> table32;
-  std::vector<double> table64;
-  rad_params par{};
-  int nc = 3;            // flux/momentum components carried internally
-  double dt_cfl = 0.0;
-  // layout
-  StepDims dims{};
-  size_t pcells = 0;     // padded cells per array
-  size_t N = 0;          // interior cells
-  size_t esize = 8;      // bytes per stored value
-  std::vector<double> tab64[3];
-  std::vector<float> tab32[3];
-  int len[3] = {1, 1, 1};
-  // workspace
-  char* ws = nullptr;
-  size_t ws_bytes = 0;
-  bool ws_owned = false;
-  size_t off_state[2][8] = {};  // E, F0..F2, e, m0..m2 per buffer
-  size_t off_rho = 0, off_tab = 0, off_tab_dir[3] = {}, off_op32 = 0, off_op64 = 0;
-  size_t off_stats = 0, off_status = 0, off_stage = 0;
-  size_t total = 0;
-  cudaStream_t stream = nullptr;
-  int cur = 0;
-  bool have_gas = false, have_rad = false;
-  uint64_t steps = 0;
-  LaunchEntry launch{nullptr, 0};
-  int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
-  bool uniform = false;         // Cartesian with equal widths in every direction
-  // learned guess
-  QueueFn qpass = nullptr;
-  size_t off_mlp = 0, off_grad = 0, off_m = 0, off_v = 0, off_loss = 0, off_queue = 0;
-  size_t off_qcount = 0, off_lcount = 0;
-  bool mlp_ready = false;
-  int adam_step = 0;
-  float* log_buf = nullptr;
-  unsigned int log_cap = 0;
-  long long log_stride = 1;
-};
 
 static const char* kMsg[] = {"ok",
                              "invalid argument",
@@ -612,12 +565,12 @@ static void fill_fields(rad_ctx* c, int b, Fields<S>& f) {
 }
 
 template <class P>
-static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
+static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf) {
   using S = typename P::S;
   using T = typename P::T;
   a.dim = c->dims;
-  fill_fields<S>(c, c->cur, a.in);
-  fill_fields<S>(c, 1 - c->cur, a.out);
+  fill_fields<S>(c, in_buf, a.in);
+  fill_fields<S>(c, 1 - in_buf, a.out);
   a.rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
   for (int d = 0; d < 3; ++d) {
     a.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
@@ -699,6 +652,22 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt) {
   a.log_stride = c->log_stride;
 }
 
+size_t ctx_args_size(const rad_ctx* c) {
+  return c->esize == 8 ? sizeof(StepArgs<Fp64>) : sizeof(StepArgs<Split>);
+}
+
+void ctx_fill_args(rad_ctx* c, void* out, double dt, int in_buf) {
+  if (c->esize == 8) {
+    StepArgs<Fp64> a{};
+    fill_args<Fp64>(c, a, dt, in_buf);
+    std::memcpy(out, &a, sizeof(a));
+  } else {
+    StepArgs<Split> a{};
+    fill_args<Split>(c, a, dt, in_buf);
+    std::memcpy(out, &a, sizeof(a));
+  }
+}
+
 extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   if (!c || nsteps < 0) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
@@ -713,12 +682,12 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
       return RAD_ECUDA;
     if (c->esize == 8) {
       StepArgs<Fp64> a{};
-      fill_args<Fp64>(c, a, dt);
+      fill_args<Fp64>(c, a, dt, c->cur);
       e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
       if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     } else {
       StepArgs<Split> a{};
-      fill_args<Split>(c, a, dt);
+      fill_args<Split>(c, a, dt, c->cur);
       e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
       if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     }
@@ -940,9 +909,9 @@ extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, f
   StepArgs<Fp64> a64{};
   StepArgs<Split> a32{};
   if (c->esize == 8)
-    fill_args<Fp64>(c, a64, c->dt_cfl);
+    fill_args<Fp64>(c, a64, c->dt_cfl, c->cur);
   else
-    fill_args<Split>(c, a32, c->dt_cfl);
+    fill_args<Split>(c, a32, c->dt_cfl, c->cur);
   const void* args = c->esize == 8 ? (const void*)&a64 : (const void*)&a32;
   for (int v = 0; v < c->launch.variants && st == RAD_OK; ++v) {
     for (size_t k = 0; k < chunks.size(); ++k) {

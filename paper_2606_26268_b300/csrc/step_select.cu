@@ -1,4 +1,5 @@
-// step_select.cu -- maps (precision, ndim, geometry, components) to a launcher.
+// step_select.cu -- maps (precision, ndim, geometry, components) to the
+// single-grid and batched launchers.
 #include "step_launch.h"
 
 namespace m1 {
@@ -8,4 +9,15 @@ LaunchEntry select_split(int ndim, int geom, int nc, bool uni);
 
 LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform) {
   return split ? m1::select_split(ndim, geom, nc, uniform) : m1::select_fp64(ndim, geom, nc, uniform);
+}
+
+#include "batch_launch.h"
+
+namespace m1 {
+BatchEntry select_batch_fp64(int ndim, int nc, bool uni);
+BatchEntry select_batch_split(int ndim, int nc, bool uni);
+}  // namespace m1
+
+BatchEntry select_batch(bool split, int ndim, int nc, bool uniform) {
+  return split ? m1::select_batch_split(ndim, nc, uniform) : m1::select_batch_fp64(ndim, nc, uniform);
 }
