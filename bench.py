@@ -46,10 +46,16 @@ def peaks():
         return 6400.0, "fallback"
 
 
+# sources the single-grid step kernel is compiled from (a change to any of
+# them invalidates the profiled DRAM traffic)
+STEP_SOURCES = ("m1_math.cuh", "m1_internal.h", "m1_cell.cuh", "m1_step.cuh", "step_launch.cuh",
+                "step_split.cu", "step_fp64.cu")
+
+
 def kernel_hash():
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_26268_b300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in STEP_SOURCES:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -173,6 +179,85 @@ def time_steps(r, torch, steps, warmup, dt):
     torch.cuda.synchronize()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     return sum(per), per
+
+
+def time_batch(b, torch, steps, warmup):
+    """Device time of `steps` batch steps replayed as one captured graph,
+    after `warmup` steps (events on the batch's stream)."""
+    s = b.stream
+    b.step(warmup)
+    b.step(steps)          # captures the graph of `steps` steps once
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with torch.cuda.stream(s):
+        e0.record(s)
+        b.step(steps)
+        e1.record(s)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def run_batched(args, R, torch, dev, theta, hbm):
+    """64 independent 2D turbulent boxes of uneven sizes (64^2 to 512^2,
+    kappa0 scale log-uniform in [1e-2, 1e2]) advanced together: FP32
+    transport, Newton coupling from the learned guess, one persistent launch
+    per step (plus the queue pass) replayed from a CUDA graph with the tuned
+    launch shape; against the plain FP64 loop of one rad_step per grid."""
+    import workloads as W
+    probs = W.batched_2d(64)
+    cells = int(sum(p.N for p in probs))
+    rtol = 1e-7
+    for p in probs:
+        p.newton_rtol = rtol
+    extra = dict(use_mlp=1, mlp_gate=args.mlp_gate) if theta is not None else {}
+    mem = [R.from_problem(p, "split", device=dev, implicit_mode="newton", **extra) for p in probs]
+    b = R.RadBatch(mem)
+    if theta is not None:
+        b.mlp_set(theta)
+    tuned = b.tune(3)
+    steps = max(args.steps, 10)
+    ms = time_batch(b, torch, steps, args.warmup)
+    status = b.sync()
+    st = b.stats()
+    launch = b.get_launch()
+    lps = b.launches_per_step()
+    b.close()
+    for m in mem:
+        m.close()
+    # plain FP64 per-grid loop on the same grids
+    mem64 = [R.from_problem(p, "fp64", device=dev, implicit_mode="once") for p in probs]
+    for m in mem64:
+        m.step(1)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    k64 = 2
+    e0.record()
+    for _ in range(k64):
+        for m in mem64:
+            m.step(1)
+    e1.record()
+    torch.cuda.synchronize()
+    ms64 = e0.elapsed_time(e1)
+    for m in mem64:
+        m.close()
+    value = cells * steps / (ms * 1e-3)
+    bpc = BYTES_PER_CELL[("split", 2)]
+    achieved = bpc * cells / (ms / steps * 1e-3) / 1e9
+    state_gb = cells * (2 * 6 + 1) * 4 / 1e9
+    return {"workload": "batched_2d_64", "grids": len(probs), "cells": cells,
+            "sizes": [int(p.n[0]) for p in probs], "value": value, "unit": UNIT,
+            "steps": steps, "ms_per_step": ms / steps, "graph": True,
+            "launch": {"variant": launch[0], "chunk": launch[1], "ctas": launch[3],
+                       "tuned_ms": tuned[2]},
+            "form": "split transport, Newton coupling (rtol %g)%s" % (
+                rtol, " from the learned guess" if theta is not None else ""),
+            "gpu_launches": steps * lps, "status": int(status), "iters": st["iters"],
+            "hbm": {"achieved": achieved, "peak": hbm, "frac": achieved / hbm,
+                    "bytes_per_cell": bpc},
+            "l2": "state %.2f GB (both buffers), above the 126 MB L2" % state_gb,
+            "fp64_loop": {"value": cells * k64 / (ms64 * 1e-3), "unit": UNIT,
+                          "ms_per_step": ms64 / k64, "launches_per_step": len(probs),
+                          "form": "FP64, single linearised solve, one rad_step per grid"}}
 
 
 def run_ours(args):
@@ -327,6 +412,11 @@ def run_ours(args):
                 "steps": k64, "ms_per_step": float(t64.item()) / k64,
                 "hbm_frac": b64 * N / (km64 * 1e-3) / 1e9 / hbm}
 
+    # --- batched grids --------------------------------------------------------
+    batched = None
+    if not args.skip_batch:
+        batched = run_batched(args, R, torch, dev, theta, hbm)
+
     # --- CPU baseline: the oracle on the host cores, bounded sample ---------
     cpu = None
     if rank == 0 and not args.skip_cpu:
@@ -356,6 +446,7 @@ def run_ours(args):
             "cpu_baseline": cpu,
             "fp64_plain": fp64,
             "forms": forms,
+            "batched": batched,
             "gpu_launches": launches,
             "clocks": clocks,
             "status": int(status),
@@ -445,6 +536,7 @@ def main():
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
+    ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
