@@ -394,6 +394,27 @@ def run_ours(args):
                            "ms_per_step": ms_ / args.steps, "iters": st_["iters"],
                            "launches_per_step": 1}
 
+    # --- the spherical disk (table opacity) in the headline form ------------
+    if not args.skip_forms and not args.skip_disk:
+        import workloads as W
+        pd = W.disk_spherical()
+        pd.newton_rtol = rtol
+        rd = R.from_problem(pd, args.precision, device=dev, implicit_mode=implicit, **extra)
+        if theta is not None:
+            rd.mlp_set(theta)
+        tv = rd.tune(2)
+        dtd = rd.dt()
+        msd, perd = time_steps(rd, torch, 10, 3, dtd)
+        std_ = rd.stats()
+        sd = rd.sync()
+        rd.close()
+        forms["disk_spherical"] = {
+            "workload": pd.name, "cells": pd.N, "value": pd.N * 10 / (msd * 1e-3), "unit": UNIT,
+            "ms_per_step": msd / 10, "steps": 10, "form": args.form, "iters": std_["iters"],
+            "status": int(sd), "launch": {"variant": tv[0], "chunk": tv[1]},
+            "hbm_frac": BYTES_PER_CELL[(args.precision, 3)] * pd.N / (statistics.mean(perd) * 1e-3)
+            / 1e9 / hbm}
+
     # --- plain FP64 form on the same grid -----------------------------------
     fp64 = None
     if args.precision != "fp64" and not args.skip_fp64:
@@ -477,9 +498,17 @@ def cpu_baseline(prob, dt, seconds):
     t0 = time.perf_counter()
     o.step_cells(cells, dt)
     t2 = time.perf_counter() - t0
+    # the same oracle on one host thread, on a tenth of the sample
+    o1 = oracle.Oracle(prob, nthreads=1)
+    n1 = max(1000, n2 // 10)
+    c1 = rng.choice(prob.N, size=n1, replace=False)
+    t0 = time.perf_counter()
+    o1.step_cells(c1, dt)
+    t3 = time.perf_counter() - t0
     return {"value": n2 / t2, "unit": UNIT, "cores": threads, "kind": "oracle",
             "sample": "%d random cells of %s, one step each from the initial state "
-                      "(%.1f s)" % (n2, prob.name, t2)}
+                      "(%.1f s)" % (n2, prob.name, t2),
+            "one_thread": {"value": n1 / t3, "cores": 1, "cells": n1}}
 
 
 def run_reference(args):
@@ -537,6 +566,7 @@ def main():
     ap.add_argument("--skip-fp64", action="store_true")
     ap.add_argument("--no-tune", action="store_true")
     ap.add_argument("--skip-batch", action="store_true")
+    ap.add_argument("--skip-disk", action="store_true")
     ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

@@ -1,6 +1,16 @@
 """Shared helpers of the parity tests: run a problem on the GPU through the
 C ABI and on the CPU oracle, and compare them with the per-cell error metric
-(|dE|/|E|, |dF|/E, |de|/|e|, |dm|/(|m| + E/chat))."""
+(|dE|/|E|, |dF|/E, |de|/(|e| + 5e-5 n (c/chat) E), |dm|/(|m| + E/chat)).
+
+The internal energy follows from the conservation of E_gas + (c/chat) E_r
+(Sect. 2.7): each step changes it by the difference of (c/chat) E_r before
+and after the coupling, which the definition (and so the oracle) forms by
+subtracting two rounded radiation energies.  After n steps e therefore
+carries up to about n units in the last place of (c/chat) E (2.2e-16 n
+(c/chat) E) even when computed exactly as defined.  Where e is so small that
+this floor exceeds the 1e-11 bound relative to e, the metric measures e
+against 5e-5 n (c/chat) E instead: the FP64 bound then allows about two
+units in the last place of (c/chat) E per step."""
 import numpy as np
 
 import oracle
@@ -39,10 +49,11 @@ def run_oracle(p, nsteps, dt=None, nthreads=0):
             "dt": dt}
 
 
-def errors(g, o, ncomp, chat):
+def errors(g, o, ncomp, chat, ratio=1.0, nsteps=1):
     E = o["E"]
+    escale = np.abs(o["e"]) + 5e-5 * nsteps * ratio * np.abs(E)
     out = {"E": np.max(np.abs(g["E"] - E) / np.abs(E)),
-           "e": np.max(np.abs(g["e"] - o["e"]) / np.abs(o["e"]))}
+           "e": np.max(np.abs(g["e"] - o["e"]) / escale)}
     out["F"] = max(np.max(np.abs(g["F"][q] - o["F"][q]) / E) for q in range(ncomp))
     scale = np.sqrt(np.sum(o["m"] ** 2, axis=0)) + E / chat
     out["m"] = max(np.max(np.abs(g["m"][q] - o["m"][q]) / scale) for q in range(ncomp))

@@ -100,7 +100,7 @@ def test_fp64_batch_within_the_oracle_bound():
     for p, r, dt in zip(probs, inb, dts):
         o = run_oracle(p, 5, dt=dt)
         g = {k: np.asarray(r.read(k), dtype=np.float64) for k in ("E", "F", "e", "m")}
-        err = errors(g, o, p.ncomp, p.chat)
+        err = errors(g, o, p.ncomp, p.chat, p.c / p.chat, 5)
         assert max(err.values()) <= 1e-11, (p.name, err)
     batch.close()
 

@@ -32,15 +32,16 @@ def check64(p, nsteps, tol=TOL64, stencil=False, **kw):
     ~1e5, where a cell's update is a cancellation of much larger fluxes)."""
     g = run_gpu(p, nsteps, "fp64", **kw)
     o = run_oracle(p, nsteps, dt=g["dt"])
+    ratio = p.c / p.chat
     if stencil:
         from scipy.ndimage import maximum_filter
         shape = tuple(reversed(p.n))
         scale = maximum_filter(o["E"].reshape(shape), size=5, mode="nearest").ravel()
-        err = errors(g, o, p.ncomp, p.chat)
+        err = errors(g, o, p.ncomp, p.chat, ratio, nsteps)
         err["E"] = np.max(np.abs(g["E"] - o["E"]) / scale)
         err["F"] = max(np.max(np.abs(g["F"][q] - o["F"][q]) / scale) for q in range(p.ncomp))
     else:
-        err = errors(g, o, p.ncomp, p.chat)
+        err = errors(g, o, p.ncomp, p.chat, ratio, nsteps)
     assert g["status"] == 0, g["status"]
     for k, v in err.items():
         assert v <= tol, (p.name, k, v, err)
@@ -183,7 +184,7 @@ def split_errors(p, nsteps):
     g = run_gpu(q, nsteps, "split")
     o = run_oracle(q, nsteps, dt=g["dt"])
     assert g["status"] == 0
-    err = errors(g, o, p.ncomp, p.chat)
+    err = errors(g, o, p.ncomp, p.chat, p.c / p.chat, nsteps)
     nE = np.linalg.norm(o["E"])
     err["norm_E"] = np.linalg.norm(g["E"] - o["E"]) / nE
     err["norm_F"] = np.linalg.norm(g["F"][:p.ncomp] - o["F"][:p.ncomp]) / nE
@@ -269,6 +270,69 @@ def test_launch_shapes_agree_and_tuning_keeps_the_state(precision, ndim, n):
     r.step(3)
     np.testing.assert_allclose(r.read("E").astype(np.float64), ref, rtol=tol, atol=0)
     r.close()
+
+
+def test_disk_spherical_fp64_parity():
+    """The spherical disk recipe (log-spaced r, theta in [pi/6, 5pi/6],
+    periodic phi, Keplerian v_phi, tabulated opacity) at reduced size, FP64,
+    10 steps.  Near the inner boundary a few cells sit at near-ties of the
+    f-fix / limiter decisions: the oracle itself moves there by ~1e-10 when
+    its inputs change in the last bit.  The bound is therefore the larger of
+    1e-11 and 10x that measured spread; the median cell must agree to 1e-13."""
+    import oracle
+    p = W.disk_spherical((48, 32, 40), nsteps=10)
+    g = run_gpu(p, 10, "fp64")
+    o = run_oracle(p, 10, dt=g["dt"])
+    assert g["status"] == 0
+    q = p.copy()
+    rng = np.random.default_rng(1)
+    for k in ("E", "rho", "T"):
+        a = getattr(q, k)
+        setattr(q, k, a * (1 + 1e-15 * rng.standard_normal(a.shape)))
+    o2 = oracle.Oracle(q)
+    o2.step(10, g["dt"])
+    sens = float(np.max(np.abs(o2.E - o["E"]) / o["E"]))
+    err = errors(g, o, p.ncomp, p.chat, 1.0, 10)
+    bound = max(TOL64, 10 * sens)
+    for k, v in err.items():
+        assert v <= bound, (k, v, bound, err)
+    assert np.median(np.abs(g["E"] - o["E"]) / o["E"]) <= 1e-13
+    assert err["e"] <= TOL64, err
+    assert g["stats"]["efloor"] == o["stats"][1]
+
+
+def test_disk_spherical_split_and_learned_guess():
+    """Same disk in the split form: normwise within 1e-5 of the FP64 oracle
+    after 10 steps (single solve); in Newton mode the learned guess (any
+    parameters) changes only where the iteration starts, so the results
+    with and without it agree to the iteration's tolerance."""
+    p = W.disk_spherical((48, 32, 40), nsteps=10)
+    q = rounded(p, np.float32)
+    g = run_gpu(q, 10, "split")
+    o = run_oracle(q, 10, dt=g["dt"])
+    assert g["status"] == 0
+    nE = np.linalg.norm(o["E"])
+    assert np.linalg.norm(g["E"] - o["E"]) / nE <= 1e-5
+    assert np.linalg.norm(g["F"] - o["F"]) / nE <= 1e-5
+    assert np.linalg.norm(g["e"] - o["e"]) / np.linalg.norm(o["e"]) <= 1e-5
+    import paper_2606_26268_b300 as R
+    outs = []
+    for mlp in (False, True):
+        kw = dict(implicit_mode="newton", newton_rtol=1e-7)
+        if mlp:
+            kw.update(use_mlp=1, mlp_gate=0.0)
+        r = R.from_problem(q, "split", **kw)
+        if mlp:
+            r.mlp_init(3)
+        r.step(10, g["dt"])
+        assert r.sync() == 0
+        outs.append((np.asarray(r.read("E"), dtype=np.float64),
+                     np.asarray(r.read("e"), dtype=np.float64), r.stats()))
+        r.close()
+    (E0, e0, s0), (E1, e1, s1) = outs
+    assert np.max(np.abs(E1 - E0) / E0) <= 1e-5
+    assert np.max(np.abs(e1 - e0) / e0) <= 1e-5
+    assert s0["noconv"] == s1["noconv"] == 0
 
 
 def test_split_large_box_stays_physical():

@@ -259,8 +259,12 @@ def disk_spherical(n: Tuple[int, int, int] = (192, 128, 256), nsteps: int = 50) 
     """3D spherical (r, theta, phi): r log-spaced on [1, 100], theta in
     [pi/6, 5pi/6], phi in [0, 2pi) periodic, outflow in r and theta.
     rho = r^-1.5 exp(-cos^2 theta / (2 0.1^2)) exp(0.3 g - 0.045) (seed 9),
-    v_phi = (r sin theta)^-1/2, T = 1000 r^-1/2, E = T^4, F = 0, tabulated
-    opacity, chat = c = 20."""
+    v_phi = (r sin theta)^-1/2, T = 1000 r^-1/2, E = a_R T^4, F = 0, tabulated
+    opacity, chat = c = 20.  a_R = 1e-12 in these code units, so that the
+    radiation energy is 1e-3 of the gas energy in the midplane at r = 1, as in
+    a protoplanetary disk (with a_R = 1 and T = 1000 the radiation would
+    exceed the gas energy by 1e9, and its pressure would drive the gas
+    internal energy negative within a few steps)."""
     nr, nth, nph = n
     xf = [log_faces(nr, 1.0, 100.0), uniform_faces(nth, math.pi / 6, 5 * math.pi / 6),
           uniform_faces(nph, 0.0, 2 * math.pi)]
@@ -272,7 +276,8 @@ def disk_spherical(n: Tuple[int, int, int] = (192, 128, 256), nsteps: int = 50) 
     p.v = np.zeros((3, p.N))
     p.v[2] = (r * np.sin(th)) ** -0.5
     p.T = 1000.0 * r ** -0.5
-    p.E = p.T ** 4
+    p.a_rad = 1e-12
+    p.E = p.a_rad * p.T ** 4
     p.F = np.zeros((3, p.N))
     p.opacity = opacity_table()
     return p
