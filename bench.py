@@ -181,6 +181,23 @@ def time_steps(r, torch, steps, warmup, dt):
     return sum(per), per
 
 
+def max_over_ranks(x, world, device):
+    """Largest value of x over the ranks (x itself at world size 1)."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(cells_per_rank, steps, ms_max, world):
+    """Cell updates per second of all ranks over the slowest rank's time
+    (every rank advances its own replica: weak scaling)."""
+    return world * cells_per_rank * steps / (ms_max * 1e-3)
+
+
 def time_batch(b, torch, steps, warmup):
     """Device time of `steps` batch steps replayed as one captured graph,
     after `warmup` steps (events on the batch's stream)."""
@@ -197,7 +214,7 @@ def time_batch(b, torch, steps, warmup):
     return e0.elapsed_time(e1)
 
 
-def run_batched(args, R, torch, dev, theta, hbm):
+def run_batched(args, R, torch, dev, theta, hbm, world=1):
     """64 independent 2D turbulent boxes of uneven sizes (64^2 to 512^2,
     kappa0 scale log-uniform in [1e-2, 1e2]) advanced together: FP32
     transport, Newton coupling from the learned guess, one persistent launch
@@ -216,7 +233,8 @@ def run_batched(args, R, torch, dev, theta, hbm):
         b.mlp_set(theta)
     tuned = b.tune(3)
     steps = max(args.steps, 10)
-    ms = time_batch(b, torch, steps, args.warmup)
+    ms_local = time_batch(b, torch, steps, args.warmup)
+    ms = max_over_ranks(ms_local, world, dev)
     status = b.sync()
     st = b.stats()
     launch = b.get_launch()
@@ -240,9 +258,9 @@ def run_batched(args, R, torch, dev, theta, hbm):
     ms64 = e0.elapsed_time(e1)
     for m in mem64:
         m.close()
-    value = cells * steps / (ms * 1e-3)
+    value = whole_job_rate(cells, steps, ms, world)
     bpc = BYTES_PER_CELL[("split", 2)]
-    achieved = bpc * cells / (ms / steps * 1e-3) / 1e9
+    achieved = bpc * cells / (ms_local / steps * 1e-3) / 1e9
     state_gb = cells * (2 * 6 + 1) * 4 / 1e9
     return {"workload": "batched_2d_64", "grids": len(probs), "cells": cells,
             "sizes": [int(p.n[0]) for p in probs], "value": value, "unit": UNIT,
@@ -322,11 +340,8 @@ def run_ours(args):
     status = r.sync()
     st = r.stats()
     launches = args.steps * r.launches_per_step()
-    t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * N * args.steps / (ms_max * 1e-3)
+    ms_max = max_over_ranks(total_ms, world, dev)
+    value = whole_job_rate(N, args.steps, ms_max, world)
     kernel_ms = statistics.mean(per)
     bpc = BYTES_PER_CELL[(args.precision, ndim)]
     achieved = bpc * N / (kernel_ms * 1e-3) / 1e9
@@ -368,12 +383,9 @@ def run_ours(args):
             for k in outs:
                 r2.read(k, out=outs[k])
         torch.cuda.synchronize()
-        e2e_s = time.perf_counter() - t0
-        tt = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        e2e_s = max_over_ranks(time.perf_counter() - t0, world, dev)
         isz = np.dtype(dtype).itemsize
-        e2e = {"value": world * N * ksteps / float(tt.item()), "unit": UNIT,
+        e2e = {"value": whole_job_rate(N, ksteps, e2e_s * 1e3, world), "unit": UNIT,
                "h2d_bytes_per_step": int((3 + 2 * nc) * N * isz),
                "d2h_bytes_per_step": int((2 + 2 * nc) * N * isz), "steps": ksteps}
         r2.close()
@@ -424,19 +436,17 @@ def run_ours(args):
         k64 = max(2, args.steps // 4)
         ms64, per64 = time_steps(r3, torch, k64, 2, dt)
         r3.close()
-        t64 = torch.tensor([ms64], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t64, op=dist.ReduceOp.MAX)
+        ms64 = max_over_ranks(ms64, world, dev)
         b64 = BYTES_PER_CELL[("fp64", ndim)]
         km64 = statistics.mean(per64)
-        fp64 = {"value": world * N * k64 / (float(t64.item()) * 1e-3), "unit": UNIT,
-                "steps": k64, "ms_per_step": float(t64.item()) / k64,
+        fp64 = {"value": whole_job_rate(N, k64, ms64, world), "unit": UNIT,
+                "steps": k64, "ms_per_step": ms64 / k64,
                 "hbm_frac": b64 * N / (km64 * 1e-3) / 1e9 / hbm}
 
     # --- batched grids --------------------------------------------------------
     batched = None
     if not args.skip_batch:
-        batched = run_batched(args, R, torch, dev, theta, hbm)
+        batched = run_batched(args, R, torch, dev, theta, hbm, world)
 
     # --- CPU baseline: the oracle on the host cores, bounded sample ---------
     cpu = None
