@@ -2,6 +2,7 @@
 // the single-grid host code (rad_api.cu) and the batched host code
 // (batch_api.cu).  Not part of the public ABI.
 #pragma once
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -11,6 +12,13 @@
 #include "mlp_launch.h"
 #include "rad.h"
 #include "step_launch.h"
+
+// Tensor maps of the TMA-staged step for one box shape: per state buffer,
+// E, F0..F2, rho and e (the order of the kernel's TmaMaps).
+struct TmaSet {
+  int bx = 0, by = 0;
+  CUtensorMap maps[2][6];
+};
 
 struct rad_ctx {
   // description
@@ -55,6 +63,8 @@ struct rad_ctx {
   float* log_buf = nullptr;
   unsigned int log_cap = 0;
   long long log_stride = 1;
+  // tensor maps of the TMA-staged variants, built on first use per box shape
+  std::vector<TmaSet> tma;
 };
 
 // Size of the step-kernel argument block of this context (StepArgs of its

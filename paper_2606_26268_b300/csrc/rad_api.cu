@@ -8,6 +8,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <numeric>
 #include <vector>
@@ -348,6 +349,7 @@ extern "C" rad_status rad_bind_workspace(rad_ctx* c, void* ptr, size_t bytes) {
   c->ws = static_cast<char*>(ptr);
   c->ws_bytes = bytes;
   c->have_gas = c->have_rad = false;
+  c->tma.clear();
   return upload_static(c);
 }
 
@@ -652,6 +654,70 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf) {
   a.log_stride = c->log_stride;
 }
 
+// ---------------------------------------------------------------------------
+// tensor maps of the TMA-staged step (split precision, 3D Cartesian)
+// ---------------------------------------------------------------------------
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library); nullptr if the driver does not provide it.
+static EncodeTiledFn encode_tiled() {
+  static std::mutex mu;
+  static bool looked = false;
+  static EncodeTiledFn fn = nullptr;
+  std::lock_guard<std::mutex> lock(mu);
+  if (!looked) {
+    looked = true;
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// The six tensor maps (E, F0..F2, rho, e of the current input buffer) of a
+// TMA-staged variant; nullptr if the variant is not TMA-staged here or the
+// maps cannot be encoded.  Each map views one padded field array as a 3D
+// tensor (pn0, pn1, pn2) with boxes of bx x by x 1 elements; reads outside
+// the array are zero-filled.
+static const void* tma_maps(rad_ctx* c, int variant) {
+  if (variant < 0 || variant >= kMaxVariants) return nullptr;
+  const int bx = c->launch.tma_box[variant][0], by = c->launch.tma_box[variant][1];
+  if (bx <= 0 || c->esize != 4 || c->ndim != 3 || c->nc != 3 || !c->ws) return nullptr;
+  for (const TmaSet& t : c->tma)
+    if (t.bx == bx && t.by == by) return t.maps[c->cur];
+  EncodeTiledFn enc = encode_tiled();
+  if (!enc) return nullptr;
+  TmaSet t;
+  t.bx = bx;
+  t.by = by;
+  const StepDims& D = c->dims;
+  const cuuint64_t dims[3] = {cuuint64_t(D.pn[0]), cuuint64_t(D.pn[1]), cuuint64_t(D.pn[2])};
+  const cuuint64_t strides[2] = {cuuint64_t(D.pn[0]) * 4, cuuint64_t(D.pn[0]) * D.pn[1] * 4};
+  const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
+  const cuuint32_t estr[3] = {1, 1, 1};
+  for (int b = 0; b < 2; ++b) {
+    void* fields[6] = {state_ptr(c, b, 0), state_ptr(c, b, 1), state_ptr(c, b, 2),
+                       state_ptr(c, b, 3), c->ws + c->off_rho, state_ptr(c, b, 4)};
+    for (int f = 0; f < 6; ++f) {
+      if (!fields[f] || reinterpret_cast<uintptr_t>(fields[f]) % 16) return nullptr;
+      if (enc(&t.maps[b][f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fields[f], dims, strides, box,
+              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return nullptr;
+    }
+  }
+  c->tma.push_back(t);
+  return c->tma.back().maps[c->cur];
+}
+
 size_t ctx_args_size(const rad_ctx* c) {
   return c->esize == 8 ? sizeof(StepArgs<Fp64>) : sizeof(StepArgs<Split>);
 }
@@ -675,20 +741,23 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   if (!(dt > 0.0)) dt = c->dt_cfl;
   if (!std::isfinite(dt)) return RAD_EINVAL;
   const bool queue = c->par.implicit_mode == RAD_NEWTON;
+  const bool staged = c->launch.tma_box[c->variant][0] > 0;
   for (int s = 0; s < nsteps; ++s) {
     cudaError_t e;
+    const void* maps = staged ? tma_maps(c, c->variant) : nullptr;
+    if (staged && !maps) return RAD_EUNSUPPORTED;
     if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
                      cudaSuccess)
       return RAD_ECUDA;
     if (c->esize == 8) {
       StepArgs<Fp64> a{};
       fill_args<Fp64>(c, a, dt, c->cur);
-      e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
+      e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
       if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     } else {
       StepArgs<Split> a{};
       fill_args<Split>(c, a, dt, c->cur);
-      e = c->launch.fn(&a, c->stream, c->variant, c->chunk);
+      e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
       if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     }
     if (e != cudaSuccess) return RAD_ECUDA;
@@ -914,15 +983,18 @@ extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, f
     fill_args<Split>(c, a32, c->dt_cfl, c->cur);
   const void* args = c->esize == 8 ? (const void*)&a64 : (const void*)&a32;
   for (int v = 0; v < c->launch.variants && st == RAD_OK; ++v) {
+    const bool staged = c->launch.tma_box[v][0] > 0;
+    const void* maps = staged ? tma_maps(c, v) : nullptr;
+    if (staged && !maps) continue;  // TMA maps unavailable: skip the staged shapes
     for (size_t k = 0; k < chunks.size(); ++k) {
       int ch = chunks[k];
       if (k > 0 && ch >= 2 * nmarch) break;
-      if (c->launch.fn(args, c->stream, v, ch) != cudaSuccess) {
+      if (c->launch.fn(args, maps, c->stream, v, ch) != cudaSuccess) {
         st = RAD_ECUDA;
         break;
       }
       cudaEventRecord(e0, c->stream);
-      for (int r = 0; r < reps; ++r) c->launch.fn(args, c->stream, v, ch);
+      for (int r = 0; r < reps; ++r) c->launch.fn(args, maps, c->stream, v, ch);
       cudaEventRecord(e1, c->stream);
       if (cudaEventSynchronize(e1) != cudaSuccess) {
         st = RAD_ECUDA;

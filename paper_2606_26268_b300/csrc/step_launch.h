@@ -2,14 +2,20 @@
 #pragma once
 #include <cuda_runtime.h>
 
-// Launches one step; `args` points to the StepArgs of the policy.  `variant`
+// Launches one step; `args` points to the StepArgs of the policy and `tma`
+// to the six tensor maps (CUtensorMap: E, F0..F2, rho, e of the input
+// buffer) of the TMA-staged variants (ignored by the others).  `variant`
 // selects the CTA shape (0 = default; see step_launch.cuh) and `chunk` the
 // number of cells each CTA marches (0 = default).
-typedef cudaError_t (*LaunchFn)(const void* args, cudaStream_t stream, int variant, int chunk);
+typedef cudaError_t (*LaunchFn)(const void* args, const void* tma, cudaStream_t stream,
+                                int variant, int chunk);
+
+constexpr int kMaxVariants = 8;
 
 struct LaunchEntry {
   LaunchFn fn;
-  int variants;  // number of CTA shapes instantiated
+  int variants;                    // number of CTA shapes instantiated
+  int tma_box[kMaxVariants][2];    // TMA box (columns, rows) of a TMA-staged variant, else 0
 };
 
 // The launcher for (precision, active directions, geometry, carried flux
