@@ -67,7 +67,7 @@ __global__ void __launch_bounds__(128)
   const float* w = args[0].mlp_w;
   if (w)
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = w[i];
-  if (threadIdx.x < ST_N) s_red[threadIdx.x] = 0ull;
+  counters_reset(s_red, threadIdx.x);
   if (threadIdx.x == 0) {
     unsigned int acc = 0;
     s_off[0] = 0;
@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128)
     const StepArgs<P>& a = args[lo];
     queue_cell<P, NDIM, NC>(a, a.queue[q - s_off[lo]], s_w, cnt);
   }
-  flush_counters<P>(args[0], cnt, s_red);
+  counters_flush<P>(args[0], cnt, s_red, threadIdx.x);
 }
 
 template <class P, int NDIM, int NC, bool UNI, int TX, int TY, int MINB>

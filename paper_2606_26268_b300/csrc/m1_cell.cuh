@@ -8,11 +8,62 @@
 
 namespace m1 {
 
+// Counters of one CTA.  The frequent events (fixed face states, coupling
+// iterations) are counted per thread in registers; the rare ones (E floor,
+// |F| clip, Newton restart, no convergence, an iteration count above 1) go
+// straight to the CTA's shared counters s_rare, so that they hold no
+// registers in the step's main loop.  Status bits go to the status word
+// directly (rare too).
 struct Counters {
-  unsigned int fix = 0, efloor = 0, fclip = 0, fallback = 0, noconv = 0, itmax = 0;
-  unsigned long long iters = 0;
-  int status = 0;
+  unsigned int fix = 0, iters = 0;
 };
+
+enum { RARE_EFLOOR = 0, RARE_FCLIP, RARE_FALLBACK, RARE_NOCONV, RARE_ITMAX, RARE_N };
+static __shared__ unsigned int s_rare[RARE_N];
+
+__device__ __forceinline__ void rare_add(int k) { atomicAdd(&s_rare[k], 1u); }
+
+// Zeroes the CTA's shared counters; a barrier must follow before any event.
+__device__ __forceinline__ void counters_reset(unsigned long long* s_red, int tid) {
+  if (tid < ST_N) s_red[tid] = 0ull;
+  if (tid < RARE_N) s_rare[tid] = 0u;
+}
+
+// Adds the CTA's counters to stats (one atomic per counter per CTA).  Called
+// by every thread of the CTA; s_red holds ST_N shared words zeroed by
+// counters_reset.
+template <class P>
+__device__ __forceinline__ void counters_flush(const StepArgs<P>& a, const Counters& c,
+                                               unsigned long long* s_red, int tid) {
+  unsigned long long f = c.fix, it = c.iters;
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    f += __shfl_down_sync(0xffffffffu, f, off);
+    it += __shfl_down_sync(0xffffffffu, it, off);
+  }
+  __syncthreads();  // every event of the CTA has been counted
+  if ((tid & 31) == 0) {
+    if (f) atomicAdd(&s_red[ST_FIX], f);
+    if (it) atomicAdd(&s_red[ST_ITERS], it);
+  }
+  __syncthreads();
+  if (tid == 0) {
+    s_red[ST_EFLOOR] = s_rare[RARE_EFLOOR];
+    s_red[ST_FCLIP] = s_rare[RARE_FCLIP];
+    s_red[ST_FALLBACK] = s_rare[RARE_FALLBACK];
+    s_red[ST_NOCONV] = s_rare[RARE_NOCONV];
+    // every finished cell took at least one iteration
+    const unsigned int im = s_rare[RARE_ITMAX];
+    s_red[ST_ITMAX] = s_red[ST_ITERS] ? (im > 1u ? im : 1u) : 0u;
+  }
+  __syncthreads();
+  if (tid < ST_N && s_red[tid]) {
+    if (tid == ST_ITMAX)
+      atomicMax(a.stats + tid, s_red[tid]);
+    else
+      atomicAdd(a.stats + tid, s_red[tid]);
+  }
+}
 
 // Dimensionless inputs of the converged coupling: the root y = T/T^n of
 // (y - 1) + alpha (y^4 - eps) = 0 depends only on
@@ -62,10 +113,12 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
   using T = typename P::T;
   const StepDims& Dm = a.dim;
   c.iters += co.iters;
-  c.itmax = max(c.itmax, (unsigned)co.iters);
-  c.fallback += co.fallback;
-  c.noconv += co.noconv;
-  if (co.noconv) c.status |= STATUS_NOCONV;
+  if (co.iters > 1) atomicMax(&s_rare[RARE_ITMAX], (unsigned int)co.iters);
+  if (co.fallback) rare_add(RARE_FALLBACK);
+  if (co.noconv) {
+    rare_add(RARE_NOCONV);
+    atomicOr(a.status, STATUS_NOCONV);
+  }
   // record (features, converged log(T/T^n)) for training the learned guess
   if (a.log_cap && a.cp.newton && !co.noconv) {
     long long lin_idx = ci[0] + (long long)Dm.n[0] * (ci[1] + (long long)Dm.n[1] * ci[2]);
@@ -83,7 +136,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
   if (En < a.efloor) {
     En = a.efloor;
     dE = En - Us[0];
-    ++c.efloor;
+    rare_add(RARE_EFLOOR);
   }
   // Eq. (source_discrete2): F^{n+1} (1 + dt chat chi rho) = F*
   T x = a.dt * a.chat * chi * T(rho_s);
@@ -111,7 +164,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
       Fn[v] *= r;
       dF[v] = Fn[v] - Us[1 + v];
     }
-    ++c.fclip;
+    rare_add(RARE_FCLIP);
   }
   // Sect. 2.7: E_gas + (c/chat) E_r and m + F/chat are conserved; the
   // internal energy takes the kinetic-energy change.
@@ -128,7 +181,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
     en = T(e_s) - a.ratio * dE - dke / (T(2) * rr);
   else
     en = T(e_s) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
-  if (!(En > T(0)) || !(en == en) || !(en > T(0))) c.status |= STATUS_NONPHYS;
+  if (!(En > T(0)) || !(en == en) || !(en > T(0))) atomicOr(a.status, STATUS_NONPHYS);
   // stores: own cell and the ghost copies it feeds
   a.out.E[ic] = S(En);
 #pragma unroll

@@ -181,7 +181,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
   const int m0 = MARCH ? mblk * a.chunk : 0;
   const int m1 = MARCH ? min(m0 + a.chunk, Dm.n[MA]) : 1;
 
-  if (tid < ST_N) s_red[tid] = 0ull;
+  counters_reset(s_red, tid);
 
   const int cx = x0 + tx;
   const int cy = TILE_Y ? y0 + ty : 0;
@@ -515,7 +515,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
-        ++cnt.efloor;
+        rare_add(RARE_EFLOOR);
       }
       const int ci[3] = {cx, TILE_Y ? cy : (MARCH ? m : 0), TILE_Y ? m : 0};
       // Newton mode with the queue: the single linearised solve here; cells
@@ -567,35 +567,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
     }
   }
 
-  // block reduction of the counters, one atomic per counter per CTA
-  unsigned long long v[ST_N] = {cnt.fix, cnt.efloor, cnt.fclip, cnt.iters, cnt.itmax,
-                                cnt.fallback, cnt.noconv, 0};
-#pragma unroll
-  for (int k = 0; k < ST_N; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      unsigned long long o = __shfl_down_sync(0xffffffffu, v[k], off);
-      v[k] = (k == ST_ITMAX) ? (o > v[k] ? o : v[k]) : v[k] + o;
-    }
-  }
-  __syncthreads();
-  if ((tid & 31) == 0) {
-#pragma unroll
-    for (int k = 0; k < ST_N; ++k) {
-      if (k == ST_ITMAX)
-        atomicMax(&s_red[k], v[k]);
-      else if (v[k])
-        atomicAdd(&s_red[k], v[k]);
-    }
-  }
-  if (cnt.status) atomicOr(a.status, cnt.status);
-  __syncthreads();
-  if (tid < ST_N && s_red[tid]) {
-    if (tid == ST_ITMAX)
-      atomicMax(a.stats + tid, s_red[tid]);
-    else
-      atomicAdd(a.stats + tid, s_red[tid]);
-  }
+  counters_flush<P>(a, cnt, s_red, tid);
 }
 
 template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>

@@ -125,7 +125,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     mbar_fence_init();
     s_abort = 0;
   }
-  if (tid < ST_N) s_red[tid] = 0ull;
+  counters_reset(s_red, tid);
   __syncthreads();
   if (tid == 0)
     for (int j = 0; j < R && j <= jlast; ++j) issue(j);
@@ -294,7 +294,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
-        ++cnt.efloor;
+        rare_add(RARE_EFLOOR);
       }
       const S rho_m = sl0[FR * BOXP + own], e_m = sl0[FE * BOXP + own];
       const int ci[3] = {cx, cy, m};
@@ -347,34 +347,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     for (int j = 0; j <= jissued; ++j) mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit);
   }
 
-  // block reduction of the counters, one atomic per counter per CTA
-  unsigned long long v[ST_N] = {cnt.fix, cnt.efloor, cnt.fclip, cnt.iters, cnt.itmax,
-                                cnt.fallback, cnt.noconv, 0};
-#pragma unroll
-  for (int k = 0; k < ST_N; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      unsigned long long o = __shfl_down_sync(0xffffffffu, v[k], off);
-      v[k] = (k == ST_ITMAX) ? (o > v[k] ? o : v[k]) : v[k] + o;
-    }
-  }
-  if ((tid & 31) == 0) {
-#pragma unroll
-    for (int k = 0; k < ST_N; ++k) {
-      if (k == ST_ITMAX)
-        atomicMax(&s_red[k], v[k]);
-      else if (v[k])
-        atomicAdd(&s_red[k], v[k]);
-    }
-  }
-  if (cnt.status) atomicOr(a.status, cnt.status);
-  __syncthreads();
-  if (tid < ST_N && s_red[tid]) {
-    if (tid == ST_ITMAX)
-      atomicMax(a.stats + tid, s_red[tid]);
-    else
-      atomicAdd(a.stats + tid, s_red[tid]);
-  }
+  counters_flush<P>(a, cnt, s_red, tid);
 }
 
 }  // namespace m1

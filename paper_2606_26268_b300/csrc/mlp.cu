@@ -24,14 +24,14 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
   if (a.mlp_w)
     for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = a.mlp_w[i];
   __shared__ unsigned long long s_red[ST_N];
-  if (threadIdx.x < ST_N) s_red[threadIdx.x] = 0ull;
+  counters_reset(s_red, threadIdx.x);
   __syncthreads();
   const unsigned int count = min(*a.queue_count, a.queue_cap);
   Counters cnt;
   for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < count;
        q += gridDim.x * blockDim.x)
     queue_cell<P, NDIM, NC>(a, a.queue[q], s_w, cnt);
-  flush_counters<P>(a, cnt, s_red);
+  counters_flush<P>(a, cnt, s_red, threadIdx.x);
 }
 
 template <class P, int NDIM, int NC>

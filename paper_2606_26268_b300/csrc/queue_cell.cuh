@@ -53,37 +53,4 @@ __device__ __forceinline__ void queue_cell(const StepArgs<P>& a, long long ic,
   finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho, e, kp, chi, mom, co, cnt);
 }
 
-// Block reduction of the counters into a.stats and the status word.
-template <class P>
-__device__ __forceinline__ void flush_counters(const StepArgs<P>& a, const Counters& cnt,
-                                               unsigned long long* s_red) {
-  unsigned long long v[ST_N] = {0, cnt.efloor, cnt.fclip, cnt.iters, cnt.itmax,
-                                cnt.fallback, cnt.noconv, 0};
-#pragma unroll
-  for (int k = 0; k < ST_N; ++k) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-      unsigned long long o = __shfl_down_sync(0xffffffffu, v[k], off);
-      v[k] = (k == ST_ITMAX) ? (o > v[k] ? o : v[k]) : v[k] + o;
-    }
-  }
-  if ((threadIdx.x & 31) == 0) {
-#pragma unroll
-    for (int k = 0; k < ST_N; ++k) {
-      if (k == ST_ITMAX)
-        atomicMax(&s_red[k], v[k]);
-      else if (v[k])
-        atomicAdd(&s_red[k], v[k]);
-    }
-  }
-  if (cnt.status) atomicOr(a.status, cnt.status);
-  __syncthreads();
-  if (threadIdx.x < ST_N && s_red[threadIdx.x]) {
-    if (threadIdx.x == ST_ITMAX)
-      atomicMax(a.stats + threadIdx.x, s_red[threadIdx.x]);
-    else
-      atomicAdd(a.stats + threadIdx.x, s_red[threadIdx.x]);
-  }
-}
-
 }  // namespace m1
