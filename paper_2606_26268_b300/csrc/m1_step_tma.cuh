@@ -61,9 +61,11 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
   // ring of R plane slots in dynamic shared memory, aligned here to the
   // 128 bytes a TMA destination needs (128 bytes of slack are allocated)
+  // (the pointer is formed from s_dyn by an offset, so that the compiler
+  // keeps the shared state space and addresses the slots directly)
   extern __shared__ unsigned char s_dyn[];
-  float* const s_ring = reinterpret_cast<float*>(
-      (reinterpret_cast<uintptr_t>(s_dyn) + uintptr_t(127)) & ~uintptr_t(127));
+  float* const s_ring =
+      reinterpret_cast<float*>(s_dyn + ((128u - (smem_addr(s_dyn) & 127u)) & 127u));
   __shared__ __align__(8) unsigned long long s_bar[R];
   __shared__ T s_tau[TY + 1][TX + 1];
   __shared__ T s_fx[NV][TY][TX];
