@@ -93,7 +93,8 @@ __device__ __forceinline__ void riemann(const T (&uL)[4], const T (&uR)[4], T ch
 // Face flux from four consecutive cells um2, um1 | u0, up1 along D (the
 // face between um1 and u0).  ix_k = 1 / (centre distance) of the pairs
 // (um2, um1), (um1, u0), (u0, up1); hh = offset of the upper face of um1,
-// hl = offset of the lower face of u0.  Returns the number of fixed states.
+// hl = offset of the lower face of u0.  Returns which face states the fix
+// replaced: bit 0 the upper state of um1, bit 1 the lower state of u0.
 // Half of the van Leer limited slope on a uniform grid, in units of the
 // cell difference: vl(dl, dr) / 2 = dl dr / (dl + dr) when dl dr > 0.
 template <class T>
@@ -130,10 +131,10 @@ __device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const
     plm_state<T, NV>(d0, d1, um1, hh, uL);
     plm_state<T, NV>(d1, d2, u0, hl, uR);
   }
-  int nfix = fix_face<T, NC>(uL, um1, flux2<T, NC>(um1), Ops<T>::rcp(um1[0]));
-  nfix += fix_face<T, NC>(uR, u0, n2_u0, inv_u0);
+  const int fixL = fix_face<T, NC>(uL, um1, flux2<T, NC>(um1), Ops<T>::rcp(um1[0]));
+  const int fixR = fix_face<T, NC>(uR, u0, n2_u0, inv_u0);
   riemann<T, NC, D>(uL, uR, chat, tau, out);
-  return nfix;
+  return fixL | (fixR << 1);
 }
 
 template <class S, int NC, class T>
@@ -242,7 +243,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
     int nf = face4<T, NC, MA, UNI>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
                                    HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat,
                                    Ops<T>::rcp(q[0][0]), flux2<T, NC>(q[0]), zlo);
-    if (upd_col && m0 == 0) cnt.fix += nf;
+    if (upd_col) cnt.fix += nf >> 1;  // the lower march state of cell m0
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
     T d1[4], d2[4];
 #pragma unroll
@@ -362,8 +363,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       int nf = face4<T, NC, 0, UNI>(um2, um1, u0, up1, IXC(0, px - 2),
                                IXC(0, px - 1), IXC(0, px),
                                HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx);
-      bool own = (tx >= 1 || x0 == 0) && cx <= Dm.n[0] && (!TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]));
-      if (own) cnt.fix += nf;
+      // fixed states of updated cells: the lower one of this cell, the upper
+      // one of the cell to the left
+      const bool row_upd = !TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]);
+      if (upd_col) cnt.fix += nf >> 1;
+      if (row_upd && tx >= 1 && cx - 1 < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = fx[v];
     }
@@ -382,8 +386,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       int nf = face4<T, NC, 1, UNI>(um2, um1, u0, up1, IXC(1, py - 2),
                                IXC(1, py - 1), IXC(1, py),
                                HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy);
-      bool own = (ty >= 1 || y0 == 0) && cy <= Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0];
-      if (own) cnt.fix += nf;
+      if (upd_col) cnt.fix += nf >> 1;
+      if (ty >= 1 && cy - 1 < Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = fy[v];
     }
@@ -417,7 +421,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
       riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
       // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
-      if (upd_col) cnt.fix += nf + (m + 1 < m1 ? nf2 : 0);
+      if (upd_col && m + 1 < m1) cnt.fix += nf + nf2;  // the march states of cell m + 1
     }
     __syncthreads();
 

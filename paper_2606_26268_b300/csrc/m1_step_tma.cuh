@@ -158,7 +158,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     int nf = face4<T, NC, 2, UNI>(qm2, qm1, q[0], q[1], IXC(2, pm - 2), IXC(2, pm - 1),
                                   IXC(2, pm), HHI(2, pm - 1), HLO(2, pm),
                                   T(0.5) * (tau_prev + tau_m), chat, inv_own, n2_own, zlo);
-    if (upd_col && m0 == 0) cnt.fix += nf;
+    if (upd_col) cnt.fix += nf >> 1;  // the lower march state of cell m0
     T d1[4], d2[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -218,8 +218,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       T fx[4];
       int nf = face4<T, NC, 0, UNI>(um2, um1, u0, up1, IXC(0, px - 2), IXC(0, px - 1), IXC(0, px),
                                     HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx);
-      bool ownf = (tx >= 1 || x0 == 0) && cx <= Dm.n[0] && ty <= TY - 2 && cy < Dm.n[1];
-      if (ownf) cnt.fix += nf;
+      if (upd_col) cnt.fix += nf >> 1;
+      if (ty <= TY - 2 && cy < Dm.n[1] && tx >= 1 && cx - 1 < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = fx[v];
     }
@@ -235,8 +235,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       T fy[4];
       int nf = face4<T, NC, 1, UNI>(um2, um1, u0, up1, IXC(1, py - 2), IXC(1, py - 1), IXC(1, py),
                                     HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy);
-      bool ownf = (ty >= 1 || y0 == 0) && cy <= Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0];
-      if (ownf) cnt.fix += nf;
+      if (upd_col) cnt.fix += nf >> 1;
+      if (ty >= 1 && cy - 1 < Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = fy[v];
     }
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
       int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
       riemann<T, NC, 2>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
-      if (upd_col) cnt.fix += nf + (m + 1 < m1 ? nf2 : 0);
+      if (upd_col && m + 1 < m1) cnt.fix += nf + nf2;  // the march states of cell m + 1
     }
     __syncthreads();
 

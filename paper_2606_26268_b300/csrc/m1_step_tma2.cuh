@@ -1,0 +1,463 @@
+// m1_step_tma2.cuh -- the fused step kernel for 3D Cartesian grids in the
+// split precision, with TMA-staged planes and non-overlapping tiles.
+//
+// A CTA of TX x TY threads updates exactly its TX x TY columns and marches
+// along z (same per-cell arithmetic as step_tile).  The planes of E, F, rho
+// and e, with a 2-cell halo on every side, arrive by TMA in a ring of plane
+// slots (as in m1_step_tma.cuh).  Tile origins are multiples of TX, so the
+// boxes need no alignment shift.
+//
+// Each z plane is done in two phases separated by a barrier.
+//   Phase 1.  Every thread reconstructs the x and y face states of its own
+//   cell (one limited slope per direction, both face states, both fixed with
+//   the cell's own centre).  It keeps the lower states in registers and
+//   publishes the upper ones in shared memory.  The threads of the last
+//   three warps also produce the states of the halo ring the tile faces
+//   need: the upper state of column -1 and row -1, the lower state of
+//   column TX and row TY, with those cells' optical depths.
+//   Phase 2.  Every thread computes the HLL flux of its lower x and y faces
+//   from its neighbour's published upper state and its own lower state.  The
+//   threads of the first two warps also compute the tile's upper faces (x
+//   face TX - 1/2 per row, y face TY - 1/2 per column).
+// The march face and the cell update follow as in the other kernels.
+// Compared with overlapping tiles, no thread computes faces for a cell it
+// does not update, and each cell's slope is computed once per direction.
+#pragma once
+#include "m1_step.cuh"
+#include "m1_step_tma.cuh"
+#include "tma.cuh"
+
+namespace m1 {
+
+template <int TX, int TY>
+struct Tma2Tile {
+  static constexpr int BX = TX + 4;                  // box columns (-2 .. TX+1)
+  static constexpr int BY = TY + 4;                  // box rows (-2 .. TY+1)
+  static constexpr int BOX = BX * BY;
+  static constexpr int BOXP = (BOX + 31) / 32 * 32;  // 128-byte aligned stride
+  static constexpr int NHALO = 2 * (TX + TY);        // halo face states per plane
+  static constexpr int NEXTRA = TX + TY;             // upper tile faces per plane
+};
+
+template <int NC, int TX, int TY>
+constexpr size_t tma2_smem_bytes() {
+  return size_t(kTmaRing) * (NC + 3) * Tma2Tile<TX, TY>::BOXP * sizeof(float) + 128;
+}
+
+// Lower and upper reconstructed states of cell uc along one direction from
+// its neighbours um (below) and up (above), each fixed with the cell's own
+// centre; returns how many the fix replaced.  ixl, ixr: inverse centre
+// distances of (um, uc) and (uc, up); hl, hh: offsets of the two faces.
+template <class T, int NC, bool UNI>
+__device__ __forceinline__ int face_states(const T (&um)[4], const T (&uc)[4], const T (&up)[4],
+                                           T ixl, T ixr, T hl, T hh, T n2c, T invc, T (&lo)[4],
+                                           T (&hi)[4]) {
+  constexpr int NV = 1 + NC;
+  if constexpr (UNI && sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T hs = q < NV ? half_vanleer(uc[q] - um[q], up[q] - uc[q]) : T(0);
+      lo[q] = q < NV ? uc[q] - hs : T(0);
+      hi[q] = q < NV ? uc[q] + hs : T(0);
+    }
+  } else {
+    T dl[4], dr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dl[q] = (uc[q] - um[q]) * ixl;
+      dr[q] = (up[q] - uc[q]) * ixr;
+    }
+    plm_state<T, NV>(dl, dr, uc, hl, lo);
+    plm_state<T, NV>(dl, dr, uc, hh, hi);
+  }
+  return fix_face<T, NC>(lo, uc, n2c, invc) + fix_face<T, NC>(hi, uc, n2c, invc);
+}
+
+// One of the two states (the upper if `upper`), for the halo ring.
+template <class T, int NC, bool UNI>
+__device__ __forceinline__ void face_state1(const T (&um)[4], const T (&uc)[4], const T (&up)[4],
+                                            T ixl, T ixr, T h, bool upper, T (&out)[4]) {
+  constexpr int NV = 1 + NC;
+  if constexpr (UNI && sizeof(T) == 4) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      T hs = q < NV ? half_vanleer(uc[q] - um[q], up[q] - uc[q]) : T(0);
+      out[q] = q < NV ? (upper ? uc[q] + hs : uc[q] - hs) : T(0);
+    }
+  } else {
+    T dl[4], dr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dl[q] = (uc[q] - um[q]) * ixl;
+      dr[q] = (up[q] - uc[q]) * ixr;
+    }
+    plm_state<T, NV>(dl, dr, uc, h, out);
+  }
+  fix_face<T, NC>(out, uc, flux2<T, NC>(uc), Ops<T>::rcp(uc[0]));
+}
+
+template <class P, int NC, bool UNI, int TX, int TY, int MINB>
+__global__ void __launch_bounds__(TX * TY, MINB)
+    step_tma2_kernel(const __grid_constant__ StepArgs<P> a, const __grid_constant__ TmaMaps tm) {
+  static_assert(P::kSplit, "TMA staging is built for the split precision");
+  using S = typename P::S;
+  using T = typename P::T;
+  using TL = Tma2Tile<TX, TY>;
+  constexpr int NDIM = 3, GEOM = kCart;
+  constexpr int NV = 1 + NC, NF = NC + 3, R = kTmaRing;
+  constexpr int BX = TL::BX, BY = TL::BY, BOXP = TL::BOXP;
+  constexpr int SLOT = NF * BOXP;
+  constexpr int FR = NC + 1, FE = NC + 2;
+  constexpr int NT = TX * TY;
+  constexpr uint32_t TX_BYTES = uint32_t(NF) * BX * BY * sizeof(float);
+  static_assert(TL::NHALO <= 96 && NT >= 160, "halo states on the last three warps");
+  static_assert(TL::NEXTRA <= 64, "upper tile faces on the first two warps");
+
+  extern __shared__ unsigned char s_dyn[];
+  float* const s_ring =
+      reinterpret_cast<float*>(s_dyn + ((128u - (smem_addr(s_dyn) & 127u)) & 127u));
+  __shared__ __align__(8) unsigned long long s_bar[R];
+  __shared__ T s_tau[TY + 2][TX + 2];   // [row + 1][col + 1], rows/cols -1 .. TY/TX
+  __shared__ T s_hx[NV][TY][TX + 1];    // upper x state of column c at [c + 1], c = -1 .. TX-1
+  __shared__ T s_hy[NV][TY + 1][TX];    // upper y state of row k at [k + 1], k = -1 .. TY-1
+  __shared__ T s_lx[NV][TY];            // lower x state of column TX
+  __shared__ T s_ly[NV][TX];            // lower y state of row TY
+  __shared__ T s_fx[NV][TY][TX + 1];    // x face c - 1/2 at [c], c = 0 .. TX
+  __shared__ T s_fy[NV][TY + 1][TX];    // y face k - 1/2 at [k], k = 0 .. TY
+  __shared__ unsigned long long s_red[ST_N];
+  __shared__ int s_abort;
+
+  const StepDims& Dm = a.dim;
+  const GeomDev<T>& G = a.geo;
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int tid = tx + TX * ty;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int m0 = blockIdx.z * a.chunk;
+  const int m1 = min(m0 + a.chunk, Dm.n[2]);
+  const int jlast = m1 - m0 + 3;  // plane j <-> z = m0 - 2 + j
+
+  const int cx = x0 + tx, cy = y0 + ty;
+  const int px = min(cx + 2, G.len[0] - 1);
+  const int py = min(cy + 2, G.len[1] - 1);
+  const long long base = (long long)min(cx + 2, Dm.pn[0] - 1) + (long long)py * Dm.sy;
+  const long long ms = Dm.sz;
+  const bool in_col = cx < Dm.n[0] && cy < Dm.n[1];
+  const T chat = a.chat;
+  const int own = (ty + 2) * BX + tx + 2;
+
+  auto IXC = [&](int d, int ip) -> T { return UNI ? T(1) : tabv(G, d, TAB_IDXC, ip); };
+  auto HHI = [&](int d, int ip) -> T { return UNI ? T(0.5) : tabv(G, d, TAB_HHI, ip); };
+  auto HLO = [&](int d, int ip) -> T { return UNI ? T(-0.5) : tabv(G, d, TAB_HLO, ip); };
+  auto ALO = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_ALO, ip); };
+  auto AHI = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_AHI, ip); };
+  auto slot = [&](int j) -> const float* { return s_ring + (j % R) * SLOT; };
+  int jissued = -1;
+  auto issue = [&](int j) {  // thread 0: plane j into its slot
+    jissued = j;
+    unsigned long long* bar = &s_bar[j % R];
+    float* dst = s_ring + (j % R) * SLOT;
+    mbar_arrive_expect_tx(bar, TX_BYTES);
+    const int z = m0 + j;  // padded z of plane m0 - 2 + j
+#pragma unroll
+    for (int f = 0; f < NF; ++f) tma_load_3d(dst + f * BOXP, &tm.m[f], x0, y0, z, bar);
+  };
+  bool ok = true;
+  auto wait = [&](int j) {
+    if (!mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit)) {
+      ok = false;
+      s_abort = 1;
+    }
+  };
+  auto state_at = [&](const float* sl, int idx, T (&u)[4]) {
+    u[0] = sl[idx];
+#pragma unroll
+    for (int v = 0; v < 3; ++v) u[1 + v] = v < NC ? sl[(1 + v) * BOXP + idx] : T(0);
+  };
+
+  if (tid == 0) {
+    for (int s = 0; s < R; ++s) mbar_init(&s_bar[s], 1);
+    mbar_fence_init();
+    s_abort = 0;
+  }
+  counters_reset(s_red, tid);
+  __syncthreads();
+  if (tid == 0)
+    for (int j = 0; j < R && j <= jlast; ++j) issue(j);
+
+  Counters cnt;
+  T q[3][4], hiS[4], zlo[4], zhi[4];
+  T inv_own, n2_own, tau_m, tau_n = 0, kp_m, chi_m, kp_n = 0, chi_n = 0;
+#pragma unroll
+  for (int v = 0; v < 4; ++v) zlo[v] = zhi[v] = hiS[v] = T(0);
+
+  // prologue: planes m0-2 .. m0+1 (j = 0..3) for the face m0 - 1/2
+  for (int j = 0; j < 4; ++j) wait(j);
+  {
+    T qm2[4], qm1[4];
+    state_at(slot(0), own, qm2);
+    state_at(slot(1), own, qm1);
+    state_at(slot(2), own, q[0]);
+    state_at(slot(3), own, q[1]);
+    T kp, chi;
+    const T tau_prev = cell_tau<P, NDIM, GEOM, UNI>(a, slot(1)[FR * BOXP + own],
+                                                    slot(1)[FE * BOXP + own], px, py, m0 + 1,
+                                                    kp, chi);
+    tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, slot(2)[FR * BOXP + own], slot(2)[FE * BOXP + own],
+                                         px, py, m0 + 2, kp_m, chi_m);
+    const int pm = m0 + 2;
+    inv_own = Ops<T>::rcp(q[0][0]);
+    n2_own = flux2<T, NC>(q[0]);
+    int nf = face4<T, NC, 2, UNI>(qm2, qm1, q[0], q[1], IXC(2, pm - 2), IXC(2, pm - 1),
+                                  IXC(2, pm), HHI(2, pm - 1), HLO(2, pm),
+                                  T(0.5) * (tau_prev + tau_m), chat, inv_own, n2_own, zlo);
+    if (in_col) cnt.fix += nf >> 1;  // the lower z state of cell m0
+    T d1[4], d2[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      d1[v] = (q[0][v] - qm1[v]) * IXC(2, pm - 1);
+      d2[v] = (q[1][v] - q[0][v]) * IXC(2, pm);
+    }
+    plm_state<T, NV>(d1, d2, q[0], HHI(2, pm), hiS);
+    int nfh = fix_face<T, NC>(hiS, q[0], n2_own, inv_own);
+    if (in_col) cnt.fix += nfh;
+  }
+
+  // halo face state of this thread (last three warps): item h of
+  //   [0, TY): upper x of column -1, row h       [TY, 2TY): lower x of column TX
+  //   [2TY, 2TY+TX): upper y of row -1, col c    [2TY+TX, 2TY+2TX): lower y of row TY
+  const int h = tid - (NT - 96);
+  const bool has_h = h >= 0 && h < TL::NHALO;
+  const bool h_x = h < 2 * TY;                    // x-direction item
+  const bool h_hi = h_x ? h < TY : h < 2 * TY + TX;  // upper state wanted
+  const int h_rc = h_x ? (h < TY ? h : h - TY) : (h < 2 * TY + TX ? h - 2 * TY : h - 2 * TY - TX);
+  // smem position of the item's cell, its neighbours' stride, table indices
+  const int h_row = h_x ? h_rc + 2 : (h_hi ? 1 : TY + 2);
+  const int h_col = h_x ? (h_hi ? 1 : TX + 2) : h_rc + 2;
+  const int h_idx = h_row * BX + h_col;
+  const int h_step = h_x ? 1 : BX;
+  const int h_px = min(x0 + h_col, G.len[0] - 1);
+  const int h_py = min(y0 + h_row, G.len[1] - 1);
+  const int h_p = h_x ? h_px : h_py;  // padded index along the item's direction
+  // upper tile face of this thread (first two warps): x face TX - 1/2 of
+  // row e (e < TY) or y face TY - 1/2 of column e - TY
+  const int e = tid;
+  const bool has_e = e < TL::NEXTRA;
+  const bool e_x = e < TY;
+
+  for (int m = m0; m < m1; ++m) {
+    const int j = m - m0 + 2;  // plane m
+    const long long ic = base + (long long)(m + 2) * ms;
+    wait(j + 2);
+    const float* sl0 = slot(j);
+    const float* sl1 = slot(j + 1);
+    state_at(slot(j + 2), own, q[2]);
+    T mom[3] = {0, 0, 0};
+    if (in_col) {
+#pragma unroll
+      for (int v = 0; v < NC; ++v) mom[v] = T(__ldg(a.in.m[v] + ic));
+    }
+    // --- phase 1: face states of the own cell (x and y) and of the halo
+    T lox[4], loy[4];
+    {
+      T um[4], up[4], hx[4], hy[4];
+      state_at(sl0, own - 1, um);
+      state_at(sl0, own + 1, up);
+      int nf = face_states<T, NC, UNI>(um, q[0], up, IXC(0, px - 1), IXC(0, px), HLO(0, px),
+                                       HHI(0, px), n2_own, inv_own, lox, hx);
+      state_at(sl0, own - BX, um);
+      state_at(sl0, own + BX, up);
+      nf += face_states<T, NC, UNI>(um, q[0], up, IXC(1, py - 1), IXC(1, py), HLO(1, py),
+                                    HHI(1, py), n2_own, inv_own, loy, hy);
+      if (in_col) cnt.fix += nf;
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        s_hx[v][ty][tx + 1] = hx[v];
+        s_hy[v][ty + 1][tx] = hy[v];
+      }
+    }
+    s_tau[ty + 1][tx + 1] = tau_m;
+    if (has_h) {
+      T uc[4], um[4], up[4], st[4];
+      state_at(sl0, h_idx, uc);
+      state_at(sl0, h_idx - h_step, um);
+      state_at(sl0, h_idx + h_step, up);
+      const int d = h_x ? 0 : 1;
+      face_state1<T, NC, UNI>(um, uc, up, IXC(d, h_p - 1), IXC(d, h_p),
+                              h_hi ? HHI(d, h_p) : HLO(d, h_p), h_hi, st);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) {
+        if (h_x) {
+          if (h_hi)
+            s_hx[v][h_rc][0] = st[v];
+          else
+            s_lx[v][h_rc] = st[v];
+        } else {
+          if (h_hi)
+            s_hy[v][0][h_rc] = st[v];
+          else
+            s_ly[v][h_rc] = st[v];
+        }
+      }
+      T kp, chi;
+      s_tau[h_row - 1][h_col - 1] = cell_tau<P, NDIM, GEOM, UNI>(
+          a, sl0[FR * BOXP + h_idx], sl0[FE * BOXP + h_idx], h_px, h_py, m + 2, kp, chi);
+    }
+    tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, sl1[FR * BOXP + own], sl1[FE * BOXP + own], px, py,
+                                         m + 3, kp_n, chi_n);
+    __syncthreads();
+    if (s_abort) break;
+    // plane j - 2 (= m - 2) was last read in iteration m - 2: its slot is free
+    if (tid == 0 && j + 3 <= jlast) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      issue(j + 3);
+    }
+
+    // --- phase 2: HLL fluxes of the lower x and y faces (and upper tile faces)
+    {
+      T uL[4] = {0, 0, 0, 0}, f[4];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) uL[v] = s_hx[v][ty][tx];
+      riemann<T, NC, 0>(uL, lox, chat, T(0.5) * (s_tau[ty + 1][tx] + s_tau[ty + 1][tx + 1]), f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = f[v];
+#pragma unroll
+      for (int v = 0; v < NV; ++v) uL[v] = s_hy[v][ty][tx];
+      riemann<T, NC, 1>(uL, loy, chat, T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]), f);
+#pragma unroll
+      for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = f[v];
+    }
+    if (has_e) {
+      T uL[4] = {0, 0, 0, 0}, uR[4] = {0, 0, 0, 0}, f[4];
+      if (e_x) {
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          uL[v] = s_hx[v][e][TX];
+          uR[v] = s_lx[v][e];
+        }
+        riemann<T, NC, 0>(uL, uR, chat, T(0.5) * (s_tau[e + 1][TX] + s_tau[e + 1][TX + 1]), f);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s_fx[v][e][TX] = f[v];
+      } else {
+        const int c = e - TY;
+#pragma unroll
+        for (int v = 0; v < NV; ++v) {
+          uL[v] = s_hy[v][TY][c];
+          uR[v] = s_ly[v][c];
+        }
+        riemann<T, NC, 1>(uL, uR, chat, T(0.5) * (s_tau[TY][c + 1] + s_tau[TY + 1][c + 1]), f);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) s_fy[v][TY][c] = f[v];
+      }
+    }
+    // march face m + 1/2 from the column registers
+    T hiN[4];
+    T inv_n = Ops<T>::rcp(q[1][0]);
+    T n2_n = flux2<T, NC>(q[1]);
+    {
+      const int pm = m + 3;  // padded z of cell m + 1
+      T loN[4];
+      if constexpr (UNI) {
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          T hs = v < NV ? half_vanleer(q[1][v] - q[0][v], q[2][v] - q[1][v]) : T(0);
+          loN[v] = q[1][v] - hs;
+          hiN[v] = q[1][v] + hs;
+        }
+      } else {
+        T ix1 = IXC(2, pm - 1), ix2 = IXC(2, pm);
+        T d1[4], d2[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) {
+          d1[v] = (q[1][v] - q[0][v]) * ix1;
+          d2[v] = (q[2][v] - q[1][v]) * ix2;
+        }
+        plm_state<T, NV>(d1, d2, q[1], HLO(2, pm), loN);
+        plm_state<T, NV>(d1, d2, q[1], HHI(2, pm), hiN);
+      }
+      int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
+      int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
+      riemann<T, NC, 2>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      if (in_col && m + 1 < m1) cnt.fix += nf + nf2;  // the z states of cell m + 1
+    }
+    __syncthreads();
+
+    // update of the own cell
+    if (in_col) {
+      T dU[4] = {0, 0, 0, 0};
+      {
+        T alo = ALO(0, px), ahi = AHI(0, px);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fx[v][ty][tx + 1] - alo * s_fx[v][ty][tx];
+      }
+      {
+        T alo = ALO(1, py), ahi = AHI(1, py);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fy[v][ty + 1][tx] - alo * s_fy[v][ty][tx];
+      }
+      {
+        T alo = ALO(2, m + 2), ahi = AHI(2, m + 2);
+#pragma unroll
+        for (int v = 0; v < NV; ++v) dU[v] -= ahi * zhi[v] - alo * zlo[v];
+      }
+      const T (&u)[4] = q[0];
+      T Us[4];
+#pragma unroll
+      for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+      if (Us[0] < a.efloor) {
+        Us[0] = a.efloor;
+        rare_add(RARE_EFLOOR);
+      }
+      const S rho_m = sl0[FR * BOXP + own], e_m = sl0[FE * BOXP + own];
+      const int ci[3] = {cx, cy, m};
+      bool queued = false;
+      CoupleOut co;
+      if (a.queue_cap) {
+        co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, true);
+        queued = !co.conv1;
+        const unsigned int mask = __activemask();
+        const unsigned int want = __ballot_sync(mask, queued);
+        unsigned int base_slot = 0;
+        const int leader = __ffs(mask) - 1;
+        if ((tid & 31) == leader && want) base_slot = atomicAdd(a.queue_count, __popc(want));
+        base_slot = __shfl_sync(mask, base_slot, leader);
+        if (queued) {
+          unsigned int qs = base_slot + __popc(want & ((1u << (tid & 31)) - 1u));
+          if (qs < a.queue_cap) {
+            a.queue[qs] = ic;
+            a.out.E[ic] = S(Us[0]);
+#pragma unroll
+            for (int v = 0; v < NC; ++v) a.out.F[v][ic] = S(Us[1 + v]);
+          } else {
+            queued = false;  // queue full: iterate here
+            co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);
+          }
+        }
+      } else {
+        co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);
+      }
+      if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+    }
+#pragma unroll
+    for (int v = 0; v < 4; ++v) {
+      q[0][v] = q[1][v];
+      q[1][v] = q[2][v];
+      hiS[v] = hiN[v];
+      zlo[v] = zhi[v];
+    }
+    tau_m = tau_n;
+    inv_own = inv_n;
+    n2_own = n2_n;
+    kp_m = kp_n;
+    chi_m = chi_n;
+  }
+
+  if (!ok) atomicOr(a.status, STATUS_TIMEOUT);
+  __syncthreads();
+  if (s_abort && tid == 0) {
+    // let the copies still in flight land (bounded) before the CTA exits
+    for (int j = 0; j <= jissued; ++j) mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit);
+  }
+  counters_flush<P>(a, cnt, s_red, tid);
+}
+
+}  // namespace m1

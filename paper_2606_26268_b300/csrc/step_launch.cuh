@@ -4,6 +4,7 @@
 
 #include "m1_step.cuh"
 #include "m1_step_tma.cuh"
+#include "m1_step_tma2.cuh"
 #include "step_launch.h"
 
 namespace m1 {
@@ -46,15 +47,33 @@ cudaError_t launch_tma(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk
   return cudaGetLastError();
 }
 
+template <class P, int NC, bool UNI, int TX, int TY, int MINB>
+cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk) {
+  if (!tma) return cudaErrorInvalidValue;
+  const int* n = a.dim.n;
+  a.chunk = chunk > 0 ? chunk : 32;
+  if (a.chunk > n[2]) a.chunk = n[2];
+  constexpr size_t smem = tma2_smem_bytes<NC, TX, TY>();
+  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  if (e != cudaSuccess) return e;
+  TmaMaps maps;
+  std::memcpy(&maps, tma, sizeof(maps));
+  dim3 grid((n[0] + TX - 1) / TX, (n[1] + TY - 1) / TY, (n[2] + a.chunk - 1) / a.chunk);
+  kern<<<grid, dim3(TX, TY), smem, s>>>(a, maps);
+  return cudaGetLastError();
+}
+
 // CTA shapes.  3D: 32x8 (2 or 3 CTAs/SM), 32x16, 64x8, and for the split
-// precision on Cartesian grids the TMA-staged 32x8 (2 or 3 CTAs/SM); 2D rows
-// of 128, 256 or 64 threads; 1D: 128.  Curvilinear grids get the default
-// shape only.
+// precision on Cartesian grids the TMA-staged 32x8 with overlapping tiles
+// (variants 4, 5) and with non-overlapping tiles (6, 7), each at 2 or 3
+// CTAs/SM; 2D rows of 128, 256 or 64 threads; 1D: 128.  Curvilinear grids
+// get the default shape only.
 template <class P, int NDIM, int GEOM, int NC, bool UNI>
 struct Shapes {
   static constexpr bool tma = P::kSplit && GEOM == kCart && NDIM == 3;
   static constexpr int count =
-      (GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 6 : 4) : 3);
+      (GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 8 : 4) : 3);
   static cudaError_t launch(const void* vargs, const void* maps, cudaStream_t s, int variant,
                             int chunk) {
     const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
@@ -63,6 +82,8 @@ struct Shapes {
       if constexpr (tma) {
         if (variant == 4) return launch_tma<P, NC, UNI, 32, 8, 2>(a, maps, s, chunk);
         if (variant == 5) return launch_tma<P, NC, UNI, 32, 8, 3>(a, maps, s, chunk);
+        if (variant == 6) return launch_tma2<P, NC, UNI, 32, 8, 2>(a, maps, s, chunk);
+        if (variant == 7) return launch_tma2<P, NC, UNI, 32, 8, 3>(a, maps, s, chunk);
       }
       if constexpr (count > 1) {
         if (variant == 1) return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 3>(a, s, chunk);
@@ -90,6 +111,10 @@ LaunchEntry entry() {
     for (int v = 4; v < 6; ++v) {
       e.tma_box[v][0] = TmaTile<32, 8>::BX;
       e.tma_box[v][1] = TmaTile<32, 8>::BY;
+    }
+    for (int v = 6; v < 8; ++v) {
+      e.tma_box[v][0] = Tma2Tile<32, 8>::BX;
+      e.tma_box[v][1] = Tma2Tile<32, 8>::BY;
     }
   }
   return e;
