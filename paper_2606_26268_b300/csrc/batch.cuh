@@ -61,13 +61,9 @@ template <class P, int NDIM, int NC>
 __global__ void __launch_bounds__(128)
     batch_queue_kernel(const StepArgs<P>* __restrict__ args, int count,
                        const unsigned int* __restrict__ counts) {
-  extern __shared__ float s_w[];
+  extern __shared__ __align__(16) float s_w[];
   __shared__ unsigned int s_off[kBatchMaxGrids + 1];
   __shared__ unsigned long long s_red[ST_N];
-  const float* w = args[0].mlp_w;
-  if (w)
-    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = w[i];
-  counters_reset(s_red, threadIdx.x);
   if (threadIdx.x == 0) {
     unsigned int acc = 0;
     s_off[0] = 0;
@@ -78,6 +74,11 @@ __global__ void __launch_bounds__(128)
   }
   __syncthreads();
   const unsigned int total = s_off[count];
+  if (blockIdx.x * blockDim.x >= total) return;  // no queued cell for this block
+  const float* w = args[0].mlp_w;
+  if (w) load_mlp_weights(s_w, w);
+  counters_reset(s_red, threadIdx.x);
+  __syncthreads();
   Counters cnt;
   for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < total;
        q += gridDim.x * blockDim.x) {
@@ -142,7 +143,7 @@ struct BatchShapes {
   }
   static cudaError_t qpass(const void* args, int count, const unsigned int* counts, bool mlp,
                            cudaStream_t s) {
-    const size_t smem = mlp ? MLP_NPARAM * sizeof(float) : 0;
+    const size_t smem = mlp ? MLP_NPARAM_PAD * sizeof(float) : 0;
     batch_queue_kernel<P, NDIM, NC><<<148 * 4, 128, smem, s>>>(
         static_cast<const StepArgs<P>*>(args), count, counts);
     return cudaGetLastError();

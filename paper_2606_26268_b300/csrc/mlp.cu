@@ -20,13 +20,13 @@ namespace m1 {
 
 template <class P, int NDIM, int NC>
 __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__ StepArgs<P> a) {
-  extern __shared__ float s_w[];
-  if (a.mlp_w)
-    for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = a.mlp_w[i];
+  extern __shared__ __align__(16) float s_w[];
   __shared__ unsigned long long s_red[ST_N];
+  const unsigned int count = min(*a.queue_count, a.queue_cap);
+  if (blockIdx.x * blockDim.x >= count) return;  // no queued cell for this block
+  if (a.mlp_w) load_mlp_weights(s_w, a.mlp_w);
   counters_reset(s_red, threadIdx.x);
   __syncthreads();
-  const unsigned int count = min(*a.queue_count, a.queue_cap);
   Counters cnt;
   for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < count;
        q += gridDim.x * blockDim.x)
@@ -37,13 +37,7 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
 template <class P, int NDIM, int NC>
 cudaError_t launch_queue_pass(const void* vargs, cudaStream_t s) {
   const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
-  const size_t smem = a.mlp_w ? MLP_NPARAM * sizeof(float) : 0;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(queue_pass_kernel<P, NDIM, NC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         int(MLP_NPARAM * sizeof(float)));
-    attr_set = true;
-  }
+  const size_t smem = a.mlp_w ? MLP_NPARAM_PAD * sizeof(float) : 0;
   queue_pass_kernel<P, NDIM, NC><<<148 * 4, 128, smem, s>>>(a);
   return cudaGetLastError();
 }
@@ -180,8 +174,8 @@ __global__ void mlp_adam_kernel(float* w, float* grad, float* m, float* v, float
 
 __global__ void mlp_predict_kernel(const float* __restrict__ w, const float4* __restrict__ rec,
                                    long long n, float* out) {
-  extern __shared__ float s_w[];
-  for (int i = threadIdx.x; i < MLP_NPARAM; i += blockDim.x) s_w[i] = w[i];
+  extern __shared__ __align__(16) float s_w[];
+  load_mlp_weights(s_w, w);
   __syncthreads();
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < n;
        q += (long long)gridDim.x * blockDim.x) {
@@ -213,12 +207,7 @@ cudaError_t mlp_adam_launch(float* w, float* grad, float* m, float* v, float lr,
 
 cudaError_t mlp_predict_launch(const float* w, const float4* rec, long long n, float* out,
                                cudaStream_t s) {
-  const size_t smem = MLP_NPARAM * sizeof(float);
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaFuncSetAttribute(mlp_predict_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-    attr_set = true;
-  }
+  const size_t smem = MLP_NPARAM_PAD * sizeof(float);
   long long blocks = (n + 127) / 128;
   if (blocks > 148 * 8) blocks = 148 * 8;
   if (blocks < 1) blocks = 1;

@@ -19,6 +19,18 @@ constexpr int MLP_B3 = MLP_W3 + MLP_H * MLP_H;
 constexpr int MLP_W4 = MLP_B3 + MLP_H;
 constexpr int MLP_B4 = MLP_W4 + MLP_H;
 constexpr int MLP_NPARAM = MLP_B4 + 1;  // 8577
+// parameters as whole float4 words (the buffers holding them are allocated in
+// 256-byte pieces, so the padded tail is readable)
+constexpr int MLP_NPARAM_PAD = (MLP_NPARAM + 3) / 4 * 4;
+
+// Copies the parameters into shared memory (s_w: MLP_NPARAM_PAD floats,
+// 16-byte aligned) with 16-byte loads, several in flight per thread.
+__device__ __forceinline__ void load_mlp_weights(float* s_w, const float* w) {
+  const float4* src = reinterpret_cast<const float4*>(w);
+  float4* dst = reinterpret_cast<float4*>(s_w);
+#pragma unroll 4
+  for (int i = threadIdx.x; i < MLP_NPARAM_PAD / 4; i += blockDim.x) dst[i] = __ldg(src + i);
+}
 
 __device__ __forceinline__ float tanh_approx(float x) {
   float r;
