@@ -203,6 +203,16 @@ rad_status rad_reset_stats(rad_ctx *ctx);
  * accounting by callers). */
 int rad_launches_per_step(const rad_ctx *ctx);
 
+/* Kernel timing (not in the paper: a measurement aid).  After
+ * rad_profile_begin, each of the next max_steps steps records CUDA events on
+ * the stream around its step kernel and around its queue pass (RAD_NEWTON).
+ * rad_profile_end waits for the last of them and returns the summed device
+ * times (ms) of the step kernels and of the queue passes and the number of
+ * steps timed (any output may be NULL), then releases the events.  Errors:
+ * RAD_EINVAL (max_steps outside 1..2^20), RAD_ECUDA. */
+rad_status rad_profile_begin(rad_ctx *ctx, int max_steps);
+rad_status rad_profile_end(rad_ctx *ctx, float *step_ms, float *queue_ms, int *nsteps);
+
 /* Launch shape of the step kernel: `variant` selects one of the CTA shapes
  * instantiated for this grid (0 = default; rad_get_launch reports how many)
  * and `chunk` the number of cells a CTA marches along the slowest active

@@ -66,7 +66,8 @@ class rad_stats(C.Structure):
 EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_workspace",
            "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad", "rad_step",
            "rad_read", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
-           "rad_launches_per_step", "rad_set_launch", "rad_get_launch", "rad_tune",
+           "rad_launches_per_step", "rad_profile_begin", "rad_profile_end",
+           "rad_set_launch", "rad_get_launch", "rad_tune",
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
            "rad_mlp_grad", "rad_mlp_predict", "rad_log_bind", "rad_log_count",
            "rad_mlp_grad_noalloc",
@@ -107,6 +108,8 @@ def lib() -> C.CDLL:
     L.rad_reset_stats.argtypes = [vp]
     L.rad_launches_per_step.argtypes = [vp]
     L.rad_launches_per_step.restype = C.c_int
+    L.rad_profile_begin.argtypes = [vp, C.c_int]
+    L.rad_profile_end.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_int)]
     L.rad_set_launch.argtypes = [vp, C.c_int, C.c_int]
     L.rad_get_launch.argtypes = [vp, P(C.c_int), P(C.c_int), P(C.c_int)]
     L.rad_tune.argtypes = [vp, C.c_int, P(C.c_int), P(C.c_int), P(C.c_float)]
@@ -385,6 +388,17 @@ class Rad:
 
     def launches_per_step(self) -> int:
         return lib().rad_launches_per_step(self.ctx)
+
+    def profile_begin(self, max_steps: int):
+        """Time the step kernel and the queue pass of the next max_steps steps."""
+        check(lib().rad_profile_begin(self.ctx, int(max_steps)), "rad_profile_begin")
+
+    def profile_end(self) -> tuple:
+        """(summed step-kernel ms, summed queue-pass ms, steps timed)."""
+        a, b, n = C.c_float(), C.c_float(), C.c_int()
+        check(lib().rad_profile_end(self.ctx, C.byref(a), C.byref(b), C.byref(n)),
+              "rad_profile_end")
+        return a.value, b.value, n.value
 
     def close(self):
         if getattr(self, "ctx", None):

@@ -65,6 +65,10 @@ struct rad_ctx {
   long long log_stride = 1;
   // tensor maps of the TMA-staged variants, built on first use per box shape
   std::vector<TmaSet> tma;
+  // kernel timing: 3 events per profiled step (step kernel start, step kernel
+  // end = queue pass start, queue pass end)
+  std::vector<cudaEvent_t> prof_ev;
+  int prof_cap = 0, prof_n = 0;
 };
 
 // Size of the step-kernel argument block of this context (StepArgs of its

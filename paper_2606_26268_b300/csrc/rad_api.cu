@@ -749,21 +749,68 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
     if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
                      cudaSuccess)
       return RAD_ECUDA;
+    cudaEvent_t* ev = c->prof_n < c->prof_cap ? &c->prof_ev[3 * size_t(c->prof_n++)] : nullptr;
+    if (ev) cudaEventRecord(ev[0], c->stream);
     if (c->esize == 8) {
       StepArgs<Fp64> a{};
       fill_args<Fp64>(c, a, dt, c->cur);
       e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
+      if (ev) cudaEventRecord(ev[1], c->stream);
       if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     } else {
       StepArgs<Split> a{};
       fill_args<Split>(c, a, dt, c->cur);
       e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
+      if (ev) cudaEventRecord(ev[1], c->stream);
       if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
     }
+    if (ev) cudaEventRecord(ev[2], c->stream);
     if (e != cudaSuccess) return RAD_ECUDA;
     c->cur = 1 - c->cur;
     ++c->steps;
   }
+  return RAD_OK;
+}
+
+static void profile_release(rad_ctx* c) {
+  for (cudaEvent_t e : c->prof_ev) cudaEventDestroy(e);
+  c->prof_ev.clear();
+  c->prof_cap = c->prof_n = 0;
+}
+
+extern "C" rad_status rad_profile_begin(rad_ctx* c, int max_steps) {
+  if (!c || max_steps < 1 || max_steps > (1 << 20)) return RAD_EINVAL;
+  profile_release(c);
+  c->prof_ev.assign(3 * size_t(max_steps), nullptr);
+  for (cudaEvent_t& e : c->prof_ev)
+    if (cudaEventCreate(&e) != cudaSuccess) {
+      e = nullptr;
+      profile_release(c);
+      return RAD_ECUDA;
+    }
+  c->prof_cap = max_steps;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_profile_end(rad_ctx* c, float* step_ms, float* queue_ms, int* nsteps) {
+  if (!c) return RAD_EINVAL;
+  const int n = c->prof_n;
+  float ts = 0.f, tq = 0.f;
+  rad_status st = RAD_OK;
+  if (n > 0 && cudaEventSynchronize(c->prof_ev[3 * size_t(n - 1) + 2]) != cudaSuccess) st = RAD_ECUDA;
+  for (int i = 0; i < n && st == RAD_OK; ++i) {
+    float a = 0.f, b = 0.f;
+    if (cudaEventElapsedTime(&a, c->prof_ev[3 * i], c->prof_ev[3 * i + 1]) != cudaSuccess ||
+        cudaEventElapsedTime(&b, c->prof_ev[3 * i + 1], c->prof_ev[3 * i + 2]) != cudaSuccess)
+      st = RAD_ECUDA;
+    ts += a;
+    tq += b;
+  }
+  profile_release(c);
+  if (st != RAD_OK) return st;
+  if (step_ms) *step_ms = ts;
+  if (queue_ms) *queue_ms = tq;
+  if (nsteps) *nsteps = n;
   return RAD_OK;
 }
 
@@ -1127,6 +1174,7 @@ extern "C" rad_status rad_reset_stats(rad_ctx* c) {
 
 extern "C" void rad_destroy(rad_ctx* c) {
   if (!c) return;
+  profile_release(c);
   if (c->ws_owned && c->ws) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->ws);

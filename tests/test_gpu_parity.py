@@ -360,3 +360,24 @@ def test_stretched_cartesian_grid_fp64(ndim):
         w = 1.03 ** np.arange(n[d])
         p.xfaces[d] = np.r_[0.0, np.cumsum(w / w.sum())]
     check64(p, 5)
+
+
+def test_kernel_timing_counts_the_profiled_steps():
+    """rad_profile_begin/end time the step kernel and the queue pass of the
+    next max_steps steps only; the state is the same as without timing."""
+    import paper_2606_26268_b300 as R
+    p = W.random_smooth("cartesian", (40, 24, 18), 3, seed=9, bc="periodic", ncomp=3)
+    p.implicit_mode = "newton"
+    outs = []
+    for timed in (False, True):
+        r = R.from_problem(p, "split")
+        if timed:
+            r.profile_begin(3)
+        r.step(5)
+        if timed:
+            ks, qs, n = r.profile_end()
+            assert n == 3 and ks > 0 and qs >= 0
+        assert r.sync() == 0
+        outs.append(np.asarray(r.read("E")).copy())
+        r.close()
+    assert np.array_equal(outs[0], outs[1])
