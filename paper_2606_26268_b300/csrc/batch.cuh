@@ -4,8 +4,11 @@
 // Each tile runs exactly the single-grid tile code (step_tile), so a grid
 // advanced in a batch gets the same values as when it is stepped alone.
 #pragma once
+#include <type_traits>
+
 #include "batch_launch.h"
 #include "m1_step.cuh"
+#include "mlp_tc.cuh"
 #include "queue_cell.cuh"
 
 namespace m1 {
@@ -55,16 +58,36 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 }
 
 // Queue pass over all grids: the queues are concatenated in grid order
-// (prefix sums of their lengths in shared memory) and walked grid-stride;
-// each cell is finished by the same code as in the single-grid queue pass.
+// (prefix sums of their lengths in shared memory) and walked 128 cells per
+// CTA at a time; each cell is finished by the same code as in the
+// single-grid queue pass, with the learned guess on the tensor cores when the
+// network is set.
 template <class P, int NDIM, int NC>
-__global__ void __launch_bounds__(128)
+__device__ __forceinline__ const StepArgs<P>& grid_of(const StepArgs<P>* args,
+                                                     const unsigned int* s_off, int count,
+                                                     unsigned int q, unsigned int& local) {
+  int lo = 0, hi = count;  // grid g with s_off[g] <= q < s_off[g + 1]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (s_off[mid] <= q)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  local = q - s_off[lo];
+  return args[lo];
+}
+
+template <class P, int NDIM, int NC, bool MLP>
+__global__ void __launch_bounds__(TC_ROWS)
     batch_queue_kernel(const StepArgs<P>* __restrict__ args, int count,
                        const unsigned int* __restrict__ counts) {
-  extern __shared__ __align__(16) float s_w[];
   __shared__ unsigned int s_off[kBatchMaxGrids + 1];
   __shared__ unsigned long long s_red[ST_N];
-  if (threadIdx.x == 0) {
+  // the network's shared state only when it is used
+  __shared__ typename std::conditional<MLP, TcMlpSmem, int>::type s_tc;
+  const int tid = threadIdx.x;
+  if (tid == 0) {
     unsigned int acc = 0;
     s_off[0] = 0;
     for (int g = 0; g < count; ++g) {
@@ -74,27 +97,40 @@ __global__ void __launch_bounds__(128)
   }
   __syncthreads();
   const unsigned int total = s_off[count];
-  if (blockIdx.x * blockDim.x >= total) return;  // no queued cell for this block
-  const float* w = args[0].mlp_w;
-  if (w) load_mlp_weights(s_w, w);
-  counters_reset(s_red, threadIdx.x);
-  __syncthreads();
+  const unsigned int first = blockIdx.x * TC_ROWS;
+  if (first >= total) return;  // no queued cell for this block
+  counters_reset(s_red, tid);
+  if constexpr (MLP)
+    tc_mlp_setup(s_tc, args[0].mlp_w, tid);  // ends with a barrier
+  else
+    __syncthreads();
   Counters cnt;
-  for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < total;
-       q += gridDim.x * blockDim.x) {
-    // grid g with s_off[g] <= q < s_off[g + 1]
-    int lo = 0, hi = count;
-    while (hi - lo > 1) {
-      const int mid = (lo + hi) >> 1;
-      if (s_off[mid] <= q)
-        lo = mid;
-      else
-        hi = mid;
+  for (unsigned int base = first; base < total; base += gridDim.x * TC_ROWS) {
+    const unsigned int q = base + tid;
+    const bool valid = q < total;
+    unsigned int local = 0;
+    const StepArgs<P>& a = grid_of<P, NDIM, NC>(args, s_off, count, valid ? q : 0u, local);
+    QueuedCell<P> c;
+    float T0 = 0.f;
+    if (valid) queue_load<P, NC>(a, a.queue[local], c);
+    if constexpr (MLP) {
+      float x1 = 0.f, x2 = 0.f, lin = 0.f, Tn = 0.f;
+      if (valid)
+        coupling_features(a.cp, float(c.rho), float(c.e), float(c.kp), float(c.Us[0]), x1, x2,
+                          lin, Tn);
+      const bool gated = valid && lin > a.mlp_gate;
+      if (__syncthreads_or(gated)) {
+        const float g = tc_mlp_forward(s_tc, gated ? x1 : 0.f, gated ? x2 : 0.f, tid);
+        if (gated) T0 = guess_temperature(Tn, g);
+      }
     }
-    const StepArgs<P>& a = args[lo];
-    queue_cell<P, NDIM, NC>(a, a.queue[q - s_off[lo]], s_w, cnt);
+    if (valid) queue_solve<P, NDIM, NC>(a, c, T0, cnt);
   }
-  counters_flush<P>(args[0], cnt, s_red, threadIdx.x);
+  if constexpr (MLP) {
+    tc_mlp_teardown(s_tc, tid);
+    if (tid == 0 && s_tc.err) atomicOr(args[0].status, STATUS_TIMEOUT);
+  }
+  counters_flush<P>(args[0], cnt, s_red, tid);
 }
 
 template <class P, int NDIM, int NC, bool UNI, int TX, int TY, int MINB>
@@ -143,9 +179,12 @@ struct BatchShapes {
   }
   static cudaError_t qpass(const void* args, int count, const unsigned int* counts, bool mlp,
                            cudaStream_t s) {
-    const size_t smem = mlp ? MLP_NPARAM_PAD * sizeof(float) : 0;
-    batch_queue_kernel<P, NDIM, NC><<<148 * 4, 128, smem, s>>>(
-        static_cast<const StepArgs<P>*>(args), count, counts);
+    if (mlp)
+      batch_queue_kernel<P, NDIM, NC, true><<<148 * 4, TC_ROWS, 0, s>>>(
+          static_cast<const StepArgs<P>*>(args), count, counts);
+    else
+      batch_queue_kernel<P, NDIM, NC, false><<<148 * 4, TC_ROWS, 0, s>>>(
+          static_cast<const StepArgs<P>*>(args), count, counts);
     return cudaGetLastError();
   }
 };

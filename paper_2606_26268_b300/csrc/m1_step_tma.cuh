@@ -36,8 +36,7 @@ struct TmaTile {
   static constexpr int BOXP = (BOX + 31) / 32 * 32;  // 128-byte aligned stride
 };
 
-constexpr int kTmaRing = 5;               // plane slots
-constexpr uint32_t kWaitLimit = 1u << 21;  // polls of one mbarrier wait
+constexpr int kTmaRing = 5;  // plane slots
 
 // dynamic shared memory of the ring, with the alignment slack
 template <int NC, int TX, int TY>

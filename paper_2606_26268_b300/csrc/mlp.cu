@@ -1,16 +1,18 @@
 // mlp.cu -- kernels of the learned starting guess: the queue pass of the
-// step (network guess, then the unchanged Newton iteration, for the cells the
-// step kernel queued), and the training kernels (forward + backward over a
-// mini-batch with block-level gradient accumulation, Adam update), the
-// gradient of a given batch and plain prediction.
+// step (network guess on the tensor cores, then the unchanged Newton
+// iteration, for the cells the step kernel queued), and the training kernels
+// (forward + backward over a mini-batch with block-level gradient
+// accumulation, Adam update), the gradient of a given batch and plain FP32
+// prediction.
 #include <cuda_runtime.h>
 
 #include <cmath>
 
 #include "m1_cell.cuh"
 #include "mlp.cuh"
-#include "queue_cell.cuh"
 #include "mlp_launch.h"
+#include "mlp_tc.cuh"
+#include "queue_cell.cuh"
 
 namespace m1 {
 
@@ -18,27 +20,69 @@ namespace m1 {
 // queue pass
 // ---------------------------------------------------------------------------
 
+// Queue pass without the learned guess: Newton from T^n.
 template <class P, int NDIM, int NC>
 __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__ StepArgs<P> a) {
-  extern __shared__ __align__(16) float s_w[];
   __shared__ unsigned long long s_red[ST_N];
   const unsigned int count = min(*a.queue_count, a.queue_cap);
   if (blockIdx.x * blockDim.x >= count) return;  // no queued cell for this block
-  if (a.mlp_w) load_mlp_weights(s_w, a.mlp_w);
   counters_reset(s_red, threadIdx.x);
   __syncthreads();
   Counters cnt;
   for (unsigned int q = blockIdx.x * blockDim.x + threadIdx.x; q < count;
-       q += gridDim.x * blockDim.x)
-    queue_cell<P, NDIM, NC>(a, a.queue[q], s_w, cnt);
+       q += gridDim.x * blockDim.x) {
+    QueuedCell<P> c;
+    queue_load<P, NC>(a, a.queue[q], c);
+    queue_solve<P, NDIM, NC>(a, c, 0.f, cnt);
+  }
   counters_flush<P>(a, cnt, s_red, threadIdx.x);
+}
+
+// Queue pass with the learned guess: the CTA takes 128 queued cells at a
+// time; if any of them passes the gate, the network runs for all 128 on the
+// tensor cores (rows of cells below the gate are ignored), and each gated
+// cell starts its Newton iteration from T^n exp(output).
+template <class P, int NDIM, int NC>
+__global__ void __launch_bounds__(TC_ROWS) queue_pass_tc_kernel(const __grid_constant__ StepArgs<P> a) {
+  __shared__ TcMlpSmem s;
+  __shared__ unsigned long long s_red[ST_N];
+  const unsigned int count = min(*a.queue_count, a.queue_cap);
+  const unsigned int first = blockIdx.x * TC_ROWS;
+  if (first >= count) return;  // no queued cell for this block
+  const int tid = threadIdx.x;
+  counters_reset(s_red, tid);
+  tc_mlp_setup(s, a.mlp_w, tid);  // ends with a barrier
+  Counters cnt;
+  for (unsigned int base = first; base < count; base += gridDim.x * TC_ROWS) {
+    const unsigned int q = base + tid;
+    const bool valid = q < count;
+    QueuedCell<P> c;
+    float x1 = 0.f, x2 = 0.f, lin = 0.f, Tn = 0.f;
+    if (valid) {
+      queue_load<P, NC>(a, a.queue[q], c);
+      coupling_features(a.cp, float(c.rho), float(c.e), float(c.kp), float(c.Us[0]), x1, x2, lin,
+                        Tn);
+    }
+    const bool gated = valid && lin > a.mlp_gate;
+    float T0 = 0.f;
+    if (__syncthreads_or(gated)) {
+      const float g = tc_mlp_forward(s, gated ? x1 : 0.f, gated ? x2 : 0.f, tid);
+      if (gated) T0 = guess_temperature(Tn, g);
+    }
+    if (valid) queue_solve<P, NDIM, NC>(a, c, T0, cnt);
+  }
+  tc_mlp_teardown(s, tid);
+  if (tid == 0 && s.err) atomicOr(a.status, STATUS_TIMEOUT);
+  counters_flush<P>(a, cnt, s_red, tid);
 }
 
 template <class P, int NDIM, int NC>
 cudaError_t launch_queue_pass(const void* vargs, cudaStream_t s) {
   const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
-  const size_t smem = a.mlp_w ? MLP_NPARAM_PAD * sizeof(float) : 0;
-  queue_pass_kernel<P, NDIM, NC><<<148 * 4, 128, smem, s>>>(a);
+  if (a.mlp_w)
+    queue_pass_tc_kernel<P, NDIM, NC><<<148 * 4, TC_ROWS, 0, s>>>(a);
+  else
+    queue_pass_kernel<P, NDIM, NC><<<148 * 4, 128, 0, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -1,56 +1,65 @@
-// queue_cell.cuh -- per-cell work of the queue pass (cells the step kernel
-// left for the Newton iteration, optionally started from the learned guess)
-// and the block reduction of the step counters.
+// queue_cell.cuh -- per-cell work of the queue pass: the cells the step
+// kernel left for the Newton iteration, optionally started from the learned
+// guess.
 #pragma once
 #include "m1_cell.cuh"
 #include "mlp.cuh"
 
 namespace m1 {
 
-// One queued cell: (E*, F*) left in the output buffer by the step kernel,
-// gas state from the input buffer, opacities at (rho, T^n), the learned guess
-// T0 = T^n exp(net(x1, x2)) when the network is set and the first linearised
-// change exceeds the gate (else T^n), then the common end of the step.
-template <class P, int NDIM, int NC>
-__device__ __forceinline__ void queue_cell(const StepArgs<P>& a, long long ic,
-                                           const float* s_w, Counters& cnt) {
+// A cell the step kernel queued: (E*, F*) left in the output buffer, gas
+// state from the input buffer, opacities at (rho, T^n).
+template <class P>
+struct QueuedCell {
   using S = typename P::S;
   using T = typename P::T;
-  const StepDims& Dm = a.dim;
-  long long r = ic;
+  long long ic;
   int ci[3];
-  ci[0] = int(r % Dm.pn[0]) - Dm.g[0];
+  T Us[4], mom[3], kp, chi;
+  S rho, e;
+};
+
+template <class P, int NC>
+__device__ __forceinline__ void queue_load(const StepArgs<P>& a, long long ic, QueuedCell<P>& c) {
+  using T = typename P::T;
+  const StepDims& Dm = a.dim;
+  c.ic = ic;
+  long long r = ic;
+  c.ci[0] = int(r % Dm.pn[0]) - Dm.g[0];
   r /= Dm.pn[0];
-  ci[1] = int(r % Dm.pn[1]) - Dm.g[1];
-  ci[2] = int(r / Dm.pn[1]) - Dm.g[2];
-  T Us[4] = {T(a.out.E[ic]), 0, 0, 0};
+  c.ci[1] = int(r % Dm.pn[1]) - Dm.g[1];
+  c.ci[2] = int(r / Dm.pn[1]) - Dm.g[2];
+  c.Us[0] = T(a.out.E[ic]);
+  c.Us[1] = c.Us[2] = c.Us[3] = T(0);
+  c.mom[0] = c.mom[1] = c.mom[2] = T(0);
 #pragma unroll
-  for (int v = 0; v < NC; ++v) Us[1 + v] = T(a.out.F[v][ic]);
-  T mom[3] = {0, 0, 0};
-#pragma unroll
-  for (int v = 0; v < NC; ++v) mom[v] = T(a.in.m[v][ic]);
-  const S rho = a.rho[ic], e = a.in.e[ic];
-  T kp, chi;
-  {
-    T rr = T(rho);
-    T Temp;
-    if constexpr (sizeof(T) == 8)
-      Temp = T(e) / (rr * T(a.cp.cvfac));
-    else
-      Temp = T(e) * rcp_approx(rr * a.cp.f_cvfac);
-    opacity(a.opac, rr, Temp, kp, chi);
+  for (int v = 0; v < NC; ++v) {
+    c.Us[1 + v] = T(a.out.F[v][ic]);
+    c.mom[v] = T(a.in.m[v][ic]);
   }
-  float T0 = 0.f;  // T^n
-  if (a.mlp_w) {
-    float x1, x2, lin, Tn;
-    coupling_features(a.cp, float(rho), float(e), float(kp), float(Us[0]), x1, x2, lin, Tn);
-    if (lin > a.mlp_gate) {
-      const float guess = mlp_forward(s_w, x1, x2);
-      T0 = Tn * ex2_approx(fminf(fmaxf(guess, -20.f), 20.f) * 1.44269504088896341f);
-    }
-  }
-  const CoupleOut co = couple_cell<P>(a, rho, e, kp, Us[0], T0, false);
-  finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho, e, kp, chi, mom, co, cnt);
+  c.rho = a.rho[ic];
+  c.e = a.in.e[ic];
+  T rr = T(c.rho);
+  T Temp;
+  if constexpr (sizeof(T) == 8)
+    Temp = T(c.e) / (rr * T(a.cp.cvfac));
+  else
+    Temp = T(c.e) * rcp_approx(rr * a.cp.f_cvfac);
+  opacity(a.opac, rr, Temp, c.kp, c.chi);
+}
+
+// The Newton iteration from T0 (T^n when T0 = 0), then the common end of
+// the step.
+template <class P, int NDIM, int NC>
+__device__ __forceinline__ void queue_solve(const StepArgs<P>& a, QueuedCell<P>& c, float T0,
+                                            Counters& cnt) {
+  const CoupleOut co = couple_cell<P>(a, c.rho, c.e, c.kp, c.Us[0], T0, false);
+  finish_cell<P, NDIM, NC>(a, c.ic, c.ci, c.Us, c.rho, c.e, c.kp, c.chi, c.mom, co, cnt);
+}
+
+// Starting temperature from the network output g = log(T/T^n).
+__device__ __forceinline__ float guess_temperature(float Tn, float g) {
+  return Tn * ex2_approx(fminf(fmaxf(g, -20.f), 20.f) * 1.44269504088896341f);
 }
 
 }  // namespace m1

@@ -10,6 +10,8 @@
 
 namespace m1 {
 
+constexpr uint32_t kWaitLimit = 1u << 21;  // polls of one bounded mbarrier wait
+
 __device__ __forceinline__ uint32_t smem_addr(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
 }
