@@ -265,8 +265,14 @@ rad_status rad_mlp_train(rad_ctx *ctx, const float *dev_records, size_t n, int e
 rad_status rad_mlp_grad(rad_ctx *ctx, const float *dev_records, size_t n, float *host_grad,
                         float *host_loss);
 
-/* Network output for n device records into dev_out (n floats). */
+/* Network output for n device records into dev_out (n floats).
+ * rad_mlp_predict evaluates in FP32 on the CUDA cores; rad_mlp_predict_tc
+ * evaluates as the queue pass does, with the two hidden 64 x 64 layers on the
+ * tensor cores (bf16 operands, FP32 accumulation: about three significant
+ * digits).  A bounded wait of the tensor-core path that ran out is reported
+ * as RAD_ETIMEOUT by the next rad_sync. */
 rad_status rad_mlp_predict(rad_ctx *ctx, const float *dev_records, size_t n, float *dev_out);
+rad_status rad_mlp_predict_tc(rad_ctx *ctx, const float *dev_records, size_t n, float *dev_out);
 
 /* Logging of converged RAD_NEWTON solves for training: cells whose linear
  * index is a multiple of `stride` append one record to dev_records (up to

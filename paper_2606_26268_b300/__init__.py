@@ -69,7 +69,8 @@ EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_w
            "rad_launches_per_step", "rad_profile_begin", "rad_profile_end",
            "rad_set_launch", "rad_get_launch", "rad_tune",
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
-           "rad_mlp_grad", "rad_mlp_predict", "rad_log_bind", "rad_log_count",
+           "rad_mlp_grad", "rad_mlp_predict", "rad_mlp_predict_tc", "rad_log_bind",
+           "rad_log_count",
            "rad_mlp_grad_noalloc",
            "rad_batch_create", "rad_batch_workspace_size", "rad_batch_bind_workspace",
            "rad_batch_alloc_workspace", "rad_batch_set_stream", "rad_batch_set_graph",
@@ -122,6 +123,7 @@ def lib() -> C.CDLL:
     L.rad_mlp_train.argtypes = [vp, vp, C.c_size_t, C.c_int, C.c_int, C.c_float, C.c_uint64, fp]
     L.rad_mlp_grad.argtypes = [vp, vp, C.c_size_t, vp, fp]
     L.rad_mlp_predict.argtypes = [vp, vp, C.c_size_t, vp]
+    L.rad_mlp_predict_tc.argtypes = [vp, vp, C.c_size_t, vp]
     L.rad_log_bind.argtypes = [vp, vp, C.c_size_t, C.c_longlong]
     L.rad_log_count.argtypes = [vp, P(C.c_size_t)]
     L.rad_mlp_grad_noalloc.argtypes = [vp, vp, C.c_size_t, vp, vp, vp]
@@ -365,10 +367,13 @@ class Rad:
                                  C.c_void_p(g.ctypes.data), C.byref(loss)), "rad_mlp_grad")
         return loss.value, g
 
-    def mlp_predict(self, records):
+    def mlp_predict(self, records, tensor_cores: bool = False):
+        """Network output for a (n, 4) float32 device tensor of records; on the
+        tensor cores (as the queue pass) when tensor_cores is true."""
         out = self.torch.empty(records.shape[0], dtype=self.torch.float32, device=records.device)
-        check(lib().rad_mlp_predict(self.ctx, C.c_void_p(records.data_ptr()), records.shape[0],
-                                    C.c_void_p(out.data_ptr())), "rad_mlp_predict")
+        fn = lib().rad_mlp_predict_tc if tensor_cores else lib().rad_mlp_predict
+        check(fn(self.ctx, C.c_void_p(records.data_ptr()), records.shape[0],
+                 C.c_void_p(out.data_ptr())), "rad_mlp_predict")
         return out
 
     def log_bind(self, records, stride: int = 1):

@@ -228,6 +228,35 @@ __global__ void mlp_predict_kernel(const float* __restrict__ w, const float4* __
   }
 }
 
+// Prediction on the tensor cores (the path of the queue pass), 128 records per
+// CTA at a time; a bounded wait that ran out sets STATUS_TIMEOUT in *status.
+__global__ void __launch_bounds__(TC_ROWS) mlp_predict_tc_kernel(const float* __restrict__ w,
+                                                                 const float4* __restrict__ rec,
+                                                                 long long n, float* out,
+                                                                 int* status) {
+  __shared__ TcMlpSmem s;
+  const int tid = threadIdx.x;
+  tc_mlp_setup(s, w, tid);
+  for (long long base = (long long)blockIdx.x * TC_ROWS; base < n;
+       base += (long long)gridDim.x * TC_ROWS) {
+    const long long q = base + tid;
+    const float4 r = q < n ? rec[q] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float g = tc_mlp_forward(s, r.x, r.y, tid);
+    if (q < n) out[q] = g;
+  }
+  tc_mlp_teardown(s, tid);
+  if (tid == 0 && s.err) atomicOr(status, STATUS_TIMEOUT);
+}
+
+cudaError_t mlp_predict_tc_launch(const float* w, const float4* rec, long long n, float* out,
+                                  int* status, cudaStream_t s) {
+  long long blocks = (n + TC_ROWS - 1) / TC_ROWS;
+  if (blocks > 148 * 4) blocks = 148 * 4;
+  if (blocks < 1) blocks = 1;
+  mlp_predict_tc_kernel<<<int(blocks), TC_ROWS, 0, s>>>(w, rec, n, out, status);
+  return cudaGetLastError();
+}
+
 cudaError_t mlp_grad_launch(const float* w, const float4* rec, long long n,
                             unsigned long long a_perm, unsigned long long c_perm, long long b0,
                             int bsize, float* grad, double* loss, cudaStream_t s) {

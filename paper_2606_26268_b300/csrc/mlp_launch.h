@@ -16,5 +16,7 @@ cudaError_t mlp_adam_launch(float* w, float* grad, float* m, float* v, float lr,
                             cudaStream_t s);
 cudaError_t mlp_predict_launch(const float* w, const float4* rec, long long n, float* out,
                                cudaStream_t s);
+cudaError_t mlp_predict_tc_launch(const float* w, const float4* rec, long long n, float* out,
+                                  int* status, cudaStream_t s);
 
 }  // namespace m1

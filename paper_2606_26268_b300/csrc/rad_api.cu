@@ -954,6 +954,16 @@ extern "C" rad_status rad_mlp_predict(rad_ctx* c, const float* dev_records, size
                                      dev_out, c->stream));
 }
 
+extern "C" rad_status rad_mlp_predict_tc(rad_ctx* c, const float* dev_records, size_t n,
+                                         float* dev_out) {
+  if (!c || !dev_records || !dev_out || n == 0) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  return cuda_err(mlp_predict_tc_launch(reinterpret_cast<const float*>(c->ws + c->off_mlp),
+                                        reinterpret_cast<const float4*>(dev_records), (long long)n,
+                                        dev_out, reinterpret_cast<int*>(c->ws + c->off_status),
+                                        c->stream));
+}
+
 extern "C" rad_status rad_log_bind(rad_ctx* c, float* dev_records, size_t capacity,
                                    long long stride) {
   if (!c || (dev_records && (capacity == 0 || stride < 1)) || capacity > 0xffffffffull)

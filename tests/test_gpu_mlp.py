@@ -57,6 +57,12 @@ def test_forward_and_adam_match_the_reference(torch_mod):
     out = r.mlp_predict(drec).cpu().numpy()
     ref, _ = M.forward(theta.astype(np.float64), rec[:, :2].astype(np.float64))
     assert np.max(np.abs(out - ref)) <= 5e-3 * max(1.0, np.max(np.abs(ref)))  # tanh.approx
+    # the tensor-core path of the queue pass (bf16 hidden layers): 2048 records
+    # is 16 full products; bf16 keeps about three significant digits
+    tc = r.mlp_predict(drec, tensor_cores=True).cpu().numpy()
+    assert r.sync() == 0
+    assert np.max(np.abs(tc - ref)) <= 2e-2 * max(1.0, np.max(np.abs(ref)))
+    assert np.corrcoef(tc, ref)[0, 1] > 0.999
     # one Adam step over one full batch
     r.mlp_train(drec, epochs=1, batch=2048, lr=1e-3, seed=3)
     new = r.mlp_get()
