@@ -36,7 +36,7 @@ class _Problem(C.Structure):
                 ("nT", C.c_int), ("lrho0", C.c_double), ("lrho1", C.c_double),
                 ("lT0", C.c_double), ("lT1", C.c_double), ("ltable", _dp),
                 ("implicit_mode", C.c_int), ("newton_rtol", C.c_double),
-                ("newton_maxit", C.c_int), ("nthreads", C.c_int)]
+                ("newton_maxit", C.c_int), ("nthreads", C.c_int), ("integrator", C.c_int)]
 
 
 class _State(C.Structure):
@@ -207,6 +207,7 @@ class Oracle:
         p.newton_rtol = prob.newton_rtol
         p.newton_maxit = prob.newton_maxit
         p.nthreads = int(nthreads)
+        p.integrator = {"euler": 0, "rk2": 1}[getattr(prob, "integrator", "euler")]
         self._p = p
         self.stats = np.zeros(8, dtype=np.int64)
         self.set_state_from_problem()

@@ -61,6 +61,7 @@ enum { ORC_CART = 0, ORC_CYL = 1, ORC_SPH = 2 };
 enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1 };
 enum { ORC_OPAC_CONST = 0, ORC_OPAC_POWERLAW = 1, ORC_OPAC_TABLE = 2 };
 enum { ORC_ONCE = 0, ORC_NEWTON = 1 };
+enum { ORC_EULER = 0, ORC_RK2 = 1 };
 
 /* Problem description.  Face coordinates xf[d] hold n[d]+1 values; for an
  * inactive direction n[d] = 1 and xf[d] gives its extent. */
@@ -85,6 +86,9 @@ typedef struct {
   double newton_rtol;
   int newton_maxit;
   int nthreads;
+  /* time integration: ORC_EULER (one transport + coupling step) or ORC_RK2
+   * (two such stages, then the average of the conserved variables) */
+  int integrator;
 } orc_problem;
 
 /* State: SoA arrays of N = n0 n1 n2 cells, x fastest.  Three flux and three
@@ -642,53 +646,113 @@ int orc_max_threads(void) {
 #endif
 }
 
+/* One Euler step of every cell (transport from `s`, then the local
+ * coupling) into `w`; counters accumulated into tot. */
+static void euler_pass(const orc_problem *p, const orc_state *s, orc_state *w, double dt,
+                       int64_t tot[ORC_NSTATS]) {
+  size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+#pragma omp parallel
+  {
+    int64_t loc[ORC_NSTATS] = {0};
+#pragma omp for schedule(static)
+    for (long long cc = 0; cc < (long long)N; ++cc) {
+      int i = (int)(cc % p->n[0]);
+      int j = (int)((cc / p->n[0]) % p->n[1]);
+      int k = (int)(cc / ((long long)p->n[0] * p->n[1]));
+      double o[9];
+      cell_step(p, s, dt, i, j, k, -1.0, o, loc);
+      w->E[cc] = o[0];
+      w->F0[cc] = o[1];
+      w->F1[cc] = o[2];
+      w->F2[cc] = o[3];
+      w->e[cc] = o[4];
+      w->m0[cc] = o[5];
+      w->m1[cc] = o[6];
+      w->m2[cc] = o[7];
+    }
+#pragma omp critical
+    {
+      for (int q = 0; q < ORC_NSTATS; ++q) {
+        if (q == ORC_ST_ITMAX) {
+          if (loc[q] > tot[q]) tot[q] = loc[q];
+        } else {
+          tot[q] += loc[q];
+        }
+      }
+    }
+  }
+}
+
+static void copy_state(const orc_state *from, orc_state *to, size_t N) {
+  memcpy(to->E, from->E, N * sizeof(double));
+  memcpy(to->F0, from->F0, N * sizeof(double));
+  memcpy(to->F1, from->F1, N * sizeof(double));
+  memcpy(to->F2, from->F2, N * sizeof(double));
+  memcpy(to->e, from->e, N * sizeof(double));
+  memcpy(to->m0, from->m0, N * sizeof(double));
+  memcpy(to->m1, from->m1, N * sizeof(double));
+  memcpy(to->m2, from->m2, N * sizeof(double));
+}
+
+/* s <- (s + u) / 2 for the conserved variables E_r, F_r, m and the total gas
+ * energy E_gas = e + |m|^2 / (2 rho); e is recovered from the averaged E_gas
+ * and m (the second stage of the RK2 / IMEX1 step). */
+static void average_into(orc_state *s, const orc_state *u, size_t N) {
+#pragma omp parallel for schedule(static)
+  for (long long c = 0; c < (long long)N; ++c) {
+    double rho = s->rho[c];
+    double kn = (s->m0[c] * s->m0[c] + s->m1[c] * s->m1[c] + s->m2[c] * s->m2[c]) / (2.0 * rho);
+    double ku = (u->m0[c] * u->m0[c] + u->m1[c] * u->m1[c] + u->m2[c] * u->m2[c]) / (2.0 * rho);
+    double eg = 0.5 * ((s->e[c] + kn) + (u->e[c] + ku));
+    s->E[c] = 0.5 * (s->E[c] + u->E[c]);
+    s->F0[c] = 0.5 * (s->F0[c] + u->F0[c]);
+    s->F1[c] = 0.5 * (s->F1[c] + u->F1[c]);
+    s->F2[c] = 0.5 * (s->F2[c] + u->F2[c]);
+    s->m0[c] = 0.5 * (s->m0[c] + u->m0[c]);
+    s->m1[c] = 0.5 * (s->m1[c] + u->m1[c]);
+    s->m2[c] = 0.5 * (s->m2[c] + u->m2[c]);
+    double k = (s->m0[c] * s->m0[c] + s->m1[c] * s->m1[c] + s->m2[c] * s->m2[c]) / (2.0 * rho);
+    s->e[c] = eg - k;
+  }
+}
+
 /* Advances `s` by nsteps steps of size dt, using `w` (same shape) as the
  * second buffer; on return the result is in `s`.  stats[ORC_NSTATS] is
- * accumulated. */
+ * accumulated.
+ *   ORC_EULER: transport then coupling (Sect. 2.4).
+ *   ORC_RK2:   the same split applied in each stage of the two-stage scheme
+ *              (Sect. 2.3): U1 = step(U^n), U2 = step(U1),
+ *              U^{n+1} = (U^n + U2) / 2 for the conserved variables. */
 int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int nsteps,
              int64_t *stats) {
   set_threads(p);
   size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  orc_state u = {0};
+  double *block = NULL;
+  if (p->integrator == ORC_RK2) {
+    block = (double *)malloc(8 * N * sizeof(double));
+    if (!block) return -1;
+    u.E = block;
+    u.F0 = block + N;
+    u.F1 = block + 2 * N;
+    u.F2 = block + 3 * N;
+    u.e = block + 4 * N;
+    u.m0 = block + 5 * N;
+    u.m1 = block + 6 * N;
+    u.m2 = block + 7 * N;
+    u.rho = s->rho;
+  }
   for (int step = 0; step < nsteps; ++step) {
     int64_t tot[ORC_NSTATS] = {0};
-#pragma omp parallel
-    {
-      int64_t loc[ORC_NSTATS] = {0};
-#pragma omp for schedule(static)
-      for (long long cc = 0; cc < (long long)N; ++cc) {
-        int i = (int)(cc % p->n[0]);
-        int j = (int)((cc / p->n[0]) % p->n[1]);
-        int k = (int)(cc / ((long long)p->n[0] * p->n[1]));
-        double o[9];
-        cell_step(p, s, dt, i, j, k, -1.0, o, loc);
-        w->E[cc] = o[0];
-        w->F0[cc] = o[1];
-        w->F1[cc] = o[2];
-        w->F2[cc] = o[3];
-        w->e[cc] = o[4];
-        w->m0[cc] = o[5];
-        w->m1[cc] = o[6];
-        w->m2[cc] = o[7];
-      }
-#pragma omp critical
-      {
-        for (int q = 0; q < ORC_NSTATS; ++q) {
-          if (q == ORC_ST_ITMAX) {
-            if (loc[q] > tot[q]) tot[q] = loc[q];
-          } else {
-            tot[q] += loc[q];
-          }
-        }
-      }
+    if (p->integrator == ORC_RK2) {
+      w->rho = s->rho;
+      euler_pass(p, s, w, dt, tot);   /* stage 1: U1 in w */
+      euler_pass(p, w, &u, dt, tot);  /* stage 2: U2 in u */
+      average_into(s, &u, N);
+    } else {
+      euler_pass(p, s, w, dt, tot);
+      copy_state(w, s, N);
     }
-    memcpy(s->E, w->E, N * sizeof(double));
-    memcpy(s->F0, w->F0, N * sizeof(double));
-    memcpy(s->F1, w->F1, N * sizeof(double));
-    memcpy(s->F2, w->F2, N * sizeof(double));
-    memcpy(s->e, w->e, N * sizeof(double));
-    memcpy(s->m0, w->m0, N * sizeof(double));
-    memcpy(s->m1, w->m1, N * sizeof(double));
-    memcpy(s->m2, w->m2, N * sizeof(double));
     if (stats) {
       for (int q = 0; q < ORC_NSTATS; ++q) {
         if (q == ORC_ST_ITMAX) {
@@ -699,6 +763,7 @@ int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int ns
       }
     }
   }
+  free(block);
   return 0;
 }
 

@@ -46,6 +46,7 @@ class Problem:
     opacity: Dict = dataclasses.field(default_factory=lambda: {"kind": "const", "kappa_p": 0.0,
                                                                "kappa_r": 0.0, "sigma": 0.0})
     implicit_mode: str = "once"
+    integrator: str = "euler"     # "euler" or "rk2" (two-stage, Sect. 2.3)
     newton_rtol: float = 1e-12
     newton_maxit: int = 50
     ncomp: int = 3
