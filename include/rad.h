@@ -61,6 +61,13 @@ typedef enum { RAD_OPAC_CONST = 0, RAD_OPAC_POWERLAW = 1, RAD_OPAC_TABLE = 2 } r
 typedef enum { RAD_FP64 = 0, RAD_FP32_SPLIT = 1 } rad_precision;
 typedef enum { RAD_LINEARIZED_ONCE = 0, RAD_NEWTON = 1 } rad_implicit;
 
+/* Time integration of one step (Sect. 2.3).  RAD_EULER: transport, then
+ * the coupling (the step of Sect. 2.4).  RAD_RK2: that split applied in each
+ * stage of the two-stage scheme, U1 = S(U^n), U2 = S(U1), U^{n+1} =
+ * (U^n + U2) / 2 for the conserved variables E_r, F_r, m and E_gas = e +
+ * |m|^2 / (2 rho) (the paper's RK2, equivalent to IMEX1). */
+typedef enum { RAD_EULER = 0, RAD_RK2 = 1 } rad_integrator;
+
 /* Fields for rad_read. */
 typedef enum {
   RAD_FIELD_E = 0,    /* radiation energy density E_r, N values */
@@ -118,6 +125,7 @@ typedef struct {
                            (once rad_mlp_set/init/train has given it parameters) in cells
                            whose first linearised solve changes T by more than mlp_gate */
   double mlp_gate;      /* relative change of T above which the learned guess is used */
+  int integrator;       /* rad_integrator */
 } rad_params;
 
 /* Counters accumulated by rad_step since the last rad_reset_stats. */
@@ -136,7 +144,7 @@ typedef struct rad_ctx rad_ctx;
 
 /* Fills *p with defaults: chat = c = 1, a_rad = 1, gamma = 5/3, mu = 1,
  * cfl = 0.4, e_floor = 1e-30, RAD_FP64, RAD_LINEARIZED_ONCE, rtol = 1e-12,
- * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2.  Returns RAD_EINVAL if
+ * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2, RAD_EULER.  Returns RAD_EINVAL if
  * p is NULL. */
 rad_status rad_default_params(rad_params *p);
 
@@ -329,7 +337,8 @@ rad_status rad_mlp_grad_noalloc(const float *dev_params, const float *dev_record
  *
  * Members are contexts made by rad_create with a bound workspace and their
  * gas and radiation set; all are Cartesian with the same ndim (2 or 3),
- * precision, ncomp, implicit mode and use_mlp, and all have constant widths
+ * precision, ncomp, implicit mode and use_mlp, use RAD_EULER, and all have
+ * constant widths
  * along each direction or all do not.  The batch does not own them: they
  * must outlive it, and rad_set_gas / rad_set_rad / rad_read on a member
  * stay valid between batch steps (rad_batch_set_stream puts every member on

@@ -24,6 +24,7 @@ RAD_BC_OUTFLOW, RAD_BC_PERIODIC = range(2)
 RAD_OPAC_CONST, RAD_OPAC_POWERLAW, RAD_OPAC_TABLE = range(3)
 RAD_FP64, RAD_FP32_SPLIT = range(2)
 RAD_LINEARIZED_ONCE, RAD_NEWTON = range(2)
+RAD_EULER, RAD_RK2 = range(2)
 RAD_FIELD_E, RAD_FIELD_F, RAD_FIELD_EINT, RAD_FIELD_M, RAD_FIELD_T, RAD_FIELD_RHO = range(6)
 
 GEOMETRY = {"cartesian": RAD_CARTESIAN, "cylindrical": RAD_CYLINDRICAL,
@@ -32,6 +33,7 @@ BC = {"outflow": RAD_BC_OUTFLOW, "periodic": RAD_BC_PERIODIC}
 OPACITY = {"const": RAD_OPAC_CONST, "powerlaw": RAD_OPAC_POWERLAW, "table": RAD_OPAC_TABLE}
 PRECISION = {"fp64": RAD_FP64, "split": RAD_FP32_SPLIT}
 IMPLICIT = {"once": RAD_LINEARIZED_ONCE, "newton": RAD_NEWTON}
+INTEGRATOR = {"euler": RAD_EULER, "rk2": RAD_RK2}
 FIELDS = {"E": RAD_FIELD_E, "F": RAD_FIELD_F, "e": RAD_FIELD_EINT, "m": RAD_FIELD_M,
           "T": RAD_FIELD_T, "rho": RAD_FIELD_RHO}
 
@@ -55,7 +57,7 @@ class rad_params(C.Structure):
                 ("gamma_gas", C.c_double), ("mu", C.c_double), ("cfl", C.c_double),
                 ("e_floor", C.c_double), ("precision", C.c_int), ("implicit_mode", C.c_int),
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int),
-                ("use_mlp", C.c_int), ("mlp_gate", C.c_double)]
+                ("use_mlp", C.c_int), ("mlp_gate", C.c_double), ("integrator", C.c_int)]
 
 
 class rad_stats(C.Structure):
@@ -231,6 +233,8 @@ class Rad:
                 v = PRECISION[v] if isinstance(v, str) else v
             elif k == "implicit_mode":
                 v = IMPLICIT[v] if isinstance(v, str) else v
+            elif k == "integrator":
+                v = INTEGRATOR[v] if isinstance(v, str) else v
             setattr(p, k, v)
         self.params = p
         self.ncomp = int(p.ncomp)
@@ -515,7 +519,8 @@ def from_problem(prob, precision: str = "fp64", device=None, **overrides) -> "Ra
     params = dict(chat=prob.chat, c=prob.c, a_rad=prob.a_rad, gamma_gas=prob.gamma_gas,
                   mu=prob.mu, cfl=prob.cfl, e_floor=prob.e_floor, precision=precision,
                   implicit_mode=prob.implicit_mode, newton_rtol=prob.newton_rtol,
-                  newton_maxit=prob.newton_maxit, ncomp=prob.ncomp)
+                  newton_maxit=prob.newton_maxit, ncomp=prob.ncomp,
+                  integrator=getattr(prob, "integrator", "euler"))
     params.update(overrides)
     grid = dict(ndim=prob.ndim, n=prob.n, xfaces=prob.xfaces, bc_lo=prob.bc_lo, bc_hi=prob.bc_hi)
     r = Rad(grid, prob.geometry, prob.opacity, params, device=device)

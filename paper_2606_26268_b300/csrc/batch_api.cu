@@ -263,7 +263,8 @@ extern "C" rad_status rad_batch_create(rad_ctx* const* members, int count, rad_b
       if (members[j] == m) return RAD_EINVAL;  // a grid appears once
     if (m->geom != RAD_CARTESIAN || m->ndim != m0->ndim || m->esize != m0->esize ||
         m->nc != m0->nc || m->uniform != m0->uniform ||
-        m->par.implicit_mode != m0->par.implicit_mode || m->par.use_mlp != m0->par.use_mlp)
+        m->par.implicit_mode != m0->par.implicit_mode || m->par.use_mlp != m0->par.use_mlp ||
+        m->par.integrator != RAD_EULER)
       return RAD_EUNSUPPORTED;
   }
   BatchEntry ent = select_batch(m0->esize == 4, m0->ndim, m0->nc, m0->uniform);

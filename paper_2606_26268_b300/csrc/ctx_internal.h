@@ -13,11 +13,11 @@
 #include "rad.h"
 #include "step_launch.h"
 
-// Tensor maps of the TMA-staged step for one box shape: per state buffer,
+// Tensor maps of the TMA-staged step for one box shape: per state buffer (up to 3),
 // E, F0..F2, rho and e (the order of the kernel's TmaMaps).
 struct TmaSet {
   int bx = 0, by = 0;
-  CUtensorMap maps[2][6];
+  CUtensorMap maps[3][6];
 };
 
 struct rad_ctx {
@@ -43,7 +43,8 @@ struct rad_ctx {
   char* ws = nullptr;
   size_t ws_bytes = 0;
   bool ws_owned = false;
-  size_t off_state[2][8] = {};  // E, F0..F2, e, m0..m2 per buffer
+  size_t off_state[3][8] = {};  // E, F0..F2, e, m0..m2 per buffer (the third for RAD_RK2)
+  int nbuf = 2;                 // state buffers: 2, or 3 for RAD_RK2
   size_t off_rho = 0, off_tab = 0, off_tab_dir[3] = {}, off_op32 = 0, off_op64 = 0;
   size_t off_stats = 0, off_status = 0, off_stage = 0;
   size_t total = 0;

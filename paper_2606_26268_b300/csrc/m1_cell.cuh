@@ -208,7 +208,10 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
       long long ig = ic + (long long)(gpos - i) * stride;
       a.out.E[ig] = S(En);
 #pragma unroll
-      for (int v = 0; v < NC; ++v) a.out.F[v][ig] = S(Fn[v]);
+      for (int v = 0; v < NC; ++v) {
+        a.out.F[v][ig] = S(Fn[v]);
+        a.out.m[v][ig] = S(mn[v]);
+      }
       a.out.e[ig] = S(en);
     }
   }

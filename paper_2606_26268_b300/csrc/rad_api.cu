@@ -50,6 +50,7 @@ extern "C" rad_status rad_default_params(rad_params* p) {
   p->ncomp = 3;
   p->use_mlp = 0;
   p->mlp_gate = 1e-2;
+  p->integrator = RAD_EULER;
   return RAD_OK;
 }
 
@@ -181,6 +182,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
     return RAD_EINVAL;
   if (p.ncomp < 1 || p.ncomp > 3) return RAD_EINVAL;
   if (p.use_mlp && (p.implicit_mode != RAD_NEWTON || !(p.mlp_gate >= 0.0))) return RAD_EINVAL;
+  if (p.integrator != RAD_EULER && p.integrator != RAD_RK2) return RAD_EINVAL;
   size_t N = 1;
   for (int d = 0; d < 3; ++d) {
     int n = grid->n[d];
@@ -275,10 +277,11 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
     return o2;
   };
   const size_t arr = c->pcells * c->esize;
-  for (int b = 0; b < 2; ++b)
+  c->nbuf = p.integrator == RAD_RK2 ? 3 : 2;
+  for (int b = 0; b < 3; ++b)
     for (int k = 0; k < 8; ++k) {
       int comp = (k >= 1 && k <= 3) ? k - 1 : (k >= 5 ? k - 5 : 0);
-      bool used = (k == 0 || k == 4) || comp < c->nc;
+      bool used = b < c->nbuf && ((k == 0 || k == 4) || comp < c->nc);
       c->off_state[b][k] = used ? take(arr) : size_t(-1);
     }
   c->off_rho = take(arr);
@@ -488,7 +491,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
         src = reinterpret_cast<const S*>(slot);
       }
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < c->nbuf; ++b) {
       S* dst = static_cast<S*>(state_ptr(c, b, 5 + comp));
       if (src) {
         if ((st = pack<S>(c, dst, src, r, PK_MOM))) return st;
@@ -499,7 +502,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
   }
   const S* t = static_cast<const S*>(stage_in(c, T, c->N, 2, dev, &st));
   if (st) return st;
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < c->nbuf; ++b)
     if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 4)), t, r, PK_EINT))) return st;
   c->have_gas = true;
   return cuda_err(cudaStreamSynchronize(c->stream));
@@ -518,10 +521,10 @@ static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
   rad_status st;
   const S* e = static_cast<const S*>(stage_in(c, E, c->N, 0, dev, &st));
   if (st) return st;
-  for (int b = 0; b < 2; ++b)
+  for (int b = 0; b < c->nbuf; ++b)
     if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 0)), e, e, PK_COPY))) return st;
   for (int comp = 0; comp < c->nc; ++comp) {
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < c->nbuf; ++b) {
       S* dst = static_cast<S*>(state_ptr(c, b, 1 + comp));
       if (comp < c->par.ncomp) {
         const S* src;
@@ -567,12 +570,12 @@ static void fill_fields(rad_ctx* c, int b, Fields<S>& f) {
 }
 
 template <class P>
-static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf) {
+static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out_buf) {
   using S = typename P::S;
   using T = typename P::T;
   a.dim = c->dims;
   fill_fields<S>(c, in_buf, a.in);
-  fill_fields<S>(c, 1 - in_buf, a.out);
+  fill_fields<S>(c, out_buf, a.out);
   a.rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
   for (int d = 0; d < 3; ++d) {
     a.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
@@ -687,12 +690,12 @@ static EncodeTiledFn encode_tiled() {
 // maps cannot be encoded.  Each map views one padded field array as a 3D
 // tensor (pn0, pn1, pn2) with boxes of bx x by x 1 elements; reads outside
 // the array are zero-filled.
-static const void* tma_maps(rad_ctx* c, int variant) {
+static const void* tma_maps(rad_ctx* c, int variant, int in_buf) {
   if (variant < 0 || variant >= kMaxVariants) return nullptr;
   const int bx = c->launch.tma_box[variant][0], by = c->launch.tma_box[variant][1];
   if (bx <= 0 || c->esize != 4 || c->ndim != 3 || c->nc != 3 || !c->ws) return nullptr;
   for (const TmaSet& t : c->tma)
-    if (t.bx == bx && t.by == by) return t.maps[c->cur];
+    if (t.bx == bx && t.by == by) return t.maps[in_buf];
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return nullptr;
   TmaSet t;
@@ -703,7 +706,7 @@ static const void* tma_maps(rad_ctx* c, int variant) {
   const cuuint64_t strides[2] = {cuuint64_t(D.pn[0]) * 4, cuuint64_t(D.pn[0]) * D.pn[1] * 4};
   const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
-  for (int b = 0; b < 2; ++b) {
+  for (int b = 0; b < c->nbuf; ++b) {
     void* fields[6] = {state_ptr(c, b, 0), state_ptr(c, b, 1), state_ptr(c, b, 2),
                        state_ptr(c, b, 3), c->ws + c->off_rho, state_ptr(c, b, 4)};
     for (int f = 0; f < 6; ++f) {
@@ -715,7 +718,7 @@ static const void* tma_maps(rad_ctx* c, int variant) {
     }
   }
   c->tma.push_back(t);
-  return c->tma.back().maps[c->cur];
+  return c->tma.back().maps[in_buf];
 }
 
 size_t ctx_args_size(const rad_ctx* c) {
@@ -725,13 +728,88 @@ size_t ctx_args_size(const rad_ctx* c) {
 void ctx_fill_args(rad_ctx* c, void* out, double dt, int in_buf) {
   if (c->esize == 8) {
     StepArgs<Fp64> a{};
-    fill_args<Fp64>(c, a, dt, in_buf);
+    fill_args<Fp64>(c, a, dt, in_buf, 1 - in_buf);
     std::memcpy(out, &a, sizeof(a));
   } else {
     StepArgs<Split> a{};
-    fill_args<Split>(c, a, dt, in_buf);
+    fill_args<Split>(c, a, dt, in_buf, 1 - in_buf);
     std::memcpy(out, &a, sizeof(a));
   }
+}
+
+// The buffer a step or a trial step may write without touching the state.
+static int spare_buffer(const rad_ctx* c) { return (c->cur + 1) % c->nbuf; }
+
+// (U^n + U2) / 2 in place in u for E_r, F_r and m, and for the gas total
+// energy E_gas = e + |m|^2 / (2 rho), from which e is recovered: the last
+// stage of the RAD_RK2 step.  Runs over every padded cell (ghosts included:
+// their values are copies in both buffers, so their average is the copy of
+// the average).
+template <class S>
+__global__ void rk2_average_kernel(Fields<S> u, Fields<S> w, const S* __restrict__ rho,
+                                   long long total, int nc) {
+  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
+       p += (long long)gridDim.x * blockDim.x) {
+    const S r = rho[p];
+    S mu[3] = {0, 0, 0}, mw[3] = {0, 0, 0};
+    for (int v = 0; v < nc; ++v) {
+      mu[v] = u.m[v][p];
+      mw[v] = w.m[v][p];
+    }
+    const S ku = (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) / (S(2) * r);
+    const S kw = (mw[0] * mw[0] + mw[1] * mw[1] + mw[2] * mw[2]) / (S(2) * r);
+    const S eg = S(0.5) * ((u.e[p] + ku) + (w.e[p] + kw));
+    u.E[p] = S(0.5) * (u.E[p] + w.E[p]);
+    S m[3] = {0, 0, 0};
+    for (int v = 0; v < nc; ++v) {
+      u.F[v][p] = S(0.5) * (u.F[v][p] + w.F[v][p]);
+      m[v] = S(0.5) * (mu[v] + mw[v]);
+      u.m[v][p] = m[v];
+    }
+    const S k = (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / (S(2) * r);
+    u.e[p] = eg - k;
+  }
+}
+
+// One transport + coupling pass from buffer in_buf into out_buf: the queue
+// reset, the step kernel and (RAD_NEWTON) the queue pass, timed when
+// profiling is on.
+static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf) {
+  const bool queue = c->par.implicit_mode == RAD_NEWTON;
+  const bool staged = c->launch.tma_box[c->variant][0] > 0;
+  const void* maps = staged ? tma_maps(c, c->variant, in_buf) : nullptr;
+  if (staged && !maps) return RAD_EUNSUPPORTED;
+  if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
+                   cudaSuccess)
+    return RAD_ECUDA;
+  cudaEvent_t* ev = c->prof_n < c->prof_cap ? &c->prof_ev[3 * size_t(c->prof_n++)] : nullptr;
+  if (ev) cudaEventRecord(ev[0], c->stream);
+  cudaError_t e;
+  if (c->esize == 8) {
+    StepArgs<Fp64> a{};
+    fill_args<Fp64>(c, a, dt, in_buf, out_buf);
+    e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
+  } else {
+    StepArgs<Split> a{};
+    fill_args<Split>(c, a, dt, in_buf, out_buf);
+    e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
+    if (ev) cudaEventRecord(ev[1], c->stream);
+    if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
+  }
+  if (ev) cudaEventRecord(ev[2], c->stream);
+  return cuda_err(e);
+}
+
+template <class S>
+static rad_status enqueue_average(rad_ctx* c, int into, int from) {
+  Fields<S> u, w;
+  fill_fields<S>(c, into, u);
+  fill_fields<S>(c, from, w);
+  rk2_average_kernel<S><<<grid_for((long long)c->pcells), 256, 0, c->stream>>>(
+      u, w, reinterpret_cast<const S*>(c->ws + c->off_rho), (long long)c->pcells, c->nc);
+  return cuda_err(cudaGetLastError());
 }
 
 extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
@@ -740,33 +818,19 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
   if (!(dt > 0.0)) dt = c->dt_cfl;
   if (!std::isfinite(dt)) return RAD_EINVAL;
-  const bool queue = c->par.implicit_mode == RAD_NEWTON;
-  const bool staged = c->launch.tma_box[c->variant][0] > 0;
   for (int s = 0; s < nsteps; ++s) {
-    cudaError_t e;
-    const void* maps = staged ? tma_maps(c, c->variant) : nullptr;
-    if (staged && !maps) return RAD_EUNSUPPORTED;
-    if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
-                     cudaSuccess)
-      return RAD_ECUDA;
-    cudaEvent_t* ev = c->prof_n < c->prof_cap ? &c->prof_ev[3 * size_t(c->prof_n++)] : nullptr;
-    if (ev) cudaEventRecord(ev[0], c->stream);
-    if (c->esize == 8) {
-      StepArgs<Fp64> a{};
-      fill_args<Fp64>(c, a, dt, c->cur);
-      e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
-      if (ev) cudaEventRecord(ev[1], c->stream);
-      if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
+    rad_status st;
+    if (c->par.integrator == RAD_RK2) {
+      const int b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
+      if ((st = enqueue_pass(c, dt, c->cur, b1)) != RAD_OK) return st;
+      if ((st = enqueue_pass(c, dt, b1, b2)) != RAD_OK) return st;
+      st = c->esize == 8 ? enqueue_average<double>(c, c->cur, b2)
+                         : enqueue_average<float>(c, c->cur, b2);
+      if (st != RAD_OK) return st;
     } else {
-      StepArgs<Split> a{};
-      fill_args<Split>(c, a, dt, c->cur);
-      e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
-      if (ev) cudaEventRecord(ev[1], c->stream);
-      if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
+      if ((st = enqueue_pass(c, dt, c->cur, 1 - c->cur)) != RAD_OK) return st;
+      c->cur = 1 - c->cur;
     }
-    if (ev) cudaEventRecord(ev[2], c->stream);
-    if (e != cudaSuccess) return RAD_ECUDA;
-    c->cur = 1 - c->cur;
     ++c->steps;
   }
   return RAD_OK;
@@ -816,7 +880,8 @@ extern "C" rad_status rad_profile_end(rad_ctx* c, float* step_ms, float* queue_m
 
 extern "C" int rad_launches_per_step(const rad_ctx* c) {
   if (!c) return 0;
-  return c->par.implicit_mode == RAD_NEWTON ? 2 : 1;
+  const int pass = c->par.implicit_mode == RAD_NEWTON ? 2 : 1;
+  return c->par.integrator == RAD_RK2 ? 2 * pass + 1 : pass;
 }
 
 // ---------------------------------------------------------------------------
@@ -1035,13 +1100,13 @@ extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, f
   StepArgs<Fp64> a64{};
   StepArgs<Split> a32{};
   if (c->esize == 8)
-    fill_args<Fp64>(c, a64, c->dt_cfl, c->cur);
+    fill_args<Fp64>(c, a64, c->dt_cfl, c->cur, spare_buffer(c));
   else
-    fill_args<Split>(c, a32, c->dt_cfl, c->cur);
+    fill_args<Split>(c, a32, c->dt_cfl, c->cur, spare_buffer(c));
   const void* args = c->esize == 8 ? (const void*)&a64 : (const void*)&a32;
   for (int v = 0; v < c->launch.variants && st == RAD_OK; ++v) {
     const bool staged = c->launch.tma_box[v][0] > 0;
-    const void* maps = staged ? tma_maps(c, v) : nullptr;
+    const void* maps = staged ? tma_maps(c, v, c->cur) : nullptr;
     if (staged && !maps) continue;  // TMA maps unavailable: skip the staged shapes
     for (size_t k = 0; k < chunks.size(); ++k) {
       int ch = chunks[k];

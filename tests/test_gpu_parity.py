@@ -381,3 +381,53 @@ def test_kernel_timing_counts_the_profiled_steps():
         outs.append(np.asarray(r.read("E")).copy())
         r.close()
     assert np.array_equal(outs[0], outs[1])
+
+
+# ---------------------------------------------------------------------------
+# two-stage integration (RAD_RK2, Sect. 2.3)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("case", [0, 4, 10])
+def test_rk2_fp64_matches_oracle(case):
+    """RK2 on a 1D, a 3D Cartesian (table opacity) and a 2D spherical case."""
+    geom, n, ndim, bc, ncomp, logr, kind = CASES[case]
+    p = W.random_smooth(geom, n, ndim, seed=200 + case, bc=bc, opacity=_opacity(kind),
+                        log_r=logr, ncomp=ncomp)
+    p.integrator = "rk2"
+    check64(p, 6)
+
+
+def test_rk2_pulse_fp64_and_newton():
+    p = W.pulse_1d(512, 100)
+    p.integrator = "rk2"
+    check64(p, 100)
+    p.implicit_mode = "newton"
+    check64(p, 40)
+
+
+def test_rk2_split_and_launch_shapes():
+    """Split RK2 on a turbulent non-equilibrium box: normwise within 1e-5 of
+    the FP64 oracle; in 3D every launch shape (register, TMA overlapping, TMA
+    non-overlapping) gives the same RK2 step."""
+    import paper_2606_26268_b300 as R
+    p = W.turbulent_2d((96, 80), nsteps=20, nonequilibrium=True)
+    p.integrator = "rk2"
+    err, _, _ = split_errors(p, 20)
+    for k in ("norm_E", "norm_F", "norm_e"):
+        assert err[k] <= 1e-5, err
+    q = rounded(W.random_smooth("cartesian", (70, 41, 39), 3, seed=5, bc="periodic", ncomp=3),
+                np.float32)
+    q.integrator = "rk2"
+    q.implicit_mode = "newton"
+    ref = None
+    for v in (0, 5, 7):
+        r = R.from_problem(q, "split", newton_rtol=1e-7)
+        r.set_launch(v, 0)
+        r.step(3)
+        assert r.sync() == 0
+        E = np.asarray(r.read("E"), dtype=np.float64)
+        r.close()
+        if ref is None:
+            ref = E
+        else:
+            assert np.max(np.abs(E - ref) / ref) <= 1e-6, v
