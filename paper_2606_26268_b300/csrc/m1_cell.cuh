@@ -181,6 +181,28 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
     en = T(e_s) - a.ratio * dE - dke / (T(2) * rr);
   else
     en = T(e_s) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
+  if (a.average) {
+    // last stage of the two-stage step: average with U^n, which the output
+    // buffer holds at this cell (only this thread reads or writes it)
+    T mo[3] = {0, 0, 0}, ma[3] = {0, 0, 0};
+#pragma unroll
+    for (int v = 0; v < NC; ++v) {
+      mo[v] = T(a.out.m[v][ic]);
+      ma[v] = T(0.5) * (mo[v] + mn[v]);
+    }
+    const T h = T(0.5) * Ops<T>::rcp(T(rho_s));
+    const T ko = (mo[0] * mo[0] + mo[1] * mo[1] + mo[2] * mo[2]) * h;
+    const T kn = (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * h;
+    const T ka = (ma[0] * ma[0] + ma[1] * ma[1] + ma[2] * ma[2]) * h;
+    const T eg = T(0.5) * ((T(a.out.e[ic]) + ko) + (en + kn));
+    En = T(0.5) * (T(a.out.E[ic]) + En);
+#pragma unroll
+    for (int v = 0; v < NC; ++v) {
+      Fn[v] = T(0.5) * (T(a.out.F[v][ic]) + Fn[v]);
+      mn[v] = ma[v];
+    }
+    en = eg - ka;
+  }
   if (!(En > T(0)) || !(en == en) || !(en > T(0))) atomicOr(a.status, STATUS_NONPHYS);
   // stores: own cell and the ghost copies it feeds
   a.out.E[ic] = S(En);

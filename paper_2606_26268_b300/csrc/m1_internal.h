@@ -73,6 +73,14 @@ struct StepArgs {
   StepDims dim;
   Fields<S> in;   // U^n (read only)
   Fields<S> out;  // U^{n+1}
+  // (E*, F*) of the cells queued for the Newton iteration, read back by the
+  // queue pass (the output buffer itself, except in the last stage of the
+  // two-stage step, where the output buffer still holds U^n)
+  Fields<S> stash;
+  // last stage of the two-stage step: the result written to `out` is the
+  // average of the stage result with the U^n that `out` holds at the cell
+  // (conserved variables E_r, F_r, m and E_gas = e + |m|^2 / (2 rho))
+  int average;
   const S* rho;
   GeomDev<T> geo;
   OpacityDev opac;

@@ -540,9 +540,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
           unsigned int slot = base_slot + __popc(want & ((1u << (tid & 31)) - 1u));
           if (slot < a.queue_cap) {
             a.queue[slot] = ic;
-            a.out.E[ic] = S(Us[0]);
+            a.stash.E[ic] = S(Us[0]);
 #pragma unroll
-            for (int v = 0; v < NC; ++v) a.out.F[v][ic] = S(Us[1 + v]);
+            for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {
             queued = false;  // queue full: iterate here
             co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);

@@ -314,9 +314,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
           unsigned int qs = base_slot + __popc(want & ((1u << (tid & 31)) - 1u));
           if (qs < a.queue_cap) {
             a.queue[qs] = ic;
-            a.out.E[ic] = S(Us[0]);
+            a.stash.E[ic] = S(Us[0]);
 #pragma unroll
-            for (int v = 0; v < NC; ++v) a.out.F[v][ic] = S(Us[1 + v]);
+            for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {
             queued = false;  // queue full: iterate here
             co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);

@@ -7,7 +7,7 @@
 
 namespace m1 {
 
-// A cell the step kernel queued: (E*, F*) left in the output buffer, gas
+// A cell the step kernel queued: (E*, F*) left in the stash buffer, gas
 // state from the input buffer, opacities at (rho, T^n).
 template <class P>
 struct QueuedCell {
@@ -29,12 +29,12 @@ __device__ __forceinline__ void queue_load(const StepArgs<P>& a, long long ic, Q
   r /= Dm.pn[0];
   c.ci[1] = int(r % Dm.pn[1]) - Dm.g[1];
   c.ci[2] = int(r / Dm.pn[1]) - Dm.g[2];
-  c.Us[0] = T(a.out.E[ic]);
+  c.Us[0] = T(a.stash.E[ic]);
   c.Us[1] = c.Us[2] = c.Us[3] = T(0);
   c.mom[0] = c.mom[1] = c.mom[2] = T(0);
 #pragma unroll
   for (int v = 0; v < NC; ++v) {
-    c.Us[1 + v] = T(a.out.F[v][ic]);
+    c.Us[1 + v] = T(a.stash.F[v][ic]);
     c.mom[v] = T(a.in.m[v][ic]);
   }
   c.rho = a.rho[ic];

@@ -576,6 +576,8 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   a.dim = c->dims;
   fill_fields<S>(c, in_buf, a.in);
   fill_fields<S>(c, out_buf, a.out);
+  a.stash = a.out;
+  a.average = 0;
   a.rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
   for (int d = 0; d < 3; ++d) {
     a.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
@@ -740,41 +742,13 @@ void ctx_fill_args(rad_ctx* c, void* out, double dt, int in_buf) {
 // The buffer a step or a trial step may write without touching the state.
 static int spare_buffer(const rad_ctx* c) { return (c->cur + 1) % c->nbuf; }
 
-// (U^n + U2) / 2 in place in u for E_r, F_r and m, and for the gas total
-// energy E_gas = e + |m|^2 / (2 rho), from which e is recovered: the last
-// stage of the RAD_RK2 step.  Runs over every padded cell (ghosts included:
-// their values are copies in both buffers, so their average is the copy of
-// the average).
-template <class S>
-__global__ void rk2_average_kernel(Fields<S> u, Fields<S> w, const S* __restrict__ rho,
-                                   long long total, int nc) {
-  for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
-       p += (long long)gridDim.x * blockDim.x) {
-    const S r = rho[p];
-    S mu[3] = {0, 0, 0}, mw[3] = {0, 0, 0};
-    for (int v = 0; v < nc; ++v) {
-      mu[v] = u.m[v][p];
-      mw[v] = w.m[v][p];
-    }
-    const S ku = (mu[0] * mu[0] + mu[1] * mu[1] + mu[2] * mu[2]) / (S(2) * r);
-    const S kw = (mw[0] * mw[0] + mw[1] * mw[1] + mw[2] * mw[2]) / (S(2) * r);
-    const S eg = S(0.5) * ((u.e[p] + ku) + (w.e[p] + kw));
-    u.E[p] = S(0.5) * (u.E[p] + w.E[p]);
-    S m[3] = {0, 0, 0};
-    for (int v = 0; v < nc; ++v) {
-      u.F[v][p] = S(0.5) * (u.F[v][p] + w.F[v][p]);
-      m[v] = S(0.5) * (mu[v] + mw[v]);
-      u.m[v][p] = m[v];
-    }
-    const S k = (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / (S(2) * r);
-    u.e[p] = eg - k;
-  }
-}
-
 // One transport + coupling pass from buffer in_buf into out_buf: the queue
 // reset, the step kernel and (RAD_NEWTON) the queue pass, timed when
-// profiling is on.
-static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf) {
+// profiling is on.  stash_buf >= 0: the last stage of the two-stage step,
+// whose result is averaged in place with the U^n held by out_buf; queued
+// cells then leave (E*, F*) in stash_buf.
+static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
+                               int stash_buf = -1) {
   const bool queue = c->par.implicit_mode == RAD_NEWTON;
   const bool staged = c->launch.tma_box[c->variant][0] > 0;
   const void* maps = staged ? tma_maps(c, c->variant, in_buf) : nullptr;
@@ -788,28 +762,26 @@ static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf) {
   if (c->esize == 8) {
     StepArgs<Fp64> a{};
     fill_args<Fp64>(c, a, dt, in_buf, out_buf);
+    if (stash_buf >= 0) {
+      fill_fields<double>(c, stash_buf, a.stash);
+      a.average = 1;
+    }
     e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
     if (ev) cudaEventRecord(ev[1], c->stream);
     if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
   } else {
     StepArgs<Split> a{};
     fill_args<Split>(c, a, dt, in_buf, out_buf);
+    if (stash_buf >= 0) {
+      fill_fields<float>(c, stash_buf, a.stash);
+      a.average = 1;
+    }
     e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
     if (ev) cudaEventRecord(ev[1], c->stream);
     if (e == cudaSuccess && queue) e = c->qpass(&a, c->stream);
   }
   if (ev) cudaEventRecord(ev[2], c->stream);
   return cuda_err(e);
-}
-
-template <class S>
-static rad_status enqueue_average(rad_ctx* c, int into, int from) {
-  Fields<S> u, w;
-  fill_fields<S>(c, into, u);
-  fill_fields<S>(c, from, w);
-  rk2_average_kernel<S><<<grid_for((long long)c->pcells), 256, 0, c->stream>>>(
-      u, w, reinterpret_cast<const S*>(c->ws + c->off_rho), (long long)c->pcells, c->nc);
-  return cuda_err(cudaGetLastError());
 }
 
 extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
@@ -821,12 +793,10 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   for (int s = 0; s < nsteps; ++s) {
     rad_status st;
     if (c->par.integrator == RAD_RK2) {
+      // stage 1 into b1; stage 2 from b1 straight into the average with U^n
       const int b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;
       if ((st = enqueue_pass(c, dt, c->cur, b1)) != RAD_OK) return st;
-      if ((st = enqueue_pass(c, dt, b1, b2)) != RAD_OK) return st;
-      st = c->esize == 8 ? enqueue_average<double>(c, c->cur, b2)
-                         : enqueue_average<float>(c, c->cur, b2);
-      if (st != RAD_OK) return st;
+      if ((st = enqueue_pass(c, dt, b1, c->cur, b2)) != RAD_OK) return st;
     } else {
       if ((st = enqueue_pass(c, dt, c->cur, 1 - c->cur)) != RAD_OK) return st;
       c->cur = 1 - c->cur;
@@ -881,7 +851,7 @@ extern "C" rad_status rad_profile_end(rad_ctx* c, float* step_ms, float* queue_m
 extern "C" int rad_launches_per_step(const rad_ctx* c) {
   if (!c) return 0;
   const int pass = c->par.implicit_mode == RAD_NEWTON ? 2 : 1;
-  return c->par.integrator == RAD_RK2 ? 2 * pass + 1 : pass;
+  return c->par.integrator == RAD_RK2 ? 2 * pass : pass;
 }
 
 // ---------------------------------------------------------------------------
