@@ -65,7 +65,7 @@ typedef enum { RAD_LINEARIZED_ONCE = 0, RAD_NEWTON = 1 } rad_implicit;
  * the coupling (the step of Sect. 2.4).  RAD_RK2: that split applied in each
  * stage of the two-stage scheme, U1 = S(U^n), U2 = S(U1), U^{n+1} =
  * (U^n + U2) / 2 for the conserved variables E_r, F_r, m and E_gas = e +
- * |m|^2 / (2 rho) (the paper's RK2, equivalent to IMEX1). */
+ * |m|^2 / (2 rho) (the paper's RK2, which it identifies with IMEX1). */
 typedef enum { RAD_EULER = 0, RAD_RK2 = 1 } rad_integrator;
 
 /* Fields for rad_read. */
