@@ -61,7 +61,7 @@ typedef enum { RAD_OPAC_CONST = 0, RAD_OPAC_POWERLAW = 1, RAD_OPAC_TABLE = 2 } r
 typedef enum { RAD_FP64 = 0, RAD_FP32_SPLIT = 1 } rad_precision;
 typedef enum { RAD_LINEARIZED_ONCE = 0, RAD_NEWTON = 1 } rad_implicit;
 
-/* Time integration of one step (Sect. 2.3).  RAD_EULER: transport, then
+/* Time integration of one step (Sect. 2.4).  RAD_EULER: transport, then
  * the coupling (the step of Sect. 2.4).  RAD_RK2: that split applied in each
  * stage of the two-stage scheme, U1 = S(U^n), U2 = S(U1), U^{n+1} =
  * (U^n + U2) / 2 for the conserved variables E_r, F_r, m and E_gas = e +

@@ -36,7 +36,8 @@ class _Problem(C.Structure):
                 ("nT", C.c_int), ("lrho0", C.c_double), ("lrho1", C.c_double),
                 ("lT0", C.c_double), ("lT1", C.c_double), ("ltable", _dp),
                 ("implicit_mode", C.c_int), ("newton_rtol", C.c_double),
-                ("newton_maxit", C.c_int), ("nthreads", C.c_int), ("integrator", C.c_int)]
+                ("newton_maxit", C.c_int), ("nthreads", C.c_int), ("integrator", C.c_int),
+                ("qirr", _dp)]
 
 
 class _State(C.Structure):
@@ -65,6 +66,7 @@ def lib():
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [C.POINTER(_Problem)]
         L.orc_solve2x2.argtypes = [C.c_double] * 7 + [_dp, _dp]
+        L.orc_solve2x2_irr.argtypes = [C.c_double] * 8 + [_dp, _dp]
         L.orc_step.restype = C.c_int
         L.orc_step.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.POINTER(_State),
                                C.c_double, C.c_int, C.POINTER(C.c_int64)]
@@ -149,11 +151,17 @@ def face_flux_states(chat, d, EL, FL, ER, FR, tau=-1.0) -> np.ndarray:
     return out
 
 
-def solve2x2(Estar, Tn, Tk, Cv, g, gr, a) -> tuple:
+def solve2x2(Estar, Tn, Tk, Cv, g, gr, a, sq=None) -> tuple:
+    """The 2x2 coupling solve (Eq. implicit_matrix); sq = dt (-div F_irr) adds
+    the irradiation term of Sect. 2.9 to the gas row."""
     E = C.c_double()
     T = C.c_double()
-    lib().orc_solve2x2(float(Estar), float(Tn), float(Tk), float(Cv), float(g), float(gr),
-                       float(a), C.byref(E), C.byref(T))
+    if sq is None:
+        lib().orc_solve2x2(float(Estar), float(Tn), float(Tk), float(Cv), float(g), float(gr),
+                           float(a), C.byref(E), C.byref(T))
+    else:
+        lib().orc_solve2x2_irr(float(Estar), float(Tn), float(Tk), float(Cv), float(g),
+                               float(gr), float(a), float(sq), C.byref(E), C.byref(T))
     return E.value, T.value
 
 
@@ -208,6 +216,9 @@ class Oracle:
         p.newton_maxit = prob.newton_maxit
         p.nthreads = int(nthreads)
         p.integrator = {"euler": 0, "rk2": 1}[getattr(prob, "integrator", "euler")]
+        q = getattr(prob, "qirr", None)
+        self._qirr = None if q is None else _vec(q).copy()
+        p.qirr = _ptr(self._qirr) if self._qirr is not None else None
         self._p = p
         self.stats = np.zeros(8, dtype=np.int64)
         self.set_state_from_problem()

@@ -89,6 +89,9 @@ typedef struct {
   /* time integration: ORC_EULER (one transport + coupling step) or ORC_RK2
    * (two such stages, then the average of the conserved variables) */
   int integrator;
+  /* irradiation (Sect. 2.9): energy deposited per unit volume and time,
+   * -div F_irr, per cell (NULL: none) */
+  const double *qirr;
 } orc_problem;
 
 /* State: SoA arrays of N = n0 n1 n2 cells, x fastest.  Three flux and three
@@ -449,20 +452,27 @@ static int face_flux(const orc_problem *p, const orc_state *s, const int idx[3],
 /* ------------------------------------------------------------------------ */
 
 /* Solves the 2x2 system of Eq. (implicit_matrix) with T^4 linearised about
- * Tk.  Written out by Cramer's rule; the determinant
+ * Tk.  sq = dt * (-div F_irr) is the irradiation term of Sect. 2.9 added to
+ * the gas row of the right-hand side (S_1); it enters T's numerator with the
+ * factor (1 + g_r) of the elimination.  Written out by Cramer's rule; the determinant
  *   (1+g_r)(C_v + 4 g a Tk^3) - (4 g_r a Tk^3) g
  * simplifies exactly to (1+g_r) C_v + 4 g a Tk^3, and the T numerator to
  * (1+g_r) C_v T^n + 3 g a Tk^4 + g E*, which are used as such.  Tn enters only
  * through C_v T^n on the right-hand side. */
-void orc_solve2x2(double Estar, double Tn, double Tk, double Cv, double g, double gr, double a,
-                  double *Enew, double *Tnew) {
+void orc_solve2x2_irr(double Estar, double Tn, double Tk, double Cv, double g, double gr,
+                      double a, double sq, double *Enew, double *Tnew) {
   double aT3 = a * Tk * Tk * Tk;
   double aT4 = aT3 * Tk;
   double det = (1.0 + gr) * Cv + 4.0 * g * aT3;
-  double T = ((1.0 + gr) * Cv * Tn + 3.0 * g * aT4 + g * Estar) / det;
+  double T = ((1.0 + gr) * (Cv * Tn + sq) + 3.0 * g * aT4 + g * Estar) / det;
   double E = (Estar + gr * aT3 * (4.0 * T - 3.0 * Tk)) / (1.0 + gr);
   *Enew = E;
   *Tnew = T;
+}
+
+void orc_solve2x2(double Estar, double Tn, double Tk, double Cv, double g, double gr, double a,
+                  double *Enew, double *Tnew) {
+  orc_solve2x2_irr(Estar, Tn, Tk, Cv, g, gr, a, 0.0, Enew, Tnew);
 }
 
 /* The coupling step of one cell.  In ORC_ONCE mode this is the paper's
@@ -471,12 +481,13 @@ void orc_solve2x2(double Estar, double Tn, double Tk, double Cv, double g, doubl
  * method on C_v (T - T^n) + g/(1+g_r) (a T^4 - E*) = 0).  T0 is the starting
  * point of the iteration (T^n when no other guess is given). */
 static void couple(const orc_problem *p, double dt, double rho, double Tn, double T0, double kp,
-                   double Estar, double *Enew, double *Tnew, int64_t st[ORC_NSTATS]) {
+                   double Estar, double sq, double *Enew, double *Tnew,
+                   int64_t st[ORC_NSTATS]) {
   double Cv = rho / (p->mu * (p->gamma_gas - 1.0));
   double g = dt * p->c * kp * rho;
   double gr = dt * p->chat * kp * rho;
   if (p->implicit_mode == ORC_ONCE) {
-    orc_solve2x2(Estar, Tn, Tn, Cv, g, gr, p->a_rad, Enew, Tnew);
+    orc_solve2x2_irr(Estar, Tn, Tn, Cv, g, gr, p->a_rad, sq, Enew, Tnew);
     st[ORC_ST_ITERS] += 1;
     if (st[ORC_ST_ITMAX] < 1) st[ORC_ST_ITMAX] = 1;
     return;
@@ -486,7 +497,7 @@ static void couple(const orc_problem *p, double dt, double rho, double Tn, doubl
     double E = Estar, T = Tk;
     int it, ok = 0;
     for (it = 1; it <= p->newton_maxit; ++it) {
-      orc_solve2x2(Estar, Tn, Tk, Cv, g, gr, p->a_rad, &E, &T);
+      orc_solve2x2_irr(Estar, Tn, Tk, Cv, g, gr, p->a_rad, sq, &E, &T);
       if (!(T > 0.0)) break;
       if (fabs(T - Tk) <= p->newton_rtol * T) {
         ok = 1;
@@ -592,7 +603,8 @@ static void cell_step(const orc_problem *p, const orc_state *s, double dt, int i
   double kp, kr, sg;
   orc_opacity(p, rho, Tn, &kp, &kr, &sg);
   double En, Tnew;
-  couple(p, dt, rho, Tn, T0 > 0.0 ? T0 : Tn, kp, Es, &En, &Tnew, st);
+  const double sq = p->qirr ? dt * p->qirr[c] : 0.0;
+  couple(p, dt, rho, Tn, T0 > 0.0 ? T0 : Tn, kp, Es, sq, &En, &Tnew, st);
   if (En < p->e_floor) {
     En = p->e_floor;
     st[ORC_ST_EFLOOR] += 1;
@@ -611,7 +623,7 @@ static void cell_step(const orc_problem *p, const orc_state *s, double dt, int i
   /* Sect. 2.7: E_gas + (c/chat) E_r and m + F/chat are conserved by the
    * coupling; the internal energy absorbs the kinetic-energy change. */
   double ke0 = (m0[0] * m0[0] + m0[1] * m0[1] + m0[2] * m0[2]) / (2.0 * rho);
-  double Egas = e0 + ke0 - (p->c / p->chat) * (En - Es);
+  double Egas = e0 + ke0 - (p->c / p->chat) * (En - Es) + sq;
   double mn[3];
   for (int q = 0; q < 3; ++q) mn[q] = m0[q] - (Fn[q] - Fs[q]) / p->chat;
   double ke1 = (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) / (2.0 * rho);
@@ -721,7 +733,7 @@ static void average_into(orc_state *s, const orc_state *u, size_t N) {
  * accumulated.
  *   ORC_EULER: transport then coupling (Sect. 2.4).
  *   ORC_RK2:   the same split applied in each stage of the two-stage scheme
- *              (Sect. 2.3): U1 = step(U^n), U2 = step(U1),
+ *              (Sect. 2.4): U1 = step(U^n), U2 = step(U1),
  *              U^{n+1} = (U^n + U2) / 2 for the conserved variables. */
 int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int nsteps,
              int64_t *stats) {
@@ -792,7 +804,7 @@ int orc_couple_cells(const orc_problem *p, double dt, long long n, const double 
   for (long long q = 0; q < n; ++q) {
     int64_t st[ORC_NSTATS] = {0};
     double t0 = (T0 && T0[q] > 0.0) ? T0[q] : Tn[q];
-    couple(p, dt, rho[q], Tn[q], t0, kp[q], Estar[q], &Enew[q], &Tnew[q], st);
+    couple(p, dt, rho[q], Tn[q], t0, kp[q], Estar[q], 0.0, &Enew[q], &Tnew[q], st);
     if (iters) iters[q] = (int)st[ORC_ST_ITERS];
     if (status) status[q] = st[ORC_ST_NOCONV] ? 2 : (st[ORC_ST_FALLBACK] ? 1 : 0);
   }

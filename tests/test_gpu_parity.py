@@ -384,7 +384,7 @@ def test_kernel_timing_counts_the_profiled_steps():
 
 
 # ---------------------------------------------------------------------------
-# two-stage integration (RAD_RK2, Sect. 2.3)
+# two-stage integration (RAD_RK2, Sect. 2.4)
 # ---------------------------------------------------------------------------
 
 @pytest.mark.parametrize("case", [0, 4, 10])

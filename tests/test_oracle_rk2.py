@@ -1,4 +1,4 @@
-"""Pins of the oracle's two-stage integration (RK2 / IMEX1, Sect. 2.3): the
+"""Pins of the oracle's two-stage integration (RK2 / IMEX1, Sect. 2.4): the
 transport + coupling split applied in each stage of the two-stage scheme,
 U1 = S(U^n), U2 = S(U1), U^{n+1} = (U^n + U2) / 2 for the conserved
 variables.  CPU only."""

@@ -46,7 +46,8 @@ class Problem:
     opacity: Dict = dataclasses.field(default_factory=lambda: {"kind": "const", "kappa_p": 0.0,
                                                                "kappa_r": 0.0, "sigma": 0.0})
     implicit_mode: str = "once"
-    integrator: str = "euler"     # "euler" or "rk2" (two-stage, Sect. 2.3)
+    integrator: str = "euler"     # "euler" or "rk2" (two-stage, Sect. 2.4)
+    qirr: Optional[np.ndarray] = None  # -div F_irr per cell (Sect. 2.9), or None
     newton_rtol: float = 1e-12
     newton_maxit: int = 50
     ncomp: int = 3
