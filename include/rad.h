@@ -126,6 +126,8 @@ typedef struct {
                            whose first linearised solve changes T by more than mlp_gate */
   double mlp_gate;      /* relative change of T above which the learned guess is used */
   int integrator;       /* rad_integrator */
+  int irradiation;      /* 1: the context holds an irradiation deposit field (Sect. 2.9),
+                           set with rad_set_irradiation (zero until set) */
 } rad_params;
 
 /* Counters accumulated by rad_step since the last rad_reset_stats. */
@@ -144,7 +146,7 @@ typedef struct rad_ctx rad_ctx;
 
 /* Fills *p with defaults: chat = c = 1, a_rad = 1, gamma = 5/3, mu = 1,
  * cfl = 0.4, e_floor = 1e-30, RAD_FP64, RAD_LINEARIZED_ONCE, rtol = 1e-12,
- * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2, RAD_EULER.  Returns RAD_EINVAL if
+ * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2, RAD_EULER, irradiation = 0.  Returns RAD_EINVAL if
  * p is NULL. */
 rad_status rad_default_params(rad_params *p);
 
@@ -194,6 +196,15 @@ rad_status rad_step(rad_ctx *ctx, double dt, int nsteps);
  * status word (RAD_ENOCONV, RAD_ENONPHYS, ...) if a step recorded one.
  * Errors: RAD_EINVAL (unknown field, bytes too small). */
 rad_status rad_read(rad_ctx *ctx, int field, void *dst, size_t bytes, int on_device);
+
+/* Irradiation by an external source (Sect. 2.9): q = -div F_irr, the energy
+ * the irradiation flux deposits per unit volume and time, N values (flat, x
+ * fastest, the precision of the context), host or device.  Each step adds
+ * dt q to the gas row of the implicit solve and to the gas energy, so that
+ * E_gas + (c/chat) E_r gains dt q.  The field stays until set again.
+ * Requires params.irradiation = 1 at rad_create.  Errors: RAD_EINVAL (no
+ * irradiation field, NULL q), RAD_ENOMEM, RAD_ECUDA. */
+rad_status rad_set_irradiation(rad_ctx *ctx, const void *q, int on_device);
 
 /* Waits for the stream and returns the device status word (RAD_OK if no
  * step recorded a failure); the word is cleared by the read. */

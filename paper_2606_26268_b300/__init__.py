@@ -57,7 +57,8 @@ class rad_params(C.Structure):
                 ("gamma_gas", C.c_double), ("mu", C.c_double), ("cfl", C.c_double),
                 ("e_floor", C.c_double), ("precision", C.c_int), ("implicit_mode", C.c_int),
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int),
-                ("use_mlp", C.c_int), ("mlp_gate", C.c_double), ("integrator", C.c_int)]
+                ("use_mlp", C.c_int), ("mlp_gate", C.c_double), ("integrator", C.c_int),
+                ("irradiation", C.c_int)]
 
 
 class rad_stats(C.Structure):
@@ -66,7 +67,8 @@ class rad_stats(C.Structure):
 
 
 EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_workspace",
-           "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad", "rad_step",
+           "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad",
+           "rad_set_irradiation", "rad_step",
            "rad_read", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
            "rad_launches_per_step", "rad_profile_begin", "rad_profile_end",
            "rad_set_launch", "rad_get_launch", "rad_tune",
@@ -103,6 +105,7 @@ def lib() -> C.CDLL:
     L.rad_set_stream.argtypes = [vp, vp]
     L.rad_set_gas.argtypes = [vp, vp, vp, vp, C.c_int]
     L.rad_set_rad.argtypes = [vp, vp, vp, C.c_int]
+    L.rad_set_irradiation.argtypes = [vp, vp, C.c_int]
     L.rad_step.argtypes = [vp, C.c_double, C.c_int]
     L.rad_read.argtypes = [vp, C.c_int, vp, C.c_size_t, C.c_int]
     L.rad_sync.argtypes = [vp]
@@ -285,6 +288,11 @@ class Rad:
         f, df, kf = self._arg(F, self.N * self.ncomp)
         assert de == df, "all host or all device"
         check(lib().rad_set_rad(self.ctx, e, f, de), "rad_set_rad")
+
+    def set_irradiation(self, q):
+        """q = -div F_irr per cell (Sect. 2.9); needs irradiation=1 at creation."""
+        qq, dq, kq = self._arg(q, self.N)
+        check(lib().rad_set_irradiation(self.ctx, qq, dq), "rad_set_irradiation")
 
     def step(self, nsteps: int = 1, dt: Optional[float] = None):
         check(lib().rad_step(self.ctx, float(dt) if dt else 0.0, int(nsteps)), "rad_step")
@@ -520,11 +528,14 @@ def from_problem(prob, precision: str = "fp64", device=None, **overrides) -> "Ra
                   mu=prob.mu, cfl=prob.cfl, e_floor=prob.e_floor, precision=precision,
                   implicit_mode=prob.implicit_mode, newton_rtol=prob.newton_rtol,
                   newton_maxit=prob.newton_maxit, ncomp=prob.ncomp,
-                  integrator=getattr(prob, "integrator", "euler"))
+                  integrator=getattr(prob, "integrator", "euler"),
+                  irradiation=int(getattr(prob, "qirr", None) is not None))
     params.update(overrides)
     grid = dict(ndim=prob.ndim, n=prob.n, xfaces=prob.xfaces, bc_lo=prob.bc_lo, bc_hi=prob.bc_hi)
     r = Rad(grid, prob.geometry, prob.opacity, params, device=device)
     nc = prob.ncomp
     r.set_gas(prob.rho, np.asarray(prob.v)[:nc], prob.T)
     r.set_rad(prob.E, np.asarray(prob.F)[:nc])
+    if getattr(prob, "qirr", None) is not None:
+        r.set_irradiation(prob.qirr)
     return r

@@ -47,6 +47,7 @@ struct rad_ctx {
   int nbuf = 2;                 // state buffers: 2, or 3 for RAD_RK2
   size_t off_rho = 0, off_tab = 0, off_tab_dir[3] = {}, off_op32 = 0, off_op64 = 0;
   size_t off_stats = 0, off_status = 0, off_stage = 0;
+  size_t off_qirr = size_t(-1);  // irradiation deposit (padded), if params.irradiation
   size_t total = 0;
   cudaStream_t stream = nullptr;
   int cur = 0;

@@ -87,17 +87,23 @@ __device__ __forceinline__ void coupling_features(const CoupleParams& p, float r
   lin = alpha * fabsf(eps - 1.f) * rcp_approx(1.f + 4.f * alpha);
 }
 
-// The implicit coupling of one cell (Sect. 2.8): the single linearised solve
-// when `once`, else the mode of the parameters (Newton from T0 > 0 or T^n).
+// The implicit coupling of the cell at padded index ic (Sect. 2.8): the
+// single linearised solve when `once`, else the mode of the parameters
+// (Newton from T0 > 0 or T^n), with the irradiation deposit of Sect. 2.9
+// when the context has one.
 template <class P>
-__device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, typename P::S rho_s,
-                                                 typename P::S e_s, typename P::T kp,
-                                                 typename P::T Es, float T0, bool once) {
+__device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, long long ic,
+                                                 typename P::S rho_s, typename P::S e_s,
+                                                 typename P::T kp, typename P::T Es, float T0,
+                                                 bool once) {
+  using T = typename P::T;
+  const T sq = a.qirr ? a.dt * T(__ldg(a.qirr + ic)) : T(0);
   if constexpr (P::kSplit)
-    return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once);
+    return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once,
+                        float(sq));
   else
     return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
-                       once);
+                       once, double(sq));
 }
 
 // Bookkeeping and stores of the cell at padded index ic with unpadded
@@ -181,6 +187,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
     en = T(e_s) - a.ratio * dE - dke / (T(2) * rr);
   else
     en = T(e_s) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
+  if (a.qirr) en += T(co.sq);  // Sect. 2.9: E_gas gains dt (-div F_irr)
   if (a.average) {
     // last stage of the two-stage step: average with U^n, which the output
     // buffer holds at this cell (only this thread reads or writes it)

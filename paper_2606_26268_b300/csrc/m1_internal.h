@@ -77,6 +77,9 @@ struct StepArgs {
   // queue pass (the output buffer itself, except in the last stage of the
   // two-stage step, where the output buffer still holds U^n)
   Fields<S> stash;
+  // irradiation (Sect. 2.9): energy deposited per unit volume and time,
+  // -div F_irr, in the padded layout; nullptr: none
+  const S* qirr;
   // last stage of the two-stage step: the result written to `out` is the
   // average of the stage result with the U^n that `out` holds at the cell
   // (conserved variables E_r, F_r, m and E_gas = e + |m|^2 / (2 rho))

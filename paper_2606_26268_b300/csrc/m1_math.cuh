@@ -342,6 +342,7 @@ struct CoupleParams {
 struct CoupleOut {
   double dE;     // E^{n+1} - E*
   double Tnew;   // T^{n+1} of the solve
+  double sq;     // irradiation energy deposited in the step, dt (-div F_irr)
   int iters;
   int fallback;  // restarted from T^n
   int noconv;
@@ -350,15 +351,18 @@ struct CoupleOut {
 
 // Increments of the 2x2 system of Eq. (implicit_matrix) with T^4 linearised
 // about Tk.  With D = E* - a Tk^4, det = (1 + g_r) C_v + 4 g a Tk^3 and
-// G = (1 + g_r) C_v (T^n - Tk), Cramer's rule gives exactly
+// G = (1 + g_r) (C_v (T^n - Tk) + sq), Cramer's rule gives exactly
 //   T^{n+1} - Tk = (G + g D) / det,
-//   E^{n+1} - E* = g_r C_v (4 a Tk^3 (T^n - Tk) - D) / det,
-// which for Tk = T^n is the paper's single solve.  Newton mode repeats it
-// with Tk <- T^{n+1} until |T^{n+1} - Tk| <= rtol T^{n+1}.
+//   E^{n+1} - E* = g_r (4 a Tk^3 (C_v (T^n - Tk) + sq) - C_v D) / det,
+// which for Tk = T^n is the paper's single solve.  sq = dt (-div F_irr) is
+// the irradiation term that Sect. 2.9 adds to the gas row (0 without
+// irradiation).  Newton mode repeats the solve with Tk <- T^{n+1} until
+// |T^{n+1} - Tk| <= rtol T^{n+1}.
 __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double rho, double e,
                                                  double kp, double Es, double T0,
-                                                 bool once = false) {
+                                                 bool once = false, double sq = 0.0) {
   CoupleOut o{};
+  o.sq = sq;
   double Cv = rho * p.cvfac;
   double Tn = e / Cv;
   double gr = p.dt * p.chat * kp * rho;
@@ -370,10 +374,16 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
     double D = Es - aT3 * Tn;
     double det = c1 + 4.0 * g * aT3;
     double q = D / det;
-    o.Tnew = Tn + g * q;
+    double dT = g * q;
     o.dE = -gr * Cv * q;
+    if (sq != 0.0) {
+      const double h = sq / det;
+      dT += (1.0 + gr) * h;
+      o.dE += gr * 4.0 * aT3 * h;
+    }
+    o.Tnew = Tn + dT;
     o.iters = 1;
-    o.conv1 = fabs(g * q) <= p.rtol * o.Tnew;
+    o.conv1 = fabs(dT) <= p.rtol * o.Tnew;
     return o;
   }
   for (int attempt = 0; attempt < 2; ++attempt) {
@@ -385,7 +395,7 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
       aT3 = p.a_rad * Tk * Tk * Tk;
       D = Es - aT3 * Tk;
       det = c1 + 4.0 * g * aT3;
-      double dT = (c1 * (Tn - Tk) + g * D) / det;
+      double dT = (c1 * (Tn - Tk) + (1.0 + gr) * sq + g * D) / det;
       Tnew = Tk + dT;
       if (!(Tnew > 0.0)) break;
       if (fabs(dT) <= p.rtol * Tnew) {
@@ -398,7 +408,7 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
     o.iters += used;
     if (ok || attempt == 1) {
       o.Tnew = Tnew;
-      o.dE = gr * Cv * (4.0 * aT3 * (Tn - Tk) - D) / det;
+      o.dE = gr * (4.0 * aT3 * (Cv * (Tn - Tk) + sq) - Cv * D) / det;
       o.noconv = ok ? 0 : 1;
       return o;
     }
@@ -412,8 +422,9 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
 // terms are all positive, in float.
 __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
                                                   float kp, float Es, float T0f,
-                                                  bool once = false) {
+                                                  bool once = false, float sq = 0.f) {
   CoupleOut o{};
+  o.sq = double(sq);
   float Cv = rho * p.f_cvfac;
   float invCv = rcp_approx(Cv);
   float Tf = e * invCv;
@@ -428,11 +439,19 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
     float D = float(fma(-aT2, T2, double(Es)));
     float aT3 = p.f_a * Tf * Tf * Tf;
     float det = c1 + 4.f * g * aT3;
-    float q = D * rcp_approx(det);
-    o.Tnew = double(Tf + g * q);
-    o.dE = double(-gr * Cv * q);
+    const float rdet = rcp_approx(det);
+    float q = D * rdet;
+    float dT = g * q;
+    float dE = -gr * Cv * q;
+    if (sq != 0.f) {
+      const float h = sq * rdet;
+      dT += (1.f + gr) * h;
+      dE += gr * 4.f * aT3 * h;
+    }
+    o.Tnew = double(Tf + dT);
+    o.dE = double(dE);
     o.iters = 1;
-    o.conv1 = fabsf(g * q) <= p.f_rtol * float(o.Tnew);
+    o.conv1 = fabsf(dT) <= p.f_rtol * float(o.Tnew);
     return o;
   }
   double Tn = double(Tf);
@@ -448,7 +467,7 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
       aT3 = p.a_rad * Tk * Tk * Tk;
       D = double(Es) - aT3 * Tk;
       det = c1 + 4.f * g * float(aT3);
-      double num = c1d * (Tn - Tk) + double(g) * D;
+      double num = c1d * (Tn - Tk) + double(1.f + gr) * double(sq) + double(g) * D;
       double dT = num * double(rcp_approx(det));
       Tnew = Tk + dT;
       if (!(Tnew > 0.0)) break;
@@ -462,8 +481,8 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
     o.iters += used;
     if (ok || attempt == 1) {
       o.Tnew = Tnew;
-      float inner = float(4.0 * aT3 * (Tn - Tk) - D);
-      o.dE = double(gr * Cv * inner * rcp_approx(det));
+      float inner = float(4.0 * aT3 * (double(Cv) * (Tn - Tk) + double(sq)) - double(Cv) * D);
+      o.dE = double(gr * inner * rcp_approx(det));
       o.noconv = ok ? 0 : 1;
       return o;
     }

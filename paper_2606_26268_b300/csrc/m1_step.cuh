@@ -528,7 +528,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       bool queued = false;
       CoupleOut co;
       if (a.queue_cap) {
-        co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, true);
+        co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;
         const unsigned int mask = __activemask();
         const unsigned int want = __ballot_sync(mask, queued);
@@ -545,11 +545,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
             for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {
             queued = false;  // queue full: iterate here
-            co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);
+            co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
           }
         }
       } else {
-        co = couple_cell<P>(a, rho_m, e_m, kp_m, Us[0], 0.f, false);
+        co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
       if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
     }

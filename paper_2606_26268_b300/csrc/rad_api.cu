@@ -51,6 +51,7 @@ extern "C" rad_status rad_default_params(rad_params* p) {
   p->use_mlp = 0;
   p->mlp_gate = 1e-2;
   p->integrator = RAD_EULER;
+  p->irradiation = 0;
   return RAD_OK;
 }
 
@@ -183,6 +184,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   if (p.ncomp < 1 || p.ncomp > 3) return RAD_EINVAL;
   if (p.use_mlp && (p.implicit_mode != RAD_NEWTON || !(p.mlp_gate >= 0.0))) return RAD_EINVAL;
   if (p.integrator != RAD_EULER && p.integrator != RAD_RK2) return RAD_EINVAL;
+  if (p.irradiation != 0 && p.irradiation != 1) return RAD_EINVAL;
   size_t N = 1;
   for (int d = 0; d < 3; ++d) {
     int n = grid->n[d];
@@ -285,6 +287,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
       c->off_state[b][k] = used ? take(arr) : size_t(-1);
     }
   c->off_rho = take(arr);
+  if (p.irradiation) c->off_qirr = take(arr);
   const size_t tsz = c->esize;
   for (int d = 0; d < 3; ++d) c->off_tab_dir[d] = take(size_t(TAB_N) * c->len[d] * tsz);
   c->off_op32 = take(c->table32.size() * 4);
@@ -332,6 +335,10 @@ static rad_status upload_static(rad_ctx* c) {
   if (e != cudaSuccess) return RAD_ECUDA;
   e = cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(int) * 4, c->stream);
   if (e != cudaSuccess) return RAD_ECUDA;
+  if (c->off_qirr != size_t(-1)) {
+    e = cudaMemsetAsync(c->ws + c->off_qirr, 0, c->pcells * c->esize, c->stream);
+    if (e != cudaSuccess) return RAD_ECUDA;
+  }
   const size_t np = size_t(mlp_nparam()) * sizeof(float);
   e = cudaMemsetAsync(c->ws + c->off_mlp, 0, c->off_qcount - c->off_mlp, c->stream);
   if (e != cudaSuccess) return RAD_ECUDA;
@@ -548,6 +555,21 @@ static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
   return cuda_err(cudaStreamSynchronize(c->stream));
 }
 
+template <class S>
+static rad_status set_irr_t(rad_ctx* c, const void* q, int dev) {
+  rad_status st;
+  const S* src = static_cast<const S*>(stage_in(c, q, c->N, 0, dev, &st));
+  if (st) return st;
+  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_qirr), src, src, PK_COPY))) return st;
+  return cuda_err(cudaStreamSynchronize(c->stream));
+}
+
+extern "C" rad_status rad_set_irradiation(rad_ctx* c, const void* q, int on_device) {
+  if (!c || !q || c->off_qirr == size_t(-1)) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  return c->esize == 8 ? set_irr_t<double>(c, q, on_device) : set_irr_t<float>(c, q, on_device);
+}
+
 extern "C" rad_status rad_set_rad(rad_ctx* c, const void* E, const void* F, int on_device) {
   if (!c || !E || !F) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
@@ -578,6 +600,7 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   fill_fields<S>(c, out_buf, a.out);
   a.stash = a.out;
   a.average = 0;
+  a.qirr = c->off_qirr != size_t(-1) ? reinterpret_cast<const S*>(c->ws + c->off_qirr) : nullptr;
   a.rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
   for (int d = 0; d < 3; ++d) {
     a.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);

@@ -431,3 +431,32 @@ def test_rk2_split_and_launch_shapes():
             ref = E
         else:
             assert np.max(np.abs(E - ref) / ref) <= 1e-6, v
+
+
+# ---------------------------------------------------------------------------
+# irradiation deposit (Sect. 2.9)
+# ---------------------------------------------------------------------------
+
+def _irradiated(case, seed, integrator="euler", mode="once"):
+    geom, n, ndim, bc, ncomp, logr, kind = CASES[case]
+    p = W.random_smooth(geom, n, ndim, seed=seed, bc=bc, opacity=_opacity(kind), log_r=logr,
+                        ncomp=ncomp)
+    rng = np.random.default_rng(seed)
+    # heating and cooling of up to ~10 % of the gas energy per unit time
+    p.qirr = rng.uniform(-0.1, 0.3, p.N) * p.rho * p.T
+    p.integrator = integrator
+    p.implicit_mode = mode
+    return p
+
+
+@pytest.mark.parametrize("case,integrator,mode", [(4, "euler", "once"), (11, "euler", "newton"),
+                                                  (2, "rk2", "once")])
+def test_irradiation_fp64_matches_oracle(case, integrator, mode):
+    check64(_irradiated(case, 300 + case, integrator, mode), 5)
+
+
+def test_irradiation_split_normwise():
+    p = _irradiated(5, 333)
+    err, _, _ = split_errors(p, 10)
+    for k in ("norm_E", "norm_F", "norm_e"):
+        assert err[k] <= 1e-5, err
