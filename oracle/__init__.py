@@ -16,9 +16,12 @@ import numpy as np
 from . import build as _build
 
 _GEOM = {"cartesian": 0, "cylindrical": 1, "spherical": 2}
-_BC = {"outflow": 0, "periodic": 1}
+_BC = {"outflow": 0, "periodic": 1, "reflective": 2, "fixed": 3, "lte": 4}
 _OPAC = {"const": 0, "powerlaw": 1, "table": 2}
-_MODE = {"once": 0, "newton": 1}
+_MODE = {"once": 0, "newton": 1, "absorb": 2}
+_RECON = {"plm": 0, "limo3": 1}
+_FIX = {"fpreserve": 0, "pluto": 1, "clip": 2}
+_RIEMANN = {"hll": 0, "lf": 1}
 STAT_NAMES = ["fix", "efloor", "fclip", "iters", "itmax", "fallback", "noconv", "spare"]
 
 _dp = C.POINTER(C.c_double)
@@ -37,7 +40,8 @@ class _Problem(C.Structure):
                 ("lT0", C.c_double), ("lT1", C.c_double), ("ltable", _dp),
                 ("implicit_mode", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("nthreads", C.c_int), ("integrator", C.c_int),
-                ("qirr", _dp)]
+                ("qirr", _dp), ("recon", C.c_int), ("face_fix", C.c_int), ("riemann", C.c_int),
+                ("bc_val", C.c_double * 30)]
 
 
 class _State(C.Structure):
@@ -62,6 +66,11 @@ def lib():
         L.orc_fix_face.restype = C.c_int
         L.orc_fix_face.argtypes = [C.c_double, _dp, C.c_double, _dp]
         L.orc_hll.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp]
+        L.orc_lf.argtypes = [C.c_double, C.c_double, _dp, _dp, _dp, _dp, _dp]
+        L.orc_limo3.restype = C.c_double
+        L.orc_limo3.argtypes = [C.c_double, C.c_double]
+        L.orc_fix_face_mode.restype = C.c_int
+        L.orc_fix_face_mode.argtypes = [C.c_int, _dp, _dp, C.c_double, _dp]
         L.orc_opacity.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp]
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [C.POINTER(_Problem)]
@@ -144,6 +153,26 @@ def hll(sl, sr, uL, uR, fL, fR) -> np.ndarray:
     return out
 
 
+def lf(sl, sr, uL, uR, fL, fR) -> np.ndarray:
+    out = np.zeros(4)
+    lib().orc_lf(float(sl), float(sr), _ptr(_vec(uL)), _ptr(_vec(uR)), _ptr(_vec(fL)),
+                 _ptr(_vec(fR)), _ptr(out))
+    return out
+
+
+def limo3(dn: float, dt: float) -> float:
+    """LimO3 increment phi(dn/dt) dt / 2 towards the face on the dt side."""
+    return lib().orc_limo3(float(dn), float(dt))
+
+
+def fix_face_mode(mode: str, Ef: float, Ff, Ec: float, Fc) -> tuple:
+    """The f <= 1 treatment `mode` of one face state: (Ef, Ff, changed)."""
+    E = np.array([float(Ef)])
+    Ff = _vec(Ff).copy()
+    r = lib().orc_fix_face_mode(_FIX[mode], _ptr(E), _ptr(Ff), float(Ec), _ptr(_vec(Fc)))
+    return float(E[0]), Ff, bool(r)
+
+
 def face_flux_states(chat, d, EL, FL, ER, FR, tau=-1.0) -> np.ndarray:
     out = np.zeros(4)
     lib().orc_face_flux_states(float(chat), int(d), float(EL), _ptr(_vec(FL)), float(ER),
@@ -219,6 +248,12 @@ class Oracle:
         q = getattr(prob, "qirr", None)
         self._qirr = None if q is None else _vec(q).copy()
         p.qirr = _ptr(self._qirr) if self._qirr is not None else None
+        p.recon = _RECON[getattr(prob, "recon", "plm")]
+        p.face_fix = _FIX[getattr(prob, "face_fix", "fpreserve")]
+        p.riemann = _RIEMANN[getattr(prob, "riemann", "hll")]
+        for (d, side), v in getattr(prob, "bc_value", {}).items():
+            for q in range(5):
+                p.bc_val[10 * d + 5 * side + q] = float(v[q])
         self._p = p
         self.stats = np.zeros(8, dtype=np.int64)
         self.set_state_from_problem()

@@ -10,18 +10,21 @@
  * What it computes (one explicit Euler step, Sect. 2.4 "Integration scheme",
  * items 1-10, followed literally and cell by cell):
  *   1. boundary values by index mapping (outflow = copy of the nearest
- *      interior cell, periodic = wrap);
- *   3. PLM reconstruction with the van Leer limiter (Sect. 2.5);
- *   4. the f-preserving face fix, Eq. (f_reconstruct) (Sect. 2.5);
+ *      interior cell, periodic = wrap, reflective = mirror with the normal
+ *      flux negated) or from a boundary state (fixed injection, LTE);
+ *   3. PLM reconstruction with the van Leer limiter, or LimO3 (Sect. 2.5);
+ *   4. the f-preserving face fix, Eq. (f_reconstruct), or the flat
+ *      ("PLUTO") or clipping treatment of f_face > 1 (Sect. 2.5);
  *   5. signal speeds lambda_{1,3}, Sect. 2.6, with the optically thick
  *      correction of the same section;
- *   6. the HLL flux (Sect. 2.5 names HLL; the standard two-wave form);
+ *   6. the HLL flux, or the Lax-Friedrichs-Rusanov flux (Sect. 2.5);
  *   7. finite-volume flux divergence with Cartesian, cylindrical or spherical
  *      metric (orthonormal components);
  *   8. the implicit matter-radiation coupling of Sect. 2.8, Eqs.
  *      (source_discrete2) and (implicit_matrix), optionally iterated to
- *      convergence (Newton mode), and the gas energy / momentum from the
- *      rescaled conservation laws of Sect. 2.7;
+ *      convergence (Newton mode) or reduced to absorption only (the shadow
+ *      test of Sect. 3), and the gas energy / momentum from the rescaled
+ *      conservation laws of Sect. 2.7;
  *  10. the CFL time step.
  * Primitive and conservative radiation variables are identical (Sect. 2.4),
  * so items 2 and 9 are the identity.
@@ -44,6 +47,15 @@
  *   - opacities frozen at (rho, T^n) for the whole step.
  *   - E floor after transport and after the coupling; |F| <= E clip after
  *     the coupling; gas bookkeeping uses the final E and F.
+ *   - LimO3: the limiter of orc_limo3 on index-space differences, without
+ *     the smooth-extremum switch of its authors.
+ *   - PLUTO treatment and clipping act on one face state at a time;
+ *     LF-Rusanov takes S = max(|S_L|, |S_R|) after the thick-limit bound.
+ *   - absorption only: E^{n+1} = E* / (1 + g_r), gas energy by
+ *     conservation, F as in every mode.
+ *   - fixed and LTE ghosts carry the edge cell's density and the side's
+ *     boundary temperature T_b (e = C_v T_b); fixed ghosts E and F of the
+ *     boundary state, LTE ghosts E = a T_b^4 and the edge cell's F.
  * Parity status: every step above is pinned by the oracle tests (closed
  * forms, invariants, brute force and printed values of the paper); the whole
  * step has no printed reference values, so end-to-end parity of full configs
@@ -58,9 +70,12 @@
 #endif
 
 enum { ORC_CART = 0, ORC_CYL = 1, ORC_SPH = 2 };
-enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1 };
+enum { ORC_BC_OUTFLOW = 0, ORC_BC_PERIODIC = 1, ORC_BC_REFLECT = 2, ORC_BC_FIXED = 3, ORC_BC_LTE = 4 };
 enum { ORC_OPAC_CONST = 0, ORC_OPAC_POWERLAW = 1, ORC_OPAC_TABLE = 2 };
-enum { ORC_ONCE = 0, ORC_NEWTON = 1 };
+enum { ORC_ONCE = 0, ORC_NEWTON = 1, ORC_ABSORB = 2 };
+enum { ORC_PLM = 0, ORC_LIMO3 = 1 };
+enum { ORC_FIX_FPRESERVE = 0, ORC_FIX_PLUTO = 1, ORC_FIX_CLIP = 2 };
+enum { ORC_HLL = 0, ORC_LF = 1 };
 enum { ORC_EULER = 0, ORC_RK2 = 1 };
 
 /* Problem description.  Face coordinates xf[d] hold n[d]+1 values; for an
@@ -92,6 +107,14 @@ typedef struct {
   /* irradiation (Sect. 2.9): energy deposited per unit volume and time,
    * -div F_irr, per cell (NULL: none) */
   const double *qirr;
+  /* options of Sect. 2.5: reconstruction (ORC_PLM, ORC_LIMO3), the f <= 1
+   * treatment of face states (ORC_FIX_*) and the Riemann solver (ORC_HLL,
+   * ORC_LF) */
+  int recon, face_fix, riemann;
+  /* boundary states of the ORC_BC_FIXED and ORC_BC_LTE sides:
+   * bc_val[d][side] = (E, F0, F1, F2, T), side 0 = lower, 1 = upper; FIXED
+   * uses E, F and T, LTE only T (E = a T^4, F copied from the edge cell) */
+  double bc_val[3][2][5];
 } orc_problem;
 
 /* State: SoA arrays of N = n0 n1 n2 cells, x fastest.  Three flux and three
@@ -179,6 +202,30 @@ double orc_vanleer(double dl, double dr) {
   return 0.0;
 }
 
+/* LimO3, the compact third-order limited reconstruction that Sect. 2.5
+ * offers beside PLM (Cada & Torrilhon 2009).  The face value on the side of
+ * the difference dt (the other one-sided difference being dn) is
+ *   u + phi(theta) dt / 2,   theta = dn / dt,
+ *   phi = max(0, min(phi3, max(-theta/2, min(2 theta, phi3, 3/2)))),
+ * phi3 = (2 + theta) / 3 being the unlimited third-order value (exact for
+ * parabolas on a uniform grid).  The caps 2 theta and 3/2 for theta > 0 and
+ * -theta/2 for theta < 0 keep the face between the neighbouring values
+ * (total-variation bounds of the form 0 <= phi <= min(2 theta, M),
+ * phi <= (2 - M) |theta| with M = 3/2).  Returns phi(theta) dt / 2 (zero
+ * when dt = 0). */
+double orc_limo3(double dn, double dt) {
+  if (dt == 0.0) return 0.0;
+  double th = dn / dt;
+  double p3 = (2.0 + th) / 3.0;
+  double a = 2.0 * th;
+  if (p3 < a) a = p3;
+  if (1.5 < a) a = 1.5;
+  if (-0.5 * th > a) a = -0.5 * th;
+  if (p3 < a) a = p3;
+  if (a < 0.0) a = 0.0;
+  return 0.5 * a * dt;
+}
+
 /* f-preserving face fix, Eq. (f_reconstruct).  (Ef, Ff) is the reconstructed
  * face state, (Ec, Fc) the centre of the cell it was reconstructed from.
  * Returns 1 when F was recomputed. */
@@ -190,6 +237,33 @@ int orc_fix_face(double Ef, double Ff[3], double Ec, const double Fc[3]) {
   Ff[0] = Fc[0] * scale;
   Ff[1] = Fc[1] * scale;
   Ff[2] = Fc[2] * scale;
+  return 1;
+}
+
+/* The f <= 1 treatment of a face state chosen by `mode` (Sect. 2.5):
+ *   ORC_FIX_FPRESERVE  Eq. (f_reconstruct), orc_fix_face;
+ *   ORC_FIX_PLUTO      the flat state (E_c, F_c) of the cell wherever the
+ *                      reconstruction has |F_f| > E_f ("PLUTO
+ *                      reconstruction"; one face state at a time);
+ *   ORC_FIX_CLIP       F_f rescaled to |F_f| = E_f wherever |F_f| > E_f
+ *                      (the plain limiter that Sect. 3's beam test shows to
+ *                      fail).
+ * Returns 1 when the state was changed. */
+int orc_fix_face_mode(int mode, double *Ef, double Ff[3], double Ec, const double Fc[3]) {
+  if (mode == ORC_FIX_FPRESERVE) return orc_fix_face(*Ef, Ff, Ec, Fc);
+  double nf = norm3(Ff);
+  if (nf <= *Ef) return 0;
+  if (mode == ORC_FIX_PLUTO) {
+    *Ef = Ec;
+    Ff[0] = Fc[0];
+    Ff[1] = Fc[1];
+    Ff[2] = Fc[2];
+  } else {
+    double r = *Ef / nf;
+    Ff[0] *= r;
+    Ff[1] *= r;
+    Ff[2] *= r;
+  }
   return 1;
 }
 
@@ -205,6 +279,15 @@ void orc_hll(double sl, double sr, const double uL[4], const double uR[4], const
     for (int q = 0; q < 4; ++q)
       out[q] = (sr * fL[q] - sl * fR[q] + sl * sr * (uR[q] - uL[q])) / (sr - sl);
   }
+}
+
+/* Lax-Friedrichs-Rusanov flux (Sect. 2.5 lists it beside HLL) with the
+ * local speed S = max(|S_L|, |S_R|) of the same (thick-limited) signal
+ * speeds: (F_L + F_R) / 2 - S (U_R - U_L) / 2. */
+void orc_lf(double sl, double sr, const double uL[4], const double uR[4], const double fL[4],
+            const double fR[4], double out[4]) {
+  double S = fabs(sl) > fabs(sr) ? fabs(sl) : fabs(sr);
+  for (int q = 0; q < 4; ++q) out[q] = 0.5 * (fL[q] + fR[q]) - 0.5 * S * (uR[q] - uL[q]);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -256,15 +339,25 @@ void orc_opacity(const orc_problem *p, double rho, double T, double *kp, double 
 /* Grid geometry                                                             */
 /* ------------------------------------------------------------------------ */
 
+/* The interior cell that ghost index i along d copies: the wrapped cell
+ * (periodic), the mirror image (reflective) or the edge cell (outflow; also
+ * the cell whose density and geometry the ghosts of the fixed and LTE sides
+ * take).  Interior indices map to themselves. */
 static int map_index(const orc_problem *p, int d, int i) {
   int n = p->n[d];
-  if (i < 0) return (p->bc_lo[d] == ORC_BC_PERIODIC) ? ((i % n) + n) % n : 0;
-  if (i >= n) return (p->bc_hi[d] == ORC_BC_PERIODIC) ? i % n : n - 1;
-  return i;
+  if (i >= 0 && i < n) return i;
+  int bc = (i < 0) ? p->bc_lo[d] : p->bc_hi[d];
+  if (bc == ORC_BC_PERIODIC) return ((i % n) + n) % n;
+  if (bc == ORC_BC_REFLECT) {
+    int m = (i < 0) ? -1 - i : 2 * n - 1 - i;
+    return m < 0 ? 0 : (m >= n ? n - 1 : m);
+  }
+  return (i < 0) ? 0 : n - 1;
 }
 
 /* Centre coordinate of cell i along d, for i in [-2, n+1].  Ghost centres
- * mirror the boundary cells (outflow) or are shifted by the period. */
+ * are shifted by the period (periodic) or mirror the cells inside (every
+ * other boundary). */
 static double centre(const orc_problem *p, int d, int i) {
   int n = p->n[d];
   const double *x = p->xf[d];
@@ -366,14 +459,55 @@ static double temperature(const orc_problem *p, double rho, double e) {
   return e / Cv;
 }
 
-/* rho * chi * dx of a cell, with chi = kappa_R + sigma at (rho, T^n). */
-static double tau_cell(const orc_problem *p, const orc_state *s, int i, int j, int k) {
-  size_t c = lin(p, i, j, k);
-  double rho = s->rho[c];
-  double T = temperature(p, rho, s->e[c]);
+/* Values of the cell with index a (a[d] may be a ghost index along d; the
+ * other two are interior): u = (E, F0, F1, F2), rho and e.  Boundary
+ * conditions (Sect. 3 uses all of them):
+ *   periodic, outflow   the wrapped or edge cell;
+ *   reflective          the mirror cell with the normal flux F_d negated;
+ *   fixed (injection)   E and F of the side's boundary state, the edge
+ *                       cell's rho and e = C_v T_b;
+ *   LTE                 E = a T_b^4, F of the edge cell (zero gradient), the
+ *                       edge cell's rho and e = C_v T_b. */
+static void cell_values(const orc_problem *p, const orc_state *s, const int a[3], int d,
+                        double u[4], double *rho, double *e) {
+  int b[3] = {a[0], a[1], a[2]};
+  int i = a[d], n = p->n[d];
+  b[d] = map_index(p, d, i);
+  size_t c = lin(p, b[0], b[1], b[2]);
+  load_u(s, c, &u[0], u + 1);
+  *rho = s->rho[c];
+  *e = s->e[c];
+  if (i >= 0 && i < n) return;
+  int side = (i < 0) ? 0 : 1;
+  int bc = side ? p->bc_hi[d] : p->bc_lo[d];
+  const double *v = p->bc_val[d][side];
+  double Cv = *rho / (p->mu * (p->gamma_gas - 1.0));
+  if (bc == ORC_BC_REFLECT) {
+    u[1 + d] = -u[1 + d];
+  } else if (bc == ORC_BC_FIXED) {
+    u[0] = v[0];
+    u[1] = v[1];
+    u[2] = v[2];
+    u[3] = v[3];
+    *e = Cv * v[4];
+  } else if (bc == ORC_BC_LTE) {
+    u[0] = p->a_rad * v[4] * v[4] * v[4] * v[4];
+    *e = Cv * v[4];
+  }
+}
+
+/* rho * chi * dx of the cell with index a (a[d] possibly a ghost index),
+ * with chi = kappa_R + sigma at (rho, T^n); a ghost takes the width of the
+ * cell it maps to. */
+static double tau_cell(const orc_problem *p, const orc_state *s, const int a[3], int d) {
+  double u[4], rho, e;
+  cell_values(p, s, a, d, u, &rho, &e);
+  int b[3] = {a[0], a[1], a[2]};
+  b[d] = map_index(p, d, a[d]);
+  double T = temperature(p, rho, e);
   double kp, kr, sg;
   orc_opacity(p, rho, T, &kp, &kr, &sg);
-  return rho * (kr + sg) * max_active_width(p, i, j, k);
+  return rho * (kr + sg) * max_active_width(p, b[0], b[1], b[2]);
 }
 
 /* Right face state (side = +1) or left face state (side = -1) of cell ic
@@ -383,13 +517,9 @@ static void face_state(const orc_problem *p, const orc_state *s, const int idx[3
   int a[3] = {idx[0], idx[1], idx[2]};
   double u[3][4];
   for (int q = -1; q <= 1; ++q) {
-    a[d] = map_index(p, d, ic + q);
-    double E, F[3];
-    load_u(s, lin(p, a[0], a[1], a[2]), &E, F);
-    u[q + 1][0] = E;
-    u[q + 1][1] = F[0];
-    u[q + 1][2] = F[1];
-    u[q + 1][3] = F[2];
+    a[d] = ic + q;
+    double rho, e;
+    cell_values(p, s, a, d, u[q + 1], &rho, &e);
   }
   double xm = centre(p, d, ic - 1), x0 = centre(p, d, ic), xp = centre(p, d, ic + 1);
   /* face coordinate: the ghost cells -1 and n are only asked for the face
@@ -397,9 +527,15 @@ static void face_state(const orc_problem *p, const orc_state *s, const int idx[3
   double xface = (side > 0) ? p->xf[d][ic + 1] : p->xf[d][ic];
   double uf[4];
   for (int q = 0; q < 4; ++q) {
-    double dl = (u[1][q] - u[0][q]) / (x0 - xm);
-    double dr = (u[2][q] - u[1][q]) / (xp - x0);
-    uf[q] = u[1][q] + orc_vanleer(dl, dr) * (xface - x0);
+    if (p->recon == ORC_LIMO3) {
+      /* index-space differences (the limiter is defined on a uniform grid) */
+      double dm = u[1][q] - u[0][q], dp = u[2][q] - u[1][q];
+      uf[q] = (side > 0) ? u[1][q] + orc_limo3(dm, dp) : u[1][q] - orc_limo3(dp, dm);
+    } else {
+      double dl = (u[1][q] - u[0][q]) / (x0 - xm);
+      double dr = (u[2][q] - u[1][q]) / (xp - x0);
+      uf[q] = u[1][q] + orc_vanleer(dl, dr) * (xface - x0);
+    }
   }
   *Ef = uf[0];
   Ff[0] = uf[1];
@@ -411,15 +547,17 @@ static void face_state(const orc_problem *p, const orc_state *s, const int idx[3
   Fc[2] = u[1][3];
 }
 
-/* HLL flux through the lower face (between cells i_d - 1 and i_d) of the
- * cell idx along active direction d.  Returns the number of f-fix events. */
+/* Riemann flux (HLL, or LF-Rusanov) through the lower face (between cells
+ * i_d - 1 and i_d) of the cell idx along active direction d.  Returns the
+ * number of face states the f <= 1 treatment changed. */
 static int face_flux(const orc_problem *p, const orc_state *s, const int idx[3], int d,
                      double out[4]) {
   int i = idx[d];
   double EL, FL[3], EcL, FcL[3], ER, FR[3], EcR, FcR[3];
   face_state(p, s, idx, d, i - 1, +1, &EL, FL, &EcL, FcL);
   face_state(p, s, idx, d, i, -1, &ER, FR, &EcR, FcR);
-  int nfix = orc_fix_face(EL, FL, EcL, FcL) + orc_fix_face(ER, FR, EcR, FcR);
+  int nfix = orc_fix_face_mode(p->face_fix, &EL, FL, EcL, FcL) +
+             orc_fix_face_mode(p->face_fix, &ER, FR, EcR, FcR);
 
   double fL[4], fR[4];
   orc_phys_flux(p->chat, EL, FL, d, fL);
@@ -432,10 +570,10 @@ static int face_flux(const orc_problem *p, const orc_state *s, const int idx[3],
 
   /* optically thick correction (Sect. 2.6), tau = mean of the two cells */
   int a[3] = {idx[0], idx[1], idx[2]};
-  a[d] = map_index(p, d, i - 1);
-  double tL = tau_cell(p, s, a[0], a[1], a[2]);
-  a[d] = map_index(p, d, i);
-  double tR = tau_cell(p, s, a[0], a[1], a[2]);
+  a[d] = i - 1;
+  double tL = tau_cell(p, s, a, d);
+  a[d] = i;
+  double tR = tau_cell(p, s, a, d);
   double tau = 0.5 * (tL + tR);
   if (tau > 0.0) {
     double bound = 4.0 * p->chat / (3.0 * tau);
@@ -443,7 +581,10 @@ static int face_flux(const orc_problem *p, const orc_state *s, const int idx[3],
     if (sr > bound) sr = bound;
   }
   double uL[4] = {EL, FL[0], FL[1], FL[2]}, uR[4] = {ER, FR[0], FR[1], FR[2]};
-  orc_hll(sl, sr, uL, uR, fL, fR, out);
+  if (p->riemann == ORC_LF)
+    orc_lf(sl, sr, uL, uR, fL, fR, out);
+  else
+    orc_hll(sl, sr, uL, uR, fL, fR, out);
   return nfix;
 }
 
@@ -486,6 +627,16 @@ static void couple(const orc_problem *p, double dt, double rho, double Tn, doubl
   double Cv = rho / (p->mu * (p->gamma_gas - 1.0));
   double g = dt * p->c * kp * rho;
   double gr = dt * p->chat * kp * rho;
+  if (p->implicit_mode == ORC_ABSORB) {
+    /* absorption only (the first shadow test of Sect. 3): no emission by
+     * the gas, E^{n+1} = E* / (1 + g_r); the gas energy follows from the
+     * conservation of Sect. 2.7 in the caller.  Tnew is T^n here. */
+    *Enew = Estar / (1.0 + gr);
+    *Tnew = Tn;
+    st[ORC_ST_ITERS] += 1;
+    if (st[ORC_ST_ITMAX] < 1) st[ORC_ST_ITMAX] = 1;
+    return;
+  }
   if (p->implicit_mode == ORC_ONCE) {
     orc_solve2x2_irr(Estar, Tn, Tn, Cv, g, gr, p->a_rad, sq, Enew, Tnew);
     st[ORC_ST_ITERS] += 1;
@@ -635,7 +786,10 @@ static void cell_step(const orc_problem *p, const orc_state *s, double dt, int i
   out[5] = mn[0];
   out[6] = mn[1];
   out[7] = mn[2];
-  out[8] = Tnew;
+  /* the coupling's T^{n+1}; absorption only: the temperature of the
+   * updated gas energy */
+  out[8] = (p->implicit_mode == ORC_ABSORB) ? out[4] / (rho / (p->mu * (p->gamma_gas - 1.0)))
+                                            : Tnew;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -841,8 +995,8 @@ void orc_face_states(const orc_problem *p, const orc_state *s, int i, int j, int
   face_state(p, s, idx, d, idx[d] - 1, +1, &EL, FL, &EcL, FcL);
   face_state(p, s, idx, d, idx[d], -1, &ER, FR, &EcR, FcR);
   double raw[8] = {EL, FL[0], FL[1], FL[2], ER, FR[0], FR[1], FR[2]};
-  orc_fix_face(EL, FL, EcL, FcL);
-  orc_fix_face(ER, FR, EcR, FcR);
+  orc_fix_face_mode(p->face_fix, &EL, FL, EcL, FcL);
+  orc_fix_face_mode(p->face_fix, &ER, FR, EcR, FcR);
   double fixed[8] = {EL, FL[0], FL[1], FL[2], ER, FR[0], FR[1], FR[2]};
   for (int q = 0; q < 8; ++q) {
     out[q] = raw[q];

@@ -48,6 +48,14 @@ class Problem:
     implicit_mode: str = "once"
     integrator: str = "euler"     # "euler" or "rk2" (two-stage, Sect. 2.4)
     qirr: Optional[np.ndarray] = None  # -div F_irr per cell (Sect. 2.9), or None
+    # options of Sect. 2.5: "plm" | "limo3"; "fpreserve" | "pluto" | "clip";
+    # "hll" | "lf"
+    recon: str = "plm"
+    face_fix: str = "fpreserve"
+    riemann: str = "hll"
+    # boundary states of "fixed" and "lte" sides: {(d, side): (E, F0, F1, F2, T)},
+    # side 0 = lower, 1 = upper ("lte" uses T only)
+    bc_value: Dict = dataclasses.field(default_factory=dict)
     newton_rtol: float = 1e-12
     newton_maxit: int = 50
     ncomp: int = 3
@@ -70,6 +78,7 @@ class Problem:
             setattr(p, k, None if a is None else a.copy())
         p.xfaces = [x.copy() for x in self.xfaces]
         p.opacity = dict(self.opacity)
+        p.bc_value = dict(self.bc_value)
         return p
 
 
