@@ -56,10 +56,55 @@ typedef enum {
 } rad_status;
 
 typedef enum { RAD_CARTESIAN = 0, RAD_CYLINDRICAL = 1, RAD_SPHERICAL = 2 } rad_geometry;
-typedef enum { RAD_BC_OUTFLOW = 0, RAD_BC_PERIODIC = 1 } rad_bc;
+/* Boundary conditions (Sect. 3 uses all of them).  The ghost cells of a
+ * side are:
+ *   OUTFLOW     copies of the edge cell (zero gradient);
+ *   PERIODIC    the wrapped cells (both sides of the direction);
+ *   REFLECTIVE  mirror images of the cells inside, with the normal flux and
+ *               momentum components negated (a wall);
+ *   FIXED       a held boundary state (E_b, F_b) and gas temperature T_b
+ *               (rad_grid.bc_value), with the edge cell's density: radiation
+ *               injection;
+ *   LTE         E_r = a_R T_b^4 and gas temperature T_b, F_r copied from
+ *               the edge cell (zero gradient), edge-cell density. */
+typedef enum {
+  RAD_BC_OUTFLOW = 0,
+  RAD_BC_PERIODIC = 1,
+  RAD_BC_REFLECTIVE = 2,
+  RAD_BC_FIXED = 3,
+  RAD_BC_LTE = 4
+} rad_bc;
 typedef enum { RAD_OPAC_CONST = 0, RAD_OPAC_POWERLAW = 1, RAD_OPAC_TABLE = 2 } rad_opac_kind;
+/* Precision.  RAD_FP32_SPLIT stores and transports in FP32 and forms the
+ * emission residual and the coupling solve in FP64.  It forms f = |F|/E from
+ * E^2 and |F|^2 in FP32, so E (and e_floor) must keep E^2 a normal float
+ * (E above about 1e-18 in the caller's units); below that use RAD_FP64 or
+ * rescale the units. */
 typedef enum { RAD_FP64 = 0, RAD_FP32_SPLIT = 1 } rad_precision;
-typedef enum { RAD_LINEARIZED_ONCE = 0, RAD_NEWTON = 1 } rad_implicit;
+/* Implicit coupling (Sect. 2.8).  RAD_ABSORPTION_ONLY drops the emission by
+ * the gas (the first shadow test of Sect. 3): E^{n+1} = E* / (1 + chat dt
+ * kappa_P rho), the gas energy following from the conservation of
+ * Sect. 2.7; F is updated as in every mode. */
+typedef enum { RAD_LINEARIZED_ONCE = 0, RAD_NEWTON = 1, RAD_ABSORPTION_ONLY = 2 } rad_implicit;
+
+/* Face reconstruction (Sect. 2.5): PLM with the van Leer limiter, or LimO3,
+ * the compact third-order limited reconstruction, face value
+ * u +/- phi(theta) delta / 2 with theta the ratio of the one-sided
+ * differences and phi = max(0, min(phi3, max(-theta/2, min(2 theta, phi3,
+ * 3/2)))), phi3 = (2 + theta)/3 (index-space differences). */
+typedef enum { RAD_PLM = 0, RAD_LIMO3 = 1 } rad_recon;
+
+/* Treatment of reconstructed face states with |F_f| > E_f (Sect. 2.5):
+ * FPRESERVE is Eq. (f_reconstruct) (F_f from the cell's F with the cell's
+ * f, also applied when f_face <= f_centre); PLUTO takes the cell's flat
+ * state (E_c, F_c) where |F_f| > E_f; CLIP rescales F_f to |F_f| = E_f
+ * (the plain limiter that Sect. 3's beam test shows to fail). */
+typedef enum { RAD_FIX_FPRESERVE = 0, RAD_FIX_PLUTO = 1, RAD_FIX_CLIP = 2 } rad_face_fix;
+
+/* Riemann solver (Sect. 2.5): HLL, or Lax-Friedrichs-Rusanov with the local
+ * speed max(|S_L|, |S_R|) of the same thick-limited signal speeds
+ * (Sect. 2.6). */
+typedef enum { RAD_HLL = 0, RAD_LF = 1 } rad_riemann;
 
 /* Time integration of one step (Sect. 2.4).  RAD_EULER: transport, then
  * the coupling (the step of Sect. 2.4).  RAD_RK2: that split applied in each
@@ -87,6 +132,10 @@ typedef struct {
   int n[3];                /* cells per direction, >= 1; n[d] = 1 for d >= ndim */
   const double *xface[3];  /* host, n[d]+1 face coordinates each, copied */
   int bc_lo[3], bc_hi[3];  /* rad_bc per active direction; periodic needs both */
+  /* boundary state of FIXED and LTE sides: bc_value[d][side] = (E_r, F_0,
+   * F_1, F_2, T_b), side 0 lower, 1 upper; FIXED needs E_r > 0, |F| <= E_r
+   * and T_b > 0, LTE reads T_b > 0 only; ignored for the other kinds */
+  double bc_value[3][2][5];
 } rad_grid;
 
 /* Opacity model (per unit mass); the absorption coefficient is kappa*rho.
@@ -128,6 +177,13 @@ typedef struct {
   int integrator;       /* rad_integrator */
   int irradiation;      /* 1: the context holds an irradiation deposit field (Sect. 2.9),
                            set with rad_set_irradiation (zero until set) */
+  int reconstruction;   /* rad_recon */
+  int face_fix;         /* rad_face_fix */
+  int riemann;          /* rad_riemann.  Options other than PLM, FPRESERVE and HLL,
+                           RAD_ABSORPTION_ONLY and irradiation run on the general
+                           form of the step kernel: its register-tiled shapes
+                           only (rad_get_launch reports fewer than the default
+                           form's on split 3D Cartesian grids) */
 } rad_params;
 
 /* Counters accumulated by rad_step since the last rad_reset_stats. */
@@ -146,7 +202,8 @@ typedef struct rad_ctx rad_ctx;
 
 /* Fills *p with defaults: chat = c = 1, a_rad = 1, gamma = 5/3, mu = 1,
  * cfl = 0.4, e_floor = 1e-30, RAD_FP64, RAD_LINEARIZED_ONCE, rtol = 1e-12,
- * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2, RAD_EULER, irradiation = 0.  Returns RAD_EINVAL if
+ * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2, RAD_EULER, irradiation = 0,
+ * RAD_PLM, RAD_FIX_FPRESERVE, RAD_HLL.  Returns RAD_EINVAL if
  * p is NULL. */
 rad_status rad_default_params(rad_params *p);
 
@@ -360,7 +417,9 @@ typedef struct rad_batch rad_batch;
 
 /* Validates the members (1..1024 distinct contexts) and returns a batch that
  * owns no device memory yet.  Errors: RAD_EINVAL, RAD_EUNSUPPORTED (members
- * that differ in kind, or a kind without batched kernels), RAD_ENOMEM. */
+ * that differ in kind, or a kind without batched kernels: non-Cartesian,
+ * RAD_RK2, face options other than the defaults, RAD_ABSORPTION_ONLY,
+ * irradiation), RAD_ENOMEM. */
 rad_status rad_batch_create(rad_ctx *const *members, int count, rad_batch **out);
 
 /* Device memory the batch needs for its own state: the members' argument

@@ -20,19 +20,26 @@ LIB_PATH = os.path.join(_HERE, "_lib", "librad.so")
 RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ENONPHYS, RAD_ENOCONV, RAD_ETIMEOUT, \
     RAD_EUNSUPPORTED = range(8)
 RAD_CARTESIAN, RAD_CYLINDRICAL, RAD_SPHERICAL = range(3)
-RAD_BC_OUTFLOW, RAD_BC_PERIODIC = range(2)
+RAD_BC_OUTFLOW, RAD_BC_PERIODIC, RAD_BC_REFLECTIVE, RAD_BC_FIXED, RAD_BC_LTE = range(5)
 RAD_OPAC_CONST, RAD_OPAC_POWERLAW, RAD_OPAC_TABLE = range(3)
 RAD_FP64, RAD_FP32_SPLIT = range(2)
-RAD_LINEARIZED_ONCE, RAD_NEWTON = range(2)
+RAD_LINEARIZED_ONCE, RAD_NEWTON, RAD_ABSORPTION_ONLY = range(3)
+RAD_PLM, RAD_LIMO3 = range(2)
+RAD_FIX_FPRESERVE, RAD_FIX_PLUTO, RAD_FIX_CLIP = range(3)
+RAD_HLL, RAD_LF = range(2)
 RAD_EULER, RAD_RK2 = range(2)
 RAD_FIELD_E, RAD_FIELD_F, RAD_FIELD_EINT, RAD_FIELD_M, RAD_FIELD_T, RAD_FIELD_RHO = range(6)
 
 GEOMETRY = {"cartesian": RAD_CARTESIAN, "cylindrical": RAD_CYLINDRICAL,
             "spherical": RAD_SPHERICAL}
-BC = {"outflow": RAD_BC_OUTFLOW, "periodic": RAD_BC_PERIODIC}
+BC = {"outflow": RAD_BC_OUTFLOW, "periodic": RAD_BC_PERIODIC, "reflective": RAD_BC_REFLECTIVE,
+      "fixed": RAD_BC_FIXED, "lte": RAD_BC_LTE}
 OPACITY = {"const": RAD_OPAC_CONST, "powerlaw": RAD_OPAC_POWERLAW, "table": RAD_OPAC_TABLE}
 PRECISION = {"fp64": RAD_FP64, "split": RAD_FP32_SPLIT}
-IMPLICIT = {"once": RAD_LINEARIZED_ONCE, "newton": RAD_NEWTON}
+IMPLICIT = {"once": RAD_LINEARIZED_ONCE, "newton": RAD_NEWTON, "absorb": RAD_ABSORPTION_ONLY}
+RECON = {"plm": RAD_PLM, "limo3": RAD_LIMO3}
+FACE_FIX = {"fpreserve": RAD_FIX_FPRESERVE, "pluto": RAD_FIX_PLUTO, "clip": RAD_FIX_CLIP}
+RIEMANN = {"hll": RAD_HLL, "lf": RAD_LF}
 INTEGRATOR = {"euler": RAD_EULER, "rk2": RAD_RK2}
 FIELDS = {"E": RAD_FIELD_E, "F": RAD_FIELD_F, "e": RAD_FIELD_EINT, "m": RAD_FIELD_M,
           "T": RAD_FIELD_T, "rho": RAD_FIELD_RHO}
@@ -40,7 +47,7 @@ FIELDS = {"E": RAD_FIELD_E, "F": RAD_FIELD_F, "e": RAD_FIELD_EINT, "m": RAD_FIEL
 
 class rad_grid(C.Structure):
     _fields_ = [("ndim", C.c_int), ("n", C.c_int * 3), ("xface", C.c_void_p * 3),
-                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3)]
+                ("bc_lo", C.c_int * 3), ("bc_hi", C.c_int * 3), ("bc_value", C.c_double * 30)]
 
 
 class rad_opacity(C.Structure):
@@ -58,7 +65,8 @@ class rad_params(C.Structure):
                 ("e_floor", C.c_double), ("precision", C.c_int), ("implicit_mode", C.c_int),
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int),
                 ("use_mlp", C.c_int), ("mlp_gate", C.c_double), ("integrator", C.c_int),
-                ("irradiation", C.c_int)]
+                ("irradiation", C.c_int), ("reconstruction", C.c_int), ("face_fix", C.c_int),
+                ("riemann", C.c_int)]
 
 
 class rad_stats(C.Structure):
@@ -197,10 +205,13 @@ def default_params() -> rad_params:
 class Rad:
     """One radiation problem on one GPU.
 
-    grid: dict(ndim, n=(n0,n1,n2), xfaces=[3 arrays], bc_lo=(...), bc_hi=(...))
-    with bc names 'outflow' / 'periodic'; opacity: dict with 'kind' and the
-    fields of rad_opacity; params: rad_params field values, with precision
-    'fp64' | 'split' and implicit_mode 'once' | 'newton'.
+    grid: dict(ndim, n=(n0,n1,n2), xfaces=[3 arrays], bc_lo=(...), bc_hi=(...),
+    bc_value={(d, side): (E, F0, F1, F2, T_b)}) with bc names 'outflow' |
+    'periodic' | 'reflective' | 'fixed' | 'lte'; opacity: dict with 'kind'
+    and the fields of rad_opacity; params: rad_params field values, with
+    precision 'fp64' | 'split', implicit_mode 'once' | 'newton' | 'absorb',
+    reconstruction 'plm' | 'limo3', face_fix 'fpreserve' | 'pluto' | 'clip',
+    riemann 'hll' | 'lf'.
     """
 
     def __init__(self, grid: dict, geometry: str, opacity: dict, params: dict,
@@ -216,6 +227,9 @@ class Rad:
             g.xface[d] = self._xf[d].ctypes.data
             g.bc_lo[d] = BC[grid["bc_lo"][d]]
             g.bc_hi[d] = BC[grid["bc_hi"][d]]
+        for (d, side), v in grid.get("bc_value", {}).items():
+            for q in range(5):
+                g.bc_value[10 * d + 5 * side + q] = float(v[q])
         o = rad_opacity()
         o.kind = OPACITY[opacity["kind"]]
         for k in ("kappa_p", "kappa_r", "sigma", "k0", "a_rho", "b_T", "kmin", "sigma_ratio",
@@ -238,6 +252,12 @@ class Rad:
                 v = IMPLICIT[v] if isinstance(v, str) else v
             elif k == "integrator":
                 v = INTEGRATOR[v] if isinstance(v, str) else v
+            elif k == "reconstruction":
+                v = RECON[v] if isinstance(v, str) else v
+            elif k == "face_fix":
+                v = FACE_FIX[v] if isinstance(v, str) else v
+            elif k == "riemann":
+                v = RIEMANN[v] if isinstance(v, str) else v
             setattr(p, k, v)
         self.params = p
         self.ncomp = int(p.ncomp)
@@ -529,9 +549,13 @@ def from_problem(prob, precision: str = "fp64", device=None, **overrides) -> "Ra
                   implicit_mode=prob.implicit_mode, newton_rtol=prob.newton_rtol,
                   newton_maxit=prob.newton_maxit, ncomp=prob.ncomp,
                   integrator=getattr(prob, "integrator", "euler"),
-                  irradiation=int(getattr(prob, "qirr", None) is not None))
+                  irradiation=int(getattr(prob, "qirr", None) is not None),
+                  reconstruction=getattr(prob, "recon", "plm"),
+                  face_fix=getattr(prob, "face_fix", "fpreserve"),
+                  riemann=getattr(prob, "riemann", "hll"))
     params.update(overrides)
-    grid = dict(ndim=prob.ndim, n=prob.n, xfaces=prob.xfaces, bc_lo=prob.bc_lo, bc_hi=prob.bc_hi)
+    grid = dict(ndim=prob.ndim, n=prob.n, xfaces=prob.xfaces, bc_lo=prob.bc_lo, bc_hi=prob.bc_hi,
+                bc_value=dict(getattr(prob, "bc_value", {})))
     r = Rad(grid, prob.geometry, prob.opacity, params, device=device)
     nc = prob.ncomp
     r.set_gas(prob.rho, np.asarray(prob.v)[:nc], prob.T)

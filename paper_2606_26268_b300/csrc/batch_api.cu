@@ -264,8 +264,8 @@ extern "C" rad_status rad_batch_create(rad_ctx* const* members, int count, rad_b
     if (m->geom != RAD_CARTESIAN || m->ndim != m0->ndim || m->esize != m0->esize ||
         m->nc != m0->nc || m->uniform != m0->uniform ||
         m->par.implicit_mode != m0->par.implicit_mode || m->par.use_mlp != m0->par.use_mlp ||
-        m->par.integrator != RAD_EULER)
-      return RAD_EUNSUPPORTED;
+        m->par.integrator != RAD_EULER || m->general)
+      return RAD_EUNSUPPORTED;  // the batched kernel runs the default form only
   }
   BatchEntry ent = select_batch(m0->esize == 4, m0->ndim, m0->nc, m0->uniform);
   if (!ent.step) return RAD_EUNSUPPORTED;

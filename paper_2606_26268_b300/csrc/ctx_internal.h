@@ -24,6 +24,7 @@ struct rad_ctx {
   // description
   int ndim = 1, n[3] = {1, 1, 1}, geom = 0;
   int bc_lo[3] = {0, 0, 0}, bc_hi[3] = {0, 0, 0};
+  double bc_val[3][2][5] = {};  // boundary states of FIXED / LTE sides (rad_grid.bc_value)
   std::vector<double> xf[3];
   rad_opacity opac{};
   std::vector<float> table32;
@@ -56,6 +57,7 @@ struct rad_ctx {
   LaunchEntry launch{nullptr, 0};
   int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
   bool uniform = false;         // Cartesian with a constant width along each direction
+  bool general = false;         // general form of the step kernel (options, absorption, irradiation)
   // learned guess
   m1::QueueFn qpass = nullptr;
   size_t off_mlp = 0, off_grad = 0, off_m = 0, off_v = 0, off_loss = 0, off_queue = 0;

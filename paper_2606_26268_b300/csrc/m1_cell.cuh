@@ -89,27 +89,38 @@ __device__ __forceinline__ void coupling_features(const CoupleParams& p, float r
 
 // The implicit coupling of the cell at padded index ic (Sect. 2.8): the
 // single linearised solve when `once`, else the mode of the parameters
-// (Newton from T0 > 0 or T^n), with the irradiation deposit of Sect. 2.9
-// when the context has one.
-template <class P>
+// (Newton from T0 > 0 or T^n).  GEN (the general form) adds the
+// absorption-only mode and the irradiation deposit of Sect. 2.9 when the
+// context has them; the default step kernels, which such contexts do not
+// use, compile both out.
+template <class P, bool GEN = true>
 __device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, long long ic,
                                                  typename P::S rho_s, typename P::S e_s,
                                                  typename P::T kp, typename P::T Es, float T0,
                                                  bool once) {
   using T = typename P::T;
-  const T sq = a.qirr ? a.dt * T(__ldg(a.qirr + ic)) : T(0);
-  if constexpr (P::kSplit)
-    return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once,
-                        float(sq));
-  else
-    return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
-                       once, double(sq));
+  if constexpr (GEN) {
+    const bool ab = a.cp.absorb;
+    const T sq = a.qirr ? a.dt * T(__ldg(a.qirr + ic)) : T(0);
+    if constexpr (P::kSplit)
+      return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once,
+                          float(sq), ab);
+    else
+      return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
+                         once, double(sq), ab);
+  } else {
+    if constexpr (P::kSplit)
+      return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once);
+    else
+      return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
+                         once);
+  }
 }
 
 // Bookkeeping and stores of the cell at padded index ic with unpadded
 // coordinates ci, given its coupling result co.  Us = (E*, F*) after
 // transport (E* already floored).
-template <class P, int NDIM, int NC>
+template <class P, int NDIM, int NC, bool GEN = true>
 __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, const int (&ci)[3],
                                             typename P::T (&Us)[4], typename P::S rho_s,
                                             typename P::S e_s, typename P::T kp,
@@ -187,7 +198,9 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
     en = T(e_s) - a.ratio * dE - dke / (T(2) * rr);
   else
     en = T(e_s) - a.ratio * dE - dke * T(0.5) * rcp_approx(rr);
-  if (a.qirr) en += T(co.sq);  // Sect. 2.9: E_gas gains dt (-div F_irr)
+  // Sect. 2.9: E_gas gains dt (-div F_irr) (reloaded here rather than kept
+  // live through the coupling)
+  if (GEN && a.qirr) en += a.dt * T(__ldg(a.qirr + ic));
   if (a.average) {
     // last stage of the two-stage step: average with U^n, which the output
     // buffer holds at this cell (only this thread reads or writes it)
@@ -219,6 +232,9 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
     a.out.m[v][ic] = S(mn[v]);
   }
   a.out.e[ic] = S(en);
+  // ghost copies: wrapped (periodic), edge (outflow), mirrored with the
+  // normal components negated (reflective), F only (LTE: E, e held); the
+  // FIXED sides hold their boundary state
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
     const int n = Dm.n[d];
@@ -227,21 +243,31 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
     const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
 #pragma unroll
     for (int gslot = 0; gslot < 4; ++gslot) {
-      int gpos = gslot < 2 ? gslot - 2 : n + gslot - 2;  // -2, -1, n, n+1
+      const bool lo = gslot < 2;
+      const int gpos = lo ? gslot - 2 : n + gslot - 2;  // -2, -1, n, n+1
+      const int bc = lo ? Dm.bc_lo[d] : Dm.bc_hi[d];
+      if (bc == BC_FIXED) continue;
       int src;
-      if (gslot < 2)
-        src = Dm.bc_lo[d] ? ((gpos % n) + n) % n : 0;
+      if (bc == BC_PERIODIC)
+        src = lo ? ((gpos % n) + n) % n : gpos % n;
+      else if (bc == BC_REFLECT)
+        src = min(max(lo ? -1 - gpos : 2 * n - 1 - gpos, 0), n - 1);
       else
-        src = Dm.bc_hi[d] ? gpos % n : n - 1;
+        src = lo ? 0 : n - 1;
       if (src != i) continue;
-      long long ig = ic + (long long)(gpos - i) * stride;
-      a.out.E[ig] = S(En);
+      const long long ig = ic + (long long)(gpos - i) * stride;
+      const bool refl = bc == BC_REFLECT;
+      const bool all = bc != BC_LTE;
+      if (all) {
+        a.out.E[ig] = S(En);
+        a.out.e[ig] = S(en);
+      }
 #pragma unroll
       for (int v = 0; v < NC; ++v) {
-        a.out.F[v][ig] = S(Fn[v]);
-        a.out.m[v][ig] = S(mn[v]);
+        const bool neg = refl && v == d;
+        a.out.F[v][ig] = S(neg ? -Fn[v] : Fn[v]);
+        if (all) a.out.m[v][ig] = S(neg ? -mn[v] : mn[v]);
       }
-      a.out.e[ig] = S(en);
     }
   }
 }

@@ -9,6 +9,17 @@ namespace m1 {
 
 enum { kCart = 0, kCyl = 1, kSph = 2 };
 
+// Boundary kinds (the values of the public rad_bc).
+enum { BC_OUTFLOW = 0, BC_PERIODIC = 1, BC_REFLECT = 2, BC_FIXED = 3, BC_LTE = 4 };
+
+// Options of the face computation (Sect. 2.5): reconstruction (0 PLM, 1
+// LimO3), treatment of |F_f| > E_f (0 f-preserving, 1 flat, 2 clip) and
+// Riemann solver (0 HLL, 1 Lax-Friedrichs-Rusanov).  All zero on the
+// TMA-staged kernels, which implement only the defaults.
+struct Scheme {
+  int recon, ffix, riemann;
+};
+
 // Per-direction geometry tables, indexed by the padded index ip = i + g
 // (g = 2 ghost cells on active directions, 0 on inactive ones); each table
 // has len = n + 2 g entries.  Ghost entries describe the cell the ghost
@@ -41,7 +52,7 @@ struct StepDims {
   int g[3];         // ghost depth per direction
   int pn[3];        // padded extents (pn[0] may be rounded up for alignment)
   long long sy, sz; // padded strides of directions 1 and 2
-  int bc_lo[3], bc_hi[3];
+  int bc_lo[3], bc_hi[3];  // BC_* per direction
 };
 
 template <class S>
@@ -84,6 +95,7 @@ struct StepArgs {
   // average of the stage result with the U^n that `out` holds at the cell
   // (conserved variables E_r, F_r, m and E_gas = e + |m|^2 / (2 rho))
   int average;
+  Scheme scheme;
   const S* rho;
   GeomDev<T> geo;
   OpacityDev opac;

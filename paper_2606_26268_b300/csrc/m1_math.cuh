@@ -244,6 +244,44 @@ __device__ __forceinline__ void hll(const T (&uL)[4], const T (&uR)[4], const T 
   }
 }
 
+// Lax-Friedrichs-Rusanov flux (Sect. 2.5) with the local speed
+// S = max(|S_L|, |S_R|) of the thick-limited signal speeds of Sect. 2.6:
+// (F_L + F_R) / 2 - S (U_R - U_L) / 2.
+template <class T, int NV>
+__device__ __forceinline__ void lf(const T (&uL)[4], const T (&uR)[4], const T (&fL)[4],
+                                   const T (&fR)[4], T lmL, T lpL, T lmR, T lpR, T chat, T tau,
+                                   T (&out)[4]) {
+  T sl = chat * (lmL < lmR ? lmL : lmR);
+  T sr = chat * (lpL > lpR ? lpL : lpR);
+  if (tau > T(0)) {
+    T bound = Ops<T>::div(T(4) * chat, T(3) * tau);
+    if (sl < -bound) sl = -bound;
+    if (sr > bound) sr = bound;
+  }
+  const T S = fabs(sl) > fabs(sr) ? fabs(sl) : fabs(sr);
+#pragma unroll
+  for (int q = 0; q < NV; ++q) out[q] = T(0.5) * (fL[q] + fR[q]) - T(0.5) * S * (uR[q] - uL[q]);
+}
+
+// LimO3 (Sect. 2.5): the increment phi(theta) dt / 2 from the cell value to
+// its face on the side of the one-sided difference dt, theta = dn / dt with
+// dn the other one; phi = max(0, min(phi3, max(-theta/2, min(2 theta, phi3,
+// 3/2)))), phi3 = (2 + theta) / 3 the unlimited third-order value.  Zero
+// when dt = 0.
+template <class T>
+__device__ __forceinline__ T limo3(T dn, T dt) {
+  if (dt == T(0)) return T(0);
+  const T th = Ops<T>::div(dn, dt);
+  const T p3 = Ops<T>::div(T(2) + th, T(3));
+  T a = T(2) * th;
+  if (p3 < a) a = p3;
+  if (T(1.5) < a) a = T(1.5);
+  if (T(-0.5) * th > a) a = T(-0.5) * th;
+  if (p3 < a) a = p3;
+  if (a < T(0)) a = T(0);
+  return T(0.5) * a * dt;
+}
+
 // ---------------------------------------------------------------------------
 // Opacities
 // ---------------------------------------------------------------------------
@@ -334,6 +372,7 @@ struct CoupleParams {
   double dt, chat, c, a_rad, cvfac;  // cvfac = 1 / (mu (gamma - 1)): C_v = rho cvfac
   double rtol;
   int maxit, newton;
+  int absorb;  // absorption only: E^{n+1} = E* / (1 + g_r), no emission (general form)
   // float copies for the split-precision path
   float f_dtchat, f_dtc, f_cvfac, f_a, f_rtol;
   int a_is_one;  // a_R == 1 (code units): the emission term needs no scaling
@@ -342,7 +381,6 @@ struct CoupleParams {
 struct CoupleOut {
   double dE;     // E^{n+1} - E*
   double Tnew;   // T^{n+1} of the solve
-  double sq;     // irradiation energy deposited in the step, dt (-div F_irr)
   int iters;
   int fallback;  // restarted from T^n
   int noconv;
@@ -360,15 +398,22 @@ struct CoupleOut {
 // |T^{n+1} - Tk| <= rtol T^{n+1}.
 __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double rho, double e,
                                                  double kp, double Es, double T0,
-                                                 bool once = false, double sq = 0.0) {
+                                                 bool once = false, double sq = 0.0,
+                                                 bool absorb = false) {
   CoupleOut o{};
-  o.sq = sq;
   double Cv = rho * p.cvfac;
   double Tn = e / Cv;
   double gr = p.dt * p.chat * kp * rho;
   double g = p.dt * p.c * kp * rho;
   double c1 = (1.0 + gr) * Cv;
   if (T0 <= 0.0) T0 = Tn;
+  if (absorb) {  // absorption only: E^{n+1} = E* / (1 + g_r)
+    o.dE = Es / (1.0 + gr) - Es;
+    o.Tnew = Tn;
+    o.iters = 1;
+    o.conv1 = 1;
+    return o;
+  }
   if (!p.newton || once) {
     double aT3 = p.a_rad * Tn * Tn * Tn;
     double D = Es - aT3 * Tn;
@@ -422,15 +467,22 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
 // terms are all positive, in float.
 __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
                                                   float kp, float Es, float T0f,
-                                                  bool once = false, float sq = 0.f) {
+                                                  bool once = false, float sq = 0.f,
+                                                  bool absorb = false) {
   CoupleOut o{};
-  o.sq = double(sq);
   float Cv = rho * p.f_cvfac;
   float invCv = rcp_approx(Cv);
   float Tf = e * invCv;
   float gr = p.f_dtchat * kp * rho;
   float g = p.f_dtc * kp * rho;
   float c1 = (1.f + gr) * Cv;
+  if (absorb) {  // absorption only: E^{n+1} = E* / (1 + g_r)
+    o.dE = double(-Es * gr * rcp_approx(1.f + gr));
+    o.Tnew = double(Tf);
+    o.iters = 1;
+    o.conv1 = 1;
+    return o;
+  }
   if (!p.newton || once) {
     // the T^4 emission term and E* - a T^4 in double: T^2 of a float is
     // exact in double, so this is two roundings from exact

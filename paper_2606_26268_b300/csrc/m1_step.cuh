@@ -7,6 +7,11 @@
 // the unsplit flux divergence with the metric terms of the geometry, and
 // the implicit coupling of Sect. 2.8 with the gas bookkeeping of Sect. 2.7.
 //
+// Options of Sect. 2.5 (LimO3, the flat and clipping face treatments, the
+// Lax-Friedrichs-Rusanov flux), the absorption-only coupling and the
+// irradiation deposit exist in the general instantiation (GEN) only, as
+// uniform branches; the default instantiations compile them out.
+//
 // Work decomposition.  A CTA of TX x TY threads owns an x (and, in 3D, y)
 // tile and marches along the slowest active axis (y in 2D, z in 3D).  Thread
 // (tx, ty) computes the lower face of its own column in every tile direction;
@@ -90,6 +95,57 @@ __device__ __forceinline__ void riemann(const T (&uL)[4], const T (&uR)[4], T ch
   hll<T, 1 + NC>(uL, uR, fL, fR, lmL, lpL, lmR, lpR, chat, tau, out);
 }
 
+// The Riemann solver the scheme selects (HLL or Lax-Friedrichs-Rusanov).
+template <class T, int NC, int D>
+__device__ __forceinline__ void riemann_s(const Scheme& sc, const T (&uL)[4], const T (&uR)[4],
+                                          T chat, T tau, T (&out)[4]) {
+  if (sc.riemann == 0) {
+    riemann<T, NC, D>(uL, uR, chat, tau, out);
+    return;
+  }
+  T fL[4] = {0, 0, 0, 0}, fR[4] = {0, 0, 0, 0};
+  T lmL, lpL, lmR, lpR;
+  state_flux<T, NC, D>(uL, chat, fL, lmL, lpL);
+  state_flux<T, NC, D>(uR, chat, fR, lmR, lpR);
+  lf<T, 1 + NC>(uL, uR, fL, fR, lmL, lpL, lmR, lpR, chat, tau, out);
+}
+
+// The treatment of a face state with |F_f| > E_f that the scheme selects
+// (Sect. 2.5): Eq. (f_reconstruct), the cell's flat state, or F_f rescaled
+// to |F_f| = E_f.  Returns true when the state was changed.
+template <class T, int NC>
+__device__ __forceinline__ bool fix_face_s(const Scheme& sc, T (&uf)[4], const T (&uc)[4], T nc2,
+                                           T inv_Ec) {
+  if (sc.ffix == 0) return fix_face<T, NC>(uf, uc, nc2, inv_Ec);
+  const T nf2 = flux2<T, NC>(uf);
+  if (nf2 <= uf[0] * uf[0]) return false;
+  if (sc.ffix == 1) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) uf[q] = uc[q];
+  } else {
+    const T r = Ops<T>::div(uf[0], Ops<T>::sqrt_(nf2));
+#pragma unroll
+    for (int v = 0; v < NC; ++v) uf[1 + v] *= r;
+  }
+  return true;
+}
+
+// LimO3 lower (lo) and upper (hi) face states of cell u between um and up.
+template <class T, int NV>
+__device__ __forceinline__ void limo3_states(const T (&um)[4], const T (&u)[4], const T (&up)[4],
+                                             T (&lo)[4], T (&hi)[4]) {
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if (q < NV) {
+      const T dm = u[q] - um[q], dp = up[q] - u[q];
+      lo[q] = u[q] - limo3(dp, dm);
+      hi[q] = u[q] + limo3(dm, dp);
+    } else {
+      lo[q] = hi[q] = T(0);
+    }
+  }
+}
+
 // Face flux from four consecutive cells um2, um1 | u0, up1 along D (the
 // face between um1 and u0).  ix_k = 1 / (centre distance) of the pairs
 // (um2, um1), (um1, u0), (u0, up1); hh = offset of the upper face of um1,
@@ -103,13 +159,19 @@ __device__ __forceinline__ T half_vanleer(T dl, T dr) {
   return p > T(0) ? p * rcp_approx(dl + dr) : T(0);
 }
 
+// sc: the face options (all zero, the defaults, unless given).
 template <class T, int NC, int D, bool UNI>
 __device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const T (&u0)[4],
                                      const T (&up1)[4], T ix0, T ix1, T ix2, T hh, T hl, T tau,
-                                     T chat, T inv_u0, T n2_u0, T (&out)[4]) {
+                                     T chat, T inv_u0, T n2_u0, T (&out)[4],
+                                     Scheme sc = Scheme{0, 0, 0}) {
   constexpr int NV = 1 + NC;
   T uL[4], uR[4];
-  if constexpr (UNI && sizeof(T) == 4) {
+  if (sc.recon == 1) {
+    T lo[4], hi[4];
+    limo3_states<T, NV>(um2, um1, u0, lo, uL);
+    limo3_states<T, NV>(um1, u0, up1, uR, hi);
+  } else if constexpr (UNI && sizeof(T) == 4) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       if (q < NV) {
@@ -131,9 +193,9 @@ __device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const
     plm_state<T, NV>(d0, d1, um1, hh, uL);
     plm_state<T, NV>(d1, d2, u0, hl, uR);
   }
-  const int fixL = fix_face<T, NC>(uL, um1, flux2<T, NC>(um1), Ops<T>::rcp(um1[0]));
-  const int fixR = fix_face<T, NC>(uR, u0, n2_u0, inv_u0);
-  riemann<T, NC, D>(uL, uR, chat, tau, out);
+  const int fixL = fix_face_s<T, NC>(sc, uL, um1, flux2<T, NC>(um1), Ops<T>::rcp(um1[0]));
+  const int fixR = fix_face_s<T, NC>(sc, uR, u0, n2_u0, inv_u0);
+  riemann_s<T, NC, D>(sc, uL, uR, chat, tau, out);
   return fixL | (fixR << 1);
 }
 
@@ -151,7 +213,10 @@ __device__ __forceinline__ void load_state(const Fields<S>& f, long long i, T (&
 // UNI: uniform Cartesian grid (spacing from constants instead of tables; the
 // slopes use raw differences, the 1/dx factor cancelling in the van Leer
 // mean, and faces sit at -/+ 1/2 in units of the difference).
-template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY>
+// GEN: the general form, with the face options of StepArgs::scheme, the
+// absorption-only coupling and the irradiation deposit as uniform runtime
+// branches; without it those are compiled out (the defaults, no deposit).
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, bool GEN = false>
 __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, int bz) {
   using S = typename P::S;
   using T = typename P::T;
@@ -195,6 +260,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
   const bool in_col = cx < Dm.n[0] && (!TILE_Y || cy < Dm.n[1]);
   const bool upd_col = in_col && tx <= TX - 2 && (!TILE_Y || ty <= TY - 2);
   const T chat = a.chat;
+  Scheme sc{0, 0, 0};
+  if constexpr (GEN) sc = a.scheme;
 
   // march-plane coordinates for tables: p1 (2D: march; 3D: tile y), p2
   auto p1_of = [&](int m) { return TILE_Y ? py : (MARCH ? m + gm : 0); };
@@ -242,19 +309,24 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
     T ix2 = IXC(MA, pm);
     int nf = face4<T, NC, MA, UNI>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
                                    HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat,
-                                   Ops<T>::rcp(q[0][0]), flux2<T, NC>(q[0]), zlo);
+                                   Ops<T>::rcp(q[0][0]), flux2<T, NC>(q[0]), zlo, sc);
     if (upd_col) cnt.fix += nf >> 1;  // the lower march state of cell m0
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
-    T d1[4], d2[4];
+    if (sc.recon == 1) {
+      T lo[4];
+      limo3_states<T, NV>(qm1, q[0], q[1], lo, hiS);
+    } else {
+      T d1[4], d2[4];
 #pragma unroll
-    for (int v = 0; v < 4; ++v) {
-      d1[v] = (q[0][v] - qm1[v]) * ix1;
-      d2[v] = (q[1][v] - q[0][v]) * ix2;
+      for (int v = 0; v < 4; ++v) {
+        d1[v] = (q[0][v] - qm1[v]) * ix1;
+        d2[v] = (q[1][v] - q[0][v]) * ix2;
+      }
+      plm_state<T, NV>(d1, d2, q[0], HHI(MA, pm), hiS);
     }
-    plm_state<T, NV>(d1, d2, q[0], HHI(MA, pm), hiS);
     inv_own = Ops<T>::rcp(q[0][0]);
     n2_own = flux2<T, NC>(q[0]);
-    int nfh = fix_face<T, NC>(hiS, q[0], n2_own, inv_own);
+    int nfh = fix_face_s<T, NC>(sc, hiS, q[0], n2_own, inv_own);
     if (upd_col) cnt.fix += nfh;
   } else {
     load_state<S, NC>(a.in, base, q[0]);
@@ -362,7 +434,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       T fx[4];
       int nf = face4<T, NC, 0, UNI>(um2, um1, u0, up1, IXC(0, px - 2),
                                IXC(0, px - 1), IXC(0, px),
-                               HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx);
+                               HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx,
+                               sc);
       // fixed states of updated cells: the lower one of this cell, the upper
       // one of the cell to the left
       const bool row_upd = !TILE_Y || (ty <= TY - 2 && cy < Dm.n[1]);
@@ -385,7 +458,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       T fy[4];
       int nf = face4<T, NC, 1, UNI>(um2, um1, u0, up1, IXC(1, py - 2),
                                IXC(1, py - 1), IXC(1, py),
-                               HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy);
+                               HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy,
+                               sc);
       if (upd_col) cnt.fix += nf >> 1;
       if (ty >= 1 && cy - 1 < Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
@@ -397,7 +471,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
     if constexpr (MARCH) {
       const int pm = m + 1 + gm;  // padded index of cell m+1
       T loN[4];
-      if constexpr (UNI && sizeof(T) == 4) {
+      if (sc.recon == 1) {
+        limo3_states<T, NV>(q[0], q[1], q[2], loN, hiN);
+      } else if constexpr (UNI && sizeof(T) == 4) {
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
           T hs = v < NV ? half_vanleer(q[1][v] - q[0][v], q[2][v] - q[1][v]) : T(0);
@@ -417,9 +493,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       }
       inv_n = Ops<T>::rcp(q[1][0]);
       n2_n = flux2<T, NC>(q[1]);
-      int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
-      int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
-      riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      int nf = fix_face_s<T, NC>(sc, loN, q[1], n2_n, inv_n);
+      int nf2 = fix_face_s<T, NC>(sc, hiN, q[1], n2_n, inv_n);
+      riemann_s<T, NC, MA>(sc, hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
       // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
       if (upd_col && m + 1 < m1) cnt.fix += nf + nf2;  // the march states of cell m + 1
     }
@@ -528,7 +604,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       bool queued = false;
       CoupleOut co;
       if (a.queue_cap) {
-        co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
+        co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;
         const unsigned int mask = __activemask();
         const unsigned int want = __ballot_sync(mask, queued);
@@ -545,13 +621,13 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
             for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {
             queued = false;  // queue full: iterate here
-            co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
+            co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
           }
         }
       } else {
-        co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
+        co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
-      if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+      if (!queued) finish_cell<P, NDIM, NC, GEN>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
     }
     if constexpr (MARCH) {
 #pragma unroll
@@ -574,9 +650,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
   counters_flush<P>(a, cnt, s_red, tid);
 }
 
-template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB, bool GEN>
 __global__ void __launch_bounds__(TX * TY, MINB) step_kernel(const __grid_constant__ StepArgs<P> a) {
-  step_tile<P, NDIM, GEOM, NC, UNI, TX, TY>(a, blockIdx.x, blockIdx.y, blockIdx.z);
+  step_tile<P, NDIM, GEOM, NC, UNI, TX, TY, GEN>(a, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 }  // namespace m1

@@ -412,7 +412,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       bool queued = false;
       CoupleOut co;
       if (a.queue_cap) {
-        co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
+        co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;
         const unsigned int mask = __activemask();
         const unsigned int want = __ballot_sync(mask, queued);
@@ -429,13 +429,13 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {
             queued = false;  // queue full: iterate here
-            co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
+            co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
           }
         }
       } else {
-        co = couple_cell<P>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
+        co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
-      if (!queued) finish_cell<P, NDIM, NC>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+      if (!queued) finish_cell<P, NDIM, NC, false>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {

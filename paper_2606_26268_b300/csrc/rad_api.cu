@@ -52,8 +52,16 @@ extern "C" rad_status rad_default_params(rad_params* p) {
   p->mlp_gate = 1e-2;
   p->integrator = RAD_EULER;
   p->irradiation = 0;
+  p->reconstruction = RAD_PLM;
+  p->face_fix = RAD_FIX_FPRESERVE;
+  p->riemann = RAD_HLL;
   return RAD_OK;
 }
+
+static_assert(int(BC_OUTFLOW) == int(RAD_BC_OUTFLOW) && int(BC_PERIODIC) == int(RAD_BC_PERIODIC) &&
+                  int(BC_REFLECT) == int(RAD_BC_REFLECTIVE) && int(BC_FIXED) == int(RAD_BC_FIXED) &&
+                  int(BC_LTE) == int(RAD_BC_LTE),
+              "device boundary kinds follow rad_bc");
 
 // ---------------------------------------------------------------------------
 // geometry tables
@@ -178,7 +186,12 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
       !finite_pos(p.e_floor))
     return RAD_EINVAL;
   if (p.precision != RAD_FP64 && p.precision != RAD_FP32_SPLIT) return RAD_EINVAL;
-  if (p.implicit_mode != RAD_LINEARIZED_ONCE && p.implicit_mode != RAD_NEWTON) return RAD_EINVAL;
+  if (p.implicit_mode != RAD_LINEARIZED_ONCE && p.implicit_mode != RAD_NEWTON &&
+      p.implicit_mode != RAD_ABSORPTION_ONLY)
+    return RAD_EINVAL;
+  if (p.reconstruction < RAD_PLM || p.reconstruction > RAD_LIMO3) return RAD_EINVAL;
+  if (p.face_fix < RAD_FIX_FPRESERVE || p.face_fix > RAD_FIX_CLIP) return RAD_EINVAL;
+  if (p.riemann < RAD_HLL || p.riemann > RAD_LF) return RAD_EINVAL;
   if (p.implicit_mode == RAD_NEWTON && (!(p.newton_rtol > 0.0) || p.newton_maxit < 1))
     return RAD_EINVAL;
   if (p.ncomp < 1 || p.ncomp > 3) return RAD_EINVAL;
@@ -195,7 +208,22 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
         return RAD_EINVAL;
     if (d < grid->ndim) {
       int lo = grid->bc_lo[d], hi = grid->bc_hi[d];
-      if (lo < 0 || lo > 1 || hi < 0 || hi > 1 || lo != hi) return RAD_EINVAL;
+      if (lo < RAD_BC_OUTFLOW || lo > RAD_BC_LTE || hi < RAD_BC_OUTFLOW || hi > RAD_BC_LTE)
+        return RAD_EINVAL;
+      if ((lo == RAD_BC_PERIODIC) != (hi == RAD_BC_PERIODIC)) return RAD_EINVAL;
+      for (int side = 0; side < 2; ++side) {
+        const int bc = side ? hi : lo;
+        const double* v = grid->bc_value[d][side];
+        if ((bc == RAD_BC_FIXED || bc == RAD_BC_LTE) && !(v[4] > 0.0 && std::isfinite(v[4])))
+          return RAD_EINVAL;
+        if (bc == RAD_BC_FIXED &&
+            !(v[0] > 0.0 && std::isfinite(v[0]) &&
+              v[1] * v[1] + v[2] * v[2] + v[3] * v[3] <= v[0] * v[0] * (1.0 + 1e-12)))
+          return RAD_EINVAL;
+        if (bc == RAD_BC_FIXED)
+          for (int q = p.ncomp; q < 3; ++q)
+            if (v[1 + q] != 0.0) return RAD_EINVAL;  // components the caller does not carry
+      }
     }
     N *= size_t(n);
   }
@@ -223,6 +251,8 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
     c->n[d] = grid->n[d];
     c->bc_lo[d] = d < grid->ndim ? grid->bc_lo[d] : 0;
     c->bc_hi[d] = d < grid->ndim ? grid->bc_hi[d] : 0;
+    for (int side = 0; side < 2; ++side)
+      for (int q = 0; q < 5; ++q) c->bc_val[d][side][q] = grid->bc_value[d][side][q];
     c->xf[d].assign(grid->xface[d], grid->xface[d] + grid->n[d] + 1);
   }
   c->opac = o;
@@ -250,7 +280,13 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
         break;
       }
   }
-  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform);
+  // the general form of the step kernel carries the face options, the
+  // absorption-only coupling and the irradiation deposit (register-tiled
+  // shapes only); the default form compiles them out
+  c->general = p.reconstruction != RAD_PLM || p.face_fix != RAD_FIX_FPRESERVE ||
+               p.riemann != RAD_HLL || p.irradiation || p.implicit_mode == RAD_ABSORPTION_ONLY;
+  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform,
+                            c->general);
   c->qpass = select_queue_pass(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
   if (!c->launch.fn) {
     delete c;
@@ -394,12 +430,27 @@ extern "C" rad_status rad_dt(const rad_ctx* c, double* dt) {
 
 enum { PK_COPY = 0, PK_MOM = 1, PK_EINT = 2 };
 
+// What a packed array holds, for the ghost rules of the boundary kinds.
+enum { FK_RHO = 0, FK_E = 1, FK_F = 2, FK_M = 3, FK_EINT = 4, FK_OTHER = 5 };
+
+// Boundary states of the FIXED and LTE sides: (E, F0, F1, F2, T_b) per
+// direction and side, and a_R for the LTE energy a_R T_b^4.
+struct GhostVals {
+  double v[3][2][5];
+  double a_rad;
+};
+
 // Fills every padded cell (ghosts included) of dst from the flat array src
-// (x fastest) through the boundary mapping; PK_MOM multiplies by rho (flat),
-// PK_EINT by rho * cvfac.
+// (x fastest); PK_MOM multiplies by rho (flat), PK_EINT by rho * cvfac.  A
+// ghost takes the wrapped (periodic), mirrored (reflective) or edge cell
+// (the other kinds); reflective sides negate the normal component (comp ==
+// direction) of F and m; FIXED and LTE sides substitute their boundary
+// state: E (FIXED: E_b, LTE: a_R T_b^4), F (FIXED: F_b), m (zero) and
+// e = rho cvfac T_b.
 template <class S>
 __global__ void pack_kernel(S* __restrict__ dst, const S* __restrict__ src,
-                            const S* __restrict__ rho, StepDims D, int mode, double cvfac) {
+                            const S* __restrict__ rho, StepDims D, int mode, double cvfac,
+                            int field, int comp, GhostVals gv) {
   const long long total = (long long)D.pn[0] * D.pn[1] * D.pn[2];
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
        p += (long long)gridDim.x * blockDim.x) {
@@ -410,18 +461,43 @@ __global__ void pack_kernel(S* __restrict__ dst, const S* __restrict__ src,
     c[1] = int(r % D.pn[1]);
     c[2] = int(r / D.pn[1]);
     long long lin = 0, mul = 1;
+    double sign = 1.0;
+    int over = -1;             // direction whose boundary state replaces the value
+    int over_side = 0;
     for (int d = 0; d < 3; ++d) {
       int i = c[d] - D.g[d];
-      int n = D.n[d];
-      if (i < 0) i = D.bc_lo[d] ? ((i % n) + n) % n : 0;
-      if (i >= n) i = D.bc_hi[d] ? i % n : n - 1;
+      const int n = D.n[d];
+      if (i < 0 || i >= n) {
+        const int side = i < 0 ? 0 : 1;
+        const int bc = side ? D.bc_hi[d] : D.bc_lo[d];
+        if (bc == BC_PERIODIC) {
+          i = ((i % n) + n) % n;
+        } else if (bc == BC_REFLECT) {
+          i = min(max(side ? 2 * n - 1 - i : -1 - i, 0), n - 1);
+          if ((field == FK_F || field == FK_M) && comp == d) sign = -sign;
+        } else {
+          i = side ? n - 1 : 0;
+          if (bc == BC_FIXED || bc == BC_LTE) {
+            over = d;
+            over_side = side;
+          }
+        }
+      }
       lin += (long long)i * mul;
       mul *= n;
     }
-    S v = src[lin];
-    if (mode == PK_MOM) v = v * rho[lin];
-    if (mode == PK_EINT) v = S(double(v) * double(rho[lin]) * cvfac);
-    dst[p] = v;
+    double v = double(src[lin]);
+    if (mode == PK_MOM) v = v * double(rho[lin]);
+    if (mode == PK_EINT) v = v * double(rho[lin]) * cvfac;
+    if (over >= 0) {
+      const int bc = over_side ? D.bc_hi[over] : D.bc_lo[over];
+      const double* b = gv.v[over][over_side];
+      if (field == FK_E) v = bc == BC_FIXED ? b[0] : gv.a_rad * b[4] * b[4] * b[4] * b[4];
+      if (field == FK_F && bc == BC_FIXED) v = b[1 + comp];
+      if (field == FK_M) v = 0.0;
+      if (field == FK_EINT) v = b[4] * double(rho[lin]) * cvfac;
+    }
+    dst[p] = S(sign * v);
   }
 }
 
@@ -451,10 +527,16 @@ static int grid_for(long long n) {
 }
 
 template <class S>
-static rad_status pack(rad_ctx* c, S* dst, const S* src, const S* rho, int mode) {
+static rad_status pack(rad_ctx* c, S* dst, const S* src, const S* rho, int mode, int field,
+                       int comp = 0) {
   double cvfac = 1.0 / (c->par.mu * (c->par.gamma_gas - 1.0));
-  pack_kernel<S><<<grid_for((long long)c->pcells), 256, 0, c->stream>>>(dst, src, rho, c->dims, mode,
-                                                                    cvfac);
+  GhostVals gv;
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side)
+      for (int q = 0; q < 5; ++q) gv.v[d][side][q] = c->bc_val[d][side][q];
+  gv.a_rad = c->par.a_rad;
+  pack_kernel<S><<<grid_for((long long)c->pcells), 256, 0, c->stream>>>(
+      dst, src, rho, c->dims, mode, cvfac, field, comp, gv);
   return cuda_err(cudaGetLastError());
 }
 
@@ -482,7 +564,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
   // rho first (flat copy kept in stage slot 0 while m and e are built)
   const S* r = static_cast<const S*>(stage_in(c, rho, c->N, 0, dev, &st));
   if (st) return st;
-  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_rho), r, r, PK_COPY))) return st;
+  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_rho), r, r, PK_COPY, FK_RHO))) return st;
   // v: ncomp arrays (host input goes through stage slot 1 one component at a
   // time); internal components beyond ncomp are zero
   for (int comp = 0; comp < c->nc; ++comp) {
@@ -501,7 +583,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
     for (int b = 0; b < c->nbuf; ++b) {
       S* dst = static_cast<S*>(state_ptr(c, b, 5 + comp));
       if (src) {
-        if ((st = pack<S>(c, dst, src, r, PK_MOM))) return st;
+        if ((st = pack<S>(c, dst, src, r, PK_MOM, FK_M, comp))) return st;
       } else if (cudaMemsetAsync(dst, 0, c->pcells * c->esize, c->stream) != cudaSuccess) {
         return RAD_ECUDA;
       }
@@ -510,7 +592,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
   const S* t = static_cast<const S*>(stage_in(c, T, c->N, 2, dev, &st));
   if (st) return st;
   for (int b = 0; b < c->nbuf; ++b)
-    if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 4)), t, r, PK_EINT))) return st;
+    if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 4)), t, r, PK_EINT, FK_EINT))) return st;
   c->have_gas = true;
   return cuda_err(cudaStreamSynchronize(c->stream));
 }
@@ -529,7 +611,7 @@ static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
   const S* e = static_cast<const S*>(stage_in(c, E, c->N, 0, dev, &st));
   if (st) return st;
   for (int b = 0; b < c->nbuf; ++b)
-    if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 0)), e, e, PK_COPY))) return st;
+    if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 0)), e, e, PK_COPY, FK_E))) return st;
   for (int comp = 0; comp < c->nc; ++comp) {
     for (int b = 0; b < c->nbuf; ++b) {
       S* dst = static_cast<S*>(state_ptr(c, b, 1 + comp));
@@ -545,7 +627,7 @@ static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
             return RAD_ECUDA;
           src = reinterpret_cast<const S*>(slot);
         }
-        if ((st = pack<S>(c, dst, src, src, PK_COPY))) return st;
+        if ((st = pack<S>(c, dst, src, src, PK_COPY, FK_F, comp))) return st;
       } else if (cudaMemsetAsync(dst, 0, c->pcells * c->esize, c->stream) != cudaSuccess) {
         return RAD_ECUDA;
       }
@@ -560,7 +642,7 @@ static rad_status set_irr_t(rad_ctx* c, const void* q, int dev) {
   rad_status st;
   const S* src = static_cast<const S*>(stage_in(c, q, c->N, 0, dev, &st));
   if (st) return st;
-  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_qirr), src, src, PK_COPY))) return st;
+  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_qirr), src, src, PK_COPY, FK_OTHER))) return st;
   return cuda_err(cudaStreamSynchronize(c->stream));
 }
 
@@ -648,6 +730,10 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   cp.rtol = c->par.newton_rtol;
   cp.maxit = c->par.newton_maxit;
   cp.newton = c->par.implicit_mode == RAD_NEWTON;
+  cp.absorb = c->par.implicit_mode == RAD_ABSORPTION_ONLY;
+  a.scheme.recon = c->par.reconstruction;
+  a.scheme.ffix = c->par.face_fix;
+  a.scheme.riemann = c->par.riemann;
   cp.f_dtchat = float(dt * c->par.chat);
   cp.f_dtc = float(dt * c->par.c);
   cp.f_cvfac = float(cp.cvfac);

@@ -9,23 +9,23 @@
 
 namespace m1 {
 
-template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB>
+template <class P, int NDIM, int GEOM, int NC, bool UNI, int TX, int TY, int MINB, bool GEN>
 cudaError_t launch_shape(StepArgs<P> a, cudaStream_t s, int chunk) {
   const int* n = a.dim.n;
   if constexpr (NDIM == 3) {
     a.chunk = chunk > 0 ? chunk : 32;
     if (a.chunk > n[2]) a.chunk = n[2];
     dim3 grid((n[0] + TX - 2) / (TX - 1), (n[1] + TY - 2) / (TY - 1), (n[2] + a.chunk - 1) / a.chunk);
-    step_kernel<P, 3, GEOM, NC, UNI, TX, TY, MINB><<<grid, dim3(TX, TY), 0, s>>>(a);
+    step_kernel<P, 3, GEOM, NC, UNI, TX, TY, MINB, GEN><<<grid, dim3(TX, TY), 0, s>>>(a);
   } else if constexpr (NDIM == 2) {
     a.chunk = chunk > 0 ? chunk : 64;
     if (a.chunk > n[1]) a.chunk = n[1];
     dim3 grid((n[0] + TX - 2) / (TX - 1), (n[1] + a.chunk - 1) / a.chunk);
-    step_kernel<P, 2, GEOM, NC, UNI, TX, 1, MINB><<<grid, dim3(TX, 1), 0, s>>>(a);
+    step_kernel<P, 2, GEOM, NC, UNI, TX, 1, MINB, GEN><<<grid, dim3(TX, 1), 0, s>>>(a);
   } else {
     a.chunk = 1;
     dim3 grid((n[0] + TX - 2) / (TX - 1));
-    step_kernel<P, 1, GEOM, NC, UNI, TX, 1, MINB><<<grid, dim3(TX, 1), 0, s>>>(a);
+    step_kernel<P, 1, GEOM, NC, UNI, TX, 1, MINB, GEN><<<grid, dim3(TX, 1), 0, s>>>(a);
   }
   return cudaGetLastError();
 }
@@ -68,10 +68,11 @@ cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chun
 // precision on Cartesian grids the TMA-staged 32x8 with overlapping tiles
 // (variants 4, 5) and with non-overlapping tiles (6, 7), each at 2 or 3
 // CTAs/SM; 2D rows of 128, 256 or 64 threads; 1D: 128.  Curvilinear grids
-// get the default shape only.
-template <class P, int NDIM, int GEOM, int NC, bool UNI>
+// get the default shape only.  The general form (GEN: face options,
+// absorption only, irradiation) has the register-tiled shapes only.
+template <class P, int NDIM, int GEOM, int NC, bool UNI, bool GEN = false>
 struct Shapes {
-  static constexpr bool tma = P::kSplit && GEOM == kCart && NDIM == 3;
+  static constexpr bool tma = !GEN && P::kSplit && GEOM == kCart && NDIM == 3;
   static constexpr int count =
       (GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 8 : 4) : 3);
   static cudaError_t launch(const void* vargs, const void* maps, cudaStream_t s, int variant,
@@ -86,26 +87,26 @@ struct Shapes {
         if (variant == 7) return launch_tma2<P, NC, UNI, 32, 8, 3>(a, maps, s, chunk);
       }
       if constexpr (count > 1) {
-        if (variant == 1) return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 3>(a, s, chunk);
-        if (variant == 2) return launch_shape<P, 3, GEOM, NC, UNI, 32, 16, 1>(a, s, chunk);
-        if (variant == 3) return launch_shape<P, 3, GEOM, NC, UNI, 64, 8, 1>(a, s, chunk);
+        if (variant == 1) return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 3, GEN>(a, s, chunk);
+        if (variant == 2) return launch_shape<P, 3, GEOM, NC, UNI, 32, 16, 1, GEN>(a, s, chunk);
+        if (variant == 3) return launch_shape<P, 3, GEOM, NC, UNI, 64, 8, 1, GEN>(a, s, chunk);
       }
-      return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2>(a, s, chunk);
+      return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2, GEN>(a, s, chunk);
     } else if constexpr (NDIM == 2) {
       if constexpr (count > 1) {
-        if (variant == 1) return launch_shape<P, 2, GEOM, NC, UNI, 256, 1, 1>(a, s, chunk);
-        if (variant == 2) return launch_shape<P, 2, GEOM, NC, UNI, 64, 1, 1>(a, s, chunk);
+        if (variant == 1) return launch_shape<P, 2, GEOM, NC, UNI, 256, 1, 1, GEN>(a, s, chunk);
+        if (variant == 2) return launch_shape<P, 2, GEOM, NC, UNI, 64, 1, 1, GEN>(a, s, chunk);
       }
-      return launch_shape<P, 2, GEOM, NC, UNI, 128, 1, 1>(a, s, chunk);
+      return launch_shape<P, 2, GEOM, NC, UNI, 128, 1, 1, GEN>(a, s, chunk);
     } else {
-      return launch_shape<P, 1, GEOM, NC, UNI, 128, 1, 1>(a, s, chunk);
+      return launch_shape<P, 1, GEOM, NC, UNI, 128, 1, 1, GEN>(a, s, chunk);
     }
   }
 };
 
-template <class P, int NDIM, int GEOM, int NC, bool UNI = false>
+template <class P, int NDIM, int GEOM, int NC, bool UNI = false, bool GEN = false>
 LaunchEntry entry() {
-  using Sh = Shapes<P, NDIM, GEOM, NC, UNI>;
+  using Sh = Shapes<P, NDIM, GEOM, NC, UNI, GEN>;
   LaunchEntry e{&Sh::launch, Sh::count, {}};
   if constexpr (Sh::tma) {
     for (int v = 4; v < 6; ++v) {

@@ -19,6 +19,7 @@ struct LaunchEntry {
 };
 
 // The launcher for (precision, active directions, geometry, carried flux
-// components, uniform Cartesian spacing); fn == nullptr when that
-// combination is not instantiated.
-LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform);
+// components, uniform Cartesian spacing, general form); fn == nullptr when
+// that combination is not instantiated.  The general form carries the face
+// options, the absorption-only coupling and the irradiation deposit.
+LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform, bool general);

@@ -5,9 +5,14 @@
 namespace m1 {
 LaunchEntry select_fp64(int ndim, int geom, int nc, bool uni);
 LaunchEntry select_split(int ndim, int geom, int nc, bool uni);
+LaunchEntry select_fp64_gen(int ndim, int geom, int nc, bool uni);
+LaunchEntry select_split_gen(int ndim, int geom, int nc, bool uni);
 }  // namespace m1
 
-LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform) {
+LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform, bool general) {
+  if (general)
+    return split ? m1::select_split_gen(ndim, geom, nc, uniform)
+                 : m1::select_fp64_gen(ndim, geom, nc, uniform);
   return split ? m1::select_split(ndim, geom, nc, uniform) : m1::select_fp64(ndim, geom, nc, uniform);
 }
 

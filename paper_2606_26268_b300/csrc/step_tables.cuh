@@ -1,0 +1,43 @@
+// step_tables.cuh -- the instantiated (precision, active directions,
+// geometry, carried components, uniform spacing) combinations of the step
+// kernel, as one table for the default form and the general form (GEN).
+#pragma once
+#include "step_launch.cuh"
+
+namespace m1 {
+
+template <class P, bool GEN>
+LaunchEntry select_table(int ndim, int geom, int nc, bool uni) {
+  if (geom == kCart && uni) {
+    if (ndim == 1 && nc == 1) return entry<P, 1, kCart, 1, true, GEN>();
+    if (ndim == 1 && nc == 2) return entry<P, 1, kCart, 2, true, GEN>();
+    if (ndim == 1 && nc == 3) return entry<P, 1, kCart, 3, true, GEN>();
+    if (ndim == 2 && nc == 2) return entry<P, 2, kCart, 2, true, GEN>();
+    if (ndim == 2 && nc == 3) return entry<P, 2, kCart, 3, true, GEN>();
+    if (ndim == 3 && nc == 3) return entry<P, 3, kCart, 3, true, GEN>();
+    return LaunchEntry{nullptr, 0};
+  }
+  if (geom == kCart) {
+    if (ndim == 1 && nc == 1) return entry<P, 1, kCart, 1, false, GEN>();
+    if (ndim == 1 && nc == 2) return entry<P, 1, kCart, 2, false, GEN>();
+    if (ndim == 1 && nc == 3) return entry<P, 1, kCart, 3, false, GEN>();
+    if (ndim == 2 && nc == 2) return entry<P, 2, kCart, 2, false, GEN>();
+    if (ndim == 2 && nc == 3) return entry<P, 2, kCart, 3, false, GEN>();
+    if (ndim == 3 && nc == 3) return entry<P, 3, kCart, 3, false, GEN>();
+    return LaunchEntry{nullptr, 0};
+  }
+  if (nc != 3) return LaunchEntry{nullptr, 0};
+  if (geom == kCyl) {
+    if (ndim == 1) return entry<P, 1, kCyl, 3, false, GEN>();
+    if (ndim == 2) return entry<P, 2, kCyl, 3, false, GEN>();
+    if (ndim == 3) return entry<P, 3, kCyl, 3, false, GEN>();
+  }
+  if (geom == kSph) {
+    if (ndim == 1) return entry<P, 1, kSph, 3, false, GEN>();
+    if (ndim == 2) return entry<P, 2, kSph, 3, false, GEN>();
+    if (ndim == 3) return entry<P, 3, kSph, 3, false, GEN>();
+  }
+  return LaunchEntry{nullptr, 0};
+}
+
+}  // namespace m1

@@ -22,6 +22,10 @@ def rounded(p, dtype):
     q = p.copy()
     for k in ("rho", "v", "T", "E", "F"):
         setattr(q, k, np.asarray(getattr(q, k)).astype(dtype).astype(np.float64))
+    q.bc_value = {key: tuple(float(dtype(x)) for x in v)
+                  for key, v in getattr(p, "bc_value", {}).items()}
+    if getattr(p, "qirr", None) is not None:
+        q.qirr = np.asarray(p.qirr).astype(dtype).astype(np.float64)
     return q
 
 

@@ -332,6 +332,46 @@ def shock_tube(which: int, n: int, t_end: float = 20.0) -> Problem:
     return p
 
 
+# cgs constants for the shadow test
+C_LIGHT = 2.99792458e10
+A_RAD = 7.5657e-15
+KB_OVER_MU = 8.314462618e7   # k_B / m_u in erg / (g K)
+
+
+def shadow(n: Tuple[int, int] = (140, 40), coupling: str = "absorb") -> Problem:
+    """The shadow test of Sect. 3 (cgs): box x in [-0.5, 0.5], y in [0, 0.3]
+    cm, spheroid of rho_1 = 1e3 at the origin in a background rho_0 = 1,
+    rho = rho_0 + (rho_1 - rho_0) / (1 + e^D), D = 10 ((x/0.1)^2 +
+    (y/0.06)^2 - 1); T = 290 K everywhere with E = a T^4 and F = v = 0;
+    Kramers kappa = 0.1 (rho/rho_0) (T/290)^-3.5 cm^2/g, no scattering.  A
+    beam at T_r = 1740 K with F_x = E enters through the left side (fixed
+    boundary state, ghost gas at 290 K); the lower side y = 0 is reflective,
+    the right and upper sides are outflow.  chat = c; mu = 1 and Gamma = 5/3
+    (the paper gives neither).  coupling "absorb" drops the emission by the
+    gas (the paper's first panel), "once" keeps the full coupling."""
+    nx, ny = n
+    xf = [uniform_faces(nx, -0.5, 0.5), uniform_faces(ny, 0.0, 0.3), uniform_faces(1, 0.0, 1.0)]
+    p = _blank("shadow_%dx%d" % (nx, ny), 2, (nx, ny, 1), "cartesian", "outflow", xf,
+               chat=C_LIGHT, ncomp=2, implicit_mode=coupling)
+    p.bc_lo = ("fixed", "reflective", "outflow")
+    p.bc_hi = ("outflow", "outflow", "outflow")
+    p.a_rad = A_RAD
+    p.mu = 1.0 / KB_OVER_MU
+    p.gamma_gas = 5.0 / 3.0
+    Eb = A_RAD * 1740.0 ** 4
+    p.bc_value = {(0, 0): (Eb, Eb, 0.0, 0.0, 290.0)}
+    x, y, _ = mesh(p)
+    D = 10.0 * ((x / 0.1) ** 2 + (y / 0.06) ** 2 - 1.0)
+    p.rho = 1.0 + (1e3 - 1.0) / (1.0 + np.exp(np.minimum(D, 700.0)))
+    p.v = np.zeros((3, p.N))
+    p.T = np.full(p.N, 290.0)
+    p.E = A_RAD * p.T ** 4
+    p.F = np.zeros((3, p.N))
+    p.opacity = {"kind": "powerlaw", "k0": 0.1 * 290.0 ** 3.5, "a_rho": 1.0, "b_T": -3.5,
+                 "kmin": 0.0, "kmax": 1e300, "sigma_ratio": 0.0}
+    return p
+
+
 def uniform_state(geometry: str, n: Tuple[int, int, int], ndim: int, log_r: bool = False,
                   extents=None, E: float = 2.0, kappa: float = 0.5) -> Problem:
     """A uniform isotropic state (E const, F = 0) in equilibrium with the gas
