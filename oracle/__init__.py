@@ -41,7 +41,7 @@ class _Problem(C.Structure):
                 ("implicit_mode", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("nthreads", C.c_int), ("integrator", C.c_int),
                 ("qirr", _dp), ("recon", C.c_int), ("face_fix", C.c_int), ("riemann", C.c_int),
-                ("bc_val", C.c_double * 30)]
+                ("bc_val", C.c_double * 30), ("hydro", C.c_int)]
 
 
 class _State(C.Structure):
@@ -74,6 +74,10 @@ def lib():
         L.orc_opacity.argtypes = [C.POINTER(_Problem), C.c_double, C.c_double, _dp, _dp, _dp]
         L.orc_dt.restype = C.c_double
         L.orc_dt.argtypes = [C.POINTER(_Problem)]
+        L.orc_dt_gas.restype = C.c_double
+        L.orc_dt_gas.argtypes = [C.POINTER(_Problem)] + [_dp] * 5
+        L.hydro_face_flux.argtypes = [C.POINTER(_Problem), C.POINTER(_State), C.c_int * 3,
+                                      C.c_int, _dp]
         L.orc_solve2x2.argtypes = [C.c_double] * 7 + [_dp, _dp]
         L.orc_solve2x2_irr.argtypes = [C.c_double] * 8 + [_dp, _dp]
         L.orc_step.restype = C.c_int
@@ -251,6 +255,7 @@ class Oracle:
         p.recon = _RECON[getattr(prob, "recon", "plm")]
         p.face_fix = _FIX[getattr(prob, "face_fix", "fpreserve")]
         p.riemann = _RIEMANN[getattr(prob, "riemann", "hll")]
+        p.hydro = int(bool(getattr(prob, "hydro", False)))
         for (d, side), v in getattr(prob, "bc_value", {}).items():
             for q in range(5):
                 p.bc_val[10 * d + 5 * side + q] = float(v[q])
@@ -294,6 +299,11 @@ class Oracle:
 
     # stepping --------------------------------------------------------------
     def dt(self) -> float:
+        """The CFL step: radiation alone, or with the gas signal speeds when
+        the gas is evolved."""
+        if self._p.hydro:
+            return lib().orc_dt_gas(C.byref(self._p), _ptr(self.rho), _ptr(self.e),
+                                    _ptr(self.m[0]), _ptr(self.m[1]), _ptr(self.m[2]))
         return lib().orc_dt(C.byref(self._p))
 
     def step(self, nsteps: int = 1, dt: Optional[float] = None):

@@ -20,6 +20,11 @@
  *   6. the HLL flux, or the Lax-Friedrichs-Rusanov flux (Sect. 2.5);
  *   7. finite-volume flux divergence with Cartesian, cylindrical or spherical
  *      metric (orthonormal components);
+ *   0. with `hydro`: a hydrodynamic step of the gas first (Sect. 2.4 orders
+ *      the substep as gas, radiation transport, radiation sources): PLM on
+ *      primitive variables, HLL with the Davis speeds, Cartesian divergence;
+ *      the radiation transport then takes its optical depths, and the
+ *      coupling its gas, from the gas after that step;
  *   8. the implicit matter-radiation coupling of Sect. 2.8, Eqs.
  *      (source_discrete2) and (implicit_matrix), optionally iterated to
  *      convergence (Newton mode) or reduced to absorption only (the shadow
@@ -115,6 +120,9 @@ typedef struct {
    * bc_val[d][side] = (E, F0, F1, F2, T), side 0 = lower, 1 = upper; FIXED
    * uses E, F and T, LTE only T (E = a T^4, F copied from the edge cell) */
   double bc_val[3][2][5];
+  /* 1: the gas is evolved too (Cartesian grids): a hydrodynamic step before
+   * the radiation transport in every (sub)step, Sect. 2.4 */
+  int hydro;
 } orc_problem;
 
 /* State: SoA arrays of N = n0 n1 n2 cells, x fastest.  Three flux and three
@@ -416,6 +424,29 @@ double orc_dt(const orc_problem *p) {
   return p->cfl / worst;
 }
 
+/* Time step with the gas (hydro): cfl over the largest sum over active
+ * directions of max(chat, |v_d| + c_s) / h_d, c_s = sqrt(Gamma p / rho). */
+double orc_dt_gas(const orc_problem *p, const double *rho, const double *e, const double *m0,
+                  const double *m1, const double *m2) {
+  double worst = 0.0;
+  const double *m[3] = {m0, m1, m2};
+  for (int k = 0; k < p->n[2]; ++k)
+    for (int j = 0; j < p->n[1]; ++j)
+      for (int i = 0; i < p->n[0]; ++i) {
+        size_t c = lin(p, i, j, k);
+        double h[3];
+        widths(p, i, j, k, h);
+        double cs = sqrt(p->gamma_gas * (p->gamma_gas - 1.0) * e[c] / rho[c]);
+        double sum = 0.0;
+        for (int d = 0; d < p->ndim; ++d) {
+          double v = fabs(m[d][c] / rho[c]) + cs;
+          sum += (v > p->chat ? v : p->chat) / h[d];
+        }
+        if (sum > worst) worst = sum;
+      }
+  return p->cfl / worst;
+}
+
 /* Cell volume and face areas (lower/upper face along each direction). */
 static void vol_area(const orc_problem *p, int i, int j, int k, double *V, double Alo[3],
                      double Ahi[3]) {
@@ -508,6 +539,124 @@ static double tau_cell(const orc_problem *p, const orc_state *s, const int a[3],
   double kp, kr, sg;
   orc_opacity(p, rho, T, &kp, &kr, &sg);
   return rho * (kr + sg) * max_active_width(p, b[0], b[1], b[2]);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Hydrodynamics (the gas step that precedes the radiation transport in each */
+/* substep, Sect. 2.4; a standard Godunov step: PLM on primitive variables, */
+/* HLL with the Davis signal speeds, Cartesian flux divergence)              */
+/* ------------------------------------------------------------------------ */
+
+/* Primitive gas state w = (rho, v0, v1, v2, p) of the cell with index a
+ * (a[d] possibly a ghost index along d), p = (Gamma - 1) e.  Ghost gas as in
+ * cell_values: wrapped or edge cells, mirrored with v_d negated
+ * (reflective), at rest with T = T_b and the edge density (fixed, LTE). */
+static void gas_prim(const orc_problem *p, const orc_state *s, const int a[3], int d,
+                     double w[5]) {
+  double u[4], rho, e;
+  cell_values(p, s, a, d, u, &rho, &e);
+  int b[3] = {a[0], a[1], a[2]};
+  int i = a[d], n = p->n[d];
+  b[d] = map_index(p, d, i);
+  size_t c = lin(p, b[0], b[1], b[2]);
+  double m[3] = {s->m0[c], s->m1[c], s->m2[c]};
+  if (i < 0 || i >= n) {
+    int bc = (i < 0) ? p->bc_lo[d] : p->bc_hi[d];
+    if (bc == ORC_BC_REFLECT) m[d] = -m[d];
+    if (bc == ORC_BC_FIXED || bc == ORC_BC_LTE) m[0] = m[1] = m[2] = 0.0;
+  }
+  w[0] = rho;
+  w[1] = m[0] / rho;
+  w[2] = m[1] / rho;
+  w[3] = m[2] / rho;
+  w[4] = (p->gamma_gas - 1.0) * e;
+}
+
+/* Conserved state (rho, m0, m1, m2, E_gas) and physical flux along d of a
+ * primitive state. */
+static void gas_flux(const orc_problem *p, const double w[5], int d, double U[5], double f[5]) {
+  double rho = w[0], pr = w[4];
+  double v2 = w[1] * w[1] + w[2] * w[2] + w[3] * w[3];
+  double Eg = pr / (p->gamma_gas - 1.0) + 0.5 * rho * v2;
+  double vd = w[1 + d];
+  U[0] = rho;
+  U[1] = rho * w[1];
+  U[2] = rho * w[2];
+  U[3] = rho * w[3];
+  U[4] = Eg;
+  f[0] = rho * vd;
+  f[1] = rho * vd * w[1];
+  f[2] = rho * vd * w[2];
+  f[3] = rho * vd * w[3];
+  f[1 + d] += pr;
+  f[4] = (Eg + pr) * vd;
+}
+
+/* HLL flux of the gas through the lower face of cell idx along d: PLM (van
+ * Leer, the same limited slopes as the radiation) of the primitive
+ * variables, signal speeds S_L = min(v_L - c_L, v_R - c_R) and
+ * S_R = max(v_L + c_L, v_R + c_R) with c = sqrt(Gamma p / rho). */
+void hydro_face_flux(const orc_problem *p, const orc_state *s, const int idx[3], int d,
+                     double out[5]) {
+  int a[3] = {idx[0], idx[1], idx[2]};
+  int i = idx[d];
+  double w[4][5];
+  for (int q = 0; q < 4; ++q) {
+    a[d] = i - 2 + q;
+    gas_prim(p, s, a, d, w[q]);
+  }
+  double xm2 = centre(p, d, i - 2), xm1 = centre(p, d, i - 1), x0 = centre(p, d, i),
+         xp1 = centre(p, d, i + 1);
+  double xf = p->xf[d][i];
+  double wl[5], wr[5];
+  for (int q = 0; q < 5; ++q) {
+    double s0 = orc_vanleer((w[1][q] - w[0][q]) / (xm1 - xm2), (w[2][q] - w[1][q]) / (x0 - xm1));
+    double s1 = orc_vanleer((w[2][q] - w[1][q]) / (x0 - xm1), (w[3][q] - w[2][q]) / (xp1 - x0));
+    wl[q] = w[1][q] + s0 * (xf - xm1);
+    wr[q] = w[2][q] + s1 * (xf - x0);
+  }
+  double UL[5], UR[5], fL[5], fR[5];
+  gas_flux(p, wl, d, UL, fL);
+  gas_flux(p, wr, d, UR, fR);
+  double cl = sqrt(p->gamma_gas * wl[4] / wl[0]), cr = sqrt(p->gamma_gas * wr[4] / wr[0]);
+  double sl = wl[1 + d] - cl, sr = wr[1 + d] + cr;
+  if (wr[1 + d] - cr < sl) sl = wr[1 + d] - cr;
+  if (wl[1 + d] + cl > sr) sr = wl[1 + d] + cl;
+  for (int q = 0; q < 5; ++q) {
+    if (sl >= 0.0)
+      out[q] = fL[q];
+    else if (sr <= 0.0)
+      out[q] = fR[q];
+    else
+      out[q] = (sr * fL[q] - sl * fR[q] + sl * sr * (UR[q] - UL[q])) / (sr - sl);
+  }
+}
+
+/* The gas after the hydrodynamic step of length dt of cell (i,j,k):
+ * g = (rho, m0, m1, m2, e) from the Cartesian flux divergence of the
+ * conserved (rho, m, E_gas). */
+static void hydro_cell(const orc_problem *p, const orc_state *s, double dt, int i, int j, int k,
+                       double g[5]) {
+  int idx[3] = {i, j, k};
+  size_t c = lin(p, i, j, k);
+  double rho = s->rho[c];
+  double m[3] = {s->m0[c], s->m1[c], s->m2[c]};
+  double U[5] = {rho, m[0], m[1], m[2],
+                 s->e[c] + 0.5 * (m[0] * m[0] + m[1] * m[1] + m[2] * m[2]) / rho};
+  for (int d = 0; d < p->ndim; ++d) {
+    double flo[5], fhi[5];
+    hydro_face_flux(p, s, idx, d, flo);
+    int up[3] = {i, j, k};
+    up[d] += 1;
+    hydro_face_flux(p, s, up, d, fhi);
+    double h = p->xf[d][idx[d] + 1] - p->xf[d][idx[d]];
+    for (int q = 0; q < 5; ++q) U[q] -= dt * (fhi[q] - flo[q]) / h;
+  }
+  g[0] = U[0];
+  g[1] = U[1];
+  g[2] = U[2];
+  g[3] = U[3];
+  g[4] = U[4] - 0.5 * (U[1] * U[1] + U[2] * U[2] + U[3] * U[3]) / U[0];
 }
 
 /* Right face state (side = +1) or left face state (side = -1) of cell ic
@@ -817,6 +966,34 @@ int orc_max_threads(void) {
 static void euler_pass(const orc_problem *p, const orc_state *s, orc_state *w, double dt,
                        int64_t tot[ORC_NSTATS]) {
   size_t N = (size_t)p->n[0] * p->n[1] * p->n[2];
+  /* with hydro: the hydrodynamic step first (all cells), then the radiation
+   * transport of E, F from s with the optical depths, the coupling and the
+   * bookkeeping on the gas after the hydro step (Sect. 2.4) */
+  orc_state r = *s;
+  double *gbuf = NULL;
+  if (p->hydro) {
+    gbuf = (double *)malloc(5 * N * sizeof(double));
+    if (!gbuf) return;
+    r.rho = gbuf;
+    r.m0 = gbuf + N;
+    r.m1 = gbuf + 2 * N;
+    r.m2 = gbuf + 3 * N;
+    r.e = gbuf + 4 * N;
+#pragma omp parallel for schedule(static)
+    for (long long cc = 0; cc < (long long)N; ++cc) {
+      int i = (int)(cc % p->n[0]);
+      int j = (int)((cc / p->n[0]) % p->n[1]);
+      int k = (int)(cc / ((long long)p->n[0] * p->n[1]));
+      double g[5];
+      hydro_cell(p, s, dt, i, j, k, g);
+      r.rho[cc] = g[0];
+      r.m0[cc] = g[1];
+      r.m1[cc] = g[2];
+      r.m2[cc] = g[3];
+      r.e[cc] = g[4];
+    }
+    s = &r;
+  }
 #pragma omp parallel
   {
     int64_t loc[ORC_NSTATS] = {0};
@@ -847,9 +1024,14 @@ static void euler_pass(const orc_problem *p, const orc_state *s, orc_state *w, d
       }
     }
   }
+  if (gbuf) {
+    memcpy(w->rho, gbuf, N * sizeof(double));
+    free(gbuf);
+  }
 }
 
-static void copy_state(const orc_state *from, orc_state *to, size_t N) {
+static void copy_state(const orc_state *from, orc_state *to, size_t N, int with_rho) {
+  if (with_rho) memcpy(to->rho, from->rho, N * sizeof(double));
   memcpy(to->E, from->E, N * sizeof(double));
   memcpy(to->F0, from->F0, N * sizeof(double));
   memcpy(to->F1, from->F1, N * sizeof(double));
@@ -860,16 +1042,18 @@ static void copy_state(const orc_state *from, orc_state *to, size_t N) {
   memcpy(to->m2, from->m2, N * sizeof(double));
 }
 
-/* s <- (s + u) / 2 for the conserved variables E_r, F_r, m and the total gas
- * energy E_gas = e + |m|^2 / (2 rho); e is recovered from the averaged E_gas
- * and m (the second stage of the RK2 / IMEX1 step). */
+/* s <- (s + u) / 2 for the conserved variables rho, E_r, F_r, m and the
+ * total gas energy E_gas = e + |m|^2 / (2 rho); e is recovered from the
+ * averaged E_gas, m and rho (the second stage of the RK2 / IMEX1 step). */
 static void average_into(orc_state *s, const orc_state *u, size_t N) {
 #pragma omp parallel for schedule(static)
   for (long long c = 0; c < (long long)N; ++c) {
-    double rho = s->rho[c];
-    double kn = (s->m0[c] * s->m0[c] + s->m1[c] * s->m1[c] + s->m2[c] * s->m2[c]) / (2.0 * rho);
-    double ku = (u->m0[c] * u->m0[c] + u->m1[c] * u->m1[c] + u->m2[c] * u->m2[c]) / (2.0 * rho);
+    double rn = s->rho[c], ru = u->rho[c];
+    double kn = (s->m0[c] * s->m0[c] + s->m1[c] * s->m1[c] + s->m2[c] * s->m2[c]) / (2.0 * rn);
+    double ku = (u->m0[c] * u->m0[c] + u->m1[c] * u->m1[c] + u->m2[c] * u->m2[c]) / (2.0 * ru);
     double eg = 0.5 * ((s->e[c] + kn) + (u->e[c] + ku));
+    double rho = (rn == ru) ? rn : 0.5 * (rn + ru);
+    s->rho[c] = rho;
     s->E[c] = 0.5 * (s->E[c] + u->E[c]);
     s->F0[c] = 0.5 * (s->F0[c] + u->F0[c]);
     s->F1[c] = 0.5 * (s->F1[c] + u->F1[c]);
@@ -896,7 +1080,7 @@ int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int ns
   orc_state u = {0};
   double *block = NULL;
   if (p->integrator == ORC_RK2) {
-    block = (double *)malloc(8 * N * sizeof(double));
+    block = (double *)malloc(9 * N * sizeof(double));
     if (!block) return -1;
     u.E = block;
     u.F0 = block + N;
@@ -906,18 +1090,19 @@ int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int ns
     u.m0 = block + 5 * N;
     u.m1 = block + 6 * N;
     u.m2 = block + 7 * N;
-    u.rho = s->rho;
+    u.rho = p->hydro ? block + 8 * N : s->rho;
   }
+  /* without hydro rho is constant and shared; with it each state has its own */
+  if (!p->hydro) w->rho = s->rho;
   for (int step = 0; step < nsteps; ++step) {
     int64_t tot[ORC_NSTATS] = {0};
     if (p->integrator == ORC_RK2) {
-      w->rho = s->rho;
       euler_pass(p, s, w, dt, tot);   /* stage 1: U1 in w */
       euler_pass(p, w, &u, dt, tot);  /* stage 2: U2 in u */
       average_into(s, &u, N);
     } else {
       euler_pass(p, s, w, dt, tot);
-      copy_state(w, s, N);
+      copy_state(w, s, N, p->hydro);
     }
     if (stats) {
       for (int q = 0; q < ORC_NSTATS; ++q) {
@@ -937,6 +1122,7 @@ int orc_step(const orc_problem *p, orc_state *s, orc_state *w, double dt, int ns
  * the old state): out has 9 values per cell, see cell_step. */
 int orc_step_cells(const orc_problem *p, const orc_state *s, double dt, long long ncells,
                    const long long *cells, double *out) {
+  if (p->hydro) return -2; /* needs the hydro step of the neighbours: use orc_step */
   set_threads(p);
 #pragma omp parallel for schedule(dynamic, 64)
   for (long long q = 0; q < ncells; ++q) {

@@ -56,6 +56,9 @@ class Problem:
     # boundary states of "fixed" and "lte" sides: {(d, side): (E, F0, F1, F2, T)},
     # side 0 = lower, 1 = upper ("lte" uses T only)
     bc_value: Dict = dataclasses.field(default_factory=dict)
+    # evolve the gas with a hydrodynamic step before the radiation transport
+    # (Cartesian grids)
+    hydro: bool = False
     newton_rtol: float = 1e-12
     newton_maxit: int = 50
     ncomp: int = 3
