@@ -49,7 +49,8 @@ def peaks():
 # sources the single-grid step kernel is compiled from (a change to any of
 # them invalidates the profiled DRAM traffic)
 STEP_SOURCES = ("m1_math.cuh", "m1_internal.h", "m1_cell.cuh", "m1_step.cuh", "m1_step_tma.cuh",
-                "m1_step_tma2.cuh", "tma.cuh", "step_launch.cuh", "step_split.cu", "step_fp64.cu")
+                "m1_step_tma2.cuh", "tma.cuh", "step_launch.cuh", "step_tables.cuh", "step_split.cu",
+                "step_fp64.cu")
 
 
 def kernel_hash():
