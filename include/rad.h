@@ -184,6 +184,14 @@ typedef struct {
                            form of the step kernel: its register-tiled shapes
                            only (rad_get_launch reports fewer than the default
                            form's on split 3D Cartesian grids) */
+  int hydro;            /* 1: evolve the gas too (Cartesian grids; RAD_EUNSUPPORTED
+                           otherwise).  Each (sub)step is then a gas step (PLM on
+                           rho, v, p; HLL with the Davis speeds; Gamma-law gas),
+                           then the radiation transport, then the sources
+                           (Sect. 2.4), the radiation reading its optical depths
+                           and its gas from the gas step's result.  rad_dt stays
+                           the radiation's CFL step: with gas faster than chat
+                           the caller passes a smaller dt */
 } rad_params;
 
 /* Counters accumulated by rad_step since the last rad_reset_stats. */
@@ -203,7 +211,7 @@ typedef struct rad_ctx rad_ctx;
 /* Fills *p with defaults: chat = c = 1, a_rad = 1, gamma = 5/3, mu = 1,
  * cfl = 0.4, e_floor = 1e-30, RAD_FP64, RAD_LINEARIZED_ONCE, rtol = 1e-12,
  * maxit = 50, ncomp = 3, use_mlp = 0, mlp_gate = 1e-2, RAD_EULER, irradiation = 0,
- * RAD_PLM, RAD_FIX_FPRESERVE, RAD_HLL.  Returns RAD_EINVAL if
+ * RAD_PLM, RAD_FIX_FPRESERVE, RAD_HLL, hydro = 0.  Returns RAD_EINVAL if
  * p is NULL. */
 rad_status rad_default_params(rad_params *p);
 

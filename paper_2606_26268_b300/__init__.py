@@ -66,7 +66,7 @@ class rad_params(C.Structure):
                 ("newton_rtol", C.c_double), ("newton_maxit", C.c_int), ("ncomp", C.c_int),
                 ("use_mlp", C.c_int), ("mlp_gate", C.c_double), ("integrator", C.c_int),
                 ("irradiation", C.c_int), ("reconstruction", C.c_int), ("face_fix", C.c_int),
-                ("riemann", C.c_int)]
+                ("riemann", C.c_int), ("hydro", C.c_int)]
 
 
 class rad_stats(C.Structure):
@@ -552,7 +552,8 @@ def from_problem(prob, precision: str = "fp64", device=None, **overrides) -> "Ra
                   irradiation=int(getattr(prob, "qirr", None) is not None),
                   reconstruction=getattr(prob, "recon", "plm"),
                   face_fix=getattr(prob, "face_fix", "fpreserve"),
-                  riemann=getattr(prob, "riemann", "hll"))
+                  riemann=getattr(prob, "riemann", "hll"),
+                  hydro=int(bool(getattr(prob, "hydro", False))))
     params.update(overrides)
     grid = dict(ndim=prob.ndim, n=prob.n, xfaces=prob.xfaces, bc_lo=prob.bc_lo, bc_hi=prob.bc_hi,
                 bc_value=dict(getattr(prob, "bc_value", {})))

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "m1_internal.h"
+#include "hydro_launch.h"
 #include "mlp_launch.h"
 #include "rad.h"
 #include "step_launch.h"
@@ -49,6 +50,11 @@ struct rad_ctx {
   size_t off_rho = 0, off_tab = 0, off_tab_dir[3] = {}, off_op32 = 0, off_op64 = 0;
   size_t off_stats = 0, off_status = 0, off_stage = 0;
   size_t off_qirr = size_t(-1);  // irradiation deposit (padded), if params.irradiation
+  // evolved gas (params.hydro): a density per state buffer, and the gas after
+  // the gas step (rho* goes to a state buffer's density, e* and m* here)
+  size_t off_rho_buf[3] = {};
+  size_t off_gas_e = 0, off_gas_m[3] = {};
+  m1::HydroFn hydro_fn = nullptr;
   size_t total = 0;
   cudaStream_t stream = nullptr;
   int cur = 0;

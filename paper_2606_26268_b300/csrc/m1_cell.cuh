@@ -201,6 +201,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
   // Sect. 2.9: E_gas gains dt (-div F_irr) (reloaded here rather than kept
   // live through the coupling)
   if (GEN && a.qirr) en += a.dt * T(__ldg(a.qirr + ic));
+  T rfin = T(rho_s);  // the cell's final density
   if (a.average) {
     // last stage of the two-stage step: average with U^n, which the output
     // buffer holds at this cell (only this thread reads or writes it)
@@ -210,10 +211,20 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
       mo[v] = T(a.out.m[v][ic]);
       ma[v] = T(0.5) * (mo[v] + mn[v]);
     }
-    const T h = T(0.5) * Ops<T>::rcp(T(rho_s));
-    const T ko = (mo[0] * mo[0] + mo[1] * mo[1] + mo[2] * mo[2]) * h;
+    T h = T(0.5) * Ops<T>::rcp(T(rho_s));
+    T ho = h, ha = h;
+    if constexpr (GEN) {
+      if (a.rho_avg) {  // the gas step moved rho: average it too
+        const T rn = T(a.rho_avg[ic]);
+        rfin = T(0.5) * (rn + T(rho_s));
+        ho = T(0.5) * Ops<T>::rcp(rn);
+        ha = T(0.5) * Ops<T>::rcp(rfin);
+        a.rho_avg[ic] = S(rfin);
+      }
+    }
+    const T ko = (mo[0] * mo[0] + mo[1] * mo[1] + mo[2] * mo[2]) * ho;
     const T kn = (mn[0] * mn[0] + mn[1] * mn[1] + mn[2] * mn[2]) * h;
-    const T ka = (ma[0] * ma[0] + ma[1] * ma[1] + ma[2] * ma[2]) * h;
+    const T ka = (ma[0] * ma[0] + ma[1] * ma[1] + ma[2] * ma[2]) * ha;
     const T eg = T(0.5) * ((T(a.out.e[ic]) + ko) + (en + kn));
     En = T(0.5) * (T(a.out.E[ic]) + En);
 #pragma unroll
@@ -246,7 +257,9 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
       const bool lo = gslot < 2;
       const int gpos = lo ? gslot - 2 : n + gslot - 2;  // -2, -1, n, n+1
       const int bc = lo ? Dm.bc_lo[d] : Dm.bc_hi[d];
-      if (bc == BC_FIXED) continue;
+      bool gas_held = false;  // evolved gas: keep the held gas ghosts in step
+      if constexpr (GEN) gas_held = a.hydro && (bc == BC_FIXED || bc == BC_LTE);
+      if (bc == BC_FIXED && !gas_held) continue;
       int src;
       if (bc == BC_PERIODIC)
         src = lo ? ((gpos % n) + n) % n : gpos % n;
@@ -256,6 +269,18 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
         src = lo ? 0 : n - 1;
       if (src != i) continue;
       const long long ig = ic + (long long)(gpos - i) * stride;
+      if constexpr (GEN) {
+        if (a.rho_avg) a.rho_avg[ig] = S(rfin);
+        if (gas_held) {
+          a.out.e[ig] = S(T(a.cp.cvfac) * rfin * T(a.bcT[d][lo ? 0 : 1]));
+#pragma unroll
+          for (int v = 0; v < NC; ++v) a.out.m[v][ig] = S(0);
+          if (bc == BC_LTE)
+#pragma unroll
+            for (int v = 0; v < NC; ++v) a.out.F[v][ig] = S(Fn[v]);
+          continue;
+        }
+      }
       const bool refl = bc == BC_REFLECT;
       const bool all = bc != BC_LTE;
       if (all) {

@@ -96,6 +96,14 @@ struct StepArgs {
   // (conserved variables E_r, F_r, m and E_gas = e + |m|^2 / (2 rho))
   int average;
   Scheme scheme;
+  // gas evolved by the gas step (general form only): the last stage of the
+  // two-stage step reads rho^n of the cell from rho_avg and stores the
+  // average of rho there (nullptr otherwise); `hydro` makes the epilogue
+  // keep the gas ghosts of the fixed and LTE sides (edge density, e =
+  // C_v T_b with the gas temperatures bcT)
+  S* rho_avg;
+  int hydro;
+  double bcT[3][2];
   const S* rho;
   GeomDev<T> geo;
   OpacityDev opac;

@@ -14,6 +14,7 @@
 #include <vector>
 
 #include "ctx_internal.h"
+#include "hydro.cuh"
 
 using namespace m1;
 
@@ -55,6 +56,7 @@ extern "C" rad_status rad_default_params(rad_params* p) {
   p->reconstruction = RAD_PLM;
   p->face_fix = RAD_FIX_FPRESERVE;
   p->riemann = RAD_HLL;
+  p->hydro = 0;
   return RAD_OK;
 }
 
@@ -192,6 +194,8 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   if (p.reconstruction < RAD_PLM || p.reconstruction > RAD_LIMO3) return RAD_EINVAL;
   if (p.face_fix < RAD_FIX_FPRESERVE || p.face_fix > RAD_FIX_CLIP) return RAD_EINVAL;
   if (p.riemann < RAD_HLL || p.riemann > RAD_LF) return RAD_EINVAL;
+  if (p.hydro != 0 && p.hydro != 1) return RAD_EINVAL;
+  if (p.hydro && geometry != RAD_CARTESIAN) return RAD_EUNSUPPORTED;
   if (p.implicit_mode == RAD_NEWTON && (!(p.newton_rtol > 0.0) || p.newton_maxit < 1))
     return RAD_EINVAL;
   if (p.ncomp < 1 || p.ncomp > 3) return RAD_EINVAL;
@@ -284,7 +288,15 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   // absorption-only coupling and the irradiation deposit (register-tiled
   // shapes only); the default form compiles them out
   c->general = p.reconstruction != RAD_PLM || p.face_fix != RAD_FIX_FPRESERVE ||
-               p.riemann != RAD_HLL || p.irradiation || p.implicit_mode == RAD_ABSORPTION_ONLY;
+               p.riemann != RAD_HLL || p.irradiation || p.implicit_mode == RAD_ABSORPTION_ONLY ||
+               p.hydro;
+  if (p.hydro) {
+    c->hydro_fn = select_hydro(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
+    if (!c->hydro_fn) {
+      delete c;
+      return RAD_EUNSUPPORTED;
+    }
+  }
   c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform,
                             c->general);
   c->qpass = select_queue_pass(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
@@ -323,6 +335,11 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
       c->off_state[b][k] = used ? take(arr) : size_t(-1);
     }
   c->off_rho = take(arr);
+  if (p.hydro) {
+    for (int b = 0; b < c->nbuf; ++b) c->off_rho_buf[b] = b == 0 ? c->off_rho : take(arr);
+    c->off_gas_e = take(arr);
+    for (int q = 0; q < c->nc; ++q) c->off_gas_m[q] = take(arr);
+  }
   if (p.irradiation) c->off_qirr = take(arr);
   const size_t tsz = c->esize;
   for (int d = 0; d < 3; ++d) c->off_tab_dir[d] = take(size_t(TAB_N) * c->len[d] * tsz);
@@ -545,6 +562,12 @@ static void* state_ptr(rad_ctx* c, int b, int k) {
   return o == size_t(-1) ? nullptr : c->ws + o;
 }
 
+// Density of state buffer b: one shared array, or one per buffer when the
+// gas is evolved.
+static void* rho_ptr(rad_ctx* c, int b) {
+  return c->ws + (c->par.hydro ? c->off_rho_buf[b] : c->off_rho);
+}
+
 // Copies `count` values from the caller (host or device) to a device flat
 // array and returns it: the staging area for host input, else the pointer.
 static const void* stage_in(rad_ctx* c, const void* src, size_t count, int slot, int on_device,
@@ -564,7 +587,8 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
   // rho first (flat copy kept in stage slot 0 while m and e are built)
   const S* r = static_cast<const S*>(stage_in(c, rho, c->N, 0, dev, &st));
   if (st) return st;
-  if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_rho), r, r, PK_COPY, FK_RHO))) return st;
+  for (int b = 0; b < (c->par.hydro ? c->nbuf : 1); ++b)
+    if ((st = pack<S>(c, static_cast<S*>(rho_ptr(c, b)), r, r, PK_COPY, FK_RHO))) return st;
   // v: ncomp arrays (host input goes through stage slot 1 one component at a
   // time); internal components beyond ncomp are zero
   for (int comp = 0; comp < c->nc; ++comp) {
@@ -683,7 +707,11 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   a.stash = a.out;
   a.average = 0;
   a.qirr = c->off_qirr != size_t(-1) ? reinterpret_cast<const S*>(c->ws + c->off_qirr) : nullptr;
-  a.rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
+  a.rho = static_cast<const S*>(rho_ptr(c, in_buf));
+  a.rho_avg = nullptr;
+  a.hydro = c->par.hydro;
+  for (int d = 0; d < 3; ++d)
+    for (int side = 0; side < 2; ++side) a.bcT[d][side] = c->bc_val[d][side][4];
   for (int d = 0; d < 3; ++d) {
     a.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
     a.geo.len[d] = c->len[d];
@@ -819,7 +847,7 @@ static const void* tma_maps(rad_ctx* c, int variant, int in_buf) {
   const cuuint32_t estr[3] = {1, 1, 1};
   for (int b = 0; b < c->nbuf; ++b) {
     void* fields[6] = {state_ptr(c, b, 0), state_ptr(c, b, 1), state_ptr(c, b, 2),
-                       state_ptr(c, b, 3), c->ws + c->off_rho, state_ptr(c, b, 4)};
+                       state_ptr(c, b, 3), rho_ptr(c, b), state_ptr(c, b, 4)};
     for (int f = 0; f < 6; ++f) {
       if (!fields[f] || reinterpret_cast<uintptr_t>(fields[f]) % 16) return nullptr;
       if (enc(&t.maps[b][f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fields[f], dims, strides, box,
@@ -856,6 +884,43 @@ static int spare_buffer(const rad_ctx* c) { return (c->cur + 1) % c->nbuf; }
 // profiling is on.  stash_buf >= 0: the last stage of the two-stage step,
 // whose result is averaged in place with the U^n held by out_buf; queued
 // cells then leave (E*, F*) in stash_buf.
+// The gas step of a pass (evolved gas): from the gas of state buffer in_buf
+// to rho* in the density of buffer rho_buf and e*, m* in the gas arrays.
+template <class P>
+static cudaError_t enqueue_gas(rad_ctx* c, double dt, int in_buf, int rho_buf) {
+  using S = typename P::S;
+  using T = typename P::T;
+  HydroArgs<P> h{};
+  h.dim = c->dims;
+  for (int d = 0; d < 3; ++d) {
+    h.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
+    h.geo.len[d] = c->len[d];
+    for (int side = 0; side < 2; ++side) h.bcT[d][side] = T(c->bc_val[d][side][4]);
+  }
+  h.rho = static_cast<const S*>(rho_ptr(c, in_buf));
+  h.e = static_cast<const S*>(state_ptr(c, in_buf, 4));
+  h.rho_out = static_cast<S*>(rho_ptr(c, rho_buf));
+  h.e_out = reinterpret_cast<S*>(c->ws + c->off_gas_e);
+  for (int q = 0; q < 3; ++q) {
+    h.m[q] = q < c->nc ? static_cast<const S*>(state_ptr(c, in_buf, 5 + q)) : nullptr;
+    h.m_out[q] = q < c->nc ? reinterpret_cast<S*>(c->ws + c->off_gas_m[q]) : nullptr;
+  }
+  h.dt = T(dt);
+  h.gamma = T(c->par.gamma_gas);
+  h.cvfac = T(1.0 / (c->par.mu * (c->par.gamma_gas - 1.0)));
+  return c->hydro_fn(&h, c->stream);
+}
+
+// The radiation step of a pass with evolved gas reads its gas (rho*, e*, m*)
+// from the gas step's output instead of the input buffer.
+template <class P>
+static void gas_inputs(rad_ctx* c, StepArgs<P>& a, int rho_buf) {
+  using S = typename P::S;
+  a.rho = static_cast<const S*>(rho_ptr(c, rho_buf));
+  a.in.e = reinterpret_cast<S*>(c->ws + c->off_gas_e);
+  for (int q = 0; q < c->nc; ++q) a.in.m[q] = reinterpret_cast<S*>(c->ws + c->off_gas_m[q]);
+}
+
 static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
                                int stash_buf = -1) {
   const bool queue = c->par.implicit_mode == RAD_NEWTON;
@@ -865,15 +930,27 @@ static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
   if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
                    cudaSuccess)
     return RAD_ECUDA;
+  cudaError_t e = cudaSuccess;
+  // evolved gas: the gas step writes rho* to the output buffer's density, or
+  // (last stage of the two-stage step, whose output buffer still holds U^n)
+  // to the stash buffer's
+  const int rho_buf = stash_buf >= 0 ? stash_buf : out_buf;
+  if (c->par.hydro)
+    e = c->esize == 8 ? enqueue_gas<Fp64>(c, dt, in_buf, rho_buf)
+                      : enqueue_gas<Split>(c, dt, in_buf, rho_buf);
+  if (e != cudaSuccess) return RAD_ECUDA;
   cudaEvent_t* ev = c->prof_n < c->prof_cap ? &c->prof_ev[3 * size_t(c->prof_n++)] : nullptr;
   if (ev) cudaEventRecord(ev[0], c->stream);
-  cudaError_t e;
   if (c->esize == 8) {
     StepArgs<Fp64> a{};
     fill_args<Fp64>(c, a, dt, in_buf, out_buf);
     if (stash_buf >= 0) {
       fill_fields<double>(c, stash_buf, a.stash);
       a.average = 1;
+    }
+    if (c->par.hydro) {
+      gas_inputs<Fp64>(c, a, rho_buf);
+      if (stash_buf >= 0) a.rho_avg = static_cast<double*>(rho_ptr(c, out_buf));
     }
     e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
     if (ev) cudaEventRecord(ev[1], c->stream);
@@ -884,6 +961,10 @@ static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
     if (stash_buf >= 0) {
       fill_fields<float>(c, stash_buf, a.stash);
       a.average = 1;
+    }
+    if (c->par.hydro) {
+      gas_inputs<Split>(c, a, rho_buf);
+      if (stash_buf >= 0) a.rho_avg = static_cast<float*>(rho_ptr(c, out_buf));
     }
     e = c->launch.fn(&a, maps, c->stream, c->variant, c->chunk);
     if (ev) cudaEventRecord(ev[1], c->stream);
@@ -959,7 +1040,7 @@ extern "C" rad_status rad_profile_end(rad_ctx* c, float* step_ms, float* queue_m
 
 extern "C" int rad_launches_per_step(const rad_ctx* c) {
   if (!c) return 0;
-  const int pass = c->par.implicit_mode == RAD_NEWTON ? 2 : 1;
+  const int pass = (c->par.implicit_mode == RAD_NEWTON ? 2 : 1) + (c->par.hydro ? 1 : 0);
   return c->par.integrator == RAD_RK2 ? 2 * pass : pass;
 }
 
@@ -1255,7 +1336,7 @@ extern "C" rad_status rad_sync(rad_ctx* c) {
 template <class S>
 static rad_status read_t(rad_ctx* c, int field, void* dst, int dev) {
   const double cvfac = 1.0 / (c->par.mu * (c->par.gamma_gas - 1.0));
-  const S* rho = reinterpret_cast<const S*>(c->ws + c->off_rho);
+  const S* rho = static_cast<const S*>(rho_ptr(c, c->cur));
   int ncomp = (field == RAD_FIELD_F || field == RAD_FIELD_M) ? c->par.ncomp : 1;
   for (int comp = 0; comp < ncomp; ++comp) {
     const S* src;

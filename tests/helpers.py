@@ -36,7 +36,7 @@ def run_gpu(p, nsteps, precision="fp64", dt=None, **overrides):
         dt = r.dt()
     r.step(nsteps, dt)
     st = r.sync()
-    out = {k: np.asarray(r.read(k), dtype=np.float64) for k in ("E", "F", "e", "m", "T")}
+    out = {k: np.asarray(r.read(k), dtype=np.float64) for k in ("E", "F", "e", "m", "T", "rho")}
     out["stats"] = r.stats()
     out["status"] = st
     out["dt"] = dt
@@ -49,8 +49,8 @@ def run_oracle(p, nsteps, dt=None, nthreads=0):
     if dt is None:
         dt = o.dt()
     o.step(nsteps, dt)
-    return {"E": o.E, "F": o.F, "e": o.e, "m": o.m, "T": o.temperature(), "stats": o.stats,
-            "dt": dt}
+    return {"E": o.E, "F": o.F, "e": o.e, "m": o.m, "T": o.temperature(), "rho": o.rho,
+            "stats": o.stats, "dt": dt}
 
 
 def errors(g, o, ncomp, chat, ratio=1.0, nsteps=1):

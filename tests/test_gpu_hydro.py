@@ -1,0 +1,110 @@
+"""Parity of the GPU gas step + radiation step (evolved gas, Sect. 2.4 order:
+gas step, radiation transport, radiation sources) with the FP64 oracle:
+Sod's tube, random 1D-3D states with every boundary kind, the two-stage
+step and the Newton coupling; FP64 per cell within 1e-11, split normwise."""
+import numpy as np
+import pytest
+
+import oracle
+import workloads as W
+from helpers import errors, rounded, run_gpu, run_oracle
+from test_gpu_options import with_bcs
+from test_gpu_parity import CASES, _opacity
+from test_oracle_hydro import exact_riemann, gas_1d
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-11
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_26268_b300 import build
+    build.build()
+
+
+def check_gas64(p, nsteps, tol=TOL64):
+    dt = oracle.Oracle(p).dt()  # with the gas signal speeds
+    g = run_gpu(p, nsteps, "fp64", dt=dt)
+    o = run_oracle(p, nsteps, dt=dt)
+    assert g["status"] == 0, g["status"]
+    err = errors(g, o, p.ncomp, p.chat, p.c / p.chat, nsteps)
+    err["rho"] = np.max(np.abs(g["rho"] - o["rho"]) / o["rho"])
+    for k, v in err.items():
+        assert v <= tol, (p.name, k, v, err)
+    return g, o, err
+
+
+@pytest.mark.parametrize("integrator", ["euler", "rk2"])
+def test_sod_fp64_matches_oracle(integrator):
+    p, x = gas_1d(400, lambda x: np.where(x < 0.5, 1.0, 0.125), lambda x: np.zeros_like(x),
+                  lambda x: np.where(x < 0.5, 1.0, 0.1), integrator=integrator)
+    check_gas64(p, 60)
+
+
+def test_sod_on_the_gpu_matches_the_exact_solution():
+    import paper_2606_26268_b300 as R
+    p, x = gas_1d(400, lambda x: np.where(x < 0.5, 1.0, 0.125), lambda x: np.zeros_like(x),
+                  lambda x: np.where(x < 0.5, 1.0, 0.1))
+    r = R.from_problem(p, "fp64")
+    # fixed step from the initial signal speeds (c_s = 1.18 on the left)
+    dt = 0.4 / (400 * 1.2)
+    n = int(round(0.2 / dt))
+    r.step(n, 0.2 / n)
+    rho = np.asarray(r.read("rho"), dtype=np.float64)
+    assert r.sync() == 0
+    r.close()
+    ex = exact_riemann((1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4, (x - 0.5) / 0.2)
+    assert np.mean(np.abs(rho - ex[0])) < 0.0025
+
+
+HYD_CASES = [
+    (0, ("reflective",), ("fixed",), "euler"),
+    (1, ("periodic",), ("periodic",), "rk2"),
+    (3, ("reflective", "lte"), ("fixed", "reflective"), "rk2"),
+    (2, ("outflow", "periodic"), ("reflective", "periodic"), "euler"),
+    (5, ("reflective", "lte", "fixed"), ("fixed", "reflective", "outflow"), "rk2"),
+    (4, ("periodic", "periodic", "periodic"), ("periodic", "periodic", "periodic"), "euler"),
+]
+
+
+@pytest.mark.parametrize("k,lo,hi,integrator", HYD_CASES)
+def test_gas_and_radiation_fp64_match_oracle(k, lo, hi, integrator):
+    geom, n, ndim, bc, nc, logr, kind = CASES[k]
+    p = W.random_smooth(geom, n, ndim, seed=1200 + k, bc="outflow", opacity=_opacity(kind),
+                        ncomp=nc, fmax=0.8)
+    p = with_bcs(p, lo, hi, seed=k)
+    p.hydro = True
+    p.integrator = integrator
+    check_gas64(p, 4)
+
+
+def test_gas_with_newton_coupling_and_options_fp64():
+    geom, n, ndim, bc, nc, logr, kind = CASES[5]
+    p = W.random_smooth(geom, n, ndim, seed=1301, bc=bc, opacity=_opacity(kind), ncomp=nc,
+                        fmax=0.8)
+    p.hydro = True
+    p.integrator = "rk2"
+    p.implicit_mode = "newton"
+    p.recon = "limo3"
+    check_gas64(p, 3)
+
+
+def test_gas_split_normwise():
+    p = W.random_smooth("cartesian", (70, 41, 39), 3, seed=1400, bc="periodic", ncomp=3,
+                        fmax=0.8)
+    p.hydro = True
+    p.integrator = "rk2"
+    q = rounded(p, np.float32)
+    dt = oracle.Oracle(q).dt()
+    g = run_gpu(q, 5, "split", dt=dt)
+    o = run_oracle(q, 5, dt=dt)
+    assert g["status"] == 0
+    for key in ("E", "e"):
+        err = np.linalg.norm(g[key] - o[key]) / np.linalg.norm(o[key])
+        assert err <= 1e-5, (key, err)
+    err = np.linalg.norm(g["m"] - o["m"]) / np.linalg.norm(o["m"])
+    assert err <= 1e-5, ("m", err)

@@ -375,6 +375,32 @@ def shadow(n: Tuple[int, int] = (140, 40), coupling: str = "absorb") -> Problem:
     return p
 
 
+def pulse_3d_rhd(n: int = 256, nsteps: int = 20) -> Problem:
+    """The paper's performance workload (Sect. 4): the Cartesian pulse test
+    of Sect. 3 with the gas evolved and the two-stage step.  Box [-50, 50]^3,
+    rho = 1, v = 0, gas at T0, E = a T_r^4 with T_r = T0 (1 + 100 e^(-r^2/w^2)),
+    w = 5, F = 0, no absorption, scattering only (optically thin), Gamma =
+    5/3, chat = c = 1 (velocity unit c), CFL 0.4, outflow.  The paper's T0
+    and units leave the radiation and gas energies unspecified; here T0 =
+    1e-6 (sound speed ~1e-3 c) and a_R = 1e8 put the pulse's peak energy at
+    1e-2 of the gas energy, so that the gas stays nearly static as in the
+    paper's run, and keep E^2 inside FP32's normal range."""
+    xf = make_faces("cartesian", (n, n, n), [(-50.0, 50.0)] * 3)
+    p = _blank("rhd_pulse3d_%d" % n, 3, (n, n, n), "cartesian", "outflow", xf, chat=1.0,
+               ncomp=3, nsteps=nsteps, integrator="rk2", hydro=True)
+    T0 = 1e-6
+    p.a_rad = 1e8
+    x, y, z = mesh(p)
+    r2 = x * x + y * y + z * z
+    p.rho = np.ones(p.N)
+    p.v = np.zeros((3, p.N))
+    p.T = np.full(p.N, T0)
+    p.E = p.a_rad * (T0 * (1.0 + 100.0 * np.exp(-r2 / 25.0))) ** 4
+    p.F = np.zeros((3, p.N))
+    p.opacity = {"kind": "const", "kappa_p": 0.0, "kappa_r": 0.0, "sigma": 1e-6}
+    return p
+
+
 def uniform_state(geometry: str, n: Tuple[int, int, int], ndim: int, log_r: bool = False,
                   extents=None, E: float = 2.0, kappa: float = 0.5) -> Problem:
     """A uniform isotropic state (E const, F = 0) in equilibrium with the gas
