@@ -19,6 +19,9 @@
 struct TmaSet {
   int bx = 0, by = 0;
   CUtensorMap maps[3][6];
+  // evolved gas: E, F0..F2 of the input buffer, rho* of a buffer's density
+  // and e* of the gas arrays, per (input buffer, density buffer)
+  CUtensorMap gas[3][3][6];
 };
 
 struct rad_ctx {
@@ -54,7 +57,8 @@ struct rad_ctx {
   // the gas step (rho* goes to a state buffer's density, e* and m* here)
   size_t off_rho_buf[3] = {};
   size_t off_gas_e = 0, off_gas_m[3] = {};
-  m1::HydroFn hydro_fn = nullptr;
+  m1::HydroFn hydro_fn = nullptr, gas_cfl_fn = nullptr;
+  size_t off_cfl = 0;  // reduction word of the gas CFL rate
   size_t total = 0;
   cudaStream_t stream = nullptr;
   int cur = 0;

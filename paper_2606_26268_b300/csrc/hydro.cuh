@@ -6,10 +6,9 @@
 // S_L = min(v_L - c_L, v_R - c_R), S_R = max(v_L + c_L, v_R + c_R), and the
 // flux divergence of (rho, m, E_gas).
 //
-// One thread per cell computes the fluxes of its two faces in every active
-// direction (each face twice, once by each of its cells) from the padded
-// input buffer, whose ghost cells the previous step left up to date.  The
-// result (rho*, m*, e*) goes to separate arrays: the radiation kernel that
+// The kernel reads the padded input buffer, whose ghost cells the previous
+// step left up to date, and computes every face flux once.  The result
+// (rho*, m*, e*) goes to separate arrays: the radiation kernel that
 // follows reads rho* and e* of neighbouring cells for its optical depths
 // while it writes the final gas, so it must not read them from the arrays it
 // writes.  The thread also writes the ghost copies of rho* and e* that its
@@ -35,19 +34,6 @@ struct HydroArgs {
   T bcT[3][2];       // gas temperature of the fixed and LTE sides
 };
 
-// Primitive state (rho, v0, v1, v2, p) of the padded cell ip.
-template <class P, int NC>
-__device__ __forceinline__ void gas_w(const HydroArgs<P>& h, long long ip,
-                                      typename P::T (&w)[5]) {
-  using T = typename P::T;
-  const T r = T(__ldg(h.rho + ip));
-  const T ir = Ops<T>::rcp(r);
-  w[0] = r;
-#pragma unroll
-  for (int v = 0; v < 3; ++v) w[1 + v] = v < NC ? T(__ldg(h.m[v] + ip)) * ir : T(0);
-  w[4] = (h.gamma - T(1)) * T(__ldg(h.e + ip));
-}
-
 // Conserved state and physical flux along D of a primitive state.
 template <class T, int NC, int D>
 __device__ __forceinline__ void gas_flux(const T (&w)[5], T gamma, T (&U)[5], T (&f)[5]) {
@@ -67,22 +53,14 @@ __device__ __forceinline__ void gas_flux(const T (&w)[5], T gamma, T (&U)[5], T 
   f[4] = (Eg + p) * vd;
 }
 
-// HLL flux of the face between the padded cells ip - s and ip along D (s the
-// padded stride of D, pi the padded coordinate of ip along D).
-template <class P, int NC, int D>
-__device__ __forceinline__ void gas_face(const HydroArgs<P>& h, long long ip, long long s, int pi,
-                                         typename P::T (&out)[5]) {
-  using T = typename P::T;
-  T w0[5], w1[5], w2[5], w3[5];
-  gas_w<P, NC>(h, ip - 2 * s, w0);
-  gas_w<P, NC>(h, ip - s, w1);
-  gas_w<P, NC>(h, ip, w2);
-  gas_w<P, NC>(h, ip + s, w3);
-  const T* tab = h.geo.tab[D];
-  const int len = h.geo.len[D];
-  const T ix0 = __ldg(tab + TAB_IDXC * len + pi - 2), ix1 = __ldg(tab + TAB_IDXC * len + pi - 1),
-          ix2 = __ldg(tab + TAB_IDXC * len + pi);
-  const T hh = __ldg(tab + TAB_HHI * len + pi - 1), hl = __ldg(tab + TAB_HLO * len + pi);
+// HLL flux of the face between the cells of primitive states w1 and w2 along
+// D, with their outer neighbours w0 and w3: ix0..ix2 the inverse centre
+// distances of (w0, w1), (w1, w2), (w2, w3), hh and hl the offsets of the face
+// from the centres of w1 and w2.
+template <class T, int NC, int D>
+__device__ __forceinline__ void gas_riemann(const T (&w0)[5], const T (&w1)[5], const T (&w2)[5],
+                                            const T (&w3)[5], T ix0, T ix1, T ix2, T hh, T hl,
+                                            T gamma, T (&out)[5]) {
   T wl[5], wr[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -91,10 +69,10 @@ __device__ __forceinline__ void gas_face(const HydroArgs<P>& h, long long ip, lo
     wr[q] = w2[q] + vanleer(d1, d2) * hl;
   }
   T UL[5], UR[5], fL[5], fR[5];
-  gas_flux<T, NC, D>(wl, h.gamma, UL, fL);
-  gas_flux<T, NC, D>(wr, h.gamma, UR, fR);
-  const T cl = Ops<T>::sqrt_(Ops<T>::div(h.gamma * wl[4], wl[0]));
-  const T cr = Ops<T>::sqrt_(Ops<T>::div(h.gamma * wr[4], wr[0]));
+  gas_flux<T, NC, D>(wl, gamma, UL, fL);
+  gas_flux<T, NC, D>(wr, gamma, UR, fR);
+  const T cl = Ops<T>::sqrt_(Ops<T>::div(gamma * wl[4], wl[0]));
+  const T cr = Ops<T>::sqrt_(Ops<T>::div(gamma * wr[4], wr[0]));
   T sl = wl[1 + D] - cl, sr = wr[1 + D] + cr;
   if (wr[1 + D] - cr < sl) sl = wr[1 + D] - cr;
   if (wl[1 + D] + cl > sr) sr = wl[1 + D] + cl;
@@ -111,85 +89,271 @@ __device__ __forceinline__ void gas_face(const HydroArgs<P>& h, long long ip, lo
   }
 }
 
-template <class P, int NC, int D>
-__device__ __forceinline__ void gas_direction(const HydroArgs<P>& h, long long ic, int pi,
-                                              typename P::T (&U)[5]) {
-  using T = typename P::T;
-  const long long s = D == 0 ? 1ll : (D == 1 ? h.dim.sy : h.dim.sz);
-  T flo[5], fhi[5];
-  gas_face<P, NC, D>(h, ic, s, pi, flo);
-  gas_face<P, NC, D>(h, ic + s, s, pi + 1, fhi);
-  const T ih = __ldg(h.geo.tab[D] + TAB_ALO * h.geo.len[D] + pi);  // 1 / width (Cartesian)
-#pragma unroll
-  for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (fhi[q] - flo[q]);
+template <class T>
+__device__ __forceinline__ T gtab(const GeomDev<T>& G, int d, int slot, int ip) {
+  return __ldg(G.tab[d] + slot * G.len[d] + ip);
 }
 
-template <class P, int NDIM, int NC>
-__global__ void __launch_bounds__(128) hydro_kernel(const __grid_constant__ HydroArgs<P> h) {
+// The gas step.  A CTA of TX x TY threads owns a TX x TY tile of cells in x
+// (and y) and marches along z (3D).  Per z plane the CTA stages the
+// primitive states of the tile and a 2-cell halo in shared memory; each
+// thread computes the flux of its cell's lower x (and y) face, the threads of
+// the last column (row) also the upper tile face, and every face is computed
+// once.  The z faces come from the column's states held in registers, the
+// upper face of one plane being the lower face of the next.
+template <class P, int NDIM, int NC, int TX, int TY>
+__global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ HydroArgs<P> h) {
   using S = typename P::S;
   using T = typename P::T;
+  constexpr bool HY = NDIM >= 2, HZ = NDIM >= 3;
+  constexpr int SX = TX + 4, SY = HY ? TY + 4 : 1, OY = HY ? 2 : 0;
+  constexpr int NT = TX * TY;
+  __shared__ T s_w[5][SY][SX];
+  __shared__ T s_fx[5][TY][TX + 1];
+  __shared__ T s_fy[5][HY ? TY + 1 : 1][TX];
+
   const StepDims& Dm = h.dim;
-  const long long N = (long long)Dm.n[0] * Dm.n[1] * Dm.n[2];
-  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
-       q += (long long)gridDim.x * blockDim.x) {
-    int ci[3];
-    long long r = q;
-    ci[0] = int(r % Dm.n[0]);
-    r /= Dm.n[0];
-    ci[1] = int(r % Dm.n[1]);
-    ci[2] = int(r / Dm.n[1]);
-    const int p0 = ci[0] + Dm.g[0], p1 = ci[1] + Dm.g[1], p2 = ci[2] + Dm.g[2];
-    const long long ic = p0 + Dm.sy * p1 + Dm.sz * p2;
-    const T rho = T(h.rho[ic]);
-    T U[5];
-    U[0] = rho;
-    T ke = T(0);
+  const GeomDev<T>& G = h.geo;
+  const int tx = threadIdx.x, ty = HY ? threadIdx.y : 0;
+  const int tid = tx + TX * ty;
+  const int x0 = blockIdx.x * TX, y0 = HY ? blockIdx.y * TY : 0;
+  const int cx = x0 + tx, cy = y0 + ty;
+  const bool upd = cx < Dm.n[0] && (!HY || cy < Dm.n[1]);
+  const int chunk = HZ ? (Dm.n[2] + gridDim.z - 1) / gridDim.z : 1;
+  const int z0 = HZ ? blockIdx.z * chunk : 0;
+  const int z1 = HZ ? min(z0 + chunk, Dm.n[2]) : 1;
+  // padded coordinates of the own cell (clamped inside the array for the
+  // threads past the grid's edge, which update nothing)
+  const int px = min(cx, Dm.n[0] - 1) + Dm.g[0];
+  const int py = HY ? min(cy, Dm.n[1] - 1) + Dm.g[1] : 0;
+  const long long col = px + Dm.sy * (long long)py;
+  const long long sz = Dm.sz;
+  const int gz = Dm.g[2];
+
+  auto prim = [&](long long ip, T (&w)[5]) {
+    const T r = T(__ldg(h.rho + ip));
+    const T ir = Ops<T>::rcp(r);
+    w[0] = r;
 #pragma unroll
-    for (int v = 0; v < 3; ++v) {
-      U[1 + v] = v < NC ? T(h.m[v][ic]) : T(0);
-      ke += U[1 + v] * U[1 + v];
+    for (int v = 0; v < 3; ++v) w[1 + v] = v < NC ? T(__ldg(h.m[v] + ip)) * ir : T(0);
+    w[4] = (h.gamma - T(1)) * T(__ldg(h.e + ip));
+  };
+
+  // the own column's states at z - 2 .. z + 2, and the flux of the face below
+  T wz[5][5];
+  T fzlo[5] = {0, 0, 0, 0, 0};
+  if constexpr (HZ) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) prim(col + (long long)(z0 - 2 + k + gz) * sz, wz[k]);
+    const int pz = z0 + gz;
+    gas_riemann<T, NC, 2>(wz[0], wz[1], wz[2], wz[3], gtab(G, 2, TAB_IDXC, pz - 2),
+                          gtab(G, 2, TAB_IDXC, pz - 1), gtab(G, 2, TAB_IDXC, pz),
+                          gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, fzlo);
+  }
+
+  for (int z = z0; z < z1; ++z) {
+    const long long zoff = (long long)(z + gz) * sz;
+    // stage the plane: tile plus a 2-cell halo, coordinates clamped to the
+    // padded array
+    for (int k = tid; k < SX * SY; k += NT) {
+      const int iy = k / SX, ix = k - iy * SX;
+      const int gx = min(max(x0 - 2 + ix + Dm.g[0], 0), Dm.n[0] + 2 * Dm.g[0] - 1);
+      const int gy = HY ? min(max(y0 - OY + iy + Dm.g[1], 0), Dm.n[1] + 2 * Dm.g[1] - 1) : 0;
+      T w[5];
+      prim(gx + Dm.sy * (long long)gy + zoff, w);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) s_w[q][iy][ix] = w[q];
     }
-    U[4] = T(h.e[ic]) + T(0.5) * ke * Ops<T>::rcp(rho);
-    gas_direction<P, NC, 0>(h, ic, p0, U);
-    if constexpr (NDIM >= 2) gas_direction<P, NC, 1>(h, ic, p1, U);
-    if constexpr (NDIM >= 3) gas_direction<P, NC, 2>(h, ic, p2, U);
-    T k2 = T(0);
+    if constexpr (HZ) prim(col + (long long)(z + 2 + gz) * sz, wz[4]);
+    __syncthreads();
+    // x faces: the lower one of the own cell, and the tile's upper one
+    {
+      auto xface = [&](int c, T (&f)[5]) {  // face between tile columns c - 1 and c
+        T a0[5], a1[5], a2[5], a3[5];
 #pragma unroll
-    for (int v = 0; v < NC; ++v) k2 += U[1 + v] * U[1 + v];
-    const T en = U[4] - T(0.5) * k2 * Ops<T>::rcp(U[0]);
-    h.rho_out[ic] = S(U[0]);
-    h.e_out[ic] = S(en);
+        for (int q = 0; q < 5; ++q) {
+          a0[q] = s_w[q][ty + OY][c];
+          a1[q] = s_w[q][ty + OY][c + 1];
+          a2[q] = s_w[q][ty + OY][c + 2];
+          a3[q] = s_w[q][ty + OY][c + 3];
+        }
+        const int pc = min(x0 + c, Dm.n[0]) + Dm.g[0];
+        gas_riemann<T, NC, 0>(a0, a1, a2, a3, gtab(G, 0, TAB_IDXC, pc - 2),
+                              gtab(G, 0, TAB_IDXC, pc - 1), gtab(G, 0, TAB_IDXC, pc),
+                              gtab(G, 0, TAB_HHI, pc - 1), gtab(G, 0, TAB_HLO, pc), h.gamma, f);
+      };
+      T f[5];
+      xface(tx, f);
 #pragma unroll
-    for (int v = 0; v < NC; ++v) h.m_out[v][ic] = S(U[1 + v]);
-    // ghost copies of rho* and e* (the optical depths of the radiation step
-    // read them): wrapped, edge or mirrored; the fixed and LTE sides take the
-    // edge density and e = C_v T_b
+      for (int q = 0; q < 5; ++q) s_fx[q][ty][tx] = f[q];
+      if (tx == TX - 1) {
+        xface(TX, f);
 #pragma unroll
-    for (int d = 0; d < NDIM; ++d) {
-      const int n = Dm.n[d];
-      const int i = ci[d];
-      if (i >= 2 && i < n - 2) continue;
-      const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
-#pragma unroll
-      for (int gslot = 0; gslot < 4; ++gslot) {
-        const bool lo = gslot < 2;
-        const int gpos = lo ? gslot - 2 : n + gslot - 2;
-        const int bc = lo ? Dm.bc_lo[d] : Dm.bc_hi[d];
-        int src;
-        if (bc == BC_PERIODIC)
-          src = lo ? ((gpos % n) + n) % n : gpos % n;
-        else if (bc == BC_REFLECT)
-          src = min(max(lo ? -1 - gpos : 2 * n - 1 - gpos, 0), n - 1);
-        else
-          src = lo ? 0 : n - 1;
-        if (src != i) continue;
-        const long long ig = ic + (long long)(gpos - i) * stride;
-        h.rho_out[ig] = S(U[0]);
-        const bool held = bc == BC_FIXED || bc == BC_LTE;
-        h.e_out[ig] = S(held ? h.cvfac * U[0] * h.bcT[d][lo ? 0 : 1] : en);
+        for (int q = 0; q < 5; ++q) s_fx[q][ty][TX] = f[q];
       }
     }
+    if constexpr (HY) {
+      auto yface = [&](int r, T (&f)[5]) {  // face between tile rows r - 1 and r
+        T a0[5], a1[5], a2[5], a3[5];
+#pragma unroll
+        for (int q = 0; q < 5; ++q) {
+          a0[q] = s_w[q][r][tx + 2];
+          a1[q] = s_w[q][r + 1][tx + 2];
+          a2[q] = s_w[q][r + 2][tx + 2];
+          a3[q] = s_w[q][r + 3][tx + 2];
+        }
+        const int pr = min(y0 + r, Dm.n[1]) + Dm.g[1];
+        gas_riemann<T, NC, 1>(a0, a1, a2, a3, gtab(G, 1, TAB_IDXC, pr - 2),
+                              gtab(G, 1, TAB_IDXC, pr - 1), gtab(G, 1, TAB_IDXC, pr),
+                              gtab(G, 1, TAB_HHI, pr - 1), gtab(G, 1, TAB_HLO, pr), h.gamma, f);
+      };
+      T f[5];
+      yface(ty, f);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) s_fy[q][ty][tx] = f[q];
+      if (ty == TY - 1) {
+        yface(TY, f);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) s_fy[q][TY][tx] = f[q];
+      }
+    }
+    // z face above the own cell
+    T fzhi[5] = {0, 0, 0, 0, 0};
+    if constexpr (HZ) {
+      const int pz = z + 1 + gz;
+      gas_riemann<T, NC, 2>(wz[1], wz[2], wz[3], wz[4], gtab(G, 2, TAB_IDXC, pz - 2),
+                            gtab(G, 2, TAB_IDXC, pz - 1), gtab(G, 2, TAB_IDXC, pz),
+                            gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, fzhi);
+    }
+    __syncthreads();
+    if (upd) {
+      const long long ic = col + zoff;
+      T U[5];
+      {
+        const T r = T(__ldg(h.rho + ic));
+        U[0] = r;
+        T ke = T(0);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) {
+          U[1 + v] = v < NC ? T(__ldg(h.m[v] + ic)) : T(0);
+          ke += U[1 + v] * U[1 + v];
+        }
+        U[4] = T(__ldg(h.e + ic)) + T(0.5) * ke * Ops<T>::rcp(r);
+      }
+      {
+        const T ih = gtab(G, 0, TAB_ALO, px);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (s_fx[q][ty][tx + 1] - s_fx[q][ty][tx]);
+      }
+      if constexpr (HY) {
+        const T ih = gtab(G, 1, TAB_ALO, py);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (s_fy[q][ty + 1][tx] - s_fy[q][ty][tx]);
+      }
+      if constexpr (HZ) {
+        const T ih = gtab(G, 2, TAB_ALO, z + gz);
+#pragma unroll
+        for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (fzhi[q] - fzlo[q]);
+      }
+      T k2 = T(0);
+#pragma unroll
+      for (int v = 0; v < NC; ++v) k2 += U[1 + v] * U[1 + v];
+      const T en = U[4] - T(0.5) * k2 * Ops<T>::rcp(U[0]);
+      h.rho_out[ic] = S(U[0]);
+      h.e_out[ic] = S(en);
+#pragma unroll
+      for (int v = 0; v < NC; ++v) h.m_out[v][ic] = S(U[1 + v]);
+      // ghost copies of rho* and e* (the optical depths of the radiation
+      // step read them): wrapped, edge or mirrored; the fixed and LTE sides
+      // take the edge density and e = C_v T_b
+      const int ci[3] = {cx, cy, z};
+#pragma unroll
+      for (int d = 0; d < NDIM; ++d) {
+        const int n = Dm.n[d];
+        const int i = ci[d];
+        if (i >= 2 && i < n - 2) continue;
+        const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
+#pragma unroll
+        for (int gslot = 0; gslot < 4; ++gslot) {
+          const bool lo = gslot < 2;
+          const int gpos = lo ? gslot - 2 : n + gslot - 2;
+          const int bc = lo ? Dm.bc_lo[d] : Dm.bc_hi[d];
+          int src;
+          if (bc == BC_PERIODIC)
+            src = lo ? ((gpos % n) + n) % n : gpos % n;
+          else if (bc == BC_REFLECT)
+            src = min(max(lo ? -1 - gpos : 2 * n - 1 - gpos, 0), n - 1);
+          else
+            src = lo ? 0 : n - 1;
+          if (src != i) continue;
+          const long long ig = ic + (long long)(gpos - i) * stride;
+          h.rho_out[ig] = S(U[0]);
+          const bool held = bc == BC_FIXED || bc == BC_LTE;
+          h.e_out[ig] = S(held ? h.cvfac * U[0] * h.bcT[d][lo ? 0 : 1] : en);
+        }
+      }
+    }
+    if constexpr (HZ) {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) fzlo[q] = fzhi[q];
+#pragma unroll
+      for (int k = 0; k < 4; ++k)
+#pragma unroll
+        for (int q = 0; q < 5; ++q) wz[k][q] = wz[k + 1][q];
+    }
+    __syncthreads();  // the plane and the fluxes are read before the next plane lands
   }
+}
+
+// The CFL step with the gas: the largest over cells of
+// sum_d max(chat, |v_d| + c_s) / h_d (c_s = sqrt(Gamma (Gamma - 1) e / rho)),
+// reduced into *out as the bits of a non-negative double (whose order is
+// the order of the bit patterns).
+template <class P>
+struct GasCflArgs {
+  using S = typename P::S;
+  using T = typename P::T;
+  StepDims dim;
+  GeomDev<T> geo;
+  const S* rho;
+  const S* e;
+  const S* m[3];
+  double chat, gamma;
+  unsigned long long* out;
+};
+
+template <class P, int NDIM, int NC>
+__global__ void __launch_bounds__(256) gas_cfl_kernel(const __grid_constant__ GasCflArgs<P> g) {
+  const StepDims& Dm = g.dim;
+  const long long N = (long long)Dm.n[0] * Dm.n[1] * Dm.n[2];
+  double worst = 0.0;
+  for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
+       q += (long long)gridDim.x * blockDim.x) {
+    long long r = q;
+    const int i = int(r % Dm.n[0]);
+    r /= Dm.n[0];
+    const int j = int(r % Dm.n[1]);
+    const int k = int(r / Dm.n[1]);
+    const int pc[3] = {i + Dm.g[0], j + Dm.g[1], k + Dm.g[2]};
+    const long long ic = pc[0] + Dm.sy * pc[1] + Dm.sz * pc[2];
+    const double rho = double(g.rho[ic]);
+    const double cs = sqrt(g.gamma * (g.gamma - 1.0) * double(g.e[ic]) / rho);
+    double sum = 0.0;
+#pragma unroll
+    for (int d = 0; d < NDIM; ++d) {
+      const double v = fabs(double(g.m[d][ic]) / rho) + cs;
+      const double w = double(g.geo.tab[d][TAB_WID * g.geo.len[d] + pc[d]]);
+      sum += (v > g.chat ? v : g.chat) / w;
+    }
+    worst = sum > worst ? sum : worst;
+  }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) {
+    const double o = __shfl_down_sync(0xffffffffu, worst, off);
+    worst = o > worst ? o : worst;
+  }
+  if ((threadIdx.x & 31) == 0)
+    atomicMax(g.out, static_cast<unsigned long long>(__double_as_longlong(worst)));
 }
 
 }  // namespace m1

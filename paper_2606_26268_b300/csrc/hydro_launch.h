@@ -9,4 +9,8 @@ namespace m1 {
 typedef cudaError_t (*HydroFn)(const void* args, cudaStream_t stream);
 HydroFn select_hydro(bool split, int ndim, int nc);
 
+// Launches the reduction of the gas CFL rate; `args` points to the
+// GasCflArgs of the precision policy.
+HydroFn select_gas_cfl(bool split, int ndim, int nc);
+
 }  // namespace m1

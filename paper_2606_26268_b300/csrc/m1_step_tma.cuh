@@ -44,7 +44,9 @@ constexpr size_t tma_smem_bytes() {
   return size_t(kTmaRing) * (NC + 3) * TmaTile<TX, TY>::BOXP * sizeof(float) + 128;
 }
 
-template <class P, int NC, bool UNI, int TX, int TY, int MINB>
+// GEN: the general coupling and epilogue (absorption only, irradiation,
+// evolved gas); the face computation is always the default scheme.
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN = false>
 __global__ void __launch_bounds__(TX * TY, MINB)
     step_tma_kernel(const __grid_constant__ StepArgs<P> a, const __grid_constant__ TmaMaps tm) {
   static_assert(P::kSplit, "TMA staging is built for the split precision");
@@ -302,7 +304,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       bool queued = false;
       CoupleOut co;
       if (a.queue_cap) {
-        co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
+        co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;
         const unsigned int mask = __activemask();
         const unsigned int want = __ballot_sync(mask, queued);
@@ -319,13 +321,13 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {
             queued = false;  // queue full: iterate here
-            co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
+            co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
           }
         }
       } else {
-        co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
+        co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
-      if (!queued) finish_cell<P, NDIM, NC, false>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+      if (!queued) finish_cell<P, NDIM, NC, GEN>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {

@@ -292,13 +292,16 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
                p.hydro;
   if (p.hydro) {
     c->hydro_fn = select_hydro(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
-    if (!c->hydro_fn) {
+    c->gas_cfl_fn = select_gas_cfl(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
+    if (!c->hydro_fn || !c->gas_cfl_fn) {
       delete c;
       return RAD_EUNSUPPORTED;
     }
   }
+  const bool options =
+      p.reconstruction != RAD_PLM || p.face_fix != RAD_FIX_FPRESERVE || p.riemann != RAD_HLL;
   c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform,
-                            c->general);
+                            c->general, options);
   c->qpass = select_queue_pass(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
   if (!c->launch.fn) {
     delete c;
@@ -339,6 +342,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
     for (int b = 0; b < c->nbuf; ++b) c->off_rho_buf[b] = b == 0 ? c->off_rho : take(arr);
     c->off_gas_e = take(arr);
     for (int q = 0; q < c->nc; ++q) c->off_gas_m[q] = take(arr);
+    c->off_cfl = take(sizeof(unsigned long long));
   }
   if (p.irradiation) c->off_qirr = take(arr);
   const size_t tsz = c->esize;
@@ -435,10 +439,57 @@ extern "C" rad_status rad_set_stream(rad_ctx* c, void* stream) {
   return RAD_OK;
 }
 
+static void* state_ptr(rad_ctx* c, int b, int k);
+static void* rho_ptr(rad_ctx* c, int b);
+
+template <class P>
+static cudaError_t enqueue_gas_cfl(rad_ctx* c) {
+  using S = typename P::S;
+  using T = typename P::T;
+  GasCflArgs<P> g{};
+  g.dim = c->dims;
+  for (int d = 0; d < 3; ++d) {
+    g.geo.tab[d] = reinterpret_cast<const T*>(c->ws + c->off_tab_dir[d]);
+    g.geo.len[d] = c->len[d];
+  }
+  g.rho = static_cast<const S*>(rho_ptr(c, c->cur));
+  g.e = static_cast<const S*>(state_ptr(c, c->cur, 4));
+  for (int q = 0; q < 3; ++q)
+    g.m[q] = q < c->nc ? static_cast<const S*>(state_ptr(c, c->cur, 5 + q)) : nullptr;
+  g.chat = c->par.chat;
+  g.gamma = c->par.gamma_gas;
+  g.out = reinterpret_cast<unsigned long long*>(c->ws + c->off_cfl);
+  return c->gas_cfl_fn(&g, c->stream);
+}
+
+// The CFL step: the radiation's (fixed by the grid), or with evolved gas the
+// step of the current state, max(chat, |v_d| + c_s) per direction (reduced
+// on the device; the call waits for it).
+static rad_status current_dt(rad_ctx* c, double* dt) {
+  if (!c->par.hydro) {
+    *dt = c->dt_cfl;
+    return RAD_OK;
+  }
+  if (!c->ws || !c->have_gas) return RAD_EINVAL;
+  unsigned long long bits = 0;
+  if (cudaMemsetAsync(c->ws + c->off_cfl, 0, sizeof(bits), c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  cudaError_t e = c->esize == 8 ? enqueue_gas_cfl<Fp64>(c) : enqueue_gas_cfl<Split>(c);
+  if (e != cudaSuccess ||
+      cudaMemcpyAsync(&bits, c->ws + c->off_cfl, sizeof(bits), cudaMemcpyDeviceToHost,
+                      c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  double rate;
+  std::memcpy(&rate, &bits, sizeof(rate));
+  if (!(rate > 0.0) || !std::isfinite(rate)) return RAD_ENONPHYS;
+  *dt = c->par.cfl / rate;
+  return RAD_OK;
+}
+
 extern "C" rad_status rad_dt(const rad_ctx* c, double* dt) {
   if (!c || !dt) return RAD_EINVAL;
-  *dt = c->dt_cfl;
-  return RAD_OK;
+  return current_dt(const_cast<rad_ctx*>(c), dt);
 }
 
 // ---------------------------------------------------------------------------
@@ -829,12 +880,12 @@ static EncodeTiledFn encode_tiled() {
 // maps cannot be encoded.  Each map views one padded field array as a 3D
 // tensor (pn0, pn1, pn2) with boxes of bx x by x 1 elements; reads outside
 // the array are zero-filled.
-static const void* tma_maps(rad_ctx* c, int variant, int in_buf) {
+static const void* tma_maps(rad_ctx* c, int variant, int in_buf, int rho_buf = -1) {
   if (variant < 0 || variant >= kMaxVariants) return nullptr;
   const int bx = c->launch.tma_box[variant][0], by = c->launch.tma_box[variant][1];
   if (bx <= 0 || c->esize != 4 || c->ndim != 3 || c->nc != 3 || !c->ws) return nullptr;
   for (const TmaSet& t : c->tma)
-    if (t.bx == bx && t.by == by) return t.maps[in_buf];
+    if (t.bx == bx && t.by == by) return rho_buf < 0 ? t.maps[in_buf] : t.gas[in_buf][rho_buf];
   EncodeTiledFn enc = encode_tiled();
   if (!enc) return nullptr;
   TmaSet t;
@@ -845,19 +896,28 @@ static const void* tma_maps(rad_ctx* c, int variant, int in_buf) {
   const cuuint64_t strides[2] = {cuuint64_t(D.pn[0]) * 4, cuuint64_t(D.pn[0]) * D.pn[1] * 4};
   const cuuint32_t box[3] = {cuuint32_t(bx), cuuint32_t(by), 1};
   const cuuint32_t estr[3] = {1, 1, 1};
+  auto encode = [&](CUtensorMap* m, void* ptr) {
+    if (!ptr || reinterpret_cast<uintptr_t>(ptr) % 16) return false;
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, ptr, dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+  };
   for (int b = 0; b < c->nbuf; ++b) {
     void* fields[6] = {state_ptr(c, b, 0), state_ptr(c, b, 1), state_ptr(c, b, 2),
                        state_ptr(c, b, 3), rho_ptr(c, b), state_ptr(c, b, 4)};
-    for (int f = 0; f < 6; ++f) {
-      if (!fields[f] || reinterpret_cast<uintptr_t>(fields[f]) % 16) return nullptr;
-      if (enc(&t.maps[b][f], CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, fields[f], dims, strides, box,
-              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-              CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
-        return nullptr;
-    }
+    for (int f = 0; f < 6; ++f)
+      if (!encode(&t.maps[b][f], fields[f])) return nullptr;
+    if (c->par.hydro)
+      for (int rb = 0; rb < c->nbuf; ++rb) {
+        void* gf[6] = {fields[0], fields[1], fields[2], fields[3], rho_ptr(c, rb),
+                       c->ws + c->off_gas_e};
+        for (int f = 0; f < 6; ++f)
+          if (!encode(&t.gas[b][rb][f], gf[f])) return nullptr;
+      }
   }
   c->tma.push_back(t);
-  return c->tma.back().maps[in_buf];
+  return rho_buf < 0 ? c->tma.back().maps[in_buf] : c->tma.back().gas[in_buf][rho_buf];
 }
 
 size_t ctx_args_size(const rad_ctx* c) {
@@ -925,7 +985,9 @@ static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
                                int stash_buf = -1) {
   const bool queue = c->par.implicit_mode == RAD_NEWTON;
   const bool staged = c->launch.tma_box[c->variant][0] > 0;
-  const void* maps = staged ? tma_maps(c, c->variant, in_buf) : nullptr;
+  const int rho_buf = stash_buf >= 0 ? stash_buf : out_buf;
+  const void* maps =
+      staged ? tma_maps(c, c->variant, in_buf, c->par.hydro ? rho_buf : -1) : nullptr;
   if (staged && !maps) return RAD_EUNSUPPORTED;
   if (queue && cudaMemsetAsync(c->ws + c->off_qcount, 0, sizeof(unsigned int), c->stream) !=
                    cudaSuccess)
@@ -934,7 +996,6 @@ static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
   // evolved gas: the gas step writes rho* to the output buffer's density, or
   // (last stage of the two-stage step, whose output buffer still holds U^n)
   // to the stash buffer's
-  const int rho_buf = stash_buf >= 0 ? stash_buf : out_buf;
   if (c->par.hydro)
     e = c->esize == 8 ? enqueue_gas<Fp64>(c, dt, in_buf, rho_buf)
                       : enqueue_gas<Split>(c, dt, in_buf, rho_buf);
@@ -978,10 +1039,13 @@ extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
   if (!c || nsteps < 0) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
-  if (!(dt > 0.0)) dt = c->dt_cfl;
+  const bool auto_dt = !(dt > 0.0);
+  if (auto_dt) dt = c->dt_cfl;
   if (!std::isfinite(dt)) return RAD_EINVAL;
   for (int s = 0; s < nsteps; ++s) {
     rad_status st;
+    // evolved gas: the CFL step of the current state, every step
+    if (auto_dt && c->par.hydro && (st = current_dt(c, &dt)) != RAD_OK) return st;
     if (c->par.integrator == RAD_RK2) {
       // stage 1 into b1; stage 2 from b1 straight into the average with U^n
       const int b1 = (c->cur + 1) % 3, b2 = (c->cur + 2) % 3;

@@ -30,14 +30,14 @@ cudaError_t launch_shape(StepArgs<P> a, cudaStream_t s, int chunk) {
   return cudaGetLastError();
 }
 
-template <class P, int NC, bool UNI, int TX, int TY, int MINB>
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN>
 cudaError_t launch_tma(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk) {
   if (!tma) return cudaErrorInvalidValue;
   const int* n = a.dim.n;
   a.chunk = chunk > 0 ? chunk : 32;
   if (a.chunk > n[2]) a.chunk = n[2];
   constexpr size_t smem = tma_smem_bytes<NC, TX, TY>();
-  auto kern = step_tma_kernel<P, NC, UNI, TX, TY, MINB>;
+  auto kern = step_tma_kernel<P, NC, UNI, TX, TY, MINB, GEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   TmaMaps maps;
@@ -47,14 +47,14 @@ cudaError_t launch_tma(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk
   return cudaGetLastError();
 }
 
-template <class P, int NC, bool UNI, int TX, int TY, int MINB>
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN>
 cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk) {
   if (!tma) return cudaErrorInvalidValue;
   const int* n = a.dim.n;
   a.chunk = chunk > 0 ? chunk : 32;
   if (a.chunk > n[2]) a.chunk = n[2];
   constexpr size_t smem = tma2_smem_bytes<NC, TX, TY>();
-  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB>;
+  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB, GEN>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   TmaMaps maps;
@@ -69,10 +69,11 @@ cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chun
 // (variants 4, 5) and with non-overlapping tiles (6, 7), each at 2 or 3
 // CTAs/SM; 2D rows of 128, 256 or 64 threads; 1D: 128.  Curvilinear grids
 // get the default shape only.  The general form (GEN: face options,
-// absorption only, irradiation) has the register-tiled shapes only.
-template <class P, int NDIM, int GEOM, int NC, bool UNI, bool GEN = false>
+// absorption only, irradiation, evolved gas) has the TMA-staged shapes only
+// when it keeps the default face scheme (TMA_OK).
+template <class P, int NDIM, int GEOM, int NC, bool UNI, bool GEN = false, bool TMA_OK = true>
 struct Shapes {
-  static constexpr bool tma = !GEN && P::kSplit && GEOM == kCart && NDIM == 3;
+  static constexpr bool tma = TMA_OK && P::kSplit && GEOM == kCart && NDIM == 3;
   static constexpr int count =
       (GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 8 : 4) : 3);
   static cudaError_t launch(const void* vargs, const void* maps, cudaStream_t s, int variant,
@@ -81,10 +82,10 @@ struct Shapes {
     if (variant < 0 || variant >= count) variant = 0;
     if constexpr (NDIM == 3) {
       if constexpr (tma) {
-        if (variant == 4) return launch_tma<P, NC, UNI, 32, 8, 2>(a, maps, s, chunk);
-        if (variant == 5) return launch_tma<P, NC, UNI, 32, 8, 3>(a, maps, s, chunk);
-        if (variant == 6) return launch_tma2<P, NC, UNI, 32, 8, 2>(a, maps, s, chunk);
-        if (variant == 7) return launch_tma2<P, NC, UNI, 32, 8, 3>(a, maps, s, chunk);
+        if (variant == 4) return launch_tma<P, NC, UNI, 32, 8, 2, GEN>(a, maps, s, chunk);
+        if (variant == 5) return launch_tma<P, NC, UNI, 32, 8, 3, GEN>(a, maps, s, chunk);
+        if (variant == 6) return launch_tma2<P, NC, UNI, 32, 8, 2, GEN>(a, maps, s, chunk);
+        if (variant == 7) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN>(a, maps, s, chunk);
       }
       if constexpr (count > 1) {
         if (variant == 1) return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 3, GEN>(a, s, chunk);
@@ -104,9 +105,10 @@ struct Shapes {
   }
 };
 
-template <class P, int NDIM, int GEOM, int NC, bool UNI = false, bool GEN = false>
+template <class P, int NDIM, int GEOM, int NC, bool UNI = false, bool GEN = false,
+          bool TMA_OK = true>
 LaunchEntry entry() {
-  using Sh = Shapes<P, NDIM, GEOM, NC, UNI, GEN>;
+  using Sh = Shapes<P, NDIM, GEOM, NC, UNI, GEN, TMA_OK>;
   LaunchEntry e{&Sh::launch, Sh::count, {}};
   if constexpr (Sh::tma) {
     for (int v = 4; v < 6; ++v) {

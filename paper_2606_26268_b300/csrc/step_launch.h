@@ -19,7 +19,10 @@ struct LaunchEntry {
 };
 
 // The launcher for (precision, active directions, geometry, carried flux
-// components, uniform Cartesian spacing, general form); fn == nullptr when
-// that combination is not instantiated.  The general form carries the face
-// options, the absorption-only coupling and the irradiation deposit.
-LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform, bool general);
+// components, uniform Cartesian spacing, general form, face options);
+// fn == nullptr when that combination is not instantiated.  The general form
+// carries the absorption-only coupling, the irradiation deposit and the
+// evolved gas, and with `options` the face options of Sect. 2.5, which the
+// TMA-staged shapes do not implement.
+LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform, bool general,
+                          bool options);

@@ -4,6 +4,6 @@
 
 namespace m1 {
 LaunchEntry select_split(int ndim, int geom, int nc, bool uni) {
-  return select_table<Split, false>(ndim, geom, nc, uni);
+  return select_table<Split, false>(ndim, geom, nc, uni, true);
 }
 }  // namespace m1

@@ -6,15 +6,18 @@
 
 namespace m1 {
 
+// tma: offer the TMA-staged shapes (split 3D Cartesian; the general form
+// only when it keeps the default face scheme).
 template <class P, bool GEN>
-LaunchEntry select_table(int ndim, int geom, int nc, bool uni) {
+LaunchEntry select_table(int ndim, int geom, int nc, bool uni, bool tma) {
   if (geom == kCart && uni) {
     if (ndim == 1 && nc == 1) return entry<P, 1, kCart, 1, true, GEN>();
     if (ndim == 1 && nc == 2) return entry<P, 1, kCart, 2, true, GEN>();
     if (ndim == 1 && nc == 3) return entry<P, 1, kCart, 3, true, GEN>();
     if (ndim == 2 && nc == 2) return entry<P, 2, kCart, 2, true, GEN>();
     if (ndim == 2 && nc == 3) return entry<P, 2, kCart, 3, true, GEN>();
-    if (ndim == 3 && nc == 3) return entry<P, 3, kCart, 3, true, GEN>();
+    if (ndim == 3 && nc == 3)
+      return tma ? entry<P, 3, kCart, 3, true, GEN, true>() : entry<P, 3, kCart, 3, true, GEN, false>();
     return LaunchEntry{nullptr, 0};
   }
   if (geom == kCart) {
@@ -23,7 +26,8 @@ LaunchEntry select_table(int ndim, int geom, int nc, bool uni) {
     if (ndim == 1 && nc == 3) return entry<P, 1, kCart, 3, false, GEN>();
     if (ndim == 2 && nc == 2) return entry<P, 2, kCart, 2, false, GEN>();
     if (ndim == 2 && nc == 3) return entry<P, 2, kCart, 3, false, GEN>();
-    if (ndim == 3 && nc == 3) return entry<P, 3, kCart, 3, false, GEN>();
+    if (ndim == 3 && nc == 3)
+      return tma ? entry<P, 3, kCart, 3, false, GEN, true>() : entry<P, 3, kCart, 3, false, GEN, false>();
     return LaunchEntry{nullptr, 0};
   }
   if (nc != 3) return LaunchEntry{nullptr, 0};

@@ -108,3 +108,50 @@ def test_gas_split_normwise():
         assert err <= 1e-5, (key, err)
     err = np.linalg.norm(g["m"] - o["m"]) / np.linalg.norm(o["m"])
     assert err <= 1e-5, ("m", err)
+
+
+def test_gas_cfl_step_matches_oracle_and_drives_automatic_steps():
+    """rad_dt with evolved gas is the CFL step of the current state
+    (max(chat, |v_d| + c_s) per direction), and rad_step with dt <= 0 takes
+    it anew every step."""
+    import paper_2606_26268_b300 as R
+    p, x = gas_1d(300, lambda x: np.where(x < 0.5, 1.0, 0.125), lambda x: 0.3 * np.ones_like(x),
+                  lambda x: np.where(x < 0.5, 1.0, 0.1))
+    o = oracle.Oracle(p)
+    r = R.from_problem(p, "fp64")
+    assert r.dt() == pytest.approx(o.dt(), rel=1e-14)
+    for _ in range(5):
+        o.step(1, o.dt())
+    r.step(5, 0.0)
+    assert r.sync() == 0
+    assert r.dt() == pytest.approx(o.dt(), rel=1e-12)
+    np.testing.assert_allclose(np.asarray(r.read("rho"), dtype=np.float64), o.rho, rtol=1e-12)
+    r.close()
+
+
+def test_gas_on_every_launch_shape():
+    """With evolved gas the TMA-staged kernels read rho* and e* through their
+    own tensor maps: every shape gives the same split RK2 steps."""
+    import paper_2606_26268_b300 as R
+    p = rounded(W.random_smooth("cartesian", (70, 41, 39), 3, seed=1500, bc="periodic", ncomp=3,
+                                fmax=0.8), np.float32)
+    p.hydro = True
+    p.integrator = "rk2"
+    dt = oracle.Oracle(p).dt()
+    ref = None
+    r0 = R.from_problem(p, "split")
+    nvar = r0.get_launch()[2]
+    r0.close()
+    assert nvar == 8
+    for v in (0, 2, 5, 7):
+        r = R.from_problem(p, "split")
+        r.set_launch(v, 0)
+        r.step(3, dt)
+        assert r.sync() == 0
+        out = np.concatenate([np.asarray(r.read(k), dtype=np.float64).ravel()
+                              for k in ("E", "e", "rho")])
+        r.close()
+        if ref is None:
+            ref = out
+        else:
+            assert np.max(np.abs(out - ref) / np.abs(ref)) <= 1e-6, v
