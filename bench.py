@@ -50,7 +50,7 @@ def peaks():
 # them invalidates the profiled DRAM traffic)
 STEP_SOURCES = ("m1_math.cuh", "m1_internal.h", "m1_cell.cuh", "m1_step.cuh", "m1_step_tma.cuh",
                 "m1_step_tma2.cuh", "tma.cuh", "step_launch.cuh", "step_tables.cuh", "step_split.cu",
-                "step_fp64.cu")
+                "step_fp64.cu", "hydro.cuh")
 
 
 def kernel_hash():
@@ -464,13 +464,20 @@ def run_ours(args):
         srr = rr.sync()
         rr.close()
         pass_ms = msr / nr / 2
+        gas_ms = pass_ms - ktr["step_kernel_ms"] - ktr["queue_pass_ms"]
+        gas_bytes = (40 if args.precision != "fp64" else 80) * pr.N
         forms["rhd_pulse3d"] = {
             "workload": pr.name, "cells": pr.N, "value": pr.N * nr / (msr * 1e-3), "unit": UNIT,
             "ms_per_step": msr / nr, "steps": nr,
             "form": "gas step + radiation transport + coupling per stage, two-stage RK2, "
                     "single solve (no absorption), scattering only",
             "radiation_kernel_ms_per_pass": ktr["step_kernel_ms"],
-            "gas_step_ms_per_pass": pass_ms - ktr["step_kernel_ms"] - ktr["queue_pass_ms"],
+            "gas_step_ms_per_pass": gas_ms,
+            "gas_step_roofline": {
+                "bound": "hbm", "achieved": gas_bytes / (gas_ms * 1e-3) / 1e9, "peak": hbm,
+                "unit": "GB/s", "frac": gas_bytes / (gas_ms * 1e-3) / 1e9 / hbm,
+                "bytes_per_cell": gas_bytes // pr.N,
+                "traffic": profiled_traffic(pr.name, args.precision + "/gas_step")},
             "launches_per_step": 4, "status": int(srr),
             "launch": {"variant": tvr[0], "chunk": tvr[1]},
             "paper": "7.6e8 (MI250X node) and 1.2e9 (MI300 node) cell updates/s for this "
