@@ -40,6 +40,43 @@ __device__ __forceinline__ float lg2_approx(float x) {
   return r;
 }
 
+// Packed pairs of FP32 values: the f32x2 arithmetic of sm_100 and later
+// does both lanes in one instruction.  A state (E, F0, F1, F2) is two pairs;
+// each lane is the IEEE round-to-nearest result of the scalar operation.
+__device__ __forceinline__ unsigned long long f2_pack(float2 a) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a.x), "f"(a.y));
+  return r;
+}
+__device__ __forceinline__ float2 f2_unpack(unsigned long long r) {
+  float2 a;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a.x), "=f"(a.y) : "l"(r));
+  return a;
+}
+__device__ __forceinline__ float2 f2_add(float2 a, float2 b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+__device__ __forceinline__ float2 f2_sub(float2 a, float2 b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+__device__ __forceinline__ float2 f2_mul(float2 a, float2 b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(f2_pack(a)), "l"(f2_pack(b)));
+  return f2_unpack(r);
+}
+// a * b + c with one rounding per lane.
+__device__ __forceinline__ float2 f2_fma(float2 a, float2 b, float2 c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;"
+      : "=l"(r)
+      : "l"(f2_pack(a)), "l"(f2_pack(b)), "l"(f2_pack(c)));
+  return f2_unpack(r);
+}
+
 template <class T> struct Ops;
 
 template <> struct Ops<double> {
@@ -238,9 +275,24 @@ __device__ __forceinline__ void hll(const T (&uL)[4], const T (&uR)[4], const T 
     T sr = fminf(fmaxf(chat * fmaxf(lpL, lpR), T(0)), bound);
     T inv = rcp_approx(fmaxf(sr - sl, T(1e-30)));
     T slsr = sl * sr;
+    if constexpr (NV == 4) {  // two packed pairs
+      const float2 SR = make_float2(sr, sr), MSL = make_float2(-sl, -sl);
+      const float2 SLSR = make_float2(slsr, slsr), INV = make_float2(inv, inv);
 #pragma unroll
-    for (int q = 0; q < NV; ++q)
-      out[q] = (sr * fL[q] - sl * fR[q] + slsr * (uR[q] - uL[q])) * inv;
+      for (int h = 0; h < 4; h += 2) {
+        const float2 du = f2_sub(make_float2(uR[h], uR[h + 1]), make_float2(uL[h], uL[h + 1]));
+        float2 acc = f2_mul(MSL, make_float2(fR[h], fR[h + 1]));
+        acc = f2_fma(SLSR, du, acc);
+        acc = f2_fma(SR, make_float2(fL[h], fL[h + 1]), acc);
+        acc = f2_mul(acc, INV);
+        out[h] = acc.x;
+        out[h + 1] = acc.y;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < NV; ++q)
+        out[q] = (sr * fL[q] - sl * fR[q] + slsr * (uR[q] - uL[q])) * inv;
+    }
   }
 }
 

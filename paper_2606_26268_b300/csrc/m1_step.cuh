@@ -160,6 +160,38 @@ __device__ __forceinline__ T half_vanleer(T dl, T dr) {
 }
 
 // sc: the face options (all zero, the defaults, unless given).
+// Lower (lo) and upper (hi) PLM face states of cell uc between um and up on
+// a uniform grid, from the van Leer half slope; the float form with four
+// components runs on packed pairs.
+template <class T, int NV>
+__device__ __forceinline__ void uni_states(const T (&um)[4], const T (&uc)[4], const T (&up)[4],
+                                           T (&lo)[4], T (&hi)[4]) {
+  if constexpr (sizeof(T) == 4 && NV == 4) {
+#pragma unroll
+    for (int h = 0; h < 4; h += 2) {
+      const float2 c = make_float2(uc[h], uc[h + 1]);
+      const float2 dl = f2_sub(c, make_float2(um[h], um[h + 1]));
+      const float2 dr = f2_sub(make_float2(up[h], up[h + 1]), c);
+      const float2 pr = f2_mul(dl, dr), sm = f2_add(dl, dr);
+      float2 hs = f2_mul(pr, make_float2(rcp_approx(sm.x), rcp_approx(sm.y)));
+      hs.x = pr.x > 0.f ? hs.x : 0.f;
+      hs.y = pr.y > 0.f ? hs.y : 0.f;
+      const float2 l = f2_sub(c, hs), u = f2_add(c, hs);
+      lo[h] = l.x;
+      lo[h + 1] = l.y;
+      hi[h] = u.x;
+      hi[h + 1] = u.y;
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const T hs = q < NV ? half_vanleer(uc[q] - um[q], up[q] - uc[q]) : T(0);
+      lo[q] = q < NV ? uc[q] - hs : T(0);
+      hi[q] = q < NV ? uc[q] + hs : T(0);
+    }
+  }
+}
+
 template <class T, int NC, int D, bool UNI>
 __device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const T (&u0)[4],
                                      const T (&up1)[4], T ix0, T ix1, T ix2, T hh, T hl, T tau,
@@ -172,16 +204,9 @@ __device__ __forceinline__ int face4(const T (&um2)[4], const T (&um1)[4], const
     limo3_states<T, NV>(um2, um1, u0, lo, uL);
     limo3_states<T, NV>(um1, u0, up1, uR, hi);
   } else if constexpr (UNI && sizeof(T) == 4) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      if (q < NV) {
-        T d0 = um1[q] - um2[q], d1 = u0[q] - um1[q], d2 = up1[q] - u0[q];
-        uL[q] = um1[q] + half_vanleer(d0, d1);
-        uR[q] = u0[q] - half_vanleer(d1, d2);
-      } else {
-        uL[q] = uR[q] = T(0);
-      }
-    }
+    T lo[4], hi[4];
+    uni_states<T, NV>(um2, um1, u0, lo, uL);
+    uni_states<T, NV>(um1, u0, up1, uR, hi);
   } else {
     T d0[4], d1[4], d2[4];
 #pragma unroll
@@ -474,12 +499,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       if (sc.recon == 1) {
         limo3_states<T, NV>(q[0], q[1], q[2], loN, hiN);
       } else if constexpr (UNI && sizeof(T) == 4) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          T hs = v < NV ? half_vanleer(q[1][v] - q[0][v], q[2][v] - q[1][v]) : T(0);
-          loN[v] = q[1][v] - hs;
-          hiN[v] = q[1][v] + hs;
-        }
+        uni_states<T, NV>(q[0], q[1], q[2], loN, hiN);
       } else {
         T ix1 = IXC(MA, pm - 1), ix2 = IXC(MA, pm);
         T d1[4], d2[4];

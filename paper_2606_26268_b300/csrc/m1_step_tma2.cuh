@@ -54,12 +54,7 @@ __device__ __forceinline__ int face_states(const T (&um)[4], const T (&uc)[4], c
                                            T (&hi)[4]) {
   constexpr int NV = 1 + NC;
   if constexpr (UNI && sizeof(T) == 4) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      T hs = q < NV ? half_vanleer(uc[q] - um[q], up[q] - uc[q]) : T(0);
-      lo[q] = q < NV ? uc[q] - hs : T(0);
-      hi[q] = q < NV ? uc[q] + hs : T(0);
-    }
+    uni_states<T, NV>(um, uc, up, lo, hi);
   } else {
     T dl[4], dr[4];
 #pragma unroll
@@ -359,12 +354,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       const int pm = m + 3;  // padded z of cell m + 1
       T loN[4];
       if constexpr (UNI) {
-#pragma unroll
-        for (int v = 0; v < 4; ++v) {
-          T hs = v < NV ? half_vanleer(q[1][v] - q[0][v], q[2][v] - q[1][v]) : T(0);
-          loN[v] = q[1][v] - hs;
-          hiN[v] = q[1][v] + hs;
-        }
+        uni_states<T, NV>(q[0], q[1], q[2], loN, hiN);
       } else {
         T ix1 = IXC(2, pm - 1), ix2 = IXC(2, pm);
         T d1[4], d2[4];
@@ -385,26 +375,46 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
     // update of the own cell
     if (in_col) {
-      T dU[4] = {0, 0, 0, 0};
-      {
-        T alo = ALO(0, px), ahi = AHI(0, px);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fx[v][ty][tx + 1] - alo * s_fx[v][ty][tx];
-      }
-      {
-        T alo = ALO(1, py), ahi = AHI(1, py);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fy[v][ty + 1][tx] - alo * s_fy[v][ty][tx];
-      }
-      {
-        T alo = ALO(2, m + 2), ahi = AHI(2, m + 2);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) dU[v] -= ahi * zhi[v] - alo * zlo[v];
-      }
       const T (&u)[4] = q[0];
       T Us[4];
+      if constexpr (NV == 4) {  // flux divergence on packed pairs
+        const float2 mx = make_float2(-AHI(0, px), -AHI(0, px)), px_ = make_float2(ALO(0, px), ALO(0, px));
+        const float2 my = make_float2(-AHI(1, py), -AHI(1, py)), py_ = make_float2(ALO(1, py), ALO(1, py));
+        const float2 mz = make_float2(-AHI(2, m + 2), -AHI(2, m + 2));
+        const float2 pz = make_float2(ALO(2, m + 2), ALO(2, m + 2));
+        const float2 dt2 = make_float2(a.dt, a.dt);
 #pragma unroll
-      for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+        for (int h = 0; h < 4; h += 2) {
+          float2 d = f2_mul(mx, make_float2(s_fx[h][ty][tx + 1], s_fx[h + 1][ty][tx + 1]));
+          d = f2_fma(px_, make_float2(s_fx[h][ty][tx], s_fx[h + 1][ty][tx]), d);
+          d = f2_fma(my, make_float2(s_fy[h][ty + 1][tx], s_fy[h + 1][ty + 1][tx]), d);
+          d = f2_fma(py_, make_float2(s_fy[h][ty][tx], s_fy[h + 1][ty][tx]), d);
+          d = f2_fma(mz, make_float2(zhi[h], zhi[h + 1]), d);
+          d = f2_fma(pz, make_float2(zlo[h], zlo[h + 1]), d);
+          const float2 us = f2_fma(dt2, d, make_float2(u[h], u[h + 1]));
+          Us[h] = us.x;
+          Us[h + 1] = us.y;
+        }
+      } else {
+        T dU[4] = {0, 0, 0, 0};
+        {
+          T alo = ALO(0, px), ahi = AHI(0, px);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fx[v][ty][tx + 1] - alo * s_fx[v][ty][tx];
+        }
+        {
+          T alo = ALO(1, py), ahi = AHI(1, py);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fy[v][ty + 1][tx] - alo * s_fy[v][ty][tx];
+        }
+        {
+          T alo = ALO(2, m + 2), ahi = AHI(2, m + 2);
+#pragma unroll
+          for (int v = 0; v < NV; ++v) dU[v] -= ahi * zhi[v] - alo * zlo[v];
+        }
+#pragma unroll
+        for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+      }
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
         rare_add(RARE_EFLOOR);

@@ -8,7 +8,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import rounded, run_gpu
+from helpers import assert_shapes_agree, rounded, run_gpu
 from test_gpu_parity import CASES, _opacity, check64, split_errors
 
 pytestmark = pytest.mark.gpu
@@ -190,7 +190,7 @@ def test_boundaries_split_on_every_launch_shape():
         if ref is None:
             ref = E
         else:
-            assert np.max(np.abs(E - ref) / ref) <= 1e-6, v
+            assert_shapes_agree(E, ref, v)
 
 
 def test_invalid_boundary_states_are_rejected():
