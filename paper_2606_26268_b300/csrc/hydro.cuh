@@ -31,17 +31,18 @@ struct HydroArgs {
   S* e_out;
   S* m_out[3];
   T dt, gamma, cvfac;
+  T inv_gm1;         // 1 / (Gamma - 1)
   T bcT[3][2];       // gas temperature of the fixed and LTE sides
 };
 
 // Conserved state and physical flux along D of a primitive state.
 template <class T, int NC, int D>
-__device__ __forceinline__ void gas_flux(const T (&w)[5], T gamma, T (&U)[5], T (&f)[5]) {
+__device__ __forceinline__ void gas_flux(const T (&w)[5], T inv_gm1, T (&U)[5], T (&f)[5]) {
   const T r = w[0], p = w[4], vd = w[1 + D];
   T v2 = T(0);
 #pragma unroll
   for (int v = 0; v < NC; ++v) v2 += w[1 + v] * w[1 + v];
-  const T Eg = Ops<T>::div(p, gamma - T(1)) + T(0.5) * r * v2;
+  const T Eg = p * inv_gm1 + T(0.5) * r * v2;
   U[0] = r;
   f[0] = r * vd;
 #pragma unroll
@@ -60,7 +61,7 @@ __device__ __forceinline__ void gas_flux(const T (&w)[5], T gamma, T (&U)[5], T 
 template <class T, int NC, int D>
 __device__ __forceinline__ void gas_riemann(const T (&w0)[5], const T (&w1)[5], const T (&w2)[5],
                                             const T (&w3)[5], T ix0, T ix1, T ix2, T hh, T hl,
-                                            T gamma, T (&out)[5]) {
+                                            T gamma, T inv_gm1, T (&out)[5]) {
   T wl[5], wr[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) {
@@ -69,8 +70,8 @@ __device__ __forceinline__ void gas_riemann(const T (&w0)[5], const T (&w1)[5], 
     wr[q] = w2[q] + vanleer(d1, d2) * hl;
   }
   T UL[5], UR[5], fL[5], fR[5];
-  gas_flux<T, NC, D>(wl, gamma, UL, fL);
-  gas_flux<T, NC, D>(wr, gamma, UR, fR);
+  gas_flux<T, NC, D>(wl, inv_gm1, UL, fL);
+  gas_flux<T, NC, D>(wr, inv_gm1, UR, fR);
   const T cl = Ops<T>::sqrt_(Ops<T>::div(gamma * wl[4], wl[0]));
   const T cr = Ops<T>::sqrt_(Ops<T>::div(gamma * wr[4], wr[0]));
   T sl = wl[1 + D] - cl, sr = wr[1 + D] + cr;
@@ -148,7 +149,7 @@ __global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ 
     const int pz = z0 + gz;
     gas_riemann<T, NC, 2>(wz[0], wz[1], wz[2], wz[3], gtab(G, 2, TAB_IDXC, pz - 2),
                           gtab(G, 2, TAB_IDXC, pz - 1), gtab(G, 2, TAB_IDXC, pz),
-                          gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, fzlo);
+                          gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, h.inv_gm1, fzlo);
   }
 
   for (int z = z0; z < z1; ++z) {
@@ -180,7 +181,7 @@ __global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ 
         const int pc = min(x0 + c, Dm.n[0]) + Dm.g[0];
         gas_riemann<T, NC, 0>(a0, a1, a2, a3, gtab(G, 0, TAB_IDXC, pc - 2),
                               gtab(G, 0, TAB_IDXC, pc - 1), gtab(G, 0, TAB_IDXC, pc),
-                              gtab(G, 0, TAB_HHI, pc - 1), gtab(G, 0, TAB_HLO, pc), h.gamma, f);
+                              gtab(G, 0, TAB_HHI, pc - 1), gtab(G, 0, TAB_HLO, pc), h.gamma, h.inv_gm1, f);
       };
       T f[5];
       xface(tx, f);
@@ -205,7 +206,7 @@ __global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ 
         const int pr = min(y0 + r, Dm.n[1]) + Dm.g[1];
         gas_riemann<T, NC, 1>(a0, a1, a2, a3, gtab(G, 1, TAB_IDXC, pr - 2),
                               gtab(G, 1, TAB_IDXC, pr - 1), gtab(G, 1, TAB_IDXC, pr),
-                              gtab(G, 1, TAB_HHI, pr - 1), gtab(G, 1, TAB_HLO, pr), h.gamma, f);
+                              gtab(G, 1, TAB_HHI, pr - 1), gtab(G, 1, TAB_HLO, pr), h.gamma, h.inv_gm1, f);
       };
       T f[5];
       yface(ty, f);
@@ -223,7 +224,7 @@ __global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ 
       const int pz = z + 1 + gz;
       gas_riemann<T, NC, 2>(wz[1], wz[2], wz[3], wz[4], gtab(G, 2, TAB_IDXC, pz - 2),
                             gtab(G, 2, TAB_IDXC, pz - 1), gtab(G, 2, TAB_IDXC, pz),
-                            gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, fzhi);
+                            gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, h.inv_gm1, fzhi);
     }
     __syncthreads();
     if (upd) {
