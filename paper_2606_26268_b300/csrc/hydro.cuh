@@ -103,7 +103,7 @@ __device__ __forceinline__ T gtab(const GeomDev<T>& G, int d, int slot, int ip) 
 // once.  The z faces come from the column's states held in registers, the
 // upper face of one plane being the lower face of the next.
 template <class P, int NDIM, int NC, int TX, int TY>
-__global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ HydroArgs<P> h) {
+__global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1) hydro_kernel(const __grid_constant__ HydroArgs<P> h) {
   using S = typename P::S;
   using T = typename P::T;
   constexpr bool HY = NDIM >= 2, HZ = NDIM >= 3;
@@ -152,21 +152,52 @@ __global__ void __launch_bounds__(TX * TY) hydro_kernel(const __grid_constant__ 
                           gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, h.inv_gm1, fzlo);
   }
 
+  // The plane (tile plus a 2-cell halo, coordinates clamped to the padded
+  // array) is loaded into registers one plane ahead, so that its loads are in
+  // flight while the previous plane's faces are computed, and staged in
+  // shared memory as primitive states.
+  constexpr int KS = (SX * SY + NT - 1) / NT;  // staged cells per thread
+  S pre[KS][5];
+  auto load_plane = [&](int z) {
+    const long long zoff = (long long)(z + gz) * sz;
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) {
+      const int k = tid + kk * NT;
+      if (k < SX * SY) {
+        const int iy = k / SX, ix = k - iy * SX;
+        const int gx = min(max(x0 - 2 + ix + Dm.g[0], 0), Dm.n[0] + 2 * Dm.g[0] - 1);
+        const int gy = HY ? min(max(y0 - OY + iy + Dm.g[1], 0), Dm.n[1] + 2 * Dm.g[1] - 1) : 0;
+        const long long ip = gx + Dm.sy * (long long)gy + zoff;
+        pre[kk][0] = __ldg(h.rho + ip);
+#pragma unroll
+        for (int v = 0; v < 3; ++v) pre[kk][1 + v] = v < NC ? __ldg(h.m[v] + ip) : S(0);
+        pre[kk][4] = __ldg(h.e + ip);
+      }
+    }
+  };
+  auto store_plane = [&]() {
+#pragma unroll
+    for (int kk = 0; kk < KS; ++kk) {
+      const int k = tid + kk * NT;
+      if (k < SX * SY) {
+        const int iy = k / SX, ix = k - iy * SX;
+        const T r = T(pre[kk][0]);
+        const T ir = Ops<T>::rcp(r);
+        s_w[0][iy][ix] = r;
+#pragma unroll
+        for (int v = 0; v < 3; ++v) s_w[1 + v][iy][ix] = T(pre[kk][1 + v]) * ir;
+        s_w[4][iy][ix] = (h.gamma - T(1)) * T(pre[kk][4]);
+      }
+    }
+  };
+  load_plane(z0);
+
   for (int z = z0; z < z1; ++z) {
     const long long zoff = (long long)(z + gz) * sz;
-    // stage the plane: tile plus a 2-cell halo, coordinates clamped to the
-    // padded array
-    for (int k = tid; k < SX * SY; k += NT) {
-      const int iy = k / SX, ix = k - iy * SX;
-      const int gx = min(max(x0 - 2 + ix + Dm.g[0], 0), Dm.n[0] + 2 * Dm.g[0] - 1);
-      const int gy = HY ? min(max(y0 - OY + iy + Dm.g[1], 0), Dm.n[1] + 2 * Dm.g[1] - 1) : 0;
-      T w[5];
-      prim(gx + Dm.sy * (long long)gy + zoff, w);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) s_w[q][iy][ix] = w[q];
-    }
+    store_plane();
     if constexpr (HZ) prim(col + (long long)(z + 2 + gz) * sz, wz[4]);
     __syncthreads();
+    if (z + 1 < z1) load_plane(z + 1);
     // x faces: the lower one of the own cell, and the tile's upper one
     {
       auto xface = [&](int c, T (&f)[5]) {  // face between tile columns c - 1 and c
