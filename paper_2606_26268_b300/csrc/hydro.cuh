@@ -58,16 +58,32 @@ __device__ __forceinline__ void gas_flux(const T (&w)[5], T inv_gm1, T (&U)[5], 
 // D, with their outer neighbours w0 and w3: ix0..ix2 the inverse centre
 // distances of (w0, w1), (w1, w2), (w2, w3), hh and hl the offsets of the face
 // from the centres of w1 and w2.
-template <class T, int NC, int D>
+// UNI: uniform spacing; the faces sit half a cell from the centres and the
+// limited half slope is d0 d1 / (d0 + d1) of the raw differences (the tables
+// are not read).
+template <class T, int NC, int D, bool UNI = false>
 __device__ __forceinline__ void gas_riemann(const T (&w0)[5], const T (&w1)[5], const T (&w2)[5],
                                             const T (&w3)[5], T ix0, T ix1, T ix2, T hh, T hl,
                                             T gamma, T inv_gm1, T (&out)[5]) {
   T wl[5], wr[5];
+  if constexpr (UNI) {
+    auto half = [](T a, T b) {
+      const T p = a * b;
+      return p > T(0) ? Ops<T>::div(p, a + b) : T(0);
+    };
 #pragma unroll
-  for (int q = 0; q < 5; ++q) {
-    const T d0 = (w1[q] - w0[q]) * ix0, d1 = (w2[q] - w1[q]) * ix1, d2 = (w3[q] - w2[q]) * ix2;
-    wl[q] = w1[q] + vanleer(d0, d1) * hh;
-    wr[q] = w2[q] + vanleer(d1, d2) * hl;
+    for (int q = 0; q < 5; ++q) {
+      const T d0 = w1[q] - w0[q], d1 = w2[q] - w1[q], d2 = w3[q] - w2[q];
+      wl[q] = w1[q] + half(d0, d1);
+      wr[q] = w2[q] - half(d1, d2);
+    }
+  } else {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      const T d0 = (w1[q] - w0[q]) * ix0, d1 = (w2[q] - w1[q]) * ix1, d2 = (w3[q] - w2[q]) * ix2;
+      wl[q] = w1[q] + vanleer(d0, d1) * hh;
+      wr[q] = w2[q] + vanleer(d1, d2) * hl;
+    }
   }
   T UL[5], UR[5], fL[5], fR[5];
   gas_flux<T, NC, D>(wl, inv_gm1, UL, fL);
@@ -102,7 +118,7 @@ __device__ __forceinline__ T gtab(const GeomDev<T>& G, int d, int slot, int ip) 
 // the last column (row) also the upper tile face, and every face is computed
 // once.  The z faces come from the column's states held in registers, the
 // upper face of one plane being the lower face of the next.
-template <class P, int NDIM, int NC, int TX, int TY>
+template <class P, int NDIM, int NC, int TX, int TY, bool UNI>
 __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1) hydro_kernel(const __grid_constant__ HydroArgs<P> h) {
   using S = typename P::S;
   using T = typename P::T;
@@ -147,7 +163,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
 #pragma unroll
     for (int k = 0; k < 4; ++k) prim(col + (long long)(z0 - 2 + k + gz) * sz, wz[k]);
     const int pz = z0 + gz;
-    gas_riemann<T, NC, 2>(wz[0], wz[1], wz[2], wz[3], gtab(G, 2, TAB_IDXC, pz - 2),
+    gas_riemann<T, NC, 2, UNI>(wz[0], wz[1], wz[2], wz[3], gtab(G, 2, TAB_IDXC, pz - 2),
                           gtab(G, 2, TAB_IDXC, pz - 1), gtab(G, 2, TAB_IDXC, pz),
                           gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, h.inv_gm1, fzlo);
   }
@@ -198,62 +214,67 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
     if constexpr (HZ) prim(col + (long long)(z + 2 + gz) * sz, wz[4]);
     __syncthreads();
     if (z + 1 < z1) load_plane(z + 1);
-    // x faces: the lower one of the own cell, and the tile's upper one
-    {
-      auto xface = [&](int c, T (&f)[5]) {  // face between tile columns c - 1 and c
-        T a0[5], a1[5], a2[5], a3[5];
+    // faces of the tile directions: the lower x (and y) face of the own cell;
+    // the tile's upper faces (one per row and per column) go to the first
+    // threads of the CTA, so that they occupy as few warps as possible
+    auto xface = [&](int row, int c, T (&f)[5]) {  // face between tile columns c - 1 and c
+      T a0[5], a1[5], a2[5], a3[5];
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          a0[q] = s_w[q][ty + OY][c];
-          a1[q] = s_w[q][ty + OY][c + 1];
-          a2[q] = s_w[q][ty + OY][c + 2];
-          a3[q] = s_w[q][ty + OY][c + 3];
-        }
-        const int pc = min(x0 + c, Dm.n[0]) + Dm.g[0];
-        gas_riemann<T, NC, 0>(a0, a1, a2, a3, gtab(G, 0, TAB_IDXC, pc - 2),
-                              gtab(G, 0, TAB_IDXC, pc - 1), gtab(G, 0, TAB_IDXC, pc),
-                              gtab(G, 0, TAB_HHI, pc - 1), gtab(G, 0, TAB_HLO, pc), h.gamma, h.inv_gm1, f);
-      };
+      for (int q = 0; q < 5; ++q) {
+        a0[q] = s_w[q][row + OY][c];
+        a1[q] = s_w[q][row + OY][c + 1];
+        a2[q] = s_w[q][row + OY][c + 2];
+        a3[q] = s_w[q][row + OY][c + 3];
+      }
+      const int pc = min(x0 + c, Dm.n[0]) + Dm.g[0];
+      gas_riemann<T, NC, 0, UNI>(a0, a1, a2, a3, gtab(G, 0, TAB_IDXC, pc - 2),
+                            gtab(G, 0, TAB_IDXC, pc - 1), gtab(G, 0, TAB_IDXC, pc),
+                            gtab(G, 0, TAB_HHI, pc - 1), gtab(G, 0, TAB_HLO, pc), h.gamma,
+                            h.inv_gm1, f);
+    };
+    auto yface = [&](int r, int cl, T (&f)[5]) {  // face between tile rows r - 1 and r
+      T a0[5], a1[5], a2[5], a3[5];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        a0[q] = s_w[q][r][cl + 2];
+        a1[q] = s_w[q][r + 1][cl + 2];
+        a2[q] = s_w[q][r + 2][cl + 2];
+        a3[q] = s_w[q][r + 3][cl + 2];
+      }
+      const int pr = min(y0 + r, Dm.n[1]) + Dm.g[1];
+      gas_riemann<T, NC, 1, UNI>(a0, a1, a2, a3, gtab(G, 1, TAB_IDXC, pr - 2),
+                            gtab(G, 1, TAB_IDXC, pr - 1), gtab(G, 1, TAB_IDXC, pr),
+                            gtab(G, 1, TAB_HHI, pr - 1), gtab(G, 1, TAB_HLO, pr), h.gamma,
+                            h.inv_gm1, f);
+    };
+    {
       T f[5];
-      xface(tx, f);
+      xface(ty, tx, f);
 #pragma unroll
       for (int q = 0; q < 5; ++q) s_fx[q][ty][tx] = f[q];
-      if (tx == TX - 1) {
-        xface(TX, f);
+      if constexpr (HY) {
+        yface(ty, tx, f);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) s_fx[q][ty][TX] = f[q];
+        for (int q = 0; q < 5; ++q) s_fy[q][ty][tx] = f[q];
       }
-    }
-    if constexpr (HY) {
-      auto yface = [&](int r, T (&f)[5]) {  // face between tile rows r - 1 and r
-        T a0[5], a1[5], a2[5], a3[5];
+      if (tid < TY) {
+        xface(tid, TX, f);
 #pragma unroll
-        for (int q = 0; q < 5; ++q) {
-          a0[q] = s_w[q][r][tx + 2];
-          a1[q] = s_w[q][r + 1][tx + 2];
-          a2[q] = s_w[q][r + 2][tx + 2];
-          a3[q] = s_w[q][r + 3][tx + 2];
+        for (int q = 0; q < 5; ++q) s_fx[q][tid][TX] = f[q];
+      }
+      if constexpr (HY) {
+        if (tid >= TY && tid < TY + TX) {
+          yface(TY, tid - TY, f);
+#pragma unroll
+          for (int q = 0; q < 5; ++q) s_fy[q][TY][tid - TY] = f[q];
         }
-        const int pr = min(y0 + r, Dm.n[1]) + Dm.g[1];
-        gas_riemann<T, NC, 1>(a0, a1, a2, a3, gtab(G, 1, TAB_IDXC, pr - 2),
-                              gtab(G, 1, TAB_IDXC, pr - 1), gtab(G, 1, TAB_IDXC, pr),
-                              gtab(G, 1, TAB_HHI, pr - 1), gtab(G, 1, TAB_HLO, pr), h.gamma, h.inv_gm1, f);
-      };
-      T f[5];
-      yface(ty, f);
-#pragma unroll
-      for (int q = 0; q < 5; ++q) s_fy[q][ty][tx] = f[q];
-      if (ty == TY - 1) {
-        yface(TY, f);
-#pragma unroll
-        for (int q = 0; q < 5; ++q) s_fy[q][TY][tx] = f[q];
       }
     }
     // z face above the own cell
     T fzhi[5] = {0, 0, 0, 0, 0};
     if constexpr (HZ) {
       const int pz = z + 1 + gz;
-      gas_riemann<T, NC, 2>(wz[1], wz[2], wz[3], wz[4], gtab(G, 2, TAB_IDXC, pz - 2),
+      gas_riemann<T, NC, 2, UNI>(wz[1], wz[2], wz[3], wz[4], gtab(G, 2, TAB_IDXC, pz - 2),
                             gtab(G, 2, TAB_IDXC, pz - 1), gtab(G, 2, TAB_IDXC, pz),
                             gtab(G, 2, TAB_HHI, pz - 1), gtab(G, 2, TAB_HLO, pz), h.gamma, h.inv_gm1, fzhi);
     }

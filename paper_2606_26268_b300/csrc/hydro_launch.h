@@ -7,7 +7,7 @@ namespace m1 {
 // Launches the gas step; `args` points to the HydroArgs of the precision
 // policy.  nullptr for combinations not instantiated.
 typedef cudaError_t (*HydroFn)(const void* args, cudaStream_t stream);
-HydroFn select_hydro(bool split, int ndim, int nc);
+HydroFn select_hydro(bool split, int ndim, int nc, bool uniform);
 
 // Launches the reduction of the gas CFL rate; `args` points to the
 // GasCflArgs of the precision policy.

@@ -291,7 +291,7 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
                p.riemann != RAD_HLL || p.irradiation || p.implicit_mode == RAD_ABSORPTION_ONLY ||
                p.hydro;
   if (p.hydro) {
-    c->hydro_fn = select_hydro(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
+    c->hydro_fn = select_hydro(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc, c->uniform);
     c->gas_cfl_fn = select_gas_cfl(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
     if (!c->hydro_fn || !c->gas_cfl_fn) {
       delete c;
