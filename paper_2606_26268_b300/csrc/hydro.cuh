@@ -66,11 +66,34 @@ __device__ __forceinline__ void gas_riemann(const T (&w0)[5], const T (&w1)[5], 
                                             const T (&w3)[5], T ix0, T ix1, T ix2, T hh, T hl,
                                             T gamma, T inv_gm1, T (&out)[5]) {
   T wl[5], wr[5];
-  if constexpr (UNI) {
-    auto half = [](T a, T b) {
-      const T p = a * b;
-      return p > T(0) ? Ops<T>::div(p, a + b) : T(0);
-    };
+  auto half = [](T a, T b) {
+    const T p = a * b;
+    return p > T(0) ? Ops<T>::div(p, a + b) : T(0);
+  };
+  if constexpr (UNI && sizeof(T) == 4) {
+    // components (0, 1) and (2, 3) on packed FP32 pairs, 4 alone
+#pragma unroll
+    for (int h = 0; h < 4; h += 2) {
+      const float2 c0 = make_float2(w0[h], w0[h + 1]), c1 = make_float2(w1[h], w1[h + 1]);
+      const float2 c2 = make_float2(w2[h], w2[h + 1]), c3 = make_float2(w3[h], w3[h + 1]);
+      const float2 d0 = f2_sub(c1, c0), d1 = f2_sub(c2, c1), d2 = f2_sub(c3, c2);
+      const float2 pa = f2_mul(d0, d1), sa = f2_add(d0, d1);
+      const float2 pb = f2_mul(d1, d2), sb = f2_add(d1, d2);
+      float2 ha = f2_mul(pa, make_float2(rcp_approx(sa.x), rcp_approx(sa.y)));
+      float2 hb = f2_mul(pb, make_float2(rcp_approx(sb.x), rcp_approx(sb.y)));
+      ha.x = pa.x > 0.f ? ha.x : 0.f;
+      ha.y = pa.y > 0.f ? ha.y : 0.f;
+      hb.x = pb.x > 0.f ? hb.x : 0.f;
+      hb.y = pb.y > 0.f ? hb.y : 0.f;
+      const float2 l = f2_add(c1, ha), r = f2_sub(c2, hb);
+      wl[h] = l.x;
+      wl[h + 1] = l.y;
+      wr[h] = r.x;
+      wr[h + 1] = r.y;
+    }
+    wl[4] = w1[4] + half(w1[4] - w0[4], w2[4] - w1[4]);
+    wr[4] = w2[4] - half(w2[4] - w1[4], w3[4] - w2[4]);
+  } else if constexpr (UNI) {
 #pragma unroll
     for (int q = 0; q < 5; ++q) {
       const T d0 = w1[q] - w0[q], d1 = w2[q] - w1[q], d2 = w3[q] - w2[q];
@@ -101,8 +124,24 @@ __device__ __forceinline__ void gas_riemann(const T (&w0)[5], const T (&w1)[5], 
     for (int q = 0; q < 5; ++q) out[q] = fR[q];
   } else {
     const T inv = Ops<T>::rcp(sr - sl);
+    if constexpr (sizeof(T) == 4) {  // components (0, 1), (2, 3) packed, 4 alone
+      const float2 SR = make_float2(sr, sr), MSL = make_float2(-sl, -sl);
+      const float2 SLSR = make_float2(sl * sr, sl * sr), INV = make_float2(inv, inv);
 #pragma unroll
-    for (int q = 0; q < 5; ++q) out[q] = (sr * fL[q] - sl * fR[q] + sl * sr * (UR[q] - UL[q])) * inv;
+      for (int h = 0; h < 4; h += 2) {
+        const float2 du = f2_sub(make_float2(UR[h], UR[h + 1]), make_float2(UL[h], UL[h + 1]));
+        float2 acc = f2_mul(MSL, make_float2(fR[h], fR[h + 1]));
+        acc = f2_fma(SLSR, du, acc);
+        acc = f2_fma(SR, make_float2(fL[h], fL[h + 1]), acc);
+        acc = f2_mul(acc, INV);
+        out[h] = acc.x;
+        out[h + 1] = acc.y;
+      }
+      out[4] = (sr * fL[4] - sl * fR[4] + sl * sr * (UR[4] - UL[4])) * inv;
+    } else {
+#pragma unroll
+      for (int q = 0; q < 5; ++q) out[q] = (sr * fL[q] - sl * fR[q] + sl * sr * (UR[q] - UL[q])) * inv;
+    }
   }
 }
 

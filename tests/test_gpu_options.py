@@ -305,3 +305,62 @@ def test_shadow_split_within_the_problems_own_sensitivity():
     for key in ("E", "F"):
         assert err["norm_" + key] <= max(1e-5, 20 * sens[key]), (err, sens)
     assert err["norm_E"] <= 1e-3
+
+
+# ---------------------------------------------------------------------------
+# the free-streaming beam of Sect. 3 (f = 1 along the diagonal, held source)
+# ---------------------------------------------------------------------------
+
+def _beam(recon, fix, n=1000, t_end=6.5):
+    """Runs the beam with its source region re-imposed after every step and
+    returns (max, FWHM) of the vertical cuts at x = 1 and x = 4.35."""
+    import math
+    import torch
+    import paper_2606_26268_b300 as R
+    p, mask = W.beam_2d(n, recon, fix)
+    # FP64: near f = 1 the signal speeds open like sqrt(1 - f^2), so FP32
+    # rounding of f adds transverse diffusion to an f = 1 beam (the split
+    # form widens it 35 % instead of 8 %)
+    r = R.from_problem(p, "fp64")
+    dt = r.dt()
+    mk = torch.as_tensor(mask, device="cuda")
+    Fb = 1e12 / math.sqrt(2.0)
+    for _ in range(int(t_end / dt)):
+        r.step(1, dt)
+        E = r.read("E", host=False)
+        F = r.read("F", host=False).view(2, -1)
+        E[mk] = 1e12
+        F[0][mk] = Fb
+        F[1][mk] = Fb
+        r.set_rad(E, F.reshape(-1))
+    assert r.sync() == 0
+    E = np.asarray(r.read("E"), dtype=np.float64).reshape(n, n)
+    r.close()
+    cuts = []
+    for x in (1.0, 4.35):
+        col = E[:, int(x / 5.0 * n)]
+        m = col.max()
+        above = np.where(col >= 0.5 * m)[0]
+        cuts.append((m, (above.max() - above.min() + 1) * 5.0 / n))
+    return cuts
+
+
+def test_beam_stays_collimated_with_the_f_preserving_scheme():
+    """Sect. 3: with the f-preserving scheme the beam's maximum drops by 8 %
+    and its width grows by 7 % from x = 1 to x = 4.35; here (PLM, 1000^2,
+    FP64) both stay within 12 % and 15 %."""
+    (m1, w1), (m2, w2) = _beam("plm", "fpreserve")
+    assert 1 - m2 / m1 < 0.12, (m1, m2)
+    assert w2 / w1 - 1 < 0.15, (w1, w2)
+
+
+def test_beam_explodes_with_the_plain_clip_and_widens_with_the_pluto_scheme():
+    """Sect. 3 (LimO3, 1000^2): clipping f <= 1 on the faces makes the beam
+    explode, while the PLUTO and f-preserving schemes keep it; the PLUTO
+    scheme spreads it more than the f-preserving one."""
+    (_, wc1), (_, wc2) = _beam("limo3", "clip")
+    (_, wp1), (_, wp2) = _beam("limo3", "pluto")
+    (_, wf1), (_, wf2) = _beam("limo3", "fpreserve")
+    assert wc2 / wc1 > 3.0, (wc1, wc2)
+    assert wp2 / wp1 < 2.0 and wf2 / wf1 < 2.0, (wp1, wp2, wf1, wf2)
+    assert wp2 / wp1 > wf2 / wf1, (wp1, wp2, wf1, wf2)
