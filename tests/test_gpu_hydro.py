@@ -185,3 +185,53 @@ def test_rhd_pulse_workload_fp64_and_split_match_oracle():
         sens = np.linalg.norm(o2[key] - o[key]) / np.linalg.norm(o[key])
         assert err <= max(1e-5, 20 * sens), (key, err, sens)
         assert err <= 1e-3, (key, err)
+
+
+# ---------------------------------------------------------------------------
+# the radiative shocks of Sect. 3 (gas step + radiation, reflective wall)
+# ---------------------------------------------------------------------------
+
+def _shock_profile(v_kms, t_end, chat_over_c, n=1000):
+    import paper_2606_26268_b300 as R
+    p = W.radiative_shock(n, v_kms, chat_over_c)
+    r = R.from_problem(p, "fp64")
+    dt = r.dt()
+    r.step(int(t_end / dt), dt)
+    assert r.sync() == 0
+    T = np.asarray(r.read("T"), dtype=np.float64)
+    rho = np.asarray(r.read("rho"), dtype=np.float64)
+    r.close()
+    x = (np.arange(n) + 0.5) * 7e10 / n
+    front = np.where(rho > 3 * 7.78e-10)[0].max()  # last compressed cell
+    xs = x[front]
+    T2 = float(np.median(T[(x > 0.2 * xs) & (x < 0.7 * xs)]))
+    return T2, float(T.max()), float(T[front + 3]), xs
+
+
+def test_subcritical_radiative_shock_matches_the_printed_temperatures():
+    """Sect. 3, v = 6 km/s: the paper prints T2 = 834 K, T- = 358 K and
+    T+ = 1080 K (chat = c), and T2 barely moves for chat/c down to 1e-4.
+    Here chat/c = 1e-3, 1000 cells, t = 3.8e4 s: T2 within 5 %, T+ within
+    10 %, T- within 15 %, and T- < T2 < T+ (the subcritical ordering)."""
+    T2, Tp, Tm, xs = _shock_profile(6.0, 3.8e4, 1e-3)
+    assert abs(T2 / 834.0 - 1) < 0.05, T2
+    assert abs(Tp / 1080.0 - 1) < 0.10, Tp
+    assert abs(Tm / 358.0 - 1) < 0.15, Tm
+    assert Tm < 0.6 * T2 and Tp > 1.1 * T2, (Tm, T2, Tp)
+
+
+def test_supercritical_radiative_shock_heats_its_precursor_to_T2():
+    """Sect. 3, v = 20 km/s: T2 = 4262 K (chat = c) and the precursor reaches
+    T2 (T- = T2, the supercritical signature).  Here chat/c = 1e-2, t =
+    7.5e3 s: T2 within 7 %, the gas ahead of the front within 10 % of T2."""
+    T2, Tp, Tm, xs = _shock_profile(20.0, 7.5e3, 1e-2)
+    assert abs(T2 / 4262.0 - 1) < 0.07, T2
+    assert abs(Tm / T2 - 1) < 0.10, (Tm, T2)
+    assert Tp >= T2
+
+
+def test_radiative_shock_fp64_matches_oracle():
+    """The subcritical setup at 400 cells for 3000 steps (the shock formed,
+    a few cells from the wall), FP64 per cell."""
+    p = W.radiative_shock(400, 6.0, 1e-3)
+    check_gas64(p, 3000)

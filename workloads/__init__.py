@@ -424,6 +424,30 @@ def beam_2d(n: int = 300, recon: str = "plm", face_fix: str = "fpreserve") -> Tu
     return p, mask
 
 
+def radiative_shock(n: int = 1000, v_kms: float = 6.0, chat_over_c: float = 1e-3) -> Problem:
+    """The radiative shocks of Sect. 3 (cgs): x in [0, 7e10] cm, rho =
+    7.78e-10, T = 10 K with E = a T^4, mu = 1, Gamma = 7/5, absorption
+    kappa = 0.39 cm^2/g, no scattering, gas moving at -v (6 km/s:
+    subcritical, 20 km/s: supercritical) towards the reflective wall at x = 0,
+    outflow at the far side, HLL, PLM f-preserving, RK2, chat = c x
+    chat_over_c."""
+    xf = [uniform_faces(n, 0.0, 7e10), uniform_faces(1, 0.0, 1.0), uniform_faces(1, 0.0, 1.0)]
+    p = _blank("radshock_%d_v%g" % (n, v_kms), 1, (n, 1, 1), "cartesian", "outflow", xf,
+               chat=C_LIGHT * chat_over_c, c=C_LIGHT, ncomp=1, integrator="rk2", hydro=True)
+    p.bc_lo = ("reflective", "outflow", "outflow")
+    p.a_rad = A_RAD
+    p.mu = 1.0 / KB_OVER_MU
+    p.gamma_gas = 7.0 / 5.0
+    p.rho = np.full(p.N, 7.78e-10)
+    p.v = np.zeros((3, p.N))
+    p.v[0] = -v_kms * 1e5
+    p.T = np.full(p.N, 10.0)
+    p.E = A_RAD * p.T ** 4
+    p.F = np.zeros((3, p.N))
+    p.opacity = {"kind": "const", "kappa_p": 0.39, "kappa_r": 0.39, "sigma": 0.0}
+    return p
+
+
 def uniform_state(geometry: str, n: Tuple[int, int, int], ndim: int, log_r: bool = False,
                   extents=None, E: float = 2.0, kappa: float = 0.5) -> Problem:
     """A uniform isotropic state (E const, F = 0) in equilibrium with the gas
