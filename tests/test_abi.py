@@ -84,3 +84,82 @@ def test_missing_library_fails_loudly(R, tmp_path, monkeypatch):
     monkeypatch.setattr(R, "_lib", None)
     with pytest.raises(RuntimeError):
         R.lib()
+
+
+def test_options_boundaries_and_gas_are_validated_on_the_host(R):
+    L = R.lib()
+    g, xs = _grid(R)
+    o = R.rad_opacity()
+    ctx = C.c_void_p()
+
+    def create(gg, geom, pp):
+        c2 = C.c_void_p()
+        st = L.rad_create(C.byref(gg), geom, C.byref(o), C.byref(pp), C.byref(c2))
+        if c2.value:
+            L.rad_destroy(c2)
+        return st
+
+    for field, value in (("reconstruction", 2), ("face_fix", 3), ("riemann", 2),
+                         ("implicit_mode", 3), ("hydro", 2), ("reconstruction", -1)):
+        p = R.default_params()
+        setattr(p, field, value)
+        assert create(g, 0, p) == R.RAD_EINVAL, field
+    # the gas step is Cartesian only
+    p = R.default_params()
+    p.hydro = 1
+    gc, xc = _grid(R)
+    xs_keep = np.linspace(0.5, 1.5, 9)  # radii > 0
+    gc.xface[0] = xs_keep.ctypes.data
+    assert create(gc, R.RAD_CYLINDRICAL, p) == R.RAD_EUNSUPPORTED
+    assert create(g, 0, p) == R.RAD_OK
+    # boundary kinds and states
+    p = R.default_params()
+    gb, xb = _grid(R)
+    gb.bc_lo[0] = 5
+    assert create(gb, 0, p) == R.RAD_EINVAL
+    gb.bc_lo[0] = R.RAD_BC_FIXED
+    for state, ok in (((1.0, 0.5, 0.0, 0.0, 1.0), True), ((1.0, 1.5, 0.0, 0.0, 1.0), False),
+                      ((1.0, 0.5, 0.0, 0.0, 0.0), False), ((0.0, 0.0, 0.0, 0.0, 1.0), False),
+                      ((1.0, 0.0, 0.5, 0.0, 1.0), False)):  # F_1 beyond ncomp = 1
+        pp = R.default_params()
+        pp.ncomp = 1
+        for q in range(5):
+            gb.bc_value[q] = state[q]
+        assert create(gb, 0, pp) == (R.RAD_OK if ok else R.RAD_EINVAL), state
+    gb.bc_lo[0] = R.RAD_BC_LTE
+    for q in range(5):
+        gb.bc_value[q] = (0.0, 0.0, 0.0, 0.0, 0.0)[q]
+    assert create(gb, 0, p) == R.RAD_EINVAL        # T_b = 0
+    gb.bc_value[4] = 1.0
+    assert create(gb, 0, p) == R.RAD_OK
+    gb.bc_lo[0] = R.RAD_BC_REFLECTIVE
+    gb.bc_hi[0] = R.RAD_BC_PERIODIC
+    assert create(gb, 0, p) == R.RAD_EINVAL        # periodic on one side only
+
+
+def test_general_form_offers_the_right_launch_shapes(R):
+    """Split 3D Cartesian: eight shapes in the default form and with evolved
+    gas (the TMA-staged ones read the gas step's output), four with a face
+    option of Sect. 2.5 (the register-tiled kernel only)."""
+    L = R.lib()
+    g, xs = _grid(R, (16, 16, 16), 3)
+    o = R.rad_opacity()
+
+    def shapes(**kw):
+        p = R.default_params()
+        p.precision = R.RAD_FP32_SPLIT
+        for k, v in kw.items():
+            setattr(p, k, v)
+        c2 = C.c_void_p()
+        assert L.rad_create(C.byref(g), 0, C.byref(o), C.byref(p), C.byref(c2)) == R.RAD_OK
+        nv = C.c_int()
+        assert L.rad_get_launch(c2, None, None, C.byref(nv)) == R.RAD_OK
+        L.rad_destroy(c2)
+        return nv.value
+
+    assert shapes() == 8
+    assert shapes(hydro=1) == 8
+    assert shapes(irradiation=1) == 8
+    assert shapes(implicit_mode=R.RAD_ABSORPTION_ONLY) == 8
+    assert shapes(reconstruction=R.RAD_LIMO3) == 4
+    assert shapes(face_fix=R.RAD_FIX_PLUTO, hydro=1) == 4
