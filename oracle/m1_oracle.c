@@ -3,7 +3,7 @@
  * gray M1 module of Scepi & Lesur, "A nonrelativistic radiative transfer
  * module for Idefix" (arxiv 2606.26268).
  *
- * TEST INFRASTRUCTURE ONLY.  This file is the judge of the CUDA path: only the
+ * TEST INFRASTRUCTURE ONLY.  The CUDA path is checked against this file: only the
  * test suite, the smoke check and the benchmark's CPU-baseline leg may load
  * it.  It shares no code, header, table or helper with the CUDA library.
  *
