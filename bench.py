@@ -46,36 +46,64 @@ def peaks():
         return 6400.0, "fallback"
 
 
-# sources the single-grid step kernel is compiled from (a change to any of
-# them invalidates the profiled DRAM traffic)
+# sources each profiled kernel is compiled from (a change to any of them
+# invalidates its committed ncu figures)
 STEP_SOURCES = ("m1_math.cuh", "m1_internal.h", "m1_cell.cuh", "m1_step.cuh", "m1_step_tma.cuh",
                 "m1_step_tma2.cuh", "tma.cuh", "step_launch.cuh", "step_tables.cuh", "step_split.cu",
-                "step_fp64.cu", "hydro.cuh")
+                "step_fp64.cu")
+GAS_SOURCES = ("m1_math.cuh", "m1_internal.h", "hydro.cuh", "hydro.cu")
 
 
-def kernel_hash():
+def kernel_hash(sources=STEP_SOURCES):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2606_26268_b300", "csrc")
-    for name in STEP_SOURCES:
+    for name in sources:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
     return h.hexdigest()[:16]
 
 
-def profiled_traffic(workload, precision):
-    """DRAM bytes per launch from a committed ncu summary of the same kernel
-    source (null if the kernel changed since the capture)."""
+def _sources_of(key):
+    return GAS_SOURCES if key.endswith("gas_step") else STEP_SOURCES
+
+
+def profiled_entry(workload, precision):
+    """The committed ncu record of the same kernel source, or None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(path) as f:
             d = json.load(f)
-        e = d.get("%s/%s" % (workload, precision))
-        if e and e.get("kernel_hash") == kernel_hash():
-            return float(e["dram_bytes_per_launch"])
+        key = "%s/%s" % (workload, precision)
+        e = d.get(key)
+        if e and e.get("kernel_hash") == kernel_hash(_sources_of(key)):
+            return e
     except Exception:
         pass
     return None
+
+
+# thread instructions issued per second at 2032 MHz: 148 SMs x 4 schedulers x
+# 32 lanes (one warp instruction per scheduler per clock)
+ISSUE_PEAK = 148 * 4 * 32 * 2.032e9
+
+
+def issue_view(workload, precision, cells, kernel_ms):
+    e = profiled_entry(workload, precision)
+    if not e or "thread_inst_per_cell" not in e:
+        return None
+    ipc = float(e["thread_inst_per_cell"])
+    achieved = ipc * cells / (kernel_ms * 1e-3)
+    return {"inst_per_cell": ipc, "achieved": achieved, "peak": ISSUE_PEAK,
+            "unit": "thread-inst/s", "frac": achieved / ISSUE_PEAK,
+            "peak_kind": "148 SM x 4 schedulers x 32 lanes x 2032 MHz"}
+
+
+def profiled_traffic(workload, precision):
+    """DRAM bytes per launch from a committed ncu summary of the same kernel
+    source (null if the kernel changed since the capture)."""
+    e = profiled_entry(workload, precision)
+    return float(e["dram_bytes_per_launch"]) if e else None
 
 
 class Clocks:
@@ -530,7 +558,11 @@ def run_ours(args):
                          "bytes_per_cell": bpc, "kernel_ms": kernel_ms,
                          "kernel": "fused step kernel (events around its launches)",
                          "queue_pass_ms": kt["queue_pass_ms"], "step_ms": statistics.mean(per),
-                         "traffic": profiled_traffic(prob.name, args.precision)},
+                         "traffic": profiled_traffic(prob.name, args.precision),
+                         # the bound this kernel actually meets: instruction
+                         # issue, from the ncu instruction count of the same
+                         # source (null if the kernel changed since)
+                         "issue": issue_view(prob.name, args.precision, N, kernel_ms)},
             "e2e": e2e,
             "cpu_baseline": cpu,
             "fp64_plain": fp64,
