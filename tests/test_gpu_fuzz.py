@@ -73,3 +73,29 @@ def test_random_configuration_fp64_matches_oracle(seed):
             p.riemann, p.implicit_mode, p.integrator, p.qirr is not None, p.hydro)
     for k, v in err.items():
         assert v <= 1e-11, (desc, k, v)
+
+
+@pytest.mark.parametrize("seed", range(32))
+def test_random_configuration_split_within_its_sensitivity(seed):
+    """The split form on the same random combinations (float-rounded inputs),
+    on a random launch shape, normwise within max(1e-5, 20x the oracle's own
+    change under input perturbations of FP32 size)."""
+    import paper_2606_26268_b300 as R
+    from helpers import rounded
+    p = rounded(random_case(seed), np.float32)
+    dt = oracle.Oracle(p).dt()
+    r = R.from_problem(p, "split")
+    nvar = r.get_launch()[2]
+    r.set_launch(int(np.random.default_rng(seed).integers(nvar)), 0)
+    r.step(3, dt)
+    assert r.sync() == 0, seed
+    g = {k: np.asarray(r.read(k), dtype=np.float64) for k in ("E", "e")}
+    r.close()
+    o = run_oracle(p, 3, dt=dt)
+    q = p.copy()
+    q.E = p.E * (1 + 1e-7 * np.random.default_rng(seed + 1).standard_normal(p.N))
+    o2 = run_oracle(q, 3, dt=dt)
+    for k in ("E", "e"):
+        err = np.linalg.norm(g[k] - o[k]) / np.linalg.norm(o[k])
+        sens = np.linalg.norm(o2[k] - o[k]) / np.linalg.norm(o[k])
+        assert err <= max(1e-5, 20 * sens), (seed, k, err, sens)
