@@ -1,0 +1,141 @@
+"""The optically thin shock tubes of Sect. 3.1 on the GPU (FP64, RK2,
+CFL 0.4): parity with the oracle at 2^8 cells for PLM and LimO3 with the
+f-preserving and flat (PLUTO) face treatments; the resolution study over
+2^5 ... 2^14 cells against a 2^17-cell PLM reference; the velocity and
+pressure analogs across the contact of tube 1 at 2^17 cells; and the
+oscillations of the flat treatment with LimO3 in tube 2."""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import errors, run_gpu, run_oracle
+from test_oracle_options import excess_variation, pressure_analog
+from test_oracle_step import golden_tubes, tube_problem
+
+pytestmark = pytest.mark.gpu
+
+T_END = 20.0
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2606_26268_b300 import build
+    build.build()
+
+
+class _State:
+    """E and F of a GPU run, in the attribute names of the oracle."""
+
+    def __init__(self, E, F):
+        self.E, self.F = E, F
+
+
+def gpu_tube(which, n, recon="plm", face_fix="fpreserve"):
+    """Tube `which` on n cells to t = 20 on the GPU in FP64 with RK2, the
+    CFL step of the grid shortened to divide t = 20 evenly."""
+    import paper_2606_26268_b300 as R
+    p, x = tube_problem(which, n, T_END, recon=recon, face_fix=face_fix, integrator="rk2")
+    r = R.from_problem(p, "fp64")
+    nst = int(math.ceil(T_END / r.dt()))
+    r.step(nst, T_END / nst)
+    assert r.sync() == 0
+    out = _State(np.asarray(r.read("E"), dtype=np.float64),
+                 np.asarray(r.read("F"), dtype=np.float64))
+    r.close()
+    return x, out
+
+
+_REF = {}
+
+
+def reference(which):
+    """The 2^17-cell PLM f-preserving solution of Sect. 3.1."""
+    if which not in _REF:
+        _REF[which] = gpu_tube(which, 2 ** 17)
+    return _REF[which]
+
+
+@pytest.mark.parametrize("which", [1, 2])
+@pytest.mark.parametrize("recon,face_fix", [("plm", "fpreserve"), ("limo3", "fpreserve"),
+                                            ("plm", "pluto"), ("limo3", "pluto")])
+def test_tubes_fp64_match_oracle(which, recon, face_fix):
+    """2^8 cells to t = 20 (320 two-stage steps), per cell within 1e-11 or
+    10x the oracle's own spread under input changes of a few ulps: tube 2 has
+    f = 1 on both sides, where the signal speeds vary like sqrt(1 - f) and a
+    rounding of f moves them by ~1e-8."""
+    p, _ = tube_problem(which, 256, T_END, recon=recon, face_fix=face_fix, integrator="rk2")
+    nst = int(math.ceil(T_END / (0.4 * 40.0 / 256)))
+    dt = T_END / nst
+    g = run_gpu(p, nst, "fp64", dt=dt)
+    o = run_oracle(p, nst, dt=dt)
+    q = p.copy()
+    q.E = p.E * (1 + 4e-16 * np.random.default_rng(which).standard_normal(p.N))
+    o2 = run_oracle(q, nst, dt=dt)
+    assert g["status"] == 0
+    spread = errors(o2, o, p.ncomp, p.chat, 1.0, nst)
+    err = errors(g, o, p.ncomp, p.chat, 1.0, nst)
+    for key in ("E", "F"):
+        assert err[key] <= max(1e-11, 10 * spread[key]), (key, err, spread)
+    if which == 1:
+        assert err["E"] <= 1e-11 and err["F"] <= 1e-11, err
+
+
+@pytest.mark.parametrize("which", [1, 2])
+def test_resolution_study_converges_at_the_printed_rate(which):
+    """Sect. 3.1: L1 error of E_r against the 2^17-cell reference for
+    2^5 ... 2^14 cells, PLM and LimO3.  The paper reports N^-1/2 for both
+    tubes.  The fitted exponent must lie within 0.25 of it: a shock converges
+    like N^-1 and a contact smeared by a limited scheme like N^-1/2 to N^-2/3,
+    and the last points sit only 8-16x below the reference."""
+    _, slope_printed = golden_tubes()
+    xr, ref = reference(which)
+    ns = [2 ** k for k in range(5, 15)]
+    for recon in ("plm", "limo3"):
+        errs = []
+        for n in ns:
+            _, s = gpu_tube(which, n, recon)
+            coarse = ref.E.reshape(n, -1).mean(axis=1)
+            errs.append(np.mean(np.abs(s.E - coarse)) * 40.0)
+        slope = np.polyfit(np.log(ns), np.log(errs), 1)[0]
+        print("tube", which, recon, "L1", ["%.3e" % e for e in errs], "slope %.3f" % slope)
+        assert np.all(np.diff(errs) < 0), (recon, errs)
+        assert abs(slope - slope_printed) <= 0.25, (recon, slope, errs)
+
+
+def test_tube1_contact_keeps_the_velocity_and_pressure_analogs_at_2_17_cells():
+    """Sect. 3.1, first tube at the paper's highest resolution: across the
+    contact-like discontinuity E jumps while beta_x (read as the contact
+    speed lambda_2, (3 xi - 1) F_x E / (2 |F|^2)) and Pi stay constant:
+    means over 0.8-wide windows on either side within 5e-3 and 1e-4."""
+    x, s = reference(1)
+    nF = np.linalg.norm(s.F, axis=0)
+    f = nF / s.E
+    xi = (3 + 4 * f * f) / (5 + 2 * np.sqrt(4 - 3 * f * f))
+    Pi = (1 - xi) * s.E / 2
+    window = (x > -6) & (x < 6)
+    j = np.argmax(np.abs(np.diff(s.F[1])) * window[:-1])
+    lo = (x > x[j] - 1.2) & (x < x[j] - 0.4)
+    hi = (x > x[j] + 0.4) & (x < x[j] + 1.2)
+    beta_lo = np.mean((3 * xi[lo] - 1) * s.F[0][lo] * s.E[lo] / (2 * nF[lo] ** 2))
+    beta_hi = np.mean((3 * xi[hi] - 1) * s.F[0][hi] * s.E[hi] / (2 * nF[hi] ** 2))
+    assert abs(np.mean(s.E[lo]) - np.mean(s.E[hi])) > 0.1
+    assert beta_lo == pytest.approx(beta_hi, rel=5e-3)
+    assert np.mean(Pi[lo]) == pytest.approx(np.mean(Pi[hi]), rel=1e-4)
+
+
+def test_tube2_flat_treatment_with_limo3_oscillates_on_the_gpu():
+    """Sect. 3.1, second tube at 2^8 cells: the flat treatment with LimO3
+    leaves spurious oscillations of Pi left of the contact, the f-preserving
+    faces with LimO3 do not, and they stay close to the 2^17-cell reference."""
+    ex = {}
+    for fix in ("fpreserve", "pluto"):
+        x, s = gpu_tube(2, 256, "limo3", fix)
+        ex[fix] = excess_variation(x, pressure_analog(s))
+    xr, ref = reference(2)
+    ex_ref = excess_variation(xr, pressure_analog(ref))
+    assert ex["pluto"] > 5 * ex["fpreserve"], (ex, ex_ref)
+    assert ex["fpreserve"] < 0.005 and ex_ref < 0.005, (ex, ex_ref)

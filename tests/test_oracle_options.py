@@ -105,6 +105,56 @@ def test_limo3_wave_is_more_accurate_than_plm():
 
 
 # ---------------------------------------------------------------------------
+# the free-streaming shock tube of Sect. 3.1 with the face treatments
+# ---------------------------------------------------------------------------
+
+def pressure_analog(o):
+    """Pi = (1 - xi) E / 2, the pressure analog of Sect. 3.1."""
+    f = np.minimum(np.linalg.norm(o.F, axis=0) / o.E, 1.0)
+    xi = (3 + 4 * f * f) / (5 + 2 * np.sqrt(4 - 3 * f * f))
+    return (1 - xi) * o.E / 2
+
+
+def excess_variation(x, Pi, x_end=4.2):
+    """Total variation of Pi on x < x_end beyond a monotone rise from its
+    first value to its maximum (zero for a clean shock-plateau profile).  In
+    tube 2 the contact-like discontinuity sits at x = 4.7 at t = 20."""
+    w = Pi[x < x_end]
+    return np.sum(np.abs(np.diff(w))) - (w.max() - w[0])
+
+
+def test_tube2_flat_treatment_with_limo3_oscillates_left_of_the_contact():
+    """Sect. 3.1, second tube (f = 1 on both sides), 2^8 cells, RK2: with
+    LimO3 the flat face treatment leaves spurious oscillations of Pi on the
+    left of the contact; the f-preserving faces do not.  Here their excess
+    variation is 15x the f-preserving one and 4x that of the flat treatment
+    with PLM."""
+    from test_oracle_step import run_tube
+    ex = {}
+    for recon in ("plm", "limo3"):
+        for fix in ("fpreserve", "pluto"):
+            x, o = run_tube(2, 256, recon=recon, face_fix=fix, integrator="rk2")
+            ex[recon, fix] = excess_variation(x, pressure_analog(o))
+    assert ex["limo3", "pluto"] > 5 * ex["limo3", "fpreserve"], ex
+    assert ex["limo3", "pluto"] > 2 * ex["plm", "pluto"], ex
+    assert ex["limo3", "fpreserve"] < 0.005 and ex["plm", "fpreserve"] < 0.005, ex
+
+
+@pytest.mark.parametrize("recon", ["plm", "limo3"])
+def test_tube2_f_preserving_faces_leave_a_small_peak_of_pi_at_the_contact(recon):
+    """Sect. 3.1, second tube: with the f-preserving faces Pi is flat behind
+    the left shock and shows a small peak just left of the contact (here 4-5%
+    above the plateau at 2^8 cells)."""
+    from test_oracle_step import run_tube
+    x, o = run_tube(2, 256, recon=recon, face_fix="fpreserve", integrator="rk2")
+    Pi = pressure_analog(o)
+    plateau = Pi[(x > 0) & (x < 3)]
+    peak = Pi[(x > 3) & (x < 4.7)].max()
+    assert np.ptp(plateau) < 0.01 * plateau.mean(), np.ptp(plateau)
+    assert 1.02 < peak / plateau.mean() < 1.08, peak / plateau.mean()
+
+
+# ---------------------------------------------------------------------------
 # f <= 1 treatments of face states
 # ---------------------------------------------------------------------------
 

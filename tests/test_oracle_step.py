@@ -270,13 +270,22 @@ def golden_tubes():
     return states, slope
 
 
-def run_tube(which, n, t_end=20.0):
+def tube_problem(which, n, t_end=20.0, **opts):
+    """Tube `which` of Sect. 3.1 on n cells with its printed left/right
+    states; opts set the reconstruction, face treatment or integrator."""
     p = W.shock_tube(which, n, t_end)
     states, _ = golden_tubes()
     x, _, _ = W.mesh(p)
     for side, mask in (("L", x < 0), ("R", x >= 0)):
         E, Fx, Fy = states[(which, side)]
         p.E[mask], p.F[0][mask], p.F[1][mask] = E, Fx, Fy
+    for key, v in opts.items():
+        setattr(p, key, v)
+    return p, x
+
+
+def run_tube(which, n, t_end=20.0, **opts):
+    p, x = tube_problem(which, n, t_end, **opts)
     o = oracle.Oracle(p, nthreads=0)
     dt = o.dt()
     nst = int(math.ceil(t_end / dt))
@@ -295,7 +304,8 @@ def test_shock_tube_1_contact_has_constant_velocity_and_pressure_analogs():
     nF = np.sqrt(Fx ** 2 + Fy ** 2)
     f = nF / E
     xi = (3 + 4 * f * f) / (5 + 2 * np.sqrt(4 - 3 * f * f))
-    beta = (3 * xi - 1) * Fx * E / (2 * nF * nF)
+    with np.errstate(invalid="ignore"):  # F = 0 right of the rarefaction
+        beta = (3 * xi - 1) * Fx * E / (2 * nF * nF)
     Pi = (1 - xi) * E / 2
     # locate the contact: largest jump of F_y away from the outer waves
     window = (x > -6) & (x < 6)
