@@ -483,7 +483,7 @@ def run_ours(args):
     # RK2 (gas step, radiation transport, sources in each stage) ------------
     if not args.skip_forms and not args.skip_rhd:
         import workloads as W
-        pr = W.pulse_3d_rhd(256)
+        pr = W.pulse_3d_rhd(args.rhd_n)
         rr = R.from_problem(pr, args.precision, device=dev)
         tvr = rr.tune(2)
         dtr = rr.dt()
@@ -668,6 +668,7 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-disk", action="store_true")
     ap.add_argument("--skip-rhd", action="store_true")
+    ap.add_argument("--rhd-n", type=int, default=256, help="RHD pulse grid (n^3)")
     ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":

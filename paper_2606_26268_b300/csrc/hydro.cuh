@@ -32,6 +32,7 @@ struct HydroArgs {
   S* m_out[3];
   T dt, gamma, cvfac;
   T inv_gm1;         // 1 / (Gamma - 1)
+  T uni_inv[3];      // 1 / h per direction (uniform grids)
   T bcT[3][2];       // gas temperature of the fixed and LTE sides
 };
 
@@ -167,6 +168,10 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
   __shared__ T s_w[5][SY][SX];
   __shared__ T s_fx[5][TY][TX + 1];
   __shared__ T s_fy[5][HY ? TY + 1 : 1][TX];
+  // split precision: the tile's own input (rho, m, e) staged with the plane,
+  // so that the update reads it from shared memory (FP64 reads it again)
+  constexpr bool SU = P::kSplit;
+  __shared__ T s_u[SU ? 5 : 1][SU ? TY : 1][SU ? TX : 1];
 
   const StepDims& Dm = h.dim;
   const GeomDev<T>& G = h.geo;
@@ -242,15 +247,41 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
 #pragma unroll
         for (int v = 0; v < 3; ++v) s_w[1 + v][iy][ix] = T(pre[kk][1 + v]) * ir;
         s_w[4][iy][ix] = (h.gamma - T(1)) * T(pre[kk][4]);
+        if constexpr (SU) {
+          const int ux = ix - 2, uy = iy - OY;
+          if (ux >= 0 && ux < TX && uy >= 0 && uy < TY) {
+#pragma unroll
+            for (int q = 0; q < 5; ++q) s_u[q][uy][ux] = T(pre[kk][q]);
+          }
+        }
       }
     }
   };
+  // the own column two planes above the current one, loaded an iteration
+  // ahead
+  S zpre[5];
+  auto load_col = [&](int zz) {
+    const long long ip = col + (long long)(zz + gz) * sz;
+    zpre[0] = __ldg(h.rho + ip);
+#pragma unroll
+    for (int v = 0; v < 3; ++v) zpre[1 + v] = v < NC ? __ldg(h.m[v] + ip) : S(0);
+    zpre[4] = __ldg(h.e + ip);
+  };
+  if constexpr (HZ) load_col(z0 + 2);
   load_plane(z0);
 
   for (int z = z0; z < z1; ++z) {
     const long long zoff = (long long)(z + gz) * sz;
     store_plane();
-    if constexpr (HZ) prim(col + (long long)(z + 2 + gz) * sz, wz[4]);
+    if constexpr (HZ) {
+      const T r = T(zpre[0]);
+      const T ir = Ops<T>::rcp(r);
+      wz[4][0] = r;
+#pragma unroll
+      for (int v = 0; v < 3; ++v) wz[4][1 + v] = v < NC ? T(zpre[1 + v]) * ir : T(0);
+      wz[4][4] = (h.gamma - T(1)) * T(zpre[4]);
+      if (z + 1 < z1) load_col(z + 3);
+    }
     __syncthreads();
     if (z + 1 < z1) load_plane(z + 1);
     // faces of the tile directions: the lower x (and y) face of the own cell;
@@ -322,28 +353,28 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
       const long long ic = col + zoff;
       T U[5];
       {
-        const T r = T(__ldg(h.rho + ic));
+        const T r = SU ? s_u[0][ty][tx] : T(__ldg(h.rho + ic));
         U[0] = r;
         T ke = T(0);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          U[1 + v] = v < NC ? T(__ldg(h.m[v] + ic)) : T(0);
+          U[1 + v] = v < NC ? (SU ? s_u[1 + v][ty][tx] : T(__ldg(h.m[v] + ic))) : T(0);
           ke += U[1 + v] * U[1 + v];
         }
-        U[4] = T(__ldg(h.e + ic)) + T(0.5) * ke * Ops<T>::rcp(r);
+        U[4] = (SU ? s_u[4][ty][tx] : T(__ldg(h.e + ic))) + T(0.5) * ke * Ops<T>::rcp(r);
       }
       {
-        const T ih = gtab(G, 0, TAB_ALO, px);
+        const T ih = UNI ? h.uni_inv[0] : gtab(G, 0, TAB_ALO, px);
 #pragma unroll
         for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (s_fx[q][ty][tx + 1] - s_fx[q][ty][tx]);
       }
       if constexpr (HY) {
-        const T ih = gtab(G, 1, TAB_ALO, py);
+        const T ih = UNI ? h.uni_inv[1] : gtab(G, 1, TAB_ALO, py);
 #pragma unroll
         for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (s_fy[q][ty + 1][tx] - s_fy[q][ty][tx]);
       }
       if constexpr (HZ) {
-        const T ih = gtab(G, 2, TAB_ALO, z + gz);
+        const T ih = UNI ? h.uni_inv[2] : gtab(G, 2, TAB_ALO, z + gz);
 #pragma unroll
         for (int q = 0; q < 5; ++q) U[q] -= h.dt * ih * (fzhi[q] - fzlo[q]);
       }

@@ -969,6 +969,7 @@ static cudaError_t enqueue_gas(rad_ctx* c, double dt, int in_buf, int rho_buf) {
   h.gamma = T(c->par.gamma_gas);
   h.inv_gm1 = T(1.0 / (c->par.gamma_gas - 1.0));
   h.cvfac = T(1.0 / (c->par.mu * (c->par.gamma_gas - 1.0)));
+  for (int d = 0; d < 3; ++d) h.uni_inv[d] = T(1.0 / (c->xf[d][1] - c->xf[d][0]));
   return c->hydro_fn(&h, c->stream);
 }
 
