@@ -487,6 +487,10 @@ def run_ours(args):
         rr = R.from_problem(pr, args.precision, device=dev)
         tvr = rr.tune(2)
         dtr = rr.dt()
+        tc = time.perf_counter()
+        for _ in range(5):
+            rr.dt()  # the gas CFL reduction and its 8-byte read-back
+        cfl_ms = (time.perf_counter() - tc) / 5 * 1e3
         nr = 6
         msr, perr, ktr = time_steps(rr, torch, nr, 3, dtr)
         srr = rr.sync()
@@ -507,6 +511,7 @@ def run_ours(args):
                 "bytes_per_cell": gas_bytes // pr.N,
                 "traffic": profiled_traffic(pr.name, args.precision + "/gas_step")},
             "launches_per_step": 4, "status": int(srr),
+            "cfl_ms": cfl_ms,
             "launch": {"variant": tvr[0], "chunk": tvr[1]},
             "paper": "7.6e8 (MI250X node) and 1.2e9 (MI300 node) cell updates/s for this "
                      "cycle with 256^3 per node; not the same hardware"}

@@ -431,7 +431,9 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
 // The CFL step with the gas: the largest over cells of
 // sum_d max(chat, |v_d| + c_s) / h_d (c_s = sqrt(Gamma (Gamma - 1) e / rho)),
 // reduced into *out as the bits of a non-negative double (whose order is
-// the order of the bit patterns).
+// the order of the bit patterns).  Computed in the precision of the
+// transport (FP32 for the split form, whose step only needs the CFL bound
+// to rounding; FP64 for the FP64 form), with one reciprocal of rho per cell.
 template <class P>
 struct GasCflArgs {
   using S = typename P::S;
@@ -447,9 +449,11 @@ struct GasCflArgs {
 
 template <class P, int NDIM, int NC>
 __global__ void __launch_bounds__(256) gas_cfl_kernel(const __grid_constant__ GasCflArgs<P> g) {
+  using T = typename P::T;
   const StepDims& Dm = g.dim;
   const long long N = (long long)Dm.n[0] * Dm.n[1] * Dm.n[2];
-  double worst = 0.0;
+  const T chat = T(g.chat), gg1 = T(g.gamma * (g.gamma - 1.0));
+  T worst = T(0);
   for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < N;
        q += (long long)gridDim.x * blockDim.x) {
     long long r = q;
@@ -459,24 +463,25 @@ __global__ void __launch_bounds__(256) gas_cfl_kernel(const __grid_constant__ Ga
     const int k = int(r / Dm.n[1]);
     const int pc[3] = {i + Dm.g[0], j + Dm.g[1], k + Dm.g[2]};
     const long long ic = pc[0] + Dm.sy * pc[1] + Dm.sz * pc[2];
-    const double rho = double(g.rho[ic]);
-    const double cs = sqrt(g.gamma * (g.gamma - 1.0) * double(g.e[ic]) / rho);
-    double sum = 0.0;
+    const T ir = T(1) / T(g.rho[ic]);
+    const T cs = Ops<T>::sqrt_(gg1 * T(g.e[ic]) * ir);
+    T sum = T(0);
 #pragma unroll
     for (int d = 0; d < NDIM; ++d) {
-      const double v = fabs(double(g.m[d][ic]) / rho) + cs;
-      const double w = double(g.geo.tab[d][TAB_WID * g.geo.len[d] + pc[d]]);
-      sum += (v > g.chat ? v : g.chat) / w;
+      const T vd = T(g.m[d][ic]) * ir;
+      const T v = (vd < T(0) ? -vd : vd) + cs;
+      const T w = g.geo.tab[d][TAB_WID * g.geo.len[d] + pc[d]];
+      sum += (v > chat ? v : chat) / w;
     }
     worst = sum > worst ? sum : worst;
   }
 #pragma unroll
   for (int off = 16; off > 0; off >>= 1) {
-    const double o = __shfl_down_sync(0xffffffffu, worst, off);
+    const T o = __shfl_down_sync(0xffffffffu, worst, off);
     worst = o > worst ? o : worst;
   }
   if ((threadIdx.x & 31) == 0)
-    atomicMax(g.out, static_cast<unsigned long long>(__double_as_longlong(worst)));
+    atomicMax(g.out, static_cast<unsigned long long>(__double_as_longlong(double(worst))));
 }
 
 }  // namespace m1

@@ -136,6 +136,21 @@ def test_gas_cfl_step_matches_oracle_and_drives_automatic_steps():
     r.close()
 
 
+def test_gas_cfl_step_in_the_split_form_is_the_oracles_to_float_rounding():
+    """The split form reduces the CFL bound in FP32: on float-rounded 3D
+    inputs it equals the oracle's step within 1e-6."""
+    import paper_2606_26268_b300 as R
+    p = rounded(W.random_smooth("cartesian", (40, 33, 29), 3, seed=1600, bc="periodic", ncomp=3,
+                                fmax=0.8), np.float32)
+    p.hydro = True
+    p.v = np.asarray(p.v) * 50.0  # gas signal speeds above chat in part of the box
+    p = rounded(p, np.float32)
+    o = oracle.Oracle(p)
+    r = R.from_problem(p, "split")
+    assert r.dt() == pytest.approx(o.dt(), rel=1e-6)
+    r.close()
+
+
 def test_gas_on_every_launch_shape():
     """With evolved gas the TMA-staged kernels read rho* and e* through their
     own tensor maps: every shape gives the same split RK2 steps."""
