@@ -93,14 +93,14 @@ __device__ __forceinline__ void face_state1(const T (&um)[4], const T (&uc)[4], 
 
 // GEN: the general coupling and epilogue (absorption only, irradiation,
 // evolved gas); the face computation is always the default scheme.
-template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN = false>
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN = false, int GEOM = kCart>
 __global__ void __launch_bounds__(TX * TY, MINB)
     step_tma2_kernel(const __grid_constant__ StepArgs<P> a, const __grid_constant__ TmaMaps tm) {
   static_assert(P::kSplit, "TMA staging is built for the split precision");
   using S = typename P::S;
   using T = typename P::T;
   using TL = Tma2Tile<TX, TY>;
-  constexpr int NDIM = 3, GEOM = kCart;
+  constexpr int NDIM = 3;
   constexpr int NV = 1 + NC, NF = NC + 3, R = kTmaRing;
   constexpr int BX = TL::BX, BY = TL::BY, BOXP = TL::BOXP;
   constexpr int SLOT = NF * BOXP;
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     if (in_col) {
       const T (&u)[4] = q[0];
       T Us[4];
-      if constexpr (NV == 4) {  // flux divergence on packed pairs
+      if constexpr (GEOM == kCart && NV == 4) {  // flux divergence on packed pairs
         const float2 mx = make_float2(-AHI(0, px), -AHI(0, px)), px_ = make_float2(ALO(0, px), ALO(0, px));
         const float2 my = make_float2(-AHI(1, py), -AHI(1, py)), py_ = make_float2(ALO(1, py), ALO(1, py));
         const float2 mz = make_float2(-AHI(2, m + 2), -AHI(2, m + 2));
@@ -396,21 +396,57 @@ __global__ void __launch_bounds__(TX * TY, MINB)
           Us[h + 1] = us.y;
         }
       } else {
+        // unsplit divergence with the factorised area/volume ratios; on
+        // curvilinear grids the angular-momentum form of the phi component
+        // and the geometric sources of the centred pressure tensor
         T dU[4] = {0, 0, 0, 0};
         {
-          T alo = ALO(0, px), ahi = AHI(0, px);
+          const T alo = ALO(0, px), ahi = AHI(0, px);
 #pragma unroll
           for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fx[v][ty][tx + 1] - alo * s_fx[v][ty][tx];
+          if constexpr (GEOM != kCart) {
+            constexpr int PH = GEOM == kCyl ? 2 : 3;  // the phi component
+            const T fhi = s_fx[PH][ty][tx + 1], flo = s_fx[PH][ty][tx];
+            dU[PH] += ahi * fhi - alo * flo;
+            dU[PH] -= tabv(G, 0, TAB_AMHI, px) * fhi - tabv(G, 0, TAB_AMLO, px) * flo;
+          }
         }
+        const T met0 = GEOM != kCart ? tabv(G, 0, TAB_MET, px) : T(1);
         {
           T alo = ALO(1, py), ahi = AHI(1, py);
+          if constexpr (GEOM != kCart) {
+            alo *= met0;
+            ahi *= met0;
+          }
 #pragma unroll
           for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fy[v][ty + 1][tx] - alo * s_fy[v][ty][tx];
+          if constexpr (GEOM == kSph) {
+            const T fhi = s_fy[3][ty + 1][tx], flo = s_fy[3][ty][tx];
+            dU[3] += ahi * fhi - alo * flo;
+            dU[3] -= met0 * (tabv(G, 1, TAB_AMHI, py) * fhi - tabv(G, 1, TAB_AMLO, py) * flo);
+          }
         }
         {
           T alo = ALO(2, m + 2), ahi = AHI(2, m + 2);
+          if constexpr (GEOM == kSph) {
+            const T f = met0 * tabv(G, 1, TAB_PHF, py);
+            alo *= f;
+            ahi *= f;
+          }
 #pragma unroll
           for (int v = 0; v < NV; ++v) dU[v] -= ahi * zhi[v] - alo * zlo[v];
+        }
+        if constexpr (GEOM != kCart) {
+          T pa, pb;
+          pressure<T, NC>(u, pa, pb);
+          if constexpr (GEOM == kCyl) {
+            dU[1] += chat * met0 * (pa + pb * u[2] * u[2]);
+          } else {
+            const T Ft = u[2], Fp = u[3];
+            const T Ptt = pa + pb * Ft * Ft, Ppp = pa + pb * Fp * Fp, Prt = pb * u[1] * Ft;
+            dU[1] += chat * met0 * (Ptt + Ppp);
+            dU[2] += chat * met0 * (tabv(G, 1, TAB_MET, py) * Ppp - Prt);
+          }
         }
 #pragma unroll
         for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];

@@ -47,14 +47,14 @@ cudaError_t launch_tma(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk
   return cudaGetLastError();
 }
 
-template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN>
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN, int GEOM = kCart>
 cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk) {
   if (!tma) return cudaErrorInvalidValue;
   const int* n = a.dim.n;
   a.chunk = chunk > 0 ? chunk : 32;
   if (a.chunk > n[2]) a.chunk = n[2];
   constexpr size_t smem = tma2_smem_bytes<NC, TX, TY>();
-  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB, GEN>;
+  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB, GEN, GEOM>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   TmaMaps maps;
@@ -67,20 +67,28 @@ cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chun
 // CTA shapes.  3D: 32x8 (2 or 3 CTAs/SM), 32x16, 64x8, and for the split
 // precision on Cartesian grids the TMA-staged 32x8 with overlapping tiles
 // (variants 4, 5) and with non-overlapping tiles (6, 7), each at 2 or 3
-// CTAs/SM; 2D rows of 128, 256 or 64 threads; 1D: 128.  Curvilinear grids
-// get the default shape only.  The general form (GEN: face options,
+// CTAs/SM; 2D rows of 128, 256 or 64 threads; 1D: 128.  Curvilinear 3D
+// grids in the split precision: the default shape and the TMA-staged
+// non-overlapping 32x8 at 2 or 3 CTAs/SM (variants 1, 2); other curvilinear
+// grids the default shape only.  The general form (GEN: face options,
 // absorption only, irradiation, evolved gas) has the TMA-staged shapes only
 // when it keeps the default face scheme (TMA_OK).
 template <class P, int NDIM, int GEOM, int NC, bool UNI, bool GEN = false, bool TMA_OK = true>
 struct Shapes {
   static constexpr bool tma = TMA_OK && P::kSplit && GEOM == kCart && NDIM == 3;
+  static constexpr bool tma_curv = TMA_OK && P::kSplit && GEOM != kCart && NDIM == 3;
   static constexpr int count =
-      (GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 8 : 4) : 3);
+      tma_curv ? 3 : ((GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 8 : 4) : 3));
   static cudaError_t launch(const void* vargs, const void* maps, cudaStream_t s, int variant,
                             int chunk) {
     const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
     if (variant < 0 || variant >= count) variant = 0;
     if constexpr (NDIM == 3) {
+      if constexpr (tma_curv) {
+        if (variant == 1) return launch_tma2<P, NC, UNI, 32, 8, 2, GEN, GEOM>(a, maps, s, chunk);
+        if (variant == 2) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN, GEOM>(a, maps, s, chunk);
+        return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2, GEN>(a, s, chunk);
+      }
       if constexpr (tma) {
         if (variant == 4) return launch_tma<P, NC, UNI, 32, 8, 2, GEN>(a, maps, s, chunk);
         if (variant == 5) return launch_tma<P, NC, UNI, 32, 8, 3, GEN>(a, maps, s, chunk);
@@ -116,6 +124,12 @@ LaunchEntry entry() {
       e.tma_box[v][1] = TmaTile<32, 8>::BY;
     }
     for (int v = 6; v < 8; ++v) {
+      e.tma_box[v][0] = Tma2Tile<32, 8>::BX;
+      e.tma_box[v][1] = Tma2Tile<32, 8>::BY;
+    }
+  }
+  if constexpr (Sh::tma_curv) {
+    for (int v = 1; v < 3; ++v) {
       e.tma_box[v][0] = Tma2Tile<32, 8>::BX;
       e.tma_box[v][1] = Tma2Tile<32, 8>::BY;
     }

@@ -6,8 +6,8 @@
 
 namespace m1 {
 
-// tma: offer the TMA-staged shapes (split 3D Cartesian; the general form
-// only when it keeps the default face scheme).
+// tma: offer the TMA-staged shapes (split 3D; the general form only when it
+// keeps the default face scheme).
 template <class P, bool GEN>
 LaunchEntry select_table(int ndim, int geom, int nc, bool uni, bool tma) {
   if (geom == kCart && uni) {
@@ -34,12 +34,14 @@ LaunchEntry select_table(int ndim, int geom, int nc, bool uni, bool tma) {
   if (geom == kCyl) {
     if (ndim == 1) return entry<P, 1, kCyl, 3, false, GEN>();
     if (ndim == 2) return entry<P, 2, kCyl, 3, false, GEN>();
-    if (ndim == 3) return entry<P, 3, kCyl, 3, false, GEN>();
+    if (ndim == 3)
+      return tma ? entry<P, 3, kCyl, 3, false, GEN, true>() : entry<P, 3, kCyl, 3, false, GEN, false>();
   }
   if (geom == kSph) {
     if (ndim == 1) return entry<P, 1, kSph, 3, false, GEN>();
     if (ndim == 2) return entry<P, 2, kSph, 3, false, GEN>();
-    if (ndim == 3) return entry<P, 3, kSph, 3, false, GEN>();
+    if (ndim == 3)
+      return tma ? entry<P, 3, kSph, 3, false, GEN, true>() : entry<P, 3, kSph, 3, false, GEN, false>();
   }
   return LaunchEntry{nullptr, 0};
 }

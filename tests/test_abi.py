@@ -33,8 +33,8 @@ def test_every_declared_function_is_exported(R):
     assert set(names) == set(R.EXPORTS)
 
 
-def _grid(R, n=(8, 1, 1), ndim=1):
-    xs = [np.linspace(0, 1, k + 1) for k in n]
+def _grid(R, n=(8, 1, 1), ndim=1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
+    xs = [np.linspace(lo[d], hi[d], n[d] + 1) for d in range(3)]
     g = R.rad_grid()
     g.ndim = ndim
     for d in range(3):
@@ -163,3 +163,29 @@ def test_general_form_offers_the_right_launch_shapes(R):
     assert shapes(implicit_mode=R.RAD_ABSORPTION_ONLY) == 8
     assert shapes(reconstruction=R.RAD_LIMO3) == 4
     assert shapes(face_fix=R.RAD_FIX_PLUTO, hydro=1) == 4
+
+
+@pytest.mark.parametrize("geometry", [1, 2])
+def test_curvilinear_grids_offer_the_tma_staged_shapes_in_the_split_form(R, geometry):
+    """Split 3D cylindrical and spherical grids: the register-tiled shape and
+    the TMA-staged non-overlapping 32x8 at 2 and 3 CTAs/SM; FP64, or a face
+    option of Sect. 2.5: the register-tiled shape only."""
+    L = R.lib()
+    g, xs = _grid(R, (16, 16, 16), 3, lo=(1.0, 0.5, 0.0), hi=(2.0, 2.5, 1.0))
+    o = R.rad_opacity()
+
+    def shapes(**kw):
+        p = R.default_params()
+        for k, v in kw.items():
+            setattr(p, k, v)
+        c2 = C.c_void_p()
+        assert L.rad_create(C.byref(g), geometry, C.byref(o), C.byref(p), C.byref(c2)) == R.RAD_OK
+        nv = C.c_int()
+        assert L.rad_get_launch(c2, None, None, C.byref(nv)) == R.RAD_OK
+        L.rad_destroy(c2)
+        return nv.value
+
+    assert shapes(precision=R.RAD_FP32_SPLIT) == 3
+    assert shapes(precision=R.RAD_FP32_SPLIT, irradiation=1) == 3
+    assert shapes(precision=R.RAD_FP32_SPLIT, reconstruction=R.RAD_LIMO3) == 1
+    assert shapes(precision=R.RAD_FP64) == 1
