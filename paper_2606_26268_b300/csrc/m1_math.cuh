@@ -160,25 +160,21 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
   if (NC > 1) nF2 += F[1] * F[1];
   if (NC > 2) nF2 += F[2] * F[2];
   const T Fd = (D < NC) ? F[D] : T(0);
-  T f, fc, c2;
+  T f, fc, c2, b;
   T invE = Ops<T>::rcp(E);
   if constexpr (sizeof(T) == 8) {
-    // f and cos(theta) by correctly rounded divisions, so that a state with
-    // |F| = E (or F along an axis) has f = 1 (cos(theta) = +/-1) exactly and
-    // free streaming stays exact; 1/s is taken once for both speeds (the
-    // FP64 pipe runs at a small fraction of the FP32 rate, and a division
-    // costs several of its instructions)
     T nF = sqrt(nF2);
     f = nF / E;
     if (f > T(1)) f = T(1);
     T cth = (nF > T(0)) ? Fd / nF : T(0);
     fc = f * cth;
     c2 = cth * cth;
+    b = T(0);
     T f2 = f * f;
     T s = sqrt(T(4) - T(3) * f2);
     T xi = (T(3) + T(4) * f2) / (T(5) + T(2) * s);
     T a = T(0.5) * (T(1) - xi) * E;
-    const T b = (nF > T(0)) ? T(0.5) * (T(3) * xi - T(1)) * E / nF2 : T(0);
+    if (nF > T(0)) b = T(0.5) * (T(3) * xi - T(1)) * E / nF2;
     flux[0] = chat * Fd;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -188,9 +184,8 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
     }
     T z2 = T(2) * (T(1) - f2) * (s * (T(1) + c2) - T(2) * c2) / (s + T(1));
     T z = sqrt(z2 > T(0) ? z2 : T(0));
-    const T rs = T(1) / s;
-    lp = (fc + z) * rs;
-    lm = (fc - z) * rs;
+    lp = (fc + z) / s;
+    lm = (fc - z) / s;
   } else {
     // A denormal |F|^2 is treated as zero flux: the flush-to-zero rsqrt would
     // turn it into an infinite 1/|F|, and the closure depends on the
