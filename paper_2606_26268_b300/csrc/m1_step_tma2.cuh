@@ -93,7 +93,11 @@ __device__ __forceinline__ void face_state1(const T (&um)[4], const T (&uc)[4], 
 
 // GEN: the general coupling and epilogue (absorption only, irradiation,
 // evolved gas); the face computation is always the default scheme.
-template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN = false, int GEOM = kCart>
+// UYZ: directions 1 and 2 evenly spaced (a curvilinear grid stretched in
+// its first direction only): their reconstruction takes the uniform form,
+// while the area/volume ratios stay tabulated.
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN = false, int GEOM = kCart,
+          bool UYZ = false>
 __global__ void __launch_bounds__(TX * TY, MINB)
     step_tma2_kernel(const __grid_constant__ StepArgs<P> a, const __grid_constant__ TmaMaps tm) {
   static_assert(P::kSplit, "TMA staging is built for the split precision");
@@ -142,9 +146,11 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   const T chat = a.chat;
   const int own = (ty + 2) * BX + tx + 2;
 
-  auto IXC = [&](int d, int ip) -> T { return UNI ? T(1) : tabv(G, d, TAB_IDXC, ip); };
-  auto HHI = [&](int d, int ip) -> T { return UNI ? T(0.5) : tabv(G, d, TAB_HHI, ip); };
-  auto HLO = [&](int d, int ip) -> T { return UNI ? T(-0.5) : tabv(G, d, TAB_HLO, ip); };
+  constexpr bool U1 = UNI || UYZ;  // directions 1 and 2 evenly spaced
+  auto even = [](int d) { return d == 0 ? UNI : U1; };
+  auto IXC = [&](int d, int ip) -> T { return even(d) ? T(1) : tabv(G, d, TAB_IDXC, ip); };
+  auto HHI = [&](int d, int ip) -> T { return even(d) ? T(0.5) : tabv(G, d, TAB_HHI, ip); };
+  auto HLO = [&](int d, int ip) -> T { return even(d) ? T(-0.5) : tabv(G, d, TAB_HLO, ip); };
   auto ALO = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_ALO, ip); };
   auto AHI = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_AHI, ip); };
   auto slot = [&](int j) -> const float* { return s_ring + (j % R) * SLOT; };
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const int pm = m0 + 2;
     inv_own = Ops<T>::rcp(q[0][0]);
     n2_own = flux2<T, NC>(q[0]);
-    int nf = face4<T, NC, 2, UNI>(qm2, qm1, q[0], q[1], IXC(2, pm - 2), IXC(2, pm - 1),
+    int nf = face4<T, NC, 2, U1>(qm2, qm1, q[0], q[1], IXC(2, pm - 2), IXC(2, pm - 1),
                                   IXC(2, pm), HHI(2, pm - 1), HLO(2, pm),
                                   T(0.5) * (tau_prev + tau_m), chat, inv_own, n2_own, zlo);
     if (in_col) cnt.fix += nf >> 1;  // the lower z state of cell m0
@@ -263,7 +269,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                                        HHI(0, px), n2_own, inv_own, lox, hx);
       state_at(sl0, own - BX, um);
       state_at(sl0, own + BX, up);
-      nf += face_states<T, NC, UNI>(um, q[0], up, IXC(1, py - 1), IXC(1, py), HLO(1, py),
+      nf += face_states<T, NC, U1>(um, q[0], up, IXC(1, py - 1), IXC(1, py), HLO(1, py),
                                     HHI(1, py), n2_own, inv_own, loy, hy);
       if (in_col) cnt.fix += nf;
 #pragma unroll
@@ -353,7 +359,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     {
       const int pm = m + 3;  // padded z of cell m + 1
       T loN[4];
-      if constexpr (UNI) {
+      if constexpr (U1) {
         uni_states<T, NV>(q[0], q[1], q[2], loN, hiN);
       } else {
         T ix1 = IXC(2, pm - 1), ix2 = IXC(2, pm);

@@ -300,8 +300,20 @@ extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_o
   }
   const bool options =
       p.reconstruction != RAD_PLM || p.face_fix != RAD_FIX_FPRESERVE || p.riemann != RAD_HLL;
-  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc, c->uniform,
-                            c->general, options);
+  // directions 1 and 2 evenly spaced (a grid stretched in its first
+  // direction only, such as a log-spaced radius)
+  bool even_yz = c->ndim == 3;
+  for (int d = 1; d < 3 && even_yz; ++d) {
+    const std::vector<double>& x = c->xf[d];
+    const double w0 = x[1] - x[0];
+    for (int i = 1; i < c->n[d]; ++i)
+      if (std::fabs((x[i + 1] - x[i]) - w0) > 1e-12 * w0) {
+        even_yz = false;
+        break;
+      }
+  }
+  c->launch = select_launch(p.precision == RAD_FP32_SPLIT, c->ndim, geometry, c->nc,
+                            (c->uniform ? 1 : 0) | (even_yz ? 2 : 0), c->general, options);
   c->qpass = select_queue_pass(p.precision == RAD_FP32_SPLIT, c->ndim, c->nc);
   if (!c->launch.fn) {
     delete c;

@@ -3,7 +3,7 @@
 #include "step_tables.cuh"
 
 namespace m1 {
-LaunchEntry select_fp64(int ndim, int geom, int nc, bool uni) {
+LaunchEntry select_fp64(int ndim, int geom, int nc, int uni) {
   return select_table<Fp64, false>(ndim, geom, nc, uni, true);
 }
 }  // namespace m1

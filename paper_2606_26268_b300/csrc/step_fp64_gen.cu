@@ -3,7 +3,7 @@
 #include "step_tables.cuh"
 
 namespace m1 {
-LaunchEntry select_fp64_gen(int ndim, int geom, int nc, bool uni, bool tma) {
+LaunchEntry select_fp64_gen(int ndim, int geom, int nc, int uni, bool tma) {
   return select_table<Fp64, true>(ndim, geom, nc, uni, tma);
 }
 }  // namespace m1

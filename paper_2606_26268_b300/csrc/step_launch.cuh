@@ -47,14 +47,15 @@ cudaError_t launch_tma(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk
   return cudaGetLastError();
 }
 
-template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN, int GEOM = kCart>
+template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN, int GEOM = kCart,
+          bool UYZ = false>
 cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk) {
   if (!tma) return cudaErrorInvalidValue;
   const int* n = a.dim.n;
   a.chunk = chunk > 0 ? chunk : 32;
   if (a.chunk > n[2]) a.chunk = n[2];
   constexpr size_t smem = tma2_smem_bytes<NC, TX, TY>();
-  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB, GEN, GEOM>;
+  auto kern = step_tma2_kernel<P, NC, UNI, TX, TY, MINB, GEN, GEOM, UYZ>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
   if (e != cudaSuccess) return e;
   TmaMaps maps;
@@ -72,8 +73,10 @@ cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chun
 // non-overlapping 32x8 at 2 or 3 CTAs/SM (variants 1, 2); other curvilinear
 // grids the default shape only.  The general form (GEN: face options,
 // absorption only, irradiation, evolved gas) has the TMA-staged shapes only
-// when it keeps the default face scheme (TMA_OK).
-template <class P, int NDIM, int GEOM, int NC, bool UNI, bool GEN = false, bool TMA_OK = true>
+// when it keeps the default face scheme (TMA_OK).  UYZ: directions 1 and 2
+// evenly spaced (for the TMA-staged curvilinear shapes).
+template <class P, int NDIM, int GEOM, int NC, bool UNI, bool GEN = false, bool TMA_OK = true,
+          bool UYZ = false>
 struct Shapes {
   static constexpr bool tma = TMA_OK && P::kSplit && GEOM == kCart && NDIM == 3;
   static constexpr bool tma_curv = TMA_OK && P::kSplit && GEOM != kCart && NDIM == 3;
@@ -85,8 +88,8 @@ struct Shapes {
     if (variant < 0 || variant >= count) variant = 0;
     if constexpr (NDIM == 3) {
       if constexpr (tma_curv) {
-        if (variant == 1) return launch_tma2<P, NC, UNI, 32, 8, 2, GEN, GEOM>(a, maps, s, chunk);
-        if (variant == 2) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN, GEOM>(a, maps, s, chunk);
+        if (variant == 1) return launch_tma2<P, NC, UNI, 32, 8, 2, GEN, GEOM, UYZ>(a, maps, s, chunk);
+        if (variant == 2) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN, GEOM, UYZ>(a, maps, s, chunk);
         return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2, GEN>(a, s, chunk);
       }
       if constexpr (tma) {
@@ -114,9 +117,9 @@ struct Shapes {
 };
 
 template <class P, int NDIM, int GEOM, int NC, bool UNI = false, bool GEN = false,
-          bool TMA_OK = true>
+          bool TMA_OK = true, bool UYZ = false>
 LaunchEntry entry() {
-  using Sh = Shapes<P, NDIM, GEOM, NC, UNI, GEN, TMA_OK>;
+  using Sh = Shapes<P, NDIM, GEOM, NC, UNI, GEN, TMA_OK, UYZ>;
   LaunchEntry e{&Sh::launch, Sh::count, {}};
   if constexpr (Sh::tma) {
     for (int v = 4; v < 6; ++v) {

@@ -19,10 +19,12 @@ struct LaunchEntry {
 };
 
 // The launcher for (precision, active directions, geometry, carried flux
-// components, uniform Cartesian spacing, general form, face options);
+// components, spacing, general form, face options); uniform: bit 0 every
+// direction of a Cartesian grid evenly spaced, bit 1 directions 1 and 2
+// evenly spaced;
 // fn == nullptr when that combination is not instantiated.  The general form
 // carries the absorption-only coupling, the irradiation deposit and the
 // evolved gas, and with `options` the face options of Sect. 2.5, which the
 // TMA-staged shapes do not implement.
-LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform, bool general,
+LaunchEntry select_launch(bool split, int ndim, int geom, int nc, int uniform, bool general,
                           bool options);

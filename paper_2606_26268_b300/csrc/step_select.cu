@@ -3,13 +3,13 @@
 #include "step_launch.h"
 
 namespace m1 {
-LaunchEntry select_fp64(int ndim, int geom, int nc, bool uni);
-LaunchEntry select_split(int ndim, int geom, int nc, bool uni);
-LaunchEntry select_fp64_gen(int ndim, int geom, int nc, bool uni, bool tma);
-LaunchEntry select_split_gen(int ndim, int geom, int nc, bool uni, bool tma);
+LaunchEntry select_fp64(int ndim, int geom, int nc, int uni);
+LaunchEntry select_split(int ndim, int geom, int nc, int uni);
+LaunchEntry select_fp64_gen(int ndim, int geom, int nc, int uni, bool tma);
+LaunchEntry select_split_gen(int ndim, int geom, int nc, int uni, bool tma);
 }  // namespace m1
 
-LaunchEntry select_launch(bool split, int ndim, int geom, int nc, bool uniform, bool general,
+LaunchEntry select_launch(bool split, int ndim, int geom, int nc, int uniform, bool general,
                           bool options) {
   if (general)
     return split ? m1::select_split_gen(ndim, geom, nc, uniform, !options)

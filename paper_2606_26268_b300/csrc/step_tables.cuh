@@ -7,9 +7,11 @@
 namespace m1 {
 
 // tma: offer the TMA-staged shapes (split 3D; the general form only when it
-// keeps the default face scheme).
+// keeps the default face scheme).  uni: bit 0 every direction evenly spaced,
+// bit 1 directions 1 and 2 evenly spaced.
 template <class P, bool GEN>
-LaunchEntry select_table(int ndim, int geom, int nc, bool uni, bool tma) {
+LaunchEntry select_table(int ndim, int geom, int nc, int uni_mask, bool tma) {
+  const bool uni = uni_mask & 1, uyz = uni_mask & 2;
   if (geom == kCart && uni) {
     if (ndim == 1 && nc == 1) return entry<P, 1, kCart, 1, true, GEN>();
     if (ndim == 1 && nc == 2) return entry<P, 1, kCart, 2, true, GEN>();
@@ -34,14 +36,18 @@ LaunchEntry select_table(int ndim, int geom, int nc, bool uni, bool tma) {
   if (geom == kCyl) {
     if (ndim == 1) return entry<P, 1, kCyl, 3, false, GEN>();
     if (ndim == 2) return entry<P, 2, kCyl, 3, false, GEN>();
-    if (ndim == 3)
-      return tma ? entry<P, 3, kCyl, 3, false, GEN, true>() : entry<P, 3, kCyl, 3, false, GEN, false>();
+    if (ndim == 3) {
+      if (!tma) return entry<P, 3, kCyl, 3, false, GEN, false>();
+      return uyz ? entry<P, 3, kCyl, 3, false, GEN, true, true>() : entry<P, 3, kCyl, 3, false, GEN, true>();
+    }
   }
   if (geom == kSph) {
     if (ndim == 1) return entry<P, 1, kSph, 3, false, GEN>();
     if (ndim == 2) return entry<P, 2, kSph, 3, false, GEN>();
-    if (ndim == 3)
-      return tma ? entry<P, 3, kSph, 3, false, GEN, true>() : entry<P, 3, kSph, 3, false, GEN, false>();
+    if (ndim == 3) {
+      if (!tma) return entry<P, 3, kSph, 3, false, GEN, false>();
+      return uyz ? entry<P, 3, kSph, 3, false, GEN, true, true>() : entry<P, 3, kSph, 3, false, GEN, true>();
+    }
   }
   return LaunchEntry{nullptr, 0};
 }

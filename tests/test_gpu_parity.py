@@ -239,12 +239,20 @@ def test_split_hot_sphere_within_the_problems_own_sensitivity():
 def _curvilinear_case(which):
     if which == "disk":
         return W.disk_spherical((48, 32, 64))  # periodic phi, table opacity
+    if which == "stretched_theta":
+        # theta faces stretched too: the shape without the evenly spaced
+        # (theta, phi) reconstruction
+        p = _curvilinear_case(11)
+        t = p.xfaces[1]
+        u = np.linspace(0.0, 1.0, t.size)
+        p.xfaces[1] = t[0] + (t[-1] - t[0]) * (u + 0.15 * u * (1 - u))
+        return p
     geom, n, ndim, bc, nc, logr, kind = CASES[which]
     return W.random_smooth(geom, n, ndim, seed=1700 + which, bc=bc, opacity=_opacity(kind),
                            log_r=logr, ncomp=nc, fmax=0.8)
 
 
-@pytest.mark.parametrize("which", [8, 11, "disk"])
+@pytest.mark.parametrize("which", [8, 11, "disk", "stretched_theta"])
 def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
     """Split 3D cylindrical and spherical grids on every offered shape (the
     register-tiled one and the TMA-staged non-overlapping tiles at 2 and 3
