@@ -479,6 +479,26 @@ def run_ours(args):
             "hbm_frac": BYTES_PER_CELL[(args.precision, 3)] * pd.N / (ktd["step_kernel_ms"] * 1e-3)
             / 1e9 / hbm}
 
+    # --- the 2D turbulent box (1024^2, periodic), split and plain FP64 ------
+    if not args.skip_forms and not args.skip_2d:
+        import workloads as W
+        p2 = W.turbulent_2d((1024, 1024))
+        out2 = {"workload": p2.name, "cells": p2.N, "unit": UNIT,
+                "form": "single linearised solve, 1024^2 periodic, E = a T^4 and F = 0 at start",
+                "l2": "state 55 MB (split) / 109 MB (FP64) per buffer, inside the 126 MB L2"}
+        for prec, n2 in (("split", 50), ("fp64", 10)):
+            r2d = R.from_problem(p2, prec, device=dev, implicit_mode="once")
+            tv2 = r2d.tune(2)
+            dt2 = r2d.dt()
+            ms2, _, kt2 = time_steps(r2d, torch, n2, 3, dt2)
+            st2 = r2d.sync()
+            r2d.close()
+            out2[prec] = {"value": p2.N * n2 / (ms2 * 1e-3), "ms_per_step": ms2 / n2, "steps": n2,
+                          "status": int(st2), "launch": {"variant": tv2[0], "chunk": tv2[1]},
+                          "hbm_frac": BYTES_PER_CELL[(prec, 2)] * p2.N
+                          / (kt2["step_kernel_ms"] * 1e-3) / 1e9 / hbm}
+        forms["turb2d_1024"] = out2
+
     # --- the paper's performance workload: the 3D pulse with the gas evolved,
     # RK2 (gas step, radiation transport, sources in each stage) ------------
     if not args.skip_forms and not args.skip_rhd:
@@ -673,6 +693,7 @@ def main():
     ap.add_argument("--skip-batch", action="store_true")
     ap.add_argument("--skip-disk", action="store_true")
     ap.add_argument("--skip-rhd", action="store_true")
+    ap.add_argument("--skip-2d", action="store_true")
     ap.add_argument("--rhd-n", type=int, default=256, help="RHD pulse grid (n^3)")
     ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
     args = ap.parse_args()
