@@ -480,8 +480,8 @@ extern "C" rad_status rad_batch_tune(rad_batch* b, int reps, int* variant, int* 
                       b->stream) != cudaSuccess ||
       cudaStreamSynchronize(b->stream) != cudaSuccess)
     return RAD_ECUDA;
-  std::vector<int> chunks = b->ndim == 3 ? std::vector<int>{16, 32, 64}
-                                         : std::vector<int>{16, 32, 64, 128};
+  std::vector<int> chunks = b->ndim == 3 ? std::vector<int>{8, 16, 32, 64}
+                                         : std::vector<int>{8, 16, 32, 64, 128};
   int nmarch = 0;
   for (const rad_ctx* m : b->g) nmarch = std::max(nmarch, m->n[march_axis(b)]);
   const std::vector<double> dts = b->dt_args.empty() ? step_sizes(b, nullptr) : b->dt_args;

@@ -1325,8 +1325,8 @@ extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, f
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return RAD_ECUDA;
   std::vector<int> chunks;
-  if (c->ndim == 3) chunks = {16, 32, 64, 128};
-  else if (c->ndim == 2) chunks = {32, 64, 128, 256};
+  if (c->ndim == 3) chunks = {8, 16, 32, 64, 128};
+  else if (c->ndim == 2) chunks = {8, 16, 32, 64, 128, 256};
   else chunks = {1};
   const int nmarch = c->ndim == 3 ? c->n[2] : (c->ndim == 2 ? c->n[1] : 1);
   cudaEvent_t e0, e1;
