@@ -262,6 +262,29 @@ rad_status rad_step(rad_ctx *ctx, double dt, int nsteps);
  * Errors: RAD_EINVAL (unknown field, bytes too small). */
 rad_status rad_read(rad_ctx *ctx, int field, void *dst, size_t bytes, int on_device);
 
+/* Asynchronous host transfers, for callers that stream a state through the
+ * GPU every step (the paper has no counterpart; it is a transfer pattern of
+ * this library).  They take host pointers only, best in pinned memory, and
+ * return as soon as the work is enqueued: the host buffers must stay valid
+ * and must not be read (outputs) or changed (inputs) until rad_sync
+ * returns.  Uploads run on an upload stream of the context, read-backs on a
+ * read-back stream, ordered with the steps on the context's stream by
+ * events, so that the read-back of one step overlaps the upload of the
+ * next.  Each call uses a staging area of its own: the first call
+ * allocates it (cudaMalloc of (7 + 4 ncomp) N values) together with the
+ * two streams, and rad_destroy frees them.
+ *   rad_set_gas_host_async: as rad_set_gas with host rho (N), v (ncomp*N),
+ *   T (N).
+ *   rad_set_rad_host_async: as rad_set_rad with host E (N), F (ncomp*N).
+ *   rad_read_host_async: as rad_read into host dst; the value is the state
+ *   after the steps enqueued before the call.
+ * Errors: RAD_EINVAL (NULL, unknown field, bytes too small, no state set
+ * before a read), RAD_ENOMEM (no workspace, or the staging allocation
+ * failed), RAD_ECUDA.  Device status words surface at rad_sync. */
+rad_status rad_set_gas_host_async(rad_ctx *ctx, const void *rho, const void *v, const void *T);
+rad_status rad_set_rad_host_async(rad_ctx *ctx, const void *E, const void *F);
+rad_status rad_read_host_async(rad_ctx *ctx, int field, void *dst, size_t bytes);
+
 /* Irradiation by an external source (Sect. 2.9): q = -div F_irr, the energy
  * the irradiation flux deposits per unit volume and time, N values (flat, x
  * fastest, the precision of the context), host or device.  Each step adds

@@ -77,7 +77,8 @@ class rad_stats(C.Structure):
 EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_workspace",
            "rad_alloc_workspace", "rad_set_stream", "rad_set_gas", "rad_set_rad",
            "rad_set_irradiation", "rad_step",
-           "rad_read", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
+           "rad_read", "rad_set_gas_host_async", "rad_set_rad_host_async",
+           "rad_read_host_async", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
            "rad_launches_per_step", "rad_profile_begin", "rad_profile_end",
            "rad_set_launch", "rad_get_launch", "rad_tune",
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
@@ -117,6 +118,9 @@ def lib() -> C.CDLL:
     L.rad_step.argtypes = [vp, C.c_double, C.c_int]
     L.rad_read.argtypes = [vp, C.c_int, vp, C.c_size_t, C.c_int]
     L.rad_sync.argtypes = [vp]
+    L.rad_set_gas_host_async.argtypes = [vp, vp, vp, vp]
+    L.rad_set_rad_host_async.argtypes = [vp, vp, vp]
+    L.rad_read_host_async.argtypes = [vp, C.c_int, vp, C.c_size_t]
     L.rad_dt.argtypes = [vp, P(C.c_double)]
     L.rad_get_stats.argtypes = [vp, P(rad_stats)]
     L.rad_reset_stats.argtypes = [vp]
@@ -262,6 +266,7 @@ class Rad:
         self.params = p
         self.ncomp = int(p.ncomp)
         self.N = int(np.prod([int(x) for x in grid["n"]]))
+        self._inflight = []
         self.dtype = np.float64 if p.precision == RAD_FP64 else np.float32
         ctx = C.c_void_p()
         check(L.rad_create(C.byref(g), GEOMETRY[geometry], C.byref(o), C.byref(p),
@@ -340,8 +345,37 @@ class Rad:
               "rad_read")
         return t
 
+    def _host(self, a, count):
+        assert isinstance(a, np.ndarray) and a.dtype == self.dtype and a.flags.c_contiguous
+        assert a.size == count, "expected %d values, got %d" % (count, a.size)
+        self._inflight.append(a)  # kept alive until sync()
+        return C.c_void_p(a.ctypes.data)
+
+    def set_gas_async(self, rho, v, T):
+        """Asynchronous rad_set_gas from host arrays (pinned for overlap);
+        the arrays must stay unchanged until sync()."""
+        check(lib().rad_set_gas_host_async(self.ctx, self._host(rho, self.N),
+                                           self._host(v, self.N * self.ncomp),
+                                           self._host(T, self.N)), "rad_set_gas_host_async")
+
+    def set_rad_async(self, E, F):
+        check(lib().rad_set_rad_host_async(self.ctx, self._host(E, self.N),
+                                           self._host(F, self.N * self.ncomp)),
+              "rad_set_rad_host_async")
+
+    def read_async(self, field: str, out):
+        """Enqueues the read-back of a field into the host array `out`,
+        valid after sync()."""
+        count = self.N * (self.ncomp if field in ("F", "m") else 1)
+        ptr = self._host(out, count)
+        check(lib().rad_read_host_async(self.ctx, FIELDS[field], ptr,
+                                        count * np.dtype(self.dtype).itemsize),
+              "rad_read_host_async")
+
     def sync(self) -> int:
-        return lib().rad_sync(self.ctx)
+        st = lib().rad_sync(self.ctx)
+        self._inflight = []
+        return st
 
     def stats(self) -> dict:
         s = rad_stats()

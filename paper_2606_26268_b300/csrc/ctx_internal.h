@@ -61,6 +61,13 @@ struct rad_ctx {
   size_t off_cfl = 0;  // reduction word of the gas CFL rate
   size_t total = 0;
   cudaStream_t stream = nullptr;
+  // asynchronous host transfers (rad_*_host_async): an upload and a
+  // read-back stream, their events and a staging area of their own
+  // (input slots rho, v, T, E, F; output slots per field), allocated on
+  // first use
+  cudaStream_t up = nullptr, down = nullptr;
+  cudaEvent_t ev_up = nullptr, ev_packed = nullptr, ev_unpacked[6] = {}, ev_down[6] = {};
+  char* astage = nullptr;
   int cur = 0;
   bool have_gas = false, have_rad = false;
   uint64_t steps = 0;

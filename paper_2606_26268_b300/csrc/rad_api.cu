@@ -645,7 +645,8 @@ static const void* stage_in(rad_ctx* c, const void* src, size_t count, int slot,
 }
 
 template <class S>
-static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const void* T, int dev) {
+static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const void* T, int dev,
+                           bool wait = true) {
   rad_status st;
   // rho first (flat copy kept in stage slot 0 while m and e are built)
   const S* r = static_cast<const S*>(stage_in(c, rho, c->N, 0, dev, &st));
@@ -681,7 +682,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
   for (int b = 0; b < c->nbuf; ++b)
     if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 4)), t, r, PK_EINT, FK_EINT))) return st;
   c->have_gas = true;
-  return cuda_err(cudaStreamSynchronize(c->stream));
+  return cuda_err(wait ? cudaStreamSynchronize(c->stream) : cudaGetLastError());
 }
 
 extern "C" rad_status rad_set_gas(rad_ctx* c, const void* rho, const void* v, const void* T,
@@ -693,7 +694,7 @@ extern "C" rad_status rad_set_gas(rad_ctx* c, const void* rho, const void* v, co
 }
 
 template <class S>
-static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
+static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev, bool wait = true) {
   rad_status st;
   const S* e = static_cast<const S*>(stage_in(c, E, c->N, 0, dev, &st));
   if (st) return st;
@@ -721,7 +722,7 @@ static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev) {
     }
   }
   c->have_rad = true;
-  return cuda_err(cudaStreamSynchronize(c->stream));
+  return cuda_err(wait ? cudaStreamSynchronize(c->stream) : cudaGetLastError());
 }
 
 template <class S>
@@ -1408,6 +1409,8 @@ extern "C" rad_status rad_sync(rad_ctx* c) {
   if (!c) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
+  for (cudaStream_t s : {c->up, c->down})
+    if (s && cudaStreamSynchronize(s) != cudaSuccess) return RAD_ECUDA;
   return take_status(c);
 }
 
@@ -1458,6 +1461,138 @@ extern "C" rad_status rad_read(rad_ctx* c, int field, void* dst, size_t bytes, i
   return take_status(c);
 }
 
+// ---------------------------------------------------------------------------
+// asynchronous host transfers
+// ---------------------------------------------------------------------------
+
+// Input slots: rho, v (nc), T, E, F (nc); output slots: E, F (nc), e, m (nc),
+// T, rho.  Each slot holds N values.
+static int async_in_slot(const rad_ctx* c, int which) {  // 0 rho, 1 v, 2 T, 3 E, 4 F
+  const int nc = c->par.ncomp;
+  const int base[5] = {0, 1, 1 + nc, 2 + nc, 3 + nc};
+  return base[which];
+}
+static int async_out_slot(const rad_ctx* c, int field) {
+  const int nc = c->par.ncomp;
+  const int in = 3 + 2 * nc;
+  switch (field) {
+    case RAD_FIELD_E: return in;
+    case RAD_FIELD_F: return in + 1;
+    case RAD_FIELD_EINT: return in + 1 + nc;
+    case RAD_FIELD_M: return in + 2 + nc;
+    case RAD_FIELD_T: return in + 2 + 2 * nc;
+    default: return in + 3 + 2 * nc;  // rho
+  }
+}
+
+static rad_status async_setup(rad_ctx* c) {
+  if (c->astage) return RAD_OK;
+  const size_t slots = size_t(async_out_slot(c, RAD_FIELD_RHO)) + 1;
+  if (cudaMalloc(&c->astage, slots * c->N * c->esize) != cudaSuccess) {
+    c->astage = nullptr;
+    return RAD_ENOMEM;
+  }
+  bool ok = cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_packed, cudaEventDisableTiming) == cudaSuccess;
+  for (int f = 0; f < 6 && ok; ++f)
+    ok = cudaEventCreateWithFlags(&c->ev_unpacked[f], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&c->ev_down[f], cudaEventDisableTiming) == cudaSuccess;
+  return ok ? RAD_OK : RAD_ECUDA;
+}
+
+static void async_release(rad_ctx* c) {
+  for (cudaStream_t s : {c->up, c->down})
+    if (s) {
+      cudaStreamSynchronize(s);
+      cudaStreamDestroy(s);
+    }
+  for (cudaEvent_t e : {c->ev_up, c->ev_packed})
+    if (e) cudaEventDestroy(e);
+  for (int f = 0; f < 6; ++f) {
+    if (c->ev_unpacked[f]) cudaEventDestroy(c->ev_unpacked[f]);
+    if (c->ev_down[f]) cudaEventDestroy(c->ev_down[f]);
+  }
+  if (c->astage) cudaFree(c->astage);
+  c->astage = nullptr;
+}
+
+// Uploads `count` values per array into consecutive input slots on the
+// upload stream, once the previous packs are done with them.
+static rad_status async_upload(rad_ctx* c, const void* const* src, const size_t* count,
+                               const int* slot, int n) {
+  if (cudaStreamWaitEvent(c->up, c->ev_packed, 0) != cudaSuccess) return RAD_ECUDA;
+  for (int i = 0; i < n; ++i)
+    if (cudaMemcpyAsync(c->astage + size_t(slot[i]) * c->N * c->esize, src[i], count[i] * c->esize,
+                        cudaMemcpyHostToDevice, c->up) != cudaSuccess)
+      return RAD_ECUDA;
+  if (cudaEventRecord(c->ev_up, c->up) != cudaSuccess ||
+      cudaStreamWaitEvent(c->stream, c->ev_up, 0) != cudaSuccess)
+    return RAD_ECUDA;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_set_gas_host_async(rad_ctx* c, const void* rho, const void* v,
+                                             const void* T) {
+  if (!c || !rho || !v || !T) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  rad_status st = async_setup(c);
+  if (st != RAD_OK) return st;
+  const void* src[3] = {rho, v, T};
+  const size_t count[3] = {c->N, size_t(c->par.ncomp) * c->N, c->N};
+  const int slot[3] = {async_in_slot(c, 0), async_in_slot(c, 1), async_in_slot(c, 2)};
+  if ((st = async_upload(c, src, count, slot, 3)) != RAD_OK) return st;
+  char* base = c->astage;
+  const size_t w = c->N * c->esize;
+  st = c->esize == 8 ? set_gas_t<double>(c, base + slot[0] * w, base + slot[1] * w,
+                                         base + slot[2] * w, 1, false)
+                     : set_gas_t<float>(c, base + slot[0] * w, base + slot[1] * w,
+                                        base + slot[2] * w, 1, false);
+  if (st != RAD_OK) return st;
+  return cuda_err(cudaEventRecord(c->ev_packed, c->stream));
+}
+
+extern "C" rad_status rad_set_rad_host_async(rad_ctx* c, const void* E, const void* F) {
+  if (!c || !E || !F) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  rad_status st = async_setup(c);
+  if (st != RAD_OK) return st;
+  const void* src[2] = {E, F};
+  const size_t count[2] = {c->N, size_t(c->par.ncomp) * c->N};
+  const int slot[2] = {async_in_slot(c, 3), async_in_slot(c, 4)};
+  if ((st = async_upload(c, src, count, slot, 2)) != RAD_OK) return st;
+  const size_t w = c->N * c->esize;
+  st = c->esize == 8 ? set_rad_t<double>(c, c->astage + slot[0] * w, c->astage + slot[1] * w, 1,
+                                         false)
+                     : set_rad_t<float>(c, c->astage + slot[0] * w, c->astage + slot[1] * w, 1,
+                                        false);
+  if (st != RAD_OK) return st;
+  return cuda_err(cudaEventRecord(c->ev_packed, c->stream));
+}
+
+extern "C" rad_status rad_read_host_async(rad_ctx* c, int field, void* dst, size_t bytes) {
+  if (!c || !dst || field < 0 || field > 5) return RAD_EINVAL;
+  if (!c->ws) return RAD_ENOMEM;
+  const int ncomp = (field == RAD_FIELD_F || field == RAD_FIELD_M) ? c->par.ncomp : 1;
+  if (bytes < size_t(ncomp) * c->N * c->esize) return RAD_EINVAL;
+  if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
+  rad_status st = async_setup(c);
+  if (st != RAD_OK) return st;
+  // the field's output slots are free once its previous read-back is done
+  if (cudaStreamWaitEvent(c->stream, c->ev_down[field], 0) != cudaSuccess) return RAD_ECUDA;
+  char* out = c->astage + size_t(async_out_slot(c, field)) * c->N * c->esize;
+  st = c->esize == 8 ? read_t<double>(c, field, out, 1) : read_t<float>(c, field, out, 1);
+  if (st != RAD_OK) return st;
+  if (cudaEventRecord(c->ev_unpacked[field], c->stream) != cudaSuccess ||
+      cudaStreamWaitEvent(c->down, c->ev_unpacked[field], 0) != cudaSuccess ||
+      cudaMemcpyAsync(dst, out, size_t(ncomp) * c->N * c->esize, cudaMemcpyDeviceToHost,
+                      c->down) != cudaSuccess ||
+      cudaEventRecord(c->ev_down[field], c->down) != cudaSuccess)
+    return RAD_ECUDA;
+  return RAD_OK;
+}
+
 extern "C" rad_status rad_get_stats(rad_ctx* c, rad_stats* out) {
   if (!c || !out) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
@@ -1488,6 +1623,7 @@ extern "C" rad_status rad_reset_stats(rad_ctx* c) {
 extern "C" void rad_destroy(rad_ctx* c) {
   if (!c) return;
   profile_release(c);
+  async_release(c);
   if (c->ws_owned && c->ws) {
     cudaStreamSynchronize(c->stream);
     cudaFree(c->ws);

@@ -43,6 +43,27 @@ def _grid(R, n=(8, 1, 1), ndim=1, lo=(0.0, 0.0, 0.0), hi=(1.0, 1.0, 1.0)):
     return g, xs
 
 
+def test_async_host_transfers_validate_their_arguments(R):
+    """The asynchronous host transfers check their arguments before touching
+    the device: NULL pointers and unknown fields are RAD_EINVAL, a context
+    without a workspace RAD_ENOMEM."""
+    L = R.lib()
+    g, xs = _grid(R)
+    o = R.rad_opacity()
+    p = R.default_params()
+    ctx = C.c_void_p()
+    assert L.rad_create(C.byref(g), 0, C.byref(o), C.byref(p), C.byref(ctx)) == R.RAD_OK
+    buf = np.zeros(8)
+    ptr = C.c_void_p(buf.ctypes.data)
+    assert L.rad_set_gas_host_async(ctx, None, ptr, ptr) == R.RAD_EINVAL
+    assert L.rad_set_rad_host_async(ctx, ptr, None) == R.RAD_EINVAL
+    assert L.rad_read_host_async(ctx, 0, None, buf.nbytes) == R.RAD_EINVAL
+    assert L.rad_read_host_async(ctx, 9, ptr, buf.nbytes) == R.RAD_EINVAL
+    assert L.rad_read_host_async(ctx, 0, ptr, buf.nbytes) == R.RAD_ENOMEM
+    assert L.rad_set_gas_host_async(ctx, ptr, ptr, ptr) == R.RAD_ENOMEM
+    L.rad_destroy(ctx)
+
+
 def test_host_side_validation(R):
     L = R.lib()
     g, xs = _grid(R)
