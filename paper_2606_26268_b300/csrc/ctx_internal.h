@@ -66,7 +66,7 @@ struct rad_ctx {
   // (input slots rho, v, T, E, F; output slots per field), allocated on
   // first use
   cudaStream_t up = nullptr, down = nullptr;
-  cudaEvent_t ev_up = nullptr, ev_packed = nullptr, ev_unpacked[6] = {}, ev_down[6] = {};
+  cudaEvent_t ev_up = nullptr, ev_packed[2] = {}, ev_unpacked[6] = {}, ev_down[6] = {};
   char* astage = nullptr;
   int cur = 0;
   bool have_gas = false, have_rad = false;

@@ -1495,7 +1495,8 @@ static rad_status async_setup(rad_ctx* c) {
   bool ok = cudaStreamCreateWithFlags(&c->up, cudaStreamNonBlocking) == cudaSuccess &&
             cudaStreamCreateWithFlags(&c->down, cudaStreamNonBlocking) == cudaSuccess &&
             cudaEventCreateWithFlags(&c->ev_up, cudaEventDisableTiming) == cudaSuccess &&
-            cudaEventCreateWithFlags(&c->ev_packed, cudaEventDisableTiming) == cudaSuccess;
+            cudaEventCreateWithFlags(&c->ev_packed[0], cudaEventDisableTiming) == cudaSuccess &&
+            cudaEventCreateWithFlags(&c->ev_packed[1], cudaEventDisableTiming) == cudaSuccess;
   for (int f = 0; f < 6 && ok; ++f)
     ok = cudaEventCreateWithFlags(&c->ev_unpacked[f], cudaEventDisableTiming) == cudaSuccess &&
          cudaEventCreateWithFlags(&c->ev_down[f], cudaEventDisableTiming) == cudaSuccess;
@@ -1508,7 +1509,7 @@ static void async_release(rad_ctx* c) {
       cudaStreamSynchronize(s);
       cudaStreamDestroy(s);
     }
-  for (cudaEvent_t e : {c->ev_up, c->ev_packed})
+  for (cudaEvent_t e : {c->ev_up, c->ev_packed[0], c->ev_packed[1]})
     if (e) cudaEventDestroy(e);
   for (int f = 0; f < 6; ++f) {
     if (c->ev_unpacked[f]) cudaEventDestroy(c->ev_unpacked[f]);
@@ -1518,11 +1519,12 @@ static void async_release(rad_ctx* c) {
   c->astage = nullptr;
 }
 
-// Uploads `count` values per array into consecutive input slots on the
-// upload stream, once the previous packs are done with them.
+// Uploads `count` values per array into input slots on the upload stream,
+// once the previous packs of the same slots (gas: 0, radiation: 1) are done
+// with them.
 static rad_status async_upload(rad_ctx* c, const void* const* src, const size_t* count,
-                               const int* slot, int n) {
-  if (cudaStreamWaitEvent(c->up, c->ev_packed, 0) != cudaSuccess) return RAD_ECUDA;
+                               const int* slot, int n, int kind) {
+  if (cudaStreamWaitEvent(c->up, c->ev_packed[kind], 0) != cudaSuccess) return RAD_ECUDA;
   for (int i = 0; i < n; ++i)
     if (cudaMemcpyAsync(c->astage + size_t(slot[i]) * c->N * c->esize, src[i], count[i] * c->esize,
                         cudaMemcpyHostToDevice, c->up) != cudaSuccess)
@@ -1542,7 +1544,7 @@ extern "C" rad_status rad_set_gas_host_async(rad_ctx* c, const void* rho, const 
   const void* src[3] = {rho, v, T};
   const size_t count[3] = {c->N, size_t(c->par.ncomp) * c->N, c->N};
   const int slot[3] = {async_in_slot(c, 0), async_in_slot(c, 1), async_in_slot(c, 2)};
-  if ((st = async_upload(c, src, count, slot, 3)) != RAD_OK) return st;
+  if ((st = async_upload(c, src, count, slot, 3, 0)) != RAD_OK) return st;
   char* base = c->astage;
   const size_t w = c->N * c->esize;
   st = c->esize == 8 ? set_gas_t<double>(c, base + slot[0] * w, base + slot[1] * w,
@@ -1550,7 +1552,7 @@ extern "C" rad_status rad_set_gas_host_async(rad_ctx* c, const void* rho, const 
                      : set_gas_t<float>(c, base + slot[0] * w, base + slot[1] * w,
                                         base + slot[2] * w, 1, false);
   if (st != RAD_OK) return st;
-  return cuda_err(cudaEventRecord(c->ev_packed, c->stream));
+  return cuda_err(cudaEventRecord(c->ev_packed[0], c->stream));
 }
 
 extern "C" rad_status rad_set_rad_host_async(rad_ctx* c, const void* E, const void* F) {
@@ -1561,14 +1563,14 @@ extern "C" rad_status rad_set_rad_host_async(rad_ctx* c, const void* E, const vo
   const void* src[2] = {E, F};
   const size_t count[2] = {c->N, size_t(c->par.ncomp) * c->N};
   const int slot[2] = {async_in_slot(c, 3), async_in_slot(c, 4)};
-  if ((st = async_upload(c, src, count, slot, 2)) != RAD_OK) return st;
+  if ((st = async_upload(c, src, count, slot, 2, 1)) != RAD_OK) return st;
   const size_t w = c->N * c->esize;
   st = c->esize == 8 ? set_rad_t<double>(c, c->astage + slot[0] * w, c->astage + slot[1] * w, 1,
                                          false)
                      : set_rad_t<float>(c, c->astage + slot[0] * w, c->astage + slot[1] * w, 1,
                                         false);
   if (st != RAD_OK) return st;
-  return cuda_err(cudaEventRecord(c->ev_packed, c->stream));
+  return cuda_err(cudaEventRecord(c->ev_packed[1], c->stream));
 }
 
 extern "C" rad_status rad_read_host_async(rad_ctx* c, int field, void* dst, size_t bytes) {
