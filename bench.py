@@ -212,6 +212,36 @@ def time_steps(r, torch, steps, warmup, dt):
     return sum(per), per, {"step_kernel_ms": kern_ms / max(n, 1), "queue_pass_ms": queue_ms / max(n, 1)}
 
 
+def link_bandwidth(torch, mb=256, reps=5):
+    """Host<->device copy rates of this machine (GB/s): pinned 256 MB copies host
+    to device, device to host, and both at once on two streams."""
+    n = mb * 1024 * 1024 // 4
+    h = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    h2 = torch.empty(n, dtype=torch.float32, pin_memory=True)
+    d = torch.empty(n, dtype=torch.float32, device="cuda")
+    d2 = torch.empty(n, dtype=torch.float32, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+
+    def rate(fn, bytes_per_rep):
+        fn()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(reps):
+            fn()
+        torch.cuda.synchronize()
+        return reps * bytes_per_rep / (time.perf_counter() - t) / 1e9
+
+    def both():
+        with torch.cuda.stream(s1):
+            d.copy_(h, non_blocking=True)
+        with torch.cuda.stream(s2):
+            h2.copy_(d2, non_blocking=True)
+
+    return {"h2d": rate(lambda: d.copy_(h, non_blocking=True), 4 * n),
+            "d2h": rate(lambda: h.copy_(d, non_blocking=True), 4 * n),
+            "both": rate(both, 8 * n)}
+
+
 def max_over_ranks(x, world, device):
     """Largest value of x over the ranks (x itself at world size 1)."""
     if world <= 1:
@@ -425,7 +455,8 @@ def run_ours(args):
                "h2d_bytes_per_step": int((3 + 2 * nc) * N * isz),
                "d2h_bytes_per_step": int((2 + 2 * nc) * N * isz), "steps": ksteps,
                "transfers": "rad_set_gas/rad_set_rad/rad_read host_async from pinned memory, "
-                            "one rad_sync at the end"}
+                            "one rad_sync at the end",
+               "link_gbs": link_bandwidth(torch)}
         r2.close()
 
     # --- comparison forms on the same grid ------------------------------------
