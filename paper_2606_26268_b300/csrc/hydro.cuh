@@ -171,7 +171,10 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
   // split precision: the tile's own input (rho, m, e) staged with the plane,
   // so that the update reads it from shared memory (FP64 reads it again)
   constexpr bool SU = P::kSplit;
-  __shared__ T s_u[SU ? 5 : 1][SU ? TY : 1][SU ? TX : 1];
+  // (two copies: the update of plane z reads one while the next plane is
+  // staged into the other)
+  __shared__ T s_u[SU ? 2 : 1][SU ? 5 : 1][SU ? TY : 1][SU ? TX : 1];
+  int ub = 0;
 
   const StepDims& Dm = h.dim;
   const GeomDev<T>& G = h.geo;
@@ -251,7 +254,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
           const int ux = ix - 2, uy = iy - OY;
           if (ux >= 0 && ux < TX && uy >= 0 && uy < TY) {
 #pragma unroll
-            for (int q = 0; q < 5; ++q) s_u[q][uy][ux] = T(pre[kk][q]);
+            for (int q = 0; q < 5; ++q) s_u[ub][q][uy][ux] = T(pre[kk][q]);
           }
         }
       }
@@ -353,15 +356,15 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
       const long long ic = col + zoff;
       T U[5];
       {
-        const T r = SU ? s_u[0][ty][tx] : T(__ldg(h.rho + ic));
+        const T r = SU ? s_u[ub][0][ty][tx] : T(__ldg(h.rho + ic));
         U[0] = r;
         T ke = T(0);
 #pragma unroll
         for (int v = 0; v < 3; ++v) {
-          U[1 + v] = v < NC ? (SU ? s_u[1 + v][ty][tx] : T(__ldg(h.m[v] + ic))) : T(0);
+          U[1 + v] = v < NC ? (SU ? s_u[ub][1 + v][ty][tx] : T(__ldg(h.m[v] + ic))) : T(0);
           ke += U[1 + v] * U[1 + v];
         }
-        U[4] = (SU ? s_u[4][ty][tx] : T(__ldg(h.e + ic))) + T(0.5) * ke * Ops<T>::rcp(r);
+        U[4] = (SU ? s_u[ub][4][ty][tx] : T(__ldg(h.e + ic))) + T(0.5) * ke * Ops<T>::rcp(r);
       }
       {
         const T ih = UNI ? h.uni_inv[0] : gtab(G, 0, TAB_ALO, px);
@@ -424,7 +427,11 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
 #pragma unroll
         for (int q = 0; q < 5; ++q) wz[k][q] = wz[k + 1][q];
     }
-    __syncthreads();  // the plane and the fluxes are read before the next plane lands
+    // No barrier here: the next plane's staging writes s_w, which the faces
+    // of this plane read before the second barrier, and the other copy of
+    // s_u; its faces write s_fx, s_fy only after its first barrier, which
+    // every thread reaches after this update.
+    if constexpr (SU) ub ^= 1;
   }
 }
 
