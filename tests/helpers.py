@@ -34,6 +34,13 @@ def run_gpu(p, nsteps, precision="fp64", dt=None, **overrides):
     r = R.from_problem(p, precision=precision, **overrides)
     if dt is None:
         dt = r.dt()
+        # the library's CFL step must be the oracle's (Sect. 2.4, item 10),
+        # so that parity runs that hand the GPU's dt to the oracle do not
+        # share a mistake in it; the split form takes the gas CFL reduction
+        # in FP32
+        want = oracle.Oracle(p).dt()
+        tol = 1e-13 if precision == "fp64" else 1e-6
+        assert abs(dt - want) <= tol * want, (dt, want)
     r.step(nsteps, dt)
     st = r.sync()
     out = {k: np.asarray(r.read(k), dtype=np.float64) for k in ("E", "F", "e", "m", "T", "rho")}
