@@ -41,7 +41,7 @@ class _Problem(C.Structure):
                 ("implicit_mode", C.c_int), ("newton_rtol", C.c_double),
                 ("newton_maxit", C.c_int), ("nthreads", C.c_int), ("integrator", C.c_int),
                 ("qirr", _dp), ("recon", C.c_int), ("face_fix", C.c_int), ("riemann", C.c_int),
-                ("bc_val", C.c_double * 30), ("hydro", C.c_int)]
+                ("bc_val", C.c_double * 30), ("hydro", C.c_int), ("float_coupling", C.c_int)]
 
 
 class _State(C.Structure):
@@ -256,6 +256,9 @@ class Oracle:
         p.face_fix = _FIX[getattr(prob, "face_fix", "fpreserve")]
         p.riemann = _RIEMANN[getattr(prob, "riemann", "hll")]
         p.hydro = int(bool(getattr(prob, "hydro", False)))
+        # host emulation of the split form's float coupling products (for
+        # measuring their share of its error; never the reference)
+        p.float_coupling = int(bool(getattr(prob, "float_coupling", False)))
         for (d, side), v in getattr(prob, "bc_value", {}).items():
             for q in range(5):
                 p.bc_val[10 * d + 5 * side + q] = float(v[q])

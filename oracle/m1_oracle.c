@@ -123,6 +123,12 @@ typedef struct {
   /* 1: the gas is evolved too (Cartesian grids): a hydrodynamic step before
    * the radiation transport in every (sub)step, Sect. 2.4 */
   int hydro;
+  /* 1: a host emulation, not the definition: the coupling with the products
+   * that the CUDA library's split precision forms in float rounded to float
+   * (see couple_float), so that their share of the split form's error can be
+   * measured apart from the FP32 transport.  0 (the default): FP64 as
+   * defined. */
+  int float_coupling;
 } orc_problem;
 
 /* State: SoA arrays of N = n0 n1 n2 cells, x fastest.  Three flux and three
@@ -770,9 +776,79 @@ void orc_solve2x2(double Estar, double Tn, double Tk, double Cv, double g, doubl
  * the latest temperature until |T_{k+1} - T_k| <= rtol T_{k+1} (Newton's
  * method on C_v (T - T^n) + g/(1+g_r) (a T^4 - E*) = 0).  T0 is the starting
  * point of the iteration (T^n when no other guess is given). */
+/* The coupling of Sect. 2.8 in the precision of the CUDA library's split
+ * form (a host emulation for measuring error shares; never the reference):
+ * the products see float-rounded inputs; the emission term a T^4 and the
+ * residual D = E* - a T^4 are formed in double from the float temperature;
+ * the other products of the linearised solve (a T^3, the determinant, its
+ * reciprocal, the increments of T and E) in float.  The increments are
+ * added to the unrounded E* and T^n, so that the rounding of the stored
+ * state (float in the split form) is left out and only the products' share
+ * is measured.  Newton mode takes the single solve first and keeps it if it
+ * passes the convergence test (in float); otherwise it iterates from T^n
+ * with the residual and the numerator in double, the determinant and its
+ * reciprocal in float.  No irradiation, no absorption-only mode. */
+static void couple_float(const orc_problem *p, double dt, double rho, double Tn, double kp,
+                         double Estar, double *Enew, double *Tnew, int64_t st[ORC_NSTATS]) {
+  const float cvfac = (float)(1.0 / (p->mu * (p->gamma_gas - 1.0)));
+  const float rf = (float)rho, kf = (float)kp, Ef = (float)Estar, Tf = (float)Tn;
+  const float af = (float)p->a_rad, rtol = (float)p->newton_rtol;
+  const float Cv = rf * cvfac;
+  const float gr = (float)(dt * p->chat) * kf * rf;
+  const float g = (float)(dt * p->c) * kf * rf;
+  const float c1 = (1.0f + gr) * Cv;
+  /* single linearised solve about T^n */
+  const double T2 = (double)Tf * (double)Tf;
+  const float D = (float)fma(-(p->a_rad * T2), T2, (double)Ef);
+  const float aT3 = af * Tf * Tf * Tf;
+  const float det = c1 + 4.0f * g * aT3;
+  const float q = D * (1.0f / det);
+  const float dT = g * q;
+  const float dE = -gr * Cv * q;
+  const float T1 = Tf + dT;
+  st[ORC_ST_ITERS] += 1;
+  if (st[ORC_ST_ITMAX] < 1) st[ORC_ST_ITMAX] = 1;
+  if (p->implicit_mode == ORC_ONCE || fabsf(dT) <= rtol * T1) {
+    *Enew = Estar + (double)dE;
+    *Tnew = Tn + (double)dT;
+    return;
+  }
+  /* Newton from T^n, the single solve above counted as the first iterate
+   * of a separate pass (as the library's queue pass does) */
+  const double Tnd = (double)Tf, c1d = (double)c1;
+  double Tk = Tnd, Tnext = Tnd, aT3d = 0.0, Dd = 0.0;
+  float detf = 1.0f;
+  int it, ok = 0;
+  for (it = 1; it <= p->newton_maxit; ++it) {
+    aT3d = p->a_rad * Tk * Tk * Tk;
+    Dd = (double)Ef - aT3d * Tk;
+    detf = c1 + 4.0f * g * (float)aT3d;
+    const double num = c1d * (Tnd - Tk) + (double)g * Dd;
+    const double dTd = num * (double)(1.0f / detf);
+    Tnext = Tk + dTd;  /* Tk starts from the float T^n, as in the library */
+    if (!(Tnext > 0.0)) break;
+    if (fabsf((float)dTd) <= rtol * (float)Tnext) {
+      ok = 1;
+      break;
+    }
+    Tk = Tnext;
+  }
+  const int used = ok ? it : (it > p->newton_maxit ? p->newton_maxit : it);
+  st[ORC_ST_ITERS] += used;
+  if (st[ORC_ST_ITMAX] < used + 1) st[ORC_ST_ITMAX] = used + 1;
+  if (!ok) st[ORC_ST_NOCONV] += 1;
+  const float inner = (float)(4.0 * aT3d * ((double)Cv * (Tnd - Tk)) - (double)Cv * Dd);
+  *Enew = Estar + (double)(gr * inner * (1.0f / detf));
+  *Tnew = Tn + (Tnext - Tnd);
+}
+
 static void couple(const orc_problem *p, double dt, double rho, double Tn, double T0, double kp,
                    double Estar, double sq, double *Enew, double *Tnew,
                    int64_t st[ORC_NSTATS]) {
+  if (p->float_coupling && p->implicit_mode != ORC_ABSORB && sq == 0.0) {
+    couple_float(p, dt, rho, Tn, kp, Estar, Enew, Tnew, st);
+    return;
+  }
   double Cv = rho / (p->mu * (p->gamma_gas - 1.0));
   double g = dt * p->c * kp * rho;
   double gr = dt * p->chat * kp * rho;
