@@ -243,12 +243,17 @@ rad_status rad_set_stream(rad_ctx *ctx, void *cuda_stream);
 
 /* Sets the gas: rho (N), v (ncomp*N) and T (N), all host (on_device = 0)
  * or all device (on_device = 1).  Stores rho, m = rho v and e = C_v T.
- * Errors: RAD_EINVAL (NULL, no workspace), RAD_ECUDA.  With host pointers
- * the call returns after the copies completed. */
+ * The call returns after the copies completed.  Errors: RAD_EINVAL (NULL, no
+ * workspace), RAD_ENONPHYS (a value that is not finite, or rho or T not
+ * positive; the state is stored as given and should be replaced),
+ * RAD_ECUDA. */
 rad_status rad_set_gas(rad_ctx *ctx, const void *rho, const void *v, const void *T,
                        int on_device);
 
-/* Sets the radiation field: E (N) and F (ncomp*N), host or device. */
+/* Sets the radiation field: E (N) and F (ncomp*N), host or device, and
+ * returns after the copies completed.  Errors as rad_set_gas: RAD_ENONPHYS
+ * for a value that is not finite or an E that is not positive (|F| > E is
+ * accepted: the closure clamps f at 1). */
 rad_status rad_set_rad(rad_ctx *ctx, const void *E, const void *F, int on_device);
 
 /* Enqueues nsteps steps of size dt (dt <= 0: the CFL step of rad_dt).
@@ -280,7 +285,9 @@ rad_status rad_read(rad_ctx *ctx, int field, void *dst, size_t bytes, int on_dev
  *   after the steps enqueued before the call.
  * Errors: RAD_EINVAL (NULL, unknown field, bytes too small, no state set
  * before a read), RAD_ENOMEM (no workspace, or the staging allocation
- * failed), RAD_ECUDA.  Device status words surface at rad_sync. */
+ * failed), RAD_ECUDA.  Device status words, and RAD_ENONPHYS for
+ * non-physical uploaded values (as rad_set_gas / rad_set_rad), surface at
+ * rad_sync. */
 rad_status rad_set_gas_host_async(rad_ctx *ctx, const void *rho, const void *v, const void *T);
 rad_status rad_set_rad_host_async(rad_ctx *ctx, const void *E, const void *F);
 rad_status rad_read_host_async(rad_ctx *ctx, int field, void *dst, size_t bytes);
@@ -291,7 +298,8 @@ rad_status rad_read_host_async(rad_ctx *ctx, int field, void *dst, size_t bytes)
  * dt q to the gas row of the implicit solve and to the gas energy, so that
  * E_gas + (c/chat) E_r gains dt q.  The field stays until set again.
  * Requires params.irradiation = 1 at rad_create.  Errors: RAD_EINVAL (no
- * irradiation field, NULL q), RAD_ENOMEM, RAD_ECUDA. */
+ * irradiation field, NULL q), RAD_ENOMEM, RAD_ENONPHYS (a value that is
+ * not finite), RAD_ECUDA. */
 rad_status rad_set_irradiation(rad_ctx *ctx, const void *q, int on_device);
 
 /* Waits for the stream and returns the device status word (RAD_OK if no
@@ -328,6 +336,17 @@ rad_status rad_profile_end(rad_ctx *ctx, float *step_ms, float *queue_ms, int *n
 rad_status rad_set_launch(rad_ctx *ctx, int variant, int chunk);
 rad_status rad_get_launch(const rad_ctx *ctx, int *variant, int *chunk, int *nvariants);
 
+/* Bound on the first wait of the TMA-staged step kernels for each plane of
+ * the state (the launch variants that stage planes by TMA; the others do not
+ * wait).  0 (the default) is a bounded blocking wait of 2^21 tries, far
+ * longer than a copy takes; polls > 0 makes it that many non-blocking tests
+ * of the plane's mbarrier.  A wait that runs out stops the CTA once its
+ * copies in flight have landed, and the next rad_sync returns RAD_ETIMEOUT.
+ * The state that step leaves is not valid (set it again), but the context
+ * stays usable.  Not in the paper: it exists so that the timeout path can be
+ * exercised without a fault.  Errors: RAD_EINVAL. */
+rad_status rad_set_wait_limit(rad_ctx *ctx, unsigned int polls);
+
 /* Autotuner: times `reps` steps of every (shape, chunk) candidate on the
  * current state without advancing it (each trial recomputes the same step
  * into the spare buffer), selects the fastest, and restores the counters
@@ -344,7 +363,9 @@ rad_status rad_tune(rad_ctx *ctx, int reps, int *variant, int *chunk, float *ms)
  * tanh layers of 64 units maps (log10 alpha / 4, log10 eps / 4) to
  * log(T^{n+1}/T^n); the iteration starts from T^n exp(output) and keeps its
  * convergence test, so results agree with starting from T^n to that test.
- * Records are float4 (x1, x2, log(T^{n+1}/T^n), gate value), device memory.
+ * Records are float4 (x1, x2, log(T^{n+1}/T^n), gate value), device memory,
+ * and every record pointer must be 16-byte aligned (an offset view of a
+ * record array that starts inside a record is refused with RAD_EINVAL).
  * Parameters: rad_mlp_nparam() floats, laid out W1 (64x2, row-major), b1,
  * W2 (64x64), b2, W3 (64x64), b3, w4 (64), b4.
  * -------------------------------------------------------------------------- */
@@ -416,7 +437,8 @@ rad_status rad_log_count(rad_ctx *ctx, size_t *n);
  * array's device address (cudaGetSymbolAddress) with that device current; make
  * that first call before any stream capture.
  *
- * Errors: RAD_EINVAL for NULL pointers, n == 0 or n > RAD_NOALLOC_MAX_RECORDS
+ * Errors: RAD_EINVAL for NULL pointers, dev_records not 16-byte aligned,
+ * n == 0 or n > RAD_NOALLOC_MAX_RECORDS
  * (split larger sets and add the gradients, weighted by their counts);
  * RAD_EUNSUPPORTED for device ordinals >= 64; RAD_ECUDA if the address lookup
  * or a launch fails. */

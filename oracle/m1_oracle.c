@@ -143,7 +143,7 @@ enum {
   ORC_ST_EFLOOR = 1,   /* E floor applications */
   ORC_ST_FCLIP = 2,    /* |F| <= E clips after the coupling */
   ORC_ST_ITERS = 3,    /* coupling iterations (sum) */
-  ORC_ST_ITMAX = 4,    /* coupling iterations (max) */
+  ORC_ST_ITMAX = 4,    /* coupling iterations of one cell, both attempts (max) */
   ORC_ST_FALLBACK = 5, /* Newton restarts from T^n */
   ORC_ST_NOCONV = 6,   /* cells that did not converge */
   ORC_NSTATS = 8
@@ -868,6 +868,7 @@ static void couple(const orc_problem *p, double dt, double rho, double Tn, doubl
     if (st[ORC_ST_ITMAX] < 1) st[ORC_ST_ITMAX] = 1;
     return;
   }
+  int total = 0; /* iterations of this cell over both attempts */
   for (int attempt = 0; attempt < 2; ++attempt) {
     double Tk = (attempt == 0) ? T0 : Tn;
     double E = Estar, T = Tk;
@@ -883,7 +884,8 @@ static void couple(const orc_problem *p, double dt, double rho, double Tn, doubl
     }
     int used = ok ? it : (it > p->newton_maxit ? p->newton_maxit : it);
     st[ORC_ST_ITERS] += used;
-    if (st[ORC_ST_ITMAX] < used) st[ORC_ST_ITMAX] = used;
+    total += used;
+    if (st[ORC_ST_ITMAX] < total) st[ORC_ST_ITMAX] = total;
     if (ok) {
       *Enew = E;
       *Tnew = T;

@@ -80,7 +80,7 @@ EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_w
            "rad_read", "rad_set_gas_host_async", "rad_set_rad_host_async",
            "rad_read_host_async", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
            "rad_launches_per_step", "rad_profile_begin", "rad_profile_end",
-           "rad_set_launch", "rad_get_launch", "rad_tune",
+           "rad_set_launch", "rad_get_launch", "rad_set_wait_limit", "rad_tune",
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
            "rad_mlp_grad", "rad_mlp_predict", "rad_mlp_predict_tc", "rad_log_bind",
            "rad_log_count",
@@ -129,6 +129,7 @@ def lib() -> C.CDLL:
     L.rad_profile_begin.argtypes = [vp, C.c_int]
     L.rad_profile_end.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_int)]
     L.rad_set_launch.argtypes = [vp, C.c_int, C.c_int]
+    L.rad_set_wait_limit.argtypes = [vp, C.c_uint]
     L.rad_get_launch.argtypes = [vp, P(C.c_int), P(C.c_int), P(C.c_int)]
     L.rad_tune.argtypes = [vp, C.c_int, P(C.c_int), P(C.c_int), P(C.c_float)]
     L.rad_mlp_nparam.argtypes = []
@@ -387,6 +388,10 @@ class Rad:
 
     def set_launch(self, variant: int, chunk: int = 0):
         check(lib().rad_set_launch(self.ctx, int(variant), int(chunk)), "rad_set_launch")
+
+    def set_wait_limit(self, polls: int):
+        """Bound of the staged-plane waits (0: the default)."""
+        check(lib().rad_set_wait_limit(self.ctx, int(polls)), "rad_set_wait_limit")
 
     def get_launch(self) -> tuple:
         v, c, n = C.c_int(), C.c_int(), C.c_int()

@@ -122,6 +122,7 @@ void patch_args(rad_batch* b, void* blk, int i) {
   a.chunk = grid_chunk(b, i, b->chunk);
   a.stats = reinterpret_cast<unsigned long long*>(b->ws + b->off_stats);
   a.status = reinterpret_cast<int*>(b->ws + b->off_status);
+  a.wait_polls = 0;
   a.queue_count = reinterpret_cast<unsigned int*>(b->ws + b->off_qcounts) + i;
   a.mlp_w = (b->mlp && b->mlp_ready) ? reinterpret_cast<const float*>(b->ws + b->off_mlp)
                                      : nullptr;

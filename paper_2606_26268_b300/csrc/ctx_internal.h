@@ -73,6 +73,7 @@ struct rad_ctx {
   uint64_t steps = 0;
   LaunchEntry launch{nullptr, 0};
   int variant = 0, chunk = 0;   // CTA shape and march length (0 = defaults)
+  unsigned int wait_polls = 0;  // bound of the staged-plane waits (0 = default)
   bool uniform = false;         // Cartesian with a constant width along each direction
   bool general = false;         // general form of the step kernel (options, absorption, irradiation)
   // learned guess

@@ -113,6 +113,10 @@ struct StepArgs {
   T inv_chat;
   unsigned long long* stats;
   int* status;
+  // first wait on each TMA-staged plane: 0 = the default bounded wait,
+  // else that many non-blocking tests; a wait that runs out sets
+  // STATUS_TIMEOUT and the CTA stops once its copies in flight have landed
+  unsigned int wait_polls;
   int chunk;      // cells along the march axis per CTA
   // uniform Cartesian grids: 1 / width per direction and the largest width
   T uni_inv[3];

@@ -166,7 +166,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   };
   bool ok = true;
   auto wait = [&](int j) {
-    if (!mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit)) {
+    const uint32_t par = uint32_t((j / R) & 1);
+    if (!(a.wait_polls ? mbar_test(&s_bar[j % R], par, a.wait_polls)
+                       : mbar_wait(&s_bar[j % R], par, kWaitLimit))) {
       ok = false;
       s_abort = 1;
     }
@@ -509,7 +511,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   __syncthreads();
   if (s_abort && tid == 0) {
     // let the copies still in flight land (bounded) before the CTA exits
-    for (int j = 0; j <= jissued; ++j) mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit);
+    // (the last phase issued on each slot: the earlier ones completed first)
+    for (int j = jissued - R + 1 > 0 ? jissued - R + 1 : 0; j <= jissued; ++j)
+      mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit);
   }
   counters_flush<P>(a, cnt, s_red, tid);
 }

@@ -12,6 +12,7 @@
 // GPU loading this library holds until the process exits.
 #include <cuda_runtime.h>
 
+#include <cstdint>
 #include <mutex>
 
 #include "mlp.cuh"
@@ -177,6 +178,8 @@ extern "C" rad_status rad_mlp_grad_noalloc(const float* dev_params, const float*
                                            size_t n, float* dev_grad, float* dev_loss,
                                            void* stream) {
   if (!dev_params || !dev_records || !dev_grad || !dev_loss || n == 0) return RAD_EINVAL;
+  // the records are read as 16-byte vectors
+  if (reinterpret_cast<uintptr_t>(dev_records) & 15u) return RAD_EINVAL;
   if (n > size_t(RAD_NOALLOC_MAX_RECORDS)) return RAD_EINVAL;  // beyond the scratch
   float* partial = nullptr;
   double* loss_partial = nullptr;

@@ -99,6 +99,8 @@ struct TcMlpSmem {
   alignas(8) unsigned long long bar;            // MMA completion
   uint32_t tmem;                                // TMEM base address
   int err;                                      // a bounded wait ran out
+  int issued;                                   // thread 0 committed a product
+  uint32_t last_parity;                         // phase of its last commit
 };
 
 // Writes 64 activations of row r (this thread) into the operand tile as bf16.
@@ -137,6 +139,8 @@ __device__ __forceinline__ void tc_mlp_setup(TcMlpSmem& s, const float* __restri
   if (tid == 0) {
     s.b4 = w[MLP_B4];
     s.err = 0;
+    s.issued = 0;
+    s.last_parity = 0;
     mbar_init(&s.bar, 1);
     mbar_fence_init();
   }
@@ -155,10 +159,14 @@ __device__ __forceinline__ void tc_mlp_setup(TcMlpSmem& s, const float* __restri
 }
 
 // Releases the TMEM columns (all TC_ROWS threads; after the last forward).
+// After a wait that ran out, the product last committed may still be
+// writing the columns: thread 0 waits for it (bounded) before warp 0 frees
+// them.
 __device__ __forceinline__ void tc_mlp_teardown(TcMlpSmem& s, int tid) {
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
+  if (tid == 0 && s.err && s.issued) mbar_wait(&s.bar, s.last_parity, kWaitLimit);
   if (tid < 32)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(s.tmem),
                  "r"(TC_TMEM_COLS)
@@ -167,25 +175,40 @@ __device__ __forceinline__ void tc_mlp_teardown(TcMlpSmem& s, int tid) {
 
 // One hidden layer on the tensor cores: TMEM <- A (activations) x W^T, then
 // this thread's 64 accumulators + bias through tanh into h.  `parity`: phase
-// of the completion barrier this product completes.
+// of the completion barrier this product completes.  Once a wait of the CTA
+// has run out (s.err, read after the barrier that precedes the layer), no
+// further product is issued and the accumulators are not read: the outputs
+// are then meaningless and the launch reports STATUS_TIMEOUT.  A thread
+// whose own wait runs out does not read the columns either, since the
+// product may still be writing them.
 __device__ __forceinline__ void tc_layer(TcMlpSmem& s, const unsigned char* wtile,
                                          const float* __restrict__ bias, uint32_t parity, int tid,
                                          float (&h)[MLP_H]) {
-  if (tid == 0) {
+  const bool skip = *static_cast<volatile int*>(&s.err) != 0;
+  if (tid == 0 && !skip) {
     const uint32_t a0 = smem_addr(s.a), b0 = smem_addr(wtile);
 #pragma unroll
     for (int ks = 0; ks < MLP_H / 16; ++ks)
       tc_mma(s.tmem, tc_desc(a0 + ks * 256), tc_desc(b0 + ks * 256), ks > 0);
     tc_commit(&s.bar);
+    s.issued = 1;
+    s.last_parity = parity;
   }
-  if (!mbar_wait(&s.bar, parity, kWaitLimit)) s.err = 1;
+  const bool done = !skip && mbar_wait(&s.bar, parity, kWaitLimit);
+  if (!skip && !done) s.err = 1;
   tc_fence_after();
   const uint32_t lane = uint32_t(tid & ~31) << 16;  // this warp's 32 TMEM lanes
 #pragma unroll
   for (int c = 0; c < MLP_H / 16; ++c) {
     float v[16];
-    tc_ld16(s.tmem + lane + uint32_t(16 * c), v);
-    tc_wait_ld();
+#pragma unroll
+    for (int i = 0; i < 16; ++i) v[i] = 0.f;
+    // tcgen05.ld is warp-collective: the warp reads only if all its lanes
+    // saw the product complete
+    if (__all_sync(0xffffffffu, done)) {
+      tc_ld16(s.tmem + lane + uint32_t(16 * c), v);
+      tc_wait_ld();
+    }
 #pragma unroll
     for (int i = 0; i < 16; ++i) h[16 * c + i] = tanh_approx(v[i] + bias[16 * c + i]);
   }

@@ -6,6 +6,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdint>
 #include <cstdio>
 #include <cstring>
 #include <mutex>
@@ -176,6 +177,11 @@ static double cfl_dt(const rad_ctx* c) {
 // ---------------------------------------------------------------------------
 
 static bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+// float4 records (the learned guess's training and prediction sets, the log
+// of converged solves) are read and written as 16-byte vectors: a pointer
+// off that boundary is refused on the host instead of faulting on the device.
+static bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) != 0; }
 
 extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_opacity* opacity,
                                  const rad_params* params, rad_ctx** out) {
@@ -526,11 +532,12 @@ struct GhostVals {
 // (the other kinds); reflective sides negate the normal component (comp ==
 // direction) of F and m; FIXED and LTE sides substitute their boundary
 // state: E (FIXED: E_b, LTE: a_R T_b^4), F (FIXED: F_b), m (zero) and
-// e = rho cvfac T_b.
+// e = rho cvfac T_b.  Caller values that are not finite, and E, rho or T
+// that are not positive, set STATUS_NONPHYS in *bad.
 template <class S>
 __global__ void pack_kernel(S* __restrict__ dst, const S* __restrict__ src,
                             const S* __restrict__ rho, StepDims D, int mode, double cvfac,
-                            int field, int comp, GhostVals gv) {
+                            int field, int comp, GhostVals gv, int* __restrict__ bad) {
   const long long total = (long long)D.pn[0] * D.pn[1] * D.pn[2];
   for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < total;
        p += (long long)gridDim.x * blockDim.x) {
@@ -567,6 +574,10 @@ __global__ void pack_kernel(S* __restrict__ dst, const S* __restrict__ src,
       mul *= n;
     }
     double v = double(src[lin]);
+    {
+      const bool positive = field == FK_E || field == FK_RHO || field == FK_EINT;
+      if (!isfinite(v) || (positive && !(v > 0.0))) atomicOr(bad, STATUS_NONPHYS);
+    }
     if (mode == PK_MOM) v = v * double(rho[lin]);
     if (mode == PK_EINT) v = v * double(rho[lin]) * cvfac;
     if (over >= 0) {
@@ -616,8 +627,29 @@ static rad_status pack(rad_ctx* c, S* dst, const S* src, const S* rho, int mode,
       for (int q = 0; q < 5; ++q) gv.v[d][side][q] = c->bc_val[d][side][q];
   gv.a_rad = c->par.a_rad;
   pack_kernel<S><<<grid_for((long long)c->pcells), 256, 0, c->stream>>>(
-      dst, src, rho, c->dims, mode, cvfac, field, comp, gv);
+      dst, src, rho, c->dims, mode, cvfac, field, comp, gv,
+      reinterpret_cast<int*>(c->ws + c->off_status) + 1);
   return cuda_err(cudaGetLastError());
+}
+
+// The input word (status slot 1) that pack_kernel sets for non-physical
+// caller values: read and cleared once the uploads have finished.
+static rad_status take_input_status(rad_ctx* c) {
+  int st = 0;
+  int* w = reinterpret_cast<int*>(c->ws + c->off_status) + 1;
+  if (cudaMemcpyAsync(&st, w, sizeof(int), cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return RAD_ECUDA;
+  if (!st) return RAD_OK;
+  if (cudaMemsetAsync(w, 0, sizeof(int), c->stream) != cudaSuccess) return RAD_ECUDA;
+  return RAD_ENONPHYS;
+}
+
+// End of a synchronous upload: wait, then report non-physical input.
+static rad_status finish_upload(rad_ctx* c, bool wait) {
+  if (!wait) return cuda_err(cudaGetLastError());
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
+  return take_input_status(c);
 }
 
 static void* state_ptr(rad_ctx* c, int b, int k) {
@@ -682,7 +714,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
   for (int b = 0; b < c->nbuf; ++b)
     if ((st = pack<S>(c, static_cast<S*>(state_ptr(c, b, 4)), t, r, PK_EINT, FK_EINT))) return st;
   c->have_gas = true;
-  return cuda_err(wait ? cudaStreamSynchronize(c->stream) : cudaGetLastError());
+  return finish_upload(c, wait);
 }
 
 extern "C" rad_status rad_set_gas(rad_ctx* c, const void* rho, const void* v, const void* T,
@@ -722,7 +754,7 @@ static rad_status set_rad_t(rad_ctx* c, const void* E, const void* F, int dev, b
     }
   }
   c->have_rad = true;
-  return cuda_err(wait ? cudaStreamSynchronize(c->stream) : cudaGetLastError());
+  return finish_upload(c, wait);
 }
 
 template <class S>
@@ -731,7 +763,7 @@ static rad_status set_irr_t(rad_ctx* c, const void* q, int dev) {
   const S* src = static_cast<const S*>(stage_in(c, q, c->N, 0, dev, &st));
   if (st) return st;
   if ((st = pack<S>(c, reinterpret_cast<S*>(c->ws + c->off_qirr), src, src, PK_COPY, FK_OTHER))) return st;
-  return cuda_err(cudaStreamSynchronize(c->stream));
+  return finish_upload(c, true);
 }
 
 extern "C" rad_status rad_set_irradiation(rad_ctx* c, const void* q, int on_device) {
@@ -839,6 +871,7 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   a.inv_chat = T(1.0 / c->par.chat);
   a.stats = reinterpret_cast<unsigned long long*>(c->ws + c->off_stats);
   a.status = reinterpret_cast<int*>(c->ws + c->off_status);
+  a.wait_polls = c->wait_polls;
   a.chunk = 0;
   double hmax = 0.0;
   for (int d = 0; d < 3; ++d) {
@@ -1182,7 +1215,8 @@ extern "C" rad_status rad_mlp_init(rad_ctx* c, uint64_t seed) {
 
 extern "C" rad_status rad_mlp_grad(rad_ctx* c, const float* dev_records, size_t n,
                                    float* host_grad, float* host_loss) {
-  if (!c || !dev_records || n == 0 || n > (size_t(1) << 31)) return RAD_EINVAL;
+  if (!c || !dev_records || n == 0 || n > (size_t(1) << 31) || misaligned16(dev_records))
+    return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   float* w = reinterpret_cast<float*>(c->ws + c->off_mlp);
   float* g = reinterpret_cast<float*>(c->ws + c->off_grad);
@@ -1209,7 +1243,7 @@ extern "C" rad_status rad_mlp_grad(rad_ctx* c, const float* dev_records, size_t 
 extern "C" rad_status rad_mlp_train(rad_ctx* c, const float* dev_records, size_t n, int epochs,
                                     int batch, float lr, uint64_t seed, float* final_loss) {
   if (!c || !dev_records || n == 0 || epochs < 0 || batch < 1 || !(lr > 0.f) ||
-      n > (size_t(1) << 40))
+      n > (size_t(1) << 40) || misaligned16(dev_records))
     return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   if (!c->mlp_ready) {
@@ -1251,7 +1285,7 @@ extern "C" rad_status rad_mlp_train(rad_ctx* c, const float* dev_records, size_t
 
 extern "C" rad_status rad_mlp_predict(rad_ctx* c, const float* dev_records, size_t n,
                                       float* dev_out) {
-  if (!c || !dev_records || !dev_out || n == 0) return RAD_EINVAL;
+  if (!c || !dev_records || !dev_out || n == 0 || misaligned16(dev_records)) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   return cuda_err(mlp_predict_launch(reinterpret_cast<const float*>(c->ws + c->off_mlp),
                                      reinterpret_cast<const float4*>(dev_records), (long long)n,
@@ -1260,7 +1294,7 @@ extern "C" rad_status rad_mlp_predict(rad_ctx* c, const float* dev_records, size
 
 extern "C" rad_status rad_mlp_predict_tc(rad_ctx* c, const float* dev_records, size_t n,
                                          float* dev_out) {
-  if (!c || !dev_records || !dev_out || n == 0) return RAD_EINVAL;
+  if (!c || !dev_records || !dev_out || n == 0 || misaligned16(dev_records)) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   return cuda_err(mlp_predict_tc_launch(reinterpret_cast<const float*>(c->ws + c->off_mlp),
                                         reinterpret_cast<const float4*>(dev_records), (long long)n,
@@ -1270,7 +1304,8 @@ extern "C" rad_status rad_mlp_predict_tc(rad_ctx* c, const float* dev_records, s
 
 extern "C" rad_status rad_log_bind(rad_ctx* c, float* dev_records, size_t capacity,
                                    long long stride) {
-  if (!c || (dev_records && (capacity == 0 || stride < 1)) || capacity > 0xffffffffull)
+  if (!c || (dev_records && (capacity == 0 || stride < 1 || misaligned16(dev_records))) ||
+      capacity > 0xffffffffull)
     return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   c->log_buf = dev_records;
@@ -1299,6 +1334,12 @@ extern "C" rad_status rad_set_launch(rad_ctx* c, int variant, int chunk) {
   if (!c || variant < 0 || variant >= c->launch.variants || chunk < 0) return RAD_EINVAL;
   c->variant = variant;
   c->chunk = chunk;
+  return RAD_OK;
+}
+
+extern "C" rad_status rad_set_wait_limit(rad_ctx* c, unsigned int polls) {
+  if (!c) return RAD_EINVAL;
+  c->wait_polls = polls;
   return RAD_OK;
 }
 
@@ -1393,12 +1434,15 @@ extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, f
 // ---------------------------------------------------------------------------
 
 static rad_status take_status(rad_ctx* c) {
-  int st = 0;
-  if (cudaMemcpyAsync(&st, c->ws + c->off_status, sizeof(int), cudaMemcpyDeviceToHost,
+  // slot 0: the kernels' word; slot 1: non-physical values of asynchronous
+  // uploads (the synchronous ones report them themselves)
+  int w[2] = {0, 0};
+  if (cudaMemcpyAsync(w, c->ws + c->off_status, sizeof(w), cudaMemcpyDeviceToHost,
                       c->stream) != cudaSuccess)
     return RAD_ECUDA;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
-  if (st) cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(int), c->stream);
+  const int st = w[0] | w[1];
+  if (st) cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(w), c->stream);
   if (st & STATUS_TIMEOUT) return RAD_ETIMEOUT;
   if (st & STATUS_NONPHYS) return RAD_ENONPHYS;
   if (st & STATUS_NOCONV) return RAD_ENOCONV;

@@ -53,6 +53,25 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long* bar, uint32_t pari
   return false;
 }
 
+// As mbar_wait with `polls` non-blocking tests (mbarrier.test_wait), so
+// that the bound counts tests rather than suspensions of the thread.
+__device__ __forceinline__ bool mbar_test(unsigned long long* bar, uint32_t parity,
+                                          uint32_t polls) {
+  const uint32_t addr = smem_addr(bar);
+  for (uint32_t i = 0; i < polls; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
 // 3D tiled TMA load of the box at element coordinates (x, y, z) of the
 // tensor described by `map` (a kernel parameter) into shared memory at dst;
 // completion is signalled as transaction bytes on `bar`.  x * element size

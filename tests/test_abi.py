@@ -210,3 +210,33 @@ def test_curvilinear_grids_offer_the_tma_staged_shapes_in_the_split_form(R, geom
     assert shapes(precision=R.RAD_FP32_SPLIT, irradiation=1) == 3
     assert shapes(precision=R.RAD_FP32_SPLIT, reconstruction=R.RAD_LIMO3) == 1
     assert shapes(precision=R.RAD_FP64) == 1
+
+
+def test_record_pointers_off_a_16_byte_boundary_are_refused(R):
+    """Records are read and written as float4: a pointer that is not 16-byte
+    aligned (an offset view starting inside a record) is refused on the host
+    with RAD_EINVAL before anything is launched or the workspace is looked
+    at, for every entry point that takes one."""
+    L = R.lib()
+    g, xs = _grid(R)
+    o = R.rad_opacity()
+    p = R.default_params()
+    ctx = C.c_void_p()
+    assert L.rad_create(C.byref(g), 0, C.byref(o), C.byref(p), C.byref(ctx)) == R.RAD_OK
+    odd = C.c_void_p(0x10004)   # never dereferenced: refused on the host
+    out = C.c_void_p(0x20000)
+    loss = C.c_float()
+    assert L.rad_mlp_grad(ctx, odd, 16, None, C.byref(loss)) == R.RAD_EINVAL
+    assert L.rad_mlp_train(ctx, odd, 16, 1, 8, C.c_float(1e-3), 0, None) == R.RAD_EINVAL
+    assert L.rad_mlp_predict(ctx, odd, 16, out) == R.RAD_EINVAL
+    assert L.rad_mlp_predict_tc(ctx, odd, 16, out) == R.RAD_EINVAL
+    assert L.rad_log_bind(ctx, odd, 16, 1) == R.RAD_EINVAL
+    assert L.rad_mlp_grad_noalloc(out, odd, 16, out, out, None) == R.RAD_EINVAL
+    # an aligned pointer gets past the check (no workspace bound: RAD_ENOMEM)
+    assert L.rad_mlp_predict(ctx, C.c_void_p(0x10010), 16, out) == R.RAD_ENOMEM
+    L.rad_destroy(ctx)
+
+
+def test_wait_limit_setter_validates_its_context(R):
+    L = R.lib()
+    assert L.rad_set_wait_limit(None, 1) == R.RAD_EINVAL

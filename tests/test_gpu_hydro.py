@@ -117,6 +117,29 @@ def test_gas_split_normwise():
     assert err <= 1e-5, ("m", err)
 
 
+def test_gas_step_split_per_cell_over_full_marches():
+    """The split gas step keeps the tile's own input in two alternating
+    shared-memory copies and writes the face fluxes only after the next
+    plane's first barrier, so its march needs no barrier after the update.
+    Three full 16-plane marches per CTA column (48 planes), 32 x 8 tiles
+    with ragged x and y tails, RK2: the density (moved by the gas step
+    alone) per cell and the momentum normwise stay at FP32 rounding of the
+    oracle; a plane read before it is complete would move cells by O(1)."""
+    p = W.random_smooth("cartesian", (70, 20, 48), 3, seed=1450, bc="periodic", ncomp=3,
+                        fmax=0.8)
+    p.hydro = True
+    p.integrator = "rk2"
+    q = rounded(p, np.float32)
+    dt = oracle.Oracle(q).dt()
+    g = run_gpu(q, 4, "split", dt=dt)
+    o = run_oracle(q, 4, dt=dt)
+    assert g["status"] == 0
+    rho_cell = np.max(np.abs(g["rho"] - o["rho"]) / o["rho"])
+    assert rho_cell <= 1e-5, rho_cell
+    m_norm = np.linalg.norm(g["m"] - o["m"]) / np.linalg.norm(o["m"])
+    assert m_norm <= 1e-5, m_norm
+
+
 def test_gas_cfl_step_matches_oracle_and_drives_automatic_steps():
     """rad_dt with evolved gas is the CFL step of the current state
     (max(chat, |v_d| + c_s) per direction), and rad_step with dt <= 0 takes

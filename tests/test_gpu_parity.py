@@ -157,12 +157,11 @@ def test_invalid_states_and_sizes_are_reported():
     r.step(0)
     assert r.sync() == R.RAD_OK
     bad = p.copy()
-    bad.T = -np.ones(p.N)  # negative temperature: flagged as non-physical
-    r2 = R.from_problem(bad, "fp64")
-    r2.step(1)
-    assert r2.sync() == R.RAD_ENONPHYS
+    bad.T = -np.ones(p.N)  # negative temperature: refused as non-physical
+    with pytest.raises(R.RadError) as err:
+        R.from_problem(bad, "fp64")
+    assert err.value.status == R.RAD_ENONPHYS
     r.close()
-    r2.close()
 
 
 def test_single_cell_and_tiny_grids():

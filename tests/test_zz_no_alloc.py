@@ -2,8 +2,9 @@
 allocate device memory (frameworks that own every byte of device memory
 through a pre-sized pool, or code that must not let an allocation synchronise
 the device).  It must agree with rad_mlp_grad, which keeps its accumulators in
-a context's workspace, on two calls in a row, and refuse sets larger than its
-fixed scratch.  This file is collected last on purpose."""
+a context's workspace, and the FP64 backpropagation of the oracle, on two
+calls in a row, and refuse sets larger than its fixed scratch.  This file is
+collected last on purpose."""
 import numpy as np
 import pytest
 
@@ -44,6 +45,11 @@ def test_noalloc_gradient_matches_the_workspace_entry_point():
         scale = np.max(np.abs(ref_grad))
         assert np.max(np.abs(g - ref_grad)) <= 1e-4 * scale
         assert float(loss.item()) == pytest.approx(ref_loss, rel=1e-5)
+        # and the FP64 backpropagation of the oracle on the same records
+        o_loss, o_grad = M.loss_and_grad(theta.astype(np.float64), rec[:, :2].astype(np.float64),
+                                         rec[:, 2].astype(np.float64))
+        assert np.max(np.abs(g - o_grad)) <= 1e-4 * np.max(np.abs(o_grad))
+        assert float(loss.item()) == pytest.approx(o_loss, rel=1e-4)
     # beyond the scratch: a clear error, nothing launched
     big = torch.zeros((R.NOALLOC_MAX_RECORDS + 1, 4), dtype=torch.float32, device="cuda")
     assert R.mlp_grad_noalloc(d_params, big, grad, loss) == R.RAD_EINVAL
