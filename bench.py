@@ -35,6 +35,12 @@ UNIT = "cell updates/s"
 # algorithmic bytes per cell update of the fused step (each field read once and
 # written once; halos, tables and ghost layers excluded)
 BYTES_PER_CELL = {("split", 3): 68, ("fp64", 3): 136, ("split", 2): 52, ("fp64", 2): 104}
+PRECISION_DETAIL = {
+    "split": "FP32 storage and transport; in the coupling the emission term a T^4, the residual "
+             "E* - a T^4 and the Newton numerator in FP64, the determinant, its reciprocal and "
+             "the increments of T and E in FP32; learned guess: hidden layers bf16 x bf16 -> FP32 "
+             "on the tensor cores",
+    "fp64": "FP64 throughout"}
 
 
 def peaks():
@@ -210,6 +216,56 @@ def time_steps(r, torch, steps, warmup, dt):
     kern_ms, queue_ms, n = r.profile_end()
     per = [ev[k].elapsed_time(ev[k + 1]) for k in range(steps)]
     return sum(per), per, {"step_kernel_ms": kern_ms / max(n, 1), "queue_pass_ms": queue_ms / max(n, 1)}
+
+
+def guess_gain_2d(R, torch, dev, args, theta, n=1024, steps=10):
+    """The 2D non-equilibrium box (E = (1 + 0.5 g)^4 against T = 1), split,
+    Newton rtol 1e-7: its first `steps` steps from the initial state with and
+    without the learned guess; device time per step and Newton iterations
+    per cell and step."""
+    import workloads as W
+    p = W.turbulent_2d((n, n), nonequilibrium=True)
+    p.newton_rtol = 1e-7
+    out = {"workload": p.name, "cells": p.N, "steps": steps,
+           "form": "split, Newton rtol 1e-7, the first steps from the initial state"}
+    for name, extra in (("with_guess", dict(use_mlp=1, mlp_gate=args.mlp_gate)),
+                        ("without_guess", {})):
+        r = R.from_problem(p, "split", device=dev, implicit_mode="newton", **extra)
+        if extra:
+            r.mlp_set(theta)
+        r.set_launch(2, 8)
+        dt = r.dt()
+        ms, per, kt = time_steps(r, torch, steps, 0, dt)
+        st = r.stats()
+        r.close()
+        out[name] = {"ms_per_step": ms / steps, "step_kernel_ms": kt["step_kernel_ms"],
+                     "queue_pass_ms": kt["queue_pass_ms"],
+                     "iters_per_cell_step": st["iters"] / max(1, st["steps"]) / p.N}
+    return out
+
+
+def split_error_record():
+    """The split form's error per configuration, measured at full size by
+    tests/split_error_report.py (too long for every bench run) and committed
+    with the hash of the step-kernel sources it ran on."""
+    path = os.path.join(ROOT, "profiles", "split_error.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+    except Exception:
+        return None
+    rows = {}
+    for k, v in d.get("configs", {}).items():
+        a = v["after_steps"]
+        row = {"steps": v["steps"], "cell_E": a["cell_E"], "cell_F": a["cell_F"],
+               "cell_e": a["cell_e"], "norm_E": a["norm_E"], "norm_F": a["norm_F"],
+               "norm_e": a["norm_e"]}
+        if "oracle_spread_1e-7" in v:
+            row["oracle_spread_1e-7_norm_E"] = v["oracle_spread_1e-7"]["norm_E"]
+        rows[k] = row
+    return {"source": "profiles/split_error.json (python tests/split_error_report.py)",
+            "date": d.get("date"), "current_kernel": d.get("kernel_sources_hash") == kernel_hash(),
+            "against": "FP64 oracle on the same float-rounded inputs", "configs": rows}
 
 
 def link_bandwidth(torch, mb=256, reps=5):
@@ -468,12 +524,35 @@ def run_ours(args):
                 continue
             rr = R.from_problem(prob, prec, device=dev, implicit_mode=impl, **ex)
             rr.set_launch(tuned[0], tuned[1])
-            ms_, per_, _ = time_steps(rr, torch, args.steps, 3, dt)
+            ms_, per_, kt_ = time_steps(rr, torch, args.steps, 3, dt)
             st_ = rr.stats()
             rr.close()
             forms[name] = {"value": N * args.steps / (ms_ * 1e-3), "unit": UNIT,
                            "ms_per_step": ms_ / args.steps, "iters": st_["iters"],
-                           "launches_per_step": 1}
+                           "iters_per_cell_step": st_["iters"] / max(1, st_["steps"]) / N,
+                           "step_kernel_ms": kt_["step_kernel_ms"],
+                           "queue_pass_ms": kt_["queue_pass_ms"],
+                           "launches_per_step": 2 if impl == "newton" else 1}
+
+    # --- what the learned guess changes: Newton iterations and time per step
+    # with and without it, on the headline grid (from the timed runs above)
+    # and on the 2D non-equilibrium box (1024^2, its first steps, where the
+    # coupling moves T most)
+    if not args.skip_forms and args.form == "mlp":
+        lg = {"hotsphere": {
+            "with_guess": {"ms_per_step": ms_max / args.steps,
+                           "step_kernel_ms": kt["step_kernel_ms"],
+                           "queue_pass_ms": kt["queue_pass_ms"],
+                           "iters_per_cell_step": st["iters"] / max(1, st["steps"]) / N},
+            "without_guess": None}}
+        if "split_newton_no_guess" in forms:
+            f_ = forms["split_newton_no_guess"]
+            lg["hotsphere"]["without_guess"] = {
+                "ms_per_step": f_["ms_per_step"], "step_kernel_ms": f_["step_kernel_ms"],
+                "queue_pass_ms": f_["queue_pass_ms"],
+                "iters_per_cell_step": f_["iters_per_cell_step"]}
+        lg["turb2d_neq_1024"] = guess_gain_2d(R, torch, dev, args, theta)
+        forms["learned_guess"] = lg
 
     # --- the two-stage (RK2 / IMEX1) step of the paper's runs, headline form
     if not args.skip_forms:
@@ -606,6 +685,7 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32+f64" if args.precision == "split" else "f64",
             "data": "synthetic (seeded hot-sphere box: log-normal density, Kramers opacity)",
             "config": {"workload": prob.name, "cells": N, "precision": args.precision,
+                       "precision_detail": PRECISION_DETAIL[args.precision],
                        "form": args.form, "implicit": implicit, "chat": prob.chat, "dt": dt,
                        "mlp_gate": args.mlp_gate if args.form == "mlp" else None,
                        "newton_rtol": rtol if implicit == "newton" else None,
@@ -625,6 +705,7 @@ def run_ours(args):
                          # source (null if the kernel changed since)
                          "issue": issue_view(prob.name, args.precision, N, kernel_ms)},
             "e2e": e2e,
+            "split_error": split_error_record(),
             "cpu_baseline": cpu,
             "fp64_plain": fp64,
             "forms": forms,

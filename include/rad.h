@@ -75,8 +75,11 @@ typedef enum {
   RAD_BC_LTE = 4
 } rad_bc;
 typedef enum { RAD_OPAC_CONST = 0, RAD_OPAC_POWERLAW = 1, RAD_OPAC_TABLE = 2 } rad_opac_kind;
-/* Precision.  RAD_FP32_SPLIT stores and transports in FP32 and forms the
- * emission residual and the coupling solve in FP64.  It forms f = |F|/E from
+/* Precision.  RAD_FP32_SPLIT stores and transports in FP32.  In the
+ * coupling it forms the emission term a T^4 and the residual E* - a T^4 in
+ * FP64 (and, when iterating, the numerator of the Newton update); the other
+ * products of the linearised solve (a T^3, the determinant and its
+ * reciprocal, the increments of T and E) are FP32.  It forms f = |F|/E from
  * E^2 and |F|^2 in FP32, so E (and e_floor) must keep E^2 a normal float
  * (E above about 1e-18 in the caller's units); below that use RAD_FP64 or
  * rescale the units. */

@@ -8,6 +8,7 @@
 
 #include "batch_launch.h"
 #include "m1_step.cuh"
+#include "m1_strip2d.cuh"
 #include "mlp_tc.cuh"
 #include "queue_cell.cuh"
 
@@ -28,7 +29,8 @@ __device__ __forceinline__ void copy_args(StepArgs<P>* dst, const StepArgs<P>* s
 // (one atomic per tile), loads that grid's arguments into shared memory and
 // runs the tile.  No CTA waits on another: the last CTA to retire resets the
 // counters for the next launch, which the stream orders after this one.
-template <class P, int NDIM, int NC, bool UNI, int TX, int TY, int MINB>
+// STRIP: 2D tiles as one warp per strip (step_strip2d, TX = 32).
+template <class P, int NDIM, int NC, bool UNI, int TX, int TY, int MINB, bool STRIP = false>
 __global__ void __launch_bounds__(TX * TY, MINB)
     batch_step_kernel(const StepArgs<P>* __restrict__ args, const int4* __restrict__ items,
                       int nitems, unsigned int* ctl) {
@@ -44,7 +46,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const int4 w = __ldg(items + it);
     copy_args<P>(&s_args, args + w.x, tid, NT);
     __syncthreads();
-    step_tile<P, NDIM, kCart, NC, UNI, TX, TY>(s_args, w.y, w.z, w.w);
+    if constexpr (STRIP)
+      step_strip2d<P, NC, UNI>(s_args, w.y, w.z);
+    else
+      step_tile<P, NDIM, kCart, NC, UNI, TX, TY>(s_args, w.y, w.z, w.w);
     __syncthreads();  // s_args and s_item are rewritten by the next tile
   }
   if (tid == 0) {
@@ -133,26 +138,28 @@ __global__ void __launch_bounds__(TC_ROWS)
   counters_flush<P>(args[0], cnt, s_red, tid);
 }
 
-template <class P, int NDIM, int NC, bool UNI, int TX, int TY, int MINB>
+template <class P, int NDIM, int NC, bool UNI, int TX, int TY, int MINB, bool STRIP = false>
 struct BatchShape {
   static cudaError_t launch(const void* args, const int4* items, int nitems, unsigned int* ctl,
                             int blocks, cudaStream_t s) {
-    batch_step_kernel<P, NDIM, NC, UNI, TX, TY, MINB>
+    batch_step_kernel<P, NDIM, NC, UNI, TX, TY, MINB, STRIP>
         <<<blocks, dim3(TX, NDIM == 3 ? TY : 1), 0, s>>>(
             static_cast<const StepArgs<P>*>(args), items, nitems, ctl);
     return cudaGetLastError();
   }
   static cudaError_t occupancy(int* per_sm) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(
-        per_sm, batch_step_kernel<P, NDIM, NC, UNI, TX, TY, MINB>, TX * TY, 0);
+        per_sm, batch_step_kernel<P, NDIM, NC, UNI, TX, TY, MINB, STRIP>, TX * TY, 0);
   }
 };
 
-// CTA shapes: 2D rows of 128, 256 or 64 threads marching along y; 3D 32x8
-// (2 or 3 CTAs/SM) marching along z.
+// CTA shapes: 2D rows of 128, 256 or 64 threads marching along y, rows of
+// 64 and 128 threads held to 80 or 64 registers so that 24 or 32 warps fit
+// on an SM, and one warp per strip of 31 columns (24 or 16 strips per SM);
+// 3D 32x8 (2 or 3 CTAs/SM) marching along z.
 template <class P, int NDIM, int NC, bool UNI>
 struct BatchShapes {
-  static constexpr int count = NDIM == 3 ? 2 : 3;
+  static constexpr int count = NDIM == 3 ? 2 : 8;
   static cudaError_t step(const void* args, const int4* items, int nitems, unsigned int* ctl,
                           int variant, int blocks, cudaStream_t s) {
     if constexpr (NDIM == 3) {
@@ -164,6 +171,16 @@ struct BatchShapes {
         return BatchShape<P, 2, NC, UNI, 256, 1, 1>::launch(args, items, nitems, ctl, blocks, s);
       if (variant == 2)
         return BatchShape<P, 2, NC, UNI, 64, 1, 1>::launch(args, items, nitems, ctl, blocks, s);
+      if (variant == 3)
+        return BatchShape<P, 2, NC, UNI, 64, 1, 12>::launch(args, items, nitems, ctl, blocks, s);
+      if (variant == 4)
+        return BatchShape<P, 2, NC, UNI, 128, 1, 6>::launch(args, items, nitems, ctl, blocks, s);
+      if (variant == 5)
+        return BatchShape<P, 2, NC, UNI, 64, 1, 16>::launch(args, items, nitems, ctl, blocks, s);
+      if (variant == 6)
+        return BatchShape<P, 2, NC, UNI, 32, 1, 24, true>::launch(args, items, nitems, ctl, blocks, s);
+      if (variant == 7)
+        return BatchShape<P, 2, NC, UNI, 32, 1, 16, true>::launch(args, items, nitems, ctl, blocks, s);
       return BatchShape<P, 2, NC, UNI, 128, 1, 1>::launch(args, items, nitems, ctl, blocks, s);
     }
   }
@@ -174,6 +191,11 @@ struct BatchShapes {
     } else {
       if (variant == 1) return BatchShape<P, 2, NC, UNI, 256, 1, 1>::occupancy(per_sm);
       if (variant == 2) return BatchShape<P, 2, NC, UNI, 64, 1, 1>::occupancy(per_sm);
+      if (variant == 3) return BatchShape<P, 2, NC, UNI, 64, 1, 12>::occupancy(per_sm);
+      if (variant == 4) return BatchShape<P, 2, NC, UNI, 128, 1, 6>::occupancy(per_sm);
+      if (variant == 5) return BatchShape<P, 2, NC, UNI, 64, 1, 16>::occupancy(per_sm);
+      if (variant == 6) return BatchShape<P, 2, NC, UNI, 32, 1, 24, true>::occupancy(per_sm);
+      if (variant == 7) return BatchShape<P, 2, NC, UNI, 32, 1, 16, true>::occupancy(per_sm);
       return BatchShape<P, 2, NC, UNI, 128, 1, 1>::occupancy(per_sm);
     }
   }
@@ -192,7 +214,7 @@ struct BatchShapes {
 template <class P, int NDIM, int NC, bool UNI>
 BatchEntry batch_entry() {
   using B = BatchShapes<P, NDIM, NC, UNI>;
-  BatchEntry e{&B::step, &B::qpass, &B::occupancy, B::count, {0, 0, 0, 0}, {1, 1, 1, 1}};
+  BatchEntry e{&B::step, &B::qpass, &B::occupancy, B::count, {}, {1, 1, 1, 1, 1, 1, 1, 1}};
   if (NDIM == 3) {
     e.tx[0] = e.tx[1] = 32;
     e.ty[0] = e.ty[1] = 8;
@@ -200,6 +222,10 @@ BatchEntry batch_entry() {
     e.tx[0] = 128;
     e.tx[1] = 256;
     e.tx[2] = 64;
+    e.tx[3] = 64;
+    e.tx[4] = 128;
+    e.tx[5] = 64;
+    e.tx[6] = e.tx[7] = 32;
   }
   return e;
 }

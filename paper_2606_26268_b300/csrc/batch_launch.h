@@ -29,7 +29,7 @@ struct BatchEntry {
   BatchQueueFn qpass;
   BatchOccFn occupancy;
   int variants;
-  int tx[4], ty[4];  // CTA shape of each variant
+  int tx[8], ty[8];  // CTA shape of each variant
 };
 
 // The batched launchers for (precision, active directions, carried flux

@@ -89,31 +89,33 @@ __device__ __forceinline__ void coupling_features(const CoupleParams& p, float r
 
 // The implicit coupling of the cell at padded index ic (Sect. 2.8): the
 // single linearised solve when `once`, else the mode of the parameters
-// (Newton from T0 > 0 or T^n).  GEN (the general form) adds the
-// absorption-only mode and the irradiation deposit of Sect. 2.9 when the
-// context has them; the default step kernels, which such contexts do not
-// use, compile both out.
+// (Newton from T0 > 0 or T^n; with T1 > 0, the single solve's result, Newton
+// continues from it or from T0, whichever leaves the smaller residual).
+// GEN (the general form) adds the absorption-only mode and the irradiation
+// deposit of Sect. 2.9 when the context has them; the default step kernels,
+// which such contexts do not use, compile both out.
 template <class P, bool GEN = true>
 __device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, long long ic,
                                                  typename P::S rho_s, typename P::S e_s,
                                                  typename P::T kp, typename P::T Es, float T0,
-                                                 bool once) {
+                                                 bool once, double T1 = 0.0) {
   using T = typename P::T;
   if constexpr (GEN) {
     const bool ab = a.cp.absorb;
     const T sq = a.qirr ? a.dt * T(__ldg(a.qirr + ic)) : T(0);
     if constexpr (P::kSplit)
       return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once,
-                          float(sq), ab);
+                          float(sq), ab, float(T1));
     else
       return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
-                         once, double(sq), ab);
+                         once, double(sq), ab, T1);
   } else {
     if constexpr (P::kSplit)
-      return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once);
+      return couple_split(a.cp, float(rho_s), float(e_s), float(kp), float(Es), T0, once, 0.f,
+                          false, float(T1));
     else
       return couple_fp64(a.cp, double(rho_s), double(e_s), double(kp), double(Es), double(T0),
-                         once);
+                         once, 0.0, false, T1);
   }
 }
 

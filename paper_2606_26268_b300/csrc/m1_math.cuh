@@ -448,10 +448,26 @@ struct CoupleOut {
 // the irradiation term that Sect. 2.9 adds to the gas row (0 without
 // irradiation).  Newton mode repeats the solve with Tk <- T^{n+1} until
 // |T^{n+1} - Tk| <= rtol T^{n+1}.
+//
+// Continuing after the single solve: T1 > 0 is the single solve's T^{n+1},
+// which is the first Newton iterate from T^n.  The first attempt then
+// starts from T1 (or from the learned guess T0 when T0 is given and leaves
+// the smaller residual of the scalar equation
+//   r(T) = (1 + g_r) (C_v (T - T^n) - sq) + g (a T^4 - E*)),
+// counts the single solve as its first iteration and has maxit - 1 left;
+// the restart from T^n after a failure is unchanged.  Without T1 the first
+// attempt starts from T0 (or T^n) with maxit iterations.
+__device__ __forceinline__ double couple_residual(const CoupleParams& p, double Cv, double g,
+                                                  double gr, double Tn, double Es, double sq,
+                                                  double T) {
+  const double T2 = T * T;
+  return (1.0 + gr) * (Cv * (T - Tn) - sq) + g * (p.a_rad * T2 * T2 - Es);
+}
+
 __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double rho, double e,
                                                  double kp, double Es, double T0,
                                                  bool once = false, double sq = 0.0,
-                                                 bool absorb = false) {
+                                                 bool absorb = false, double T1 = 0.0) {
   CoupleOut o{};
   double Cv = rho * p.cvfac;
   double Tn = e / Cv;
@@ -483,12 +499,24 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
     o.conv1 = fabs(dT) <= p.rtol * o.Tnew;
     return o;
   }
+  int maxit0 = p.maxit;
+  double Tstart = T0;
+  if (T1 > 0.0) {
+    o.iters = 1;  // the single solve, the first iterate from T^n
+    maxit0 = p.maxit - 1;
+    Tstart = T1;
+    if (T0 > 0.0 && T0 != Tn &&
+        fabs(couple_residual(p, Cv, g, gr, Tn, Es, sq, T0)) <
+            fabs(couple_residual(p, Cv, g, gr, Tn, Es, sq, T1)))
+      Tstart = T0;
+  }
   for (int attempt = 0; attempt < 2; ++attempt) {
-    double Tk = attempt == 0 ? T0 : Tn;
+    double Tk = attempt == 0 ? Tstart : Tn;
+    const int maxit = attempt == 0 ? maxit0 : p.maxit;
     bool ok = false;
     int it;
     double aT3 = 0.0, D = 0.0, det = 1.0, Tnew = Tk;
-    for (it = 1; it <= p.maxit; ++it) {
+    for (it = 1; it <= maxit; ++it) {
       aT3 = p.a_rad * Tk * Tk * Tk;
       D = Es - aT3 * Tk;
       det = c1 + 4.0 * g * aT3;
@@ -501,7 +529,7 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
       }
       Tk = Tnew;
     }
-    int used = ok ? it : (it > p.maxit ? p.maxit : it);
+    int used = ok ? it : (it > maxit ? maxit : it);
     o.iters += used;
     if (ok || attempt == 1) {
       o.Tnew = Tnew;
@@ -520,7 +548,7 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
 __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
                                                   float kp, float Es, float T0f,
                                                   bool once = false, float sq = 0.f,
-                                                  bool absorb = false) {
+                                                  bool absorb = false, float T1f = 0.f) {
   CoupleOut o{};
   float Cv = rho * p.f_cvfac;
   float invCv = rcp_approx(Cv);
@@ -560,14 +588,30 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
   }
   double Tn = double(Tf);
   double c1d = double(c1);
+  // continuing after the single solve (see couple_fp64)
+  int maxit0 = p.maxit;
+  double Tstart = T0f > 0.f ? double(T0f) : Tn;
+  if (T1f > 0.f) {
+    o.iters = 1;
+    maxit0 = p.maxit - 1;
+    const double T1 = double(T1f);
+    Tstart = T1;
+    if (T0f > 0.f && double(T0f) != Tn) {
+      const double Cvd = double(Cv), gd = double(g), grd = double(gr);
+      if (fabs(couple_residual(p, Cvd, gd, grd, Tn, double(Es), double(sq), double(T0f))) <
+          fabs(couple_residual(p, Cvd, gd, grd, Tn, double(Es), double(sq), T1)))
+        Tstart = double(T0f);
+    }
+  }
   for (int attempt = 0; attempt < 2; ++attempt) {
-    double Tk = (attempt == 0 && T0f > 0.f) ? double(T0f) : Tn;
+    double Tk = attempt == 0 ? Tstart : Tn;
+    const int maxit = attempt == 0 ? maxit0 : p.maxit;
     bool ok = false;
     int it;
     double aT3 = 0.0, D = 0.0;
     float det = 1.f;
     double Tnew = Tk;
-    for (it = 1; it <= p.maxit; ++it) {
+    for (it = 1; it <= maxit; ++it) {
       aT3 = p.a_rad * Tk * Tk * Tk;
       D = double(Es) - aT3 * Tk;
       det = c1 + 4.f * g * float(aT3);
@@ -581,7 +625,7 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
       }
       Tk = Tnew;
     }
-    int used = ok ? it : (it > p.maxit ? p.maxit : it);
+    int used = ok ? it : (it > maxit ? maxit : it);
     o.iters += used;
     if (ok || attempt == 1) {
       o.Tnew = Tnew;

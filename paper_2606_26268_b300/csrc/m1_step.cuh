@@ -637,6 +637,8 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
           if (slot < a.queue_cap) {
             a.queue[slot] = ic;
             a.stash.E[ic] = S(Us[0]);
+            // the single solve's T^{n+1}: the queue pass continues from it
+            a.stash.e[ic] = S(co.Tnew);
 #pragma unroll
             for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {

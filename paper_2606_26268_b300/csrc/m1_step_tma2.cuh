@@ -481,6 +481,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
           if (qs < a.queue_cap) {
             a.queue[qs] = ic;
             a.stash.E[ic] = S(Us[0]);
+            // the single solve's T^{n+1}: the queue pass continues from it
+            a.stash.e[ic] = S(co.Tnew);
 #pragma unroll
             for (int v = 0; v < NC; ++v) a.stash.F[v][ic] = S(Us[1 + v]);
           } else {

@@ -7,8 +7,9 @@
 
 namespace m1 {
 
-// A cell the step kernel queued: (E*, F*) left in the stash buffer, gas
-// state from the input buffer, opacities at (rho, T^n).
+// A cell the step kernel queued: (E*, F*) and the single solve's T^{n+1}
+// (T1, in the stash's e) left in the stash buffer, gas state from the input
+// buffer, opacities at (rho, T^n).
 template <class P>
 struct QueuedCell {
   using S = typename P::S;
@@ -16,7 +17,7 @@ struct QueuedCell {
   long long ic;
   int ci[3];
   T Us[4], mom[3], kp, chi;
-  S rho, e;
+  S rho, e, T1;
 };
 
 template <class P, int NC>
@@ -30,6 +31,7 @@ __device__ __forceinline__ void queue_load(const StepArgs<P>& a, long long ic, Q
   c.ci[1] = int(r % Dm.pn[1]) - Dm.g[1];
   c.ci[2] = int(r / Dm.pn[1]) - Dm.g[2];
   c.Us[0] = T(a.stash.E[ic]);
+  c.T1 = a.stash.e[ic];
   c.Us[1] = c.Us[2] = c.Us[3] = T(0);
   c.mom[0] = c.mom[1] = c.mom[2] = T(0);
 #pragma unroll
@@ -48,12 +50,14 @@ __device__ __forceinline__ void queue_load(const StepArgs<P>& a, long long ic, Q
   opacity(a.opac, rr, Temp, c.kp, c.chi);
 }
 
-// The Newton iteration from T0 (T^n when T0 = 0), then the common end of
-// the step.
+// The Newton iteration continued from the single solve's T1, or from the
+// learned guess T0 when that leaves the smaller residual, then the common
+// end of the step.
 template <class P, int NDIM, int NC>
 __device__ __forceinline__ void queue_solve(const StepArgs<P>& a, QueuedCell<P>& c, float T0,
                                             Counters& cnt) {
-  const CoupleOut co = couple_cell<P>(a, c.ic, c.rho, c.e, c.kp, c.Us[0], T0, false);
+  const CoupleOut co =
+      couple_cell<P>(a, c.ic, c.rho, c.e, c.kp, c.Us[0], T0, false, double(c.T1));
   finish_cell<P, NDIM, NC>(a, c.ic, c.ci, c.Us, c.rho, c.e, c.kp, c.chi, c.mom, co, cnt);
 }
 

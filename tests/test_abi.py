@@ -159,7 +159,7 @@ def test_options_boundaries_and_gas_are_validated_on_the_host(R):
 
 
 def test_general_form_offers_the_right_launch_shapes(R):
-    """Split 3D Cartesian: eight shapes in the default form and with evolved
+    """Split 3D Cartesian: ten shapes in the default form and with evolved
     gas (the TMA-staged ones read the gas step's output), four with a face
     option of Sect. 2.5 (the register-tiled kernel only)."""
     L = R.lib()
@@ -178,10 +178,10 @@ def test_general_form_offers_the_right_launch_shapes(R):
         L.rad_destroy(c2)
         return nv.value
 
-    assert shapes() == 8
-    assert shapes(hydro=1) == 8
-    assert shapes(irradiation=1) == 8
-    assert shapes(implicit_mode=R.RAD_ABSORPTION_ONLY) == 8
+    assert shapes() == 10
+    assert shapes(hydro=1) == 10
+    assert shapes(irradiation=1) == 10
+    assert shapes(implicit_mode=R.RAD_ABSORPTION_ONLY) == 10
     assert shapes(reconstruction=R.RAD_LIMO3) == 4
     assert shapes(face_fix=R.RAD_FIX_PLUTO, hydro=1) == 4
 

@@ -160,14 +160,14 @@ def test_batch_launch_shapes_graph_and_tuner():
                     assert_same(a, b, (graph, v, chunk))
                 for a, b in zip(ref[0], out):
                     assert_close(a, b, (graph, v, chunk))
-    assert nvar == 3
+    assert nvar == 8
     inb = members(probs, "split")
     batch = R.RadBatch(inb)
     batch.step(2)
     before = [state(r) for r in inb]
     st0 = batch.stats()
     v, c, ms = batch.tune(2)
-    assert 0 <= v < 3 and c > 0 and ms > 0
+    assert 0 <= v < 8 and c > 0 and ms > 0
     assert batch.stats() == st0
     for a, r in zip(before, inb):
         assert_same(a, state(r), "tune")

@@ -472,7 +472,7 @@ def test_rk2_split_and_launch_shapes():
     q.integrator = "rk2"
     q.implicit_mode = "newton"
     ref = None
-    for v in (0, 5, 7):
+    for v in (0, 5, 7, 9):
         r = R.from_problem(q, "split", newton_rtol=1e-7)
         r.set_launch(v, 0)
         r.step(3)
