@@ -348,7 +348,12 @@ def run_batched(args, R, torch, dev, theta, hbm, world=1):
     b = R.RadBatch(mem)
     if theta is not None:
         b.mlp_set(theta)
-    tuned = b.tune(3)
+    if args.batch_launch:
+        v_, c_ = (int(x) for x in args.batch_launch.split(","))
+        b.set_launch(v_, c_)
+        tuned = (v_, c_, None)
+    else:
+        tuned = b.tune(3)
     steps = max(args.steps, 10)
     ms_local = time_batch(b, torch, steps, args.warmup)
     ms = max_over_ranks(ms_local, world, dev)
@@ -813,6 +818,8 @@ def main():
     ap.add_argument("--skip-2d", action="store_true")
     ap.add_argument("--rhd-n", type=int, default=256, help="RHD pulse grid (n^3)")
     ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
+    ap.add_argument("--batch-launch", default="",
+                    help="variant,chunk of the batched form (skips its autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
