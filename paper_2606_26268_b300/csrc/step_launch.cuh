@@ -85,8 +85,9 @@ cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chun
 // per SM; variants 3, 4), and in the default form one warp per strip of 31
 // columns with the row exchanged by shuffles (variants 5, 6: 24 or 16
 // strips per SM); 1D: 128.  Curvilinear 3D
-// grids in the split precision: the default shape and the TMA-staged
-// non-overlapping 32x8 at 2 or 3 CTAs/SM (variants 1, 2); other curvilinear
+// grids in the split precision: the default shape, the TMA-staged
+// non-overlapping 32x8 at 2 or 3 CTAs/SM (variants 1, 2) and 16x16 at 3
+// (variant 3); other curvilinear
 // grids the default shape only.  The general form (GEN: face options,
 // absorption only, irradiation, evolved gas) has the TMA-staged shapes only
 // when it keeps the default face scheme (TMA_OK).  UYZ: directions 1 and 2
@@ -97,7 +98,7 @@ struct Shapes {
   static constexpr bool tma = TMA_OK && P::kSplit && GEOM == kCart && NDIM == 3;
   static constexpr bool tma_curv = TMA_OK && P::kSplit && GEOM != kCart && NDIM == 3;
   static constexpr int count =
-      tma_curv ? 3
+      tma_curv ? 4
                : ((GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 10 : 4) : (GEN ? 5 : 7)));
   static cudaError_t launch(const void* vargs, const void* maps, cudaStream_t s, int variant,
                             int chunk) {
@@ -107,6 +108,7 @@ struct Shapes {
       if constexpr (tma_curv) {
         if (variant == 1) return launch_tma2<P, NC, UNI, 32, 8, 2, GEN, GEOM, UYZ>(a, maps, s, chunk);
         if (variant == 2) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN, GEOM, UYZ>(a, maps, s, chunk);
+        if (variant == 3) return launch_tma2<P, NC, UNI, 16, 16, 3, GEN, GEOM, UYZ>(a, maps, s, chunk);
         return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2, GEN>(a, s, chunk);
       }
       if constexpr (tma) {
@@ -165,6 +167,8 @@ LaunchEntry entry() {
       e.tma_box[v][0] = Tma2Tile<32, 8>::BX;
       e.tma_box[v][1] = Tma2Tile<32, 8>::BY;
     }
+    e.tma_box[3][0] = Tma2Tile<16, 16>::BX;
+    e.tma_box[3][1] = Tma2Tile<16, 16>::BY;
   }
   return e;
 }

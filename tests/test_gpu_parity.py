@@ -254,16 +254,17 @@ def _curvilinear_case(which):
 @pytest.mark.parametrize("which", [8, 11, "disk", "stretched_theta"])
 def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
     """Split 3D cylindrical and spherical grids on every offered shape (the
-    register-tiled one and the TMA-staged non-overlapping tiles at 2 and 3
-    CTAs/SM) and two march lengths: the shapes agree to FP32 rounding and
-    each is within 1e-5 of the FP64 oracle normwise after 5 steps."""
+    register-tiled one, the TMA-staged non-overlapping 32x8 tiles at 2 and 3
+    CTAs/SM and 16x16 at 3) and two march lengths: the shapes agree to FP32
+    rounding and each is within 1e-5 of the FP64 oracle normwise after 5
+    steps."""
     import paper_2606_26268_b300 as R
     p = rounded(_curvilinear_case(which), np.float32)
     r0 = R.from_problem(p, "split")
     nvar = r0.get_launch()[2]
     dt = r0.dt()
     r0.close()
-    assert nvar == 3
+    assert nvar == 4
     o = run_oracle(p, 5, dt=dt)
     nE, ne = np.linalg.norm(o["E"]), np.linalg.norm(o["e"])
     ref = None
