@@ -120,7 +120,8 @@ __device__ __forceinline__ T vanleer(T dl, T dr) {
 
 // uf = (Ef, Ff) is the reconstructed face state of the cell uc = (Ec, Fc)
 // with nc2 = |Fc|^2.  The reconstructed flux is kept iff f_face <= 1 and
-// f_face > f_centre (compared without division: Ef, Ec > 0); otherwise
+// f_face > f_centre (compared without division: Ef, Ec > 0; in float the
+// squared ratios, with f_centre^2 from inv_Ec = 1 / Ec); otherwise
 // F_face = F_centre * E_face / E_centre.  Returns true when recomputed.
 template <class T, int NC>
 __device__ __forceinline__ bool fix_face(T (&uf)[4], const T (&uc)[4], T nc2, T inv_Ec) {
@@ -128,7 +129,14 @@ __device__ __forceinline__ bool fix_face(T (&uf)[4], const T (&uc)[4], T nc2, T 
   if (NC > 1) nf2 += uf[2] * uf[2];
   if (NC > 2) nf2 += uf[3] * uf[3];
   const T Ef = uf[0], Ec = uc[0];
-  bool keep = (nf2 <= Ef * Ef) && (nf2 * (Ec * Ec) > nc2 * (Ef * Ef));
+  bool keep;
+  if constexpr (sizeof(T) == 8) {
+    keep = (nf2 <= Ef * Ef) && (nf2 * (Ec * Ec) > nc2 * (Ef * Ef));
+  } else {
+    // f_centre^2 = nc2 / Ec^2 is the same for every face state of the cell
+    const T Ef2 = Ef * Ef;
+    keep = (nf2 <= Ef2) && (nf2 > (nc2 * (inv_Ec * inv_Ec)) * Ef2);
+  }
   if (!keep) {
     T r = (sizeof(T) == 8) ? Ef / Ec : Ef * inv_Ec;
     uf[1] = uc[1] * r;
@@ -201,10 +209,14 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
     T q = T(4) - T(3) * f2;
     T rs = rsqrt_approx(q);
     T s = q * rs;
-    T xi = (T(3) + T(4) * f2) * rcp_approx(T(5) + T(2) * s);
+    // (5 + 2 s)(5 - 2 s) = 25 - 4 s^2 = 3 (3 + 4 f^2), so xi = (5 - 2 s) / 3
+    // exactly: (1 - xi) / 2 = (s - 1) / 3 and (3 xi - 1) / 2 = 2 - s, with no
+    // division.
+    T t = s * T(1.0 / 3.0) - T(1.0 / 3.0);
+    T b2 = T(2) - s;
     T Ec = E * chat;
-    T ac = (T(0.5) - T(0.5) * xi) * Ec;
-    T bFd = ((T(1.5) * xi - T(0.5)) * Ec) * (rn * rn) * Fd;
+    T ac = t * Ec;
+    T bFd = (b2 * Ec) * (cth * rn);
     flux[0] = chat * Fd;
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
@@ -213,8 +225,9 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
         flux[1 + j] = (j == D) ? v + ac : v;
       }
     }
-    // (1 - f^2) / (s + 1) = (s - 1) / 3 since s^2 - 1 = 3 (1 - f^2)
-    T z2 = T(2.0 / 3.0) * (s - T(1)) * (s * (T(1) + c2) - T(2) * c2);
+    // (1 - f^2) / (s + 1) = (s - 1) / 3 since s^2 - 1 = 3 (1 - f^2), and
+    // s (1 + c^2) - 2 c^2 = s - c^2 (2 - s)
+    T z2 = T(2) * t * (s - c2 * b2);
     T z = sqrt_approx(z2 > T(0) ? z2 : T(0));
     lp = (fc + z) * rs;
     lm = (fc - z) * rs;

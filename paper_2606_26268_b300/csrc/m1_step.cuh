@@ -284,7 +284,11 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
   const int gm = MARCH ? Dm.g[MA] : 0;
   const bool in_col = cx < Dm.n[0] && (!TILE_Y || cy < Dm.n[1]);
   const bool upd_col = in_col && tx <= TX - 2 && (!TILE_Y || ty <= TY - 2);
-  const T chat = a.chat;
+  // In the split precision the face fluxes and signal speeds are formed in
+  // units of chat (the flux functions take fchat = 1) and the divergence
+  // is scaled by dt chat; in FP64 they carry chat as the oracle does.
+  const T fchat = P::kSplit ? T(1) : T(a.chat);
+  const T dtf = P::kSplit ? T(a.dt) * T(a.chat) : T(a.dt);
   Scheme sc{0, 0, 0};
   if constexpr (GEN) sc = a.scheme;
 
@@ -333,7 +337,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
     T ix0 = IXC(MA, pm - 2), ix1 = IXC(MA, pm - 1);
     T ix2 = IXC(MA, pm);
     int nf = face4<T, NC, MA, UNI>(qm2, qm1, q[0], q[1], ix0, ix1, ix2, HHI(MA, pm - 1),
-                                   HLO(MA, pm), T(0.5) * (tau_prev + tau_m), chat,
+                                   HLO(MA, pm), T(0.5) * (tau_prev + tau_m), fchat,
                                    Ops<T>::rcp(q[0][0]), flux2<T, NC>(q[0]), zlo, sc);
     if (upd_col) cnt.fix += nf >> 1;  // the lower march state of cell m0
     // upper face state of cell m0 (fixed), kept for the face m0 + 1/2
@@ -459,7 +463,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       T fx[4];
       int nf = face4<T, NC, 0, UNI>(um2, um1, u0, up1, IXC(0, px - 2),
                                IXC(0, px - 1), IXC(0, px),
-                               HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx,
+                               HHI(0, px - 1), HLO(0, px), tau, fchat, inv_own, n2_own, fx,
                                sc);
       // fixed states of updated cells: the lower one of this cell, the upper
       // one of the cell to the left
@@ -483,7 +487,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       T fy[4];
       int nf = face4<T, NC, 1, UNI>(um2, um1, u0, up1, IXC(1, py - 2),
                                IXC(1, py - 1), IXC(1, py),
-                               HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy,
+                               HHI(1, py - 1), HLO(1, py), tau, fchat, inv_own, n2_own, fy,
                                sc);
       if (upd_col) cnt.fix += nf >> 1;
       if (ty >= 1 && cy - 1 < Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0]) cnt.fix += nf & 1;
@@ -515,7 +519,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       n2_n = flux2<T, NC>(q[1]);
       int nf = fix_face_s<T, NC>(sc, loN, q[1], n2_n, inv_n);
       int nf2 = fix_face_s<T, NC>(sc, hiN, q[1], n2_n, inv_n);
-      riemann_s<T, NC, MA>(sc, hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      riemann_s<T, NC, MA>(sc, hiS, loN, fchat, T(0.5) * (tau_m + tau_n), zhi);
       // hiN belongs to the face m + 3/2, computed here only if m + 1 < m1
       if (upd_col && m + 1 < m1) cnt.fix += nf + nf2;  // the march states of cell m + 1
     }
@@ -587,7 +591,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       // cell's own physical flux
       if constexpr (GEOM == kSph && NDIM == 1) {
         T fl[4] = {0, 0, 0, 0}, lm, lp;
-        state_flux<T, NC, 1>(u, chat, fl, lm, lp);
+        state_flux<T, NC, 1>(u, fchat, fl, lm, lp);
         T alo = met0 * ALO(1, 0), ahi = met0 * AHI(1, 0);
 #pragma unroll
         for (int v = 0; v < NV; ++v) dU[v] -= (ahi - alo) * fl[v];
@@ -602,17 +606,17 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
         pressure<T, NC>(u, pa, pb);
         if constexpr (GEOM == kCyl) {
           T Fp = NC >= 2 ? u[2] : T(0);
-          dU[1] += chat * met0 * (pa + pb * Fp * Fp);
+          dU[1] += fchat * met0 * (pa + pb * Fp * Fp);
         } else {
           T Ft = NC >= 2 ? u[2] : T(0), Fp = NC >= 3 ? u[3] : T(0);
           T Ptt = pa + pb * Ft * Ft, Ppp = pa + pb * Fp * Fp, Prt = pb * u[1] * Ft;
-          dU[1] += chat * met0 * (Ptt + Ppp);
-          if (NC >= 2) dU[2] += chat * met0 * (tabv(G, 1, TAB_MET, p1) * Ppp - Prt);
+          dU[1] += fchat * met0 * (Ptt + Ppp);
+          if (NC >= 2) dU[2] += fchat * met0 * (tabv(G, 1, TAB_MET, p1) * Ppp - Prt);
         }
       }
       T Us[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+      for (int v = 0; v < 4; ++v) Us[v] = u[v] + dtf * dU[v];
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
         rare_add(RARE_EFLOOR);

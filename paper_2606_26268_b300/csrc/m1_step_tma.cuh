@@ -91,7 +91,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   const long long ms = Dm.sz;
   const bool in_col = cx < Dm.n[0] && cy < Dm.n[1];
   const bool upd_col = in_col && tx <= TX - 2 && ty <= TY - 2;
-  const T chat = a.chat;
+  // The face fluxes and signal speeds are formed in units of chat (the
+  // flux functions take chat = 1) and the divergence is scaled by dt chat.
+  const T dtc = T(a.dt) * T(a.chat);
   const int own = (ty + 2) * BX + tx + 2 + xo;  // own cell inside a box
 
   auto IXC = [&](int d, int ip) -> T { return UNI ? T(1) : tabv(G, d, TAB_IDXC, ip); };
@@ -160,7 +162,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     n2_own = flux2<T, NC>(q[0]);
     int nf = face4<T, NC, 2, UNI>(qm2, qm1, q[0], q[1], IXC(2, pm - 2), IXC(2, pm - 1),
                                   IXC(2, pm), HHI(2, pm - 1), HLO(2, pm),
-                                  T(0.5) * (tau_prev + tau_m), chat, inv_own, n2_own, zlo);
+                                  T(0.5) * (tau_prev + tau_m), T(1), inv_own, n2_own, zlo);
     if (upd_col) cnt.fix += nf >> 1;  // the lower march state of cell m0
     T d1[4], d2[4];
 #pragma unroll
@@ -220,7 +222,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       T tau = T(0.5) * (s_tau[ty + 1][tx] + s_tau[ty + 1][tx + 1]);
       T fx[4];
       int nf = face4<T, NC, 0, UNI>(um2, um1, u0, up1, IXC(0, px - 2), IXC(0, px - 1), IXC(0, px),
-                                    HHI(0, px - 1), HLO(0, px), tau, chat, inv_own, n2_own, fx);
+                                    HHI(0, px - 1), HLO(0, px), tau, T(1), inv_own, n2_own, fx);
       if (upd_col) cnt.fix += nf >> 1;
       if (ty <= TY - 2 && cy < Dm.n[1] && tx >= 1 && cx - 1 < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
@@ -237,7 +239,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       T tau = T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]);
       T fy[4];
       int nf = face4<T, NC, 1, UNI>(um2, um1, u0, up1, IXC(1, py - 2), IXC(1, py - 1), IXC(1, py),
-                                    HHI(1, py - 1), HLO(1, py), tau, chat, inv_own, n2_own, fy);
+                                    HHI(1, py - 1), HLO(1, py), tau, T(1), inv_own, n2_own, fy);
       if (upd_col) cnt.fix += nf >> 1;
       if (ty >= 1 && cy - 1 < Dm.n[1] && tx <= TX - 2 && cx < Dm.n[0]) cnt.fix += nf & 1;
 #pragma unroll
@@ -270,7 +272,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       }
       int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
       int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
-      riemann<T, NC, 2>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      riemann<T, NC, 2>(hiS, loN, T(1), T(0.5) * (tau_m + tau_n), zhi);
       if (upd_col && m + 1 < m1) cnt.fix += nf + nf2;  // the march states of cell m + 1
     }
     __syncthreads();
@@ -296,7 +298,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       const T (&u)[4] = q[0];
       T Us[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+      for (int v = 0; v < 4; ++v) Us[v] = u[v] + dtc * dU[v];
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
         rare_add(RARE_EFLOOR);

@@ -39,9 +39,17 @@ struct Tma2Tile {
   static constexpr int NEXTRA = TX + TY;             // upper tile faces per plane
 };
 
+// Plane rings: E and F of a plane in one of kTma2RingEF slots, rho and e in
+// one of kTma2RingRE slots (rho and e of a plane are needed one plane later
+// than its E and F, and are released one plane earlier).
+constexpr int kTma2RingEF = 4;
+constexpr int kTma2RingRE = 3;
+
 template <int NC, int TX, int TY>
 constexpr size_t tma2_smem_bytes() {
-  return size_t(kTmaRing) * (NC + 3) * Tma2Tile<TX, TY>::BOXP * sizeof(float) + 128;
+  return size_t(kTma2RingEF * (NC + 1) + kTma2RingRE * 2) * Tma2Tile<TX, TY>::BOXP *
+             sizeof(float) +
+         128;
 }
 
 // Lower and upper reconstructed states of cell uc along one direction from
@@ -105,19 +113,22 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   using T = typename P::T;
   using TL = Tma2Tile<TX, TY>;
   constexpr int NDIM = 3;
-  constexpr int NV = 1 + NC, NF = NC + 3, R = kTmaRing;
+  constexpr int NV = 1 + NC, RF = kTma2RingEF, RR = kTma2RingRE;
   constexpr int BX = TL::BX, BY = TL::BY, BOXP = TL::BOXP;
-  constexpr int SLOT = NF * BOXP;
-  constexpr int FR = NC + 1, FE = NC + 2;
+  constexpr int SLOT_EF = NV * BOXP, SLOT_RE = 2 * BOXP;
+  constexpr int FR = NC + 1, FE = NC + 2;  // tensor maps of rho and e
   constexpr int NT = TX * TY;
-  constexpr uint32_t TX_BYTES = uint32_t(NF) * BX * BY * sizeof(float);
+  constexpr uint32_t TX_EF = uint32_t(NV) * BX * BY * sizeof(float);
+  constexpr uint32_t TX_RE = 2u * BX * BY * sizeof(float);
   static_assert(TL::NHALO <= 96 && NT >= 160, "halo states on the last three warps");
   static_assert(TL::NEXTRA <= 64, "upper tile faces on the first two warps");
+  static_assert(NC >= 2, "the upper y faces take the x solver with F_x and F_y exchanged");
 
   extern __shared__ unsigned char s_dyn[];
-  float* const s_ring =
+  float* const s_ef =
       reinterpret_cast<float*>(s_dyn + ((128u - (smem_addr(s_dyn) & 127u)) & 127u));
-  __shared__ __align__(8) unsigned long long s_bar[R];
+  float* const s_re = s_ef + RF * SLOT_EF;
+  __shared__ __align__(8) unsigned long long s_bar[RF + RR];  // E/F slots, then rho/e slots
   __shared__ T s_tau[TY + 2][TX + 2];   // [row + 1][col + 1], rows/cols -1 .. TY/TX
   __shared__ T s_hx[NV][TY][TX + 1];    // upper x state of column c at [c + 1], c = -1 .. TX-1
   __shared__ T s_hy[NV][TY + 1][TX];    // upper y state of row k at [k + 1], k = -1 .. TY-1
@@ -144,6 +155,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   const long long ms = Dm.sz;
   const bool in_col = cx < Dm.n[0] && cy < Dm.n[1];
   const T chat = a.chat;
+  // The face fluxes and signal speeds are formed in units of chat (the
+  // solver called with chat = 1) and the divergence takes dt chat.
+  const T dtc = T(a.dt) * chat;
   const int own = (ty + 2) * BX + tx + 2;
 
   constexpr bool U1 = UNI || UYZ;  // directions 1 and 2 evenly spaced
@@ -153,25 +167,39 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   auto HLO = [&](int d, int ip) -> T { return even(d) ? T(-0.5) : tabv(G, d, TAB_HLO, ip); };
   auto ALO = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_ALO, ip); };
   auto AHI = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_AHI, ip); };
-  auto slot = [&](int j) -> const float* { return s_ring + (j % R) * SLOT; };
-  int jissued = -1;
-  auto issue = [&](int j) {  // thread 0: plane j into its slot
-    jissued = j;
-    unsigned long long* bar = &s_bar[j % R];
-    float* dst = s_ring + (j % R) * SLOT;
-    mbar_arrive_expect_tx(bar, TX_BYTES);
+  // E/F of plane j in slot j % RF; rho/e of plane j >= 1 in slot (j - 1) % RR
+  // (plane 0 is read for its E and F only).
+  auto slot = [&](int j) -> const float* { return s_ef + (j % RF) * SLOT_EF; };
+  auto rslot = [&](int j) -> const float* { return s_re + ((j - 1) % RR) * SLOT_RE; };
+  int ef_issued = -1, re_issued = 0;
+  auto issue_ef = [&](int j) {  // thread 0: E and F of plane j
+    ef_issued = j;
+    unsigned long long* bar = &s_bar[j % RF];
+    float* dst = s_ef + (j % RF) * SLOT_EF;
+    mbar_arrive_expect_tx(bar, TX_EF);
     const int z = m0 + j;  // padded z of plane m0 - 2 + j
 #pragma unroll
-    for (int f = 0; f < NF; ++f) tma_load_3d(dst + f * BOXP, &tm.m[f], x0, y0, z, bar);
+    for (int f = 0; f < NV; ++f) tma_load_3d(dst + f * BOXP, &tm.m[f], x0, y0, z, bar);
+  };
+  auto issue_re = [&](int j) {  // thread 0: rho and e of plane j >= 1
+    re_issued = j;
+    unsigned long long* bar = &s_bar[RF + (j - 1) % RR];
+    float* dst = s_re + ((j - 1) % RR) * SLOT_RE;
+    mbar_arrive_expect_tx(bar, TX_RE);
+    const int z = m0 + j;
+    tma_load_3d(dst, &tm.m[FR], x0, y0, z, bar);
+    tma_load_3d(dst + BOXP, &tm.m[FE], x0, y0, z, bar);
   };
   bool ok = true;
-  auto wait = [&](int j) {
-    const uint32_t par = uint32_t((j / R) & 1);
-    if (!(a.wait_polls ? mbar_test(&s_bar[j % R], par, a.wait_polls)
-                       : mbar_wait(&s_bar[j % R], par, kWaitLimit))) {
+  auto wait_bar = [&](unsigned long long* bar, uint32_t par) {
+    if (!(a.wait_polls ? mbar_test(bar, par, a.wait_polls) : mbar_wait(bar, par, kWaitLimit))) {
       ok = false;
       s_abort = 1;
     }
+  };
+  auto wait = [&](int j) { wait_bar(&s_bar[j % RF], uint32_t((j / RF) & 1)); };
+  auto wait_re = [&](int j) {
+    wait_bar(&s_bar[RF + (j - 1) % RR], uint32_t(((j - 1) / RR) & 1));
   };
   auto state_at = [&](const float* sl, int idx, T (&u)[4]) {
     u[0] = sl[idx];
@@ -180,14 +208,16 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   };
 
   if (tid == 0) {
-    for (int s = 0; s < R; ++s) mbar_init(&s_bar[s], 1);
+    for (int s = 0; s < RF + RR; ++s) mbar_init(&s_bar[s], 1);
     mbar_fence_init();
     s_abort = 0;
   }
   counters_reset(s_red, tid);
   __syncthreads();
-  if (tid == 0)
-    for (int j = 0; j < R && j <= jlast; ++j) issue(j);
+  if (tid == 0) {
+    for (int j = 0; j < RF && j <= jlast; ++j) issue_ef(j);
+    for (int j = 1; j <= RR && j <= jlast - 1; ++j) issue_re(j);
+  }
 
   Counters cnt;
   T q[3][4], hiS[4], zlo[4], zhi[4];
@@ -197,6 +227,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
   // prologue: planes m0-2 .. m0+1 (j = 0..3) for the face m0 - 1/2
   for (int j = 0; j < 4; ++j) wait(j);
+  wait_re(1);
+  wait_re(2);
   {
     T qm2[4], qm1[4];
     state_at(slot(0), own, qm2);
@@ -204,17 +236,16 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     state_at(slot(2), own, q[0]);
     state_at(slot(3), own, q[1]);
     T kp, chi;
-    const T tau_prev = cell_tau<P, NDIM, GEOM, UNI>(a, slot(1)[FR * BOXP + own],
-                                                    slot(1)[FE * BOXP + own], px, py, m0 + 1,
-                                                    kp, chi);
-    tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, slot(2)[FR * BOXP + own], slot(2)[FE * BOXP + own],
-                                         px, py, m0 + 2, kp_m, chi_m);
+    const T tau_prev = cell_tau<P, NDIM, GEOM, UNI>(a, rslot(1)[own], rslot(1)[BOXP + own], px,
+                                                    py, m0 + 1, kp, chi);
+    tau_m = cell_tau<P, NDIM, GEOM, UNI>(a, rslot(2)[own], rslot(2)[BOXP + own], px, py, m0 + 2,
+                                         kp_m, chi_m);
     const int pm = m0 + 2;
     inv_own = Ops<T>::rcp(q[0][0]);
     n2_own = flux2<T, NC>(q[0]);
     int nf = face4<T, NC, 2, U1>(qm2, qm1, q[0], q[1], IXC(2, pm - 2), IXC(2, pm - 1),
                                   IXC(2, pm), HHI(2, pm - 1), HLO(2, pm),
-                                  T(0.5) * (tau_prev + tau_m), chat, inv_own, n2_own, zlo);
+                                  T(0.5) * (tau_prev + tau_m), T(1), inv_own, n2_own, zlo);
     if (in_col) cnt.fix += nf >> 1;  // the lower z state of cell m0
     T d1[4], d2[4];
 #pragma unroll
@@ -225,6 +256,12 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     plm_state<T, NV>(d1, d2, q[0], HHI(2, pm), hiS);
     int nfh = fix_face<T, NC>(hiS, q[0], n2_own, inv_own);
     if (in_col) cnt.fix += nfh;
+  }
+  // every thread has read plane 0: its slot takes plane RF
+  __syncthreads();
+  if (tid == 0 && RF <= jlast) {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    issue_ef(RF);
   }
 
   // halo face state of this thread (last three warps): item h of
@@ -253,8 +290,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const int j = m - m0 + 2;  // plane m
     const long long ic = base + (long long)(m + 2) * ms;
     wait(j + 2);
+    wait_re(j + 1);
     const float* sl0 = slot(j);
-    const float* sl1 = slot(j + 1);
+    const float* rl0 = rslot(j);
+    const float* rl1 = rslot(j + 1);
     state_at(slot(j + 2), own, q[2]);
     T mom[3] = {0, 0, 0};
     if (in_col) {
@@ -305,16 +344,18 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       }
       T kp, chi;
       s_tau[h_row - 1][h_col - 1] = cell_tau<P, NDIM, GEOM, UNI>(
-          a, sl0[FR * BOXP + h_idx], sl0[FE * BOXP + h_idx], h_px, h_py, m + 2, kp, chi);
+          a, rl0[h_idx], rl0[BOXP + h_idx], h_px, h_py, m + 2, kp, chi);
     }
-    tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, sl1[FR * BOXP + own], sl1[FE * BOXP + own], px, py,
-                                         m + 3, kp_n, chi_n);
+    tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, rl1[own], rl1[BOXP + own], px, py, m + 3, kp_n,
+                                         chi_n);
     __syncthreads();
     if (s_abort) break;
-    // plane j - 2 (= m - 2) was last read in iteration m - 2: its slot is free
-    if (tid == 0 && j + 3 <= jlast) {
+    // plane j - 1 was last read in iteration m - 1 (or the prologue): its
+    // slots take the E/F of plane j + 3 and the rho/e of plane j + 2
+    if (tid == 0 && (j + 3 <= jlast || j + 2 <= jlast - 1)) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      issue(j + 3);
+      if (j + 3 <= jlast) issue_ef(j + 3);
+      if (j + 2 <= jlast - 1) issue_re(j + 2);
     }
 
     // --- phase 2: HLL fluxes of the lower x and y faces (and upper tile faces)
@@ -322,36 +363,54 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       T uL[4] = {0, 0, 0, 0}, f[4];
 #pragma unroll
       for (int v = 0; v < NV; ++v) uL[v] = s_hx[v][ty][tx];
-      riemann<T, NC, 0>(uL, lox, chat, T(0.5) * (s_tau[ty + 1][tx] + s_tau[ty + 1][tx + 1]), f);
+      riemann<T, NC, 0>(uL, lox, T(1), T(0.5) * (s_tau[ty + 1][tx] + s_tau[ty + 1][tx + 1]), f);
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = f[v];
 #pragma unroll
       for (int v = 0; v < NV; ++v) uL[v] = s_hy[v][ty][tx];
-      riemann<T, NC, 1>(uL, loy, chat, T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]), f);
+      riemann<T, NC, 1>(uL, loy, T(1), T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]), f);
 #pragma unroll
       for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = f[v];
     }
     if (has_e) {
+      // x faces (rows e < TY) and y faces (columns e - TY) share one call of
+      // the x solver: a y face enters with F_x and F_y exchanged, and its
+      // flux leaves with them exchanged back, so a warp holding both kinds
+      // does not run the solver twice
       T uL[4] = {0, 0, 0, 0}, uR[4] = {0, 0, 0, 0}, f[4];
+      const int c = e - TY;
+      T tau_e;
       if (e_x) {
 #pragma unroll
         for (int v = 0; v < NV; ++v) {
           uL[v] = s_hx[v][e][TX];
           uR[v] = s_lx[v][e];
         }
-        riemann<T, NC, 0>(uL, uR, chat, T(0.5) * (s_tau[e + 1][TX] + s_tau[e + 1][TX + 1]), f);
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s_fx[v][e][TX] = f[v];
+        tau_e = T(0.5) * (s_tau[e + 1][TX] + s_tau[e + 1][TX + 1]);
       } else {
-        const int c = e - TY;
+        uL[0] = s_hy[0][TY][c];
+        uR[0] = s_ly[0][c];
+        uL[1] = s_hy[2][TY][c];
+        uR[1] = s_ly[2][c];
+        uL[2] = s_hy[1][TY][c];
+        uR[2] = s_ly[1][c];
 #pragma unroll
-        for (int v = 0; v < NV; ++v) {
+        for (int v = 3; v < NV; ++v) {
           uL[v] = s_hy[v][TY][c];
           uR[v] = s_ly[v][c];
         }
-        riemann<T, NC, 1>(uL, uR, chat, T(0.5) * (s_tau[TY][c + 1] + s_tau[TY + 1][c + 1]), f);
+        tau_e = T(0.5) * (s_tau[TY][c + 1] + s_tau[TY + 1][c + 1]);
+      }
+      riemann<T, NC, 0>(uL, uR, T(1), tau_e, f);
+      if (e_x) {
 #pragma unroll
-        for (int v = 0; v < NV; ++v) s_fy[v][TY][c] = f[v];
+        for (int v = 0; v < NV; ++v) s_fx[v][e][TX] = f[v];
+      } else {
+        s_fy[0][TY][c] = f[0];
+        s_fy[1][TY][c] = f[2];
+        s_fy[2][TY][c] = f[1];
+#pragma unroll
+        for (int v = 3; v < NV; ++v) s_fy[v][TY][c] = f[v];
       }
     }
     // march face m + 1/2 from the column registers
@@ -376,7 +435,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       }
       int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
       int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
-      riemann<T, NC, 2>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      riemann<T, NC, 2>(hiS, loN, T(1), T(0.5) * (tau_m + tau_n), zhi);
       if (in_col && m + 1 < m1) cnt.fix += nf + nf2;  // the z states of cell m + 1
     }
     __syncthreads();
@@ -390,7 +449,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         const float2 my = make_float2(-AHI(1, py), -AHI(1, py)), py_ = make_float2(ALO(1, py), ALO(1, py));
         const float2 mz = make_float2(-AHI(2, m + 2), -AHI(2, m + 2));
         const float2 pz = make_float2(ALO(2, m + 2), ALO(2, m + 2));
-        const float2 dt2 = make_float2(a.dt, a.dt);
+        const float2 dt2 = make_float2(dtc, dtc);
 #pragma unroll
         for (int h = 0; h < 4; h += 2) {
           float2 d = f2_mul(mx, make_float2(s_fx[h][ty][tx + 1], s_fx[h + 1][ty][tx + 1]));
@@ -448,22 +507,22 @@ __global__ void __launch_bounds__(TX * TY, MINB)
           T pa, pb;
           pressure<T, NC>(u, pa, pb);
           if constexpr (GEOM == kCyl) {
-            dU[1] += chat * met0 * (pa + pb * u[2] * u[2]);
+            dU[1] += met0 * (pa + pb * u[2] * u[2]);
           } else {
             const T Ft = u[2], Fp = u[3];
             const T Ptt = pa + pb * Ft * Ft, Ppp = pa + pb * Fp * Fp, Prt = pb * u[1] * Ft;
-            dU[1] += chat * met0 * (Ptt + Ppp);
-            dU[2] += chat * met0 * (tabv(G, 1, TAB_MET, py) * Ppp - Prt);
+            dU[1] += met0 * (Ptt + Ppp);
+            dU[2] += met0 * (tabv(G, 1, TAB_MET, py) * Ppp - Prt);
           }
         }
 #pragma unroll
-        for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+        for (int v = 0; v < 4; ++v) Us[v] = u[v] + dtc * dU[v];
       }
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
         rare_add(RARE_EFLOOR);
       }
-      const S rho_m = sl0[FR * BOXP + own], e_m = sl0[FE * BOXP + own];
+      const S rho_m = rl0[own], e_m = rl0[BOXP + own];
       const int ci[3] = {cx, cy, m};
       bool queued = false;
       CoupleOut co;
@@ -514,8 +573,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   if (s_abort && tid == 0) {
     // let the copies still in flight land (bounded) before the CTA exits
     // (the last phase issued on each slot: the earlier ones completed first)
-    for (int j = jissued - R + 1 > 0 ? jissued - R + 1 : 0; j <= jissued; ++j)
-      mbar_wait(&s_bar[j % R], uint32_t((j / R) & 1), kWaitLimit);
+    for (int j = ef_issued - RF + 1 > 0 ? ef_issued - RF + 1 : 0; j <= ef_issued; ++j)
+      mbar_wait(&s_bar[j % RF], uint32_t((j / RF) & 1), kWaitLimit);
+    for (int j = re_issued - RR + 1 > 1 ? re_issued - RR + 1 : 1; j <= re_issued; ++j)
+      mbar_wait(&s_bar[RF + (j - 1) % RR], uint32_t(((j - 1) / RR) & 1), kWaitLimit);
   }
   counters_flush<P>(a, cnt, s_red, tid);
 }

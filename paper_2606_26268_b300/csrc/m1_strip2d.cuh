@@ -40,7 +40,11 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
   const long long ms = Dm.sy;
   const int gm = Dm.g[1];
   const bool upd_col = cx < Dm.n[0] && k <= 30;
-  const T chat = a.chat;
+  // In the split precision the face fluxes and signal speeds are formed in
+  // units of chat (the flux functions take fchat = 1) and the divergence
+  // is scaled by dt chat; in FP64 they carry chat as the oracle does.
+  const T fchat = P::kSplit ? T(1) : T(a.chat);
+  const T dtf = P::kSplit ? T(a.dt) * T(a.chat) : T(a.dt);
 
   auto IXC = [&](int d, int ip) -> T { return UNI ? T(1) : tabv(G, d, TAB_IDXC, ip); };
   auto HHI = [&](int d, int ip) -> T { return UNI ? T(0.5) : tabv(G, d, TAB_HHI, ip); };
@@ -82,7 +86,7 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
     n2_own = flux2<T, NC>(q[0]);
     const int nf = face4<T, NC, MA, UNI>(qm2, qm1, q[0], q[1], IXC(MA, pm - 2), ix1, ix2,
                                          HHI(MA, pm - 1), HLO(MA, pm),
-                                         T(0.5) * (tau_prev + tau_m), chat, inv_own, n2_own, zlo);
+                                         T(0.5) * (tau_prev + tau_m), fchat, inv_own, n2_own, zlo);
     if (upd_col) cnt.fix += nf >> 1;  // the lower march state of cell m0
     T d1[4], d2[4];
 #pragma unroll
@@ -163,7 +167,7 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
     {
       const T tau = T(0.5) * ((k >= 1 ? tU : tH) + tau_m);
       const int nf = face4<T, NC, 0, UNI>(um2, um1, q[0], up1, IXC(0, px - 2), IXC(0, px - 1),
-                                          IXC(0, px), HHI(0, px - 1), HLO(0, px), tau, chat,
+                                          IXC(0, px), HHI(0, px - 1), HLO(0, px), tau, fchat,
                                           inv_own, n2_own, fx);
       // fixed states of updated cells: the lower one of this cell, the upper
       // one of the cell to the left
@@ -196,7 +200,7 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
       }
       const int nf = fix_face<T, NC>(loN, q[1], n2_n, inv_n);
       const int nf2 = fix_face<T, NC>(hiN, q[1], n2_n, inv_n);
-      riemann<T, NC, MA>(hiS, loN, chat, T(0.5) * (tau_m + tau_n), zhi);
+      riemann<T, NC, MA>(hiS, loN, fchat, T(0.5) * (tau_m + tau_n), zhi);
       if (upd_col && m + 1 < m1) cnt.fix += nf + nf2;  // the march states of cell m + 1
     }
 
@@ -216,7 +220,7 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
       const T (&u)[4] = q[0];
       T Us[4];
 #pragma unroll
-      for (int v = 0; v < 4; ++v) Us[v] = u[v] + a.dt * dU[v];
+      for (int v = 0; v < 4; ++v) Us[v] = u[v] + dtf * dU[v];
       if (Us[0] < a.efloor) {
         Us[0] = a.efloor;
         rare_add(RARE_EFLOOR);

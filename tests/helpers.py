@@ -71,14 +71,59 @@ def errors(g, o, ncomp, chat, ratio=1.0, nsteps=1):
     return out
 
 
-def assert_shapes_agree(out, ref, variant):
-    """Two launch shapes of the split form after a few steps: the kernels
-    sum the flux divergence in different orders (the TMA-staged one on packed
-    FP32 pairs), so they agree to FP32 rounding, amplified in a few cells by
-    the discontinuous f-fix and limiter switches: normwise within 3e-7, per
-    cell within 1e-5."""
+def _stencil_scale(ref, shape):
+    """Largest |value| in each cell's 5-cell stencil, for one or more fields
+    of the grid `shape` (n0, n1, n2), x fastest, stored one after the other."""
+    from scipy.ndimage import maximum_filter
+    grid = tuple(int(k) for k in shape)[::-1]
+    a = np.abs(np.asarray(ref, dtype=np.float64)).reshape((-1,) + grid)
+    return np.stack([maximum_filter(f, size=5, mode="nearest") for f in a]).ravel()
+
+
+def _agreement(out, ref, shape):
     out = np.asarray(out, dtype=np.float64)
     ref = np.asarray(ref, dtype=np.float64)
     norm = np.linalg.norm(out - ref) / np.linalg.norm(ref)
-    cell = np.max(np.abs(out - ref) / np.abs(ref))
-    assert norm <= 3e-7 and cell <= 1e-5, (variant, norm, cell)
+    cell = np.max(np.abs(out - ref) / _stencil_scale(ref, shape))
+    return norm, cell
+
+
+def oracle_spread(p, nsteps, dt, seeds=(0, 1)):
+    """The problem's own response to rounding: the largest change of the FP64
+    oracle's E after `nsteps` steps when its E and F inputs are perturbed by
+    6e-8 relative (half a unit in the last place of FP32), normwise and per
+    cell against the stencil's largest E, over the given seeds."""
+    o = oracle.Oracle(p)
+    o.step(nsteps, dt)
+    E0 = o.E.copy()
+    norm = cell = 0.0
+    for k in seeds:
+        q = p.copy()
+        rng = np.random.default_rng(k)
+        q.E = p.E * (1.0 + 6e-8 * rng.standard_normal(p.N))
+        q.F = p.F * (1.0 + 6e-8 * rng.standard_normal(np.shape(p.F)))
+        o2 = oracle.Oracle(q)
+        o2.step(nsteps, dt)
+        n, c = _agreement(o2.E, E0, p.n)
+        norm, cell = max(norm, n), max(cell, c)
+    return norm, cell
+
+
+def assert_shapes_agree(out, ref, variant, shape, spread=(0.0, 0.0)):
+    """Two launch shapes of the split form after a few steps.  The kernels
+    sum the flux divergence in different orders (the TMA-staged one on packed
+    FP32 pairs), so they agree to FP32 rounding, amplified in a few cells by
+    the discontinuous f-fix and limiter switches: normwise within 3e-7, and
+    per cell within 1e-5 of the largest value in the cell's 5-cell stencil,
+    or within the problem's own response to rounding (`spread`, normwise and
+    per cell, from oracle_spread) where that is larger.  The FP32 rounding of
+    a flux divergence scales with the largest flux it sums, hence with the
+    stencil's largest E, not with the cell's own: where E varies by 10^3
+    between neighbours the cell's relative rounding is 10^3 times FP32's.
+    `out` and `ref` hold one or more fields of the grid `shape` (n0, n1, n2),
+    x fastest, one after the other."""
+    ncell = int(np.prod(shape))
+    assert np.size(out) % ncell == 0
+    norm, cell = _agreement(out, ref, shape)
+    assert norm <= max(3e-7, spread[0]) and cell <= max(1e-5, spread[1]), \
+        (variant, norm, cell, spread)

@@ -187,8 +187,8 @@ def test_gas_on_every_launch_shape():
     r0 = R.from_problem(p, "split")
     nvar = r0.get_launch()[2]
     r0.close()
-    assert nvar == 10
-    for v in (0, 2, 5, 7, 9):
+    assert nvar == 13
+    for v in (0, 2, 5, 7, 9, 10, 11, 12):
         r = R.from_problem(p, "split")
         r.set_launch(v, 0)
         r.step(3, dt)
@@ -199,7 +199,7 @@ def test_gas_on_every_launch_shape():
         if ref is None:
             ref = out
         else:
-            assert_shapes_agree(out, ref, v)
+            assert_shapes_agree(out, ref, v, p.n)
 
 
 def test_rhd_pulse_workload_fp64_and_split_match_oracle():

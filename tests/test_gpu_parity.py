@@ -10,7 +10,7 @@ import numpy as np
 import pytest
 
 import workloads as W
-from helpers import assert_shapes_agree, errors, rounded, run_gpu, run_oracle
+from helpers import assert_shapes_agree, errors, oracle_spread, rounded, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
 
@@ -255,7 +255,8 @@ def _curvilinear_case(which):
 def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
     """Split 3D cylindrical and spherical grids on every offered shape (the
     register-tiled one, the TMA-staged non-overlapping 32x8 tiles at 2 and 3
-    CTAs/SM and 16x16 at 3) and two march lengths: the shapes agree to FP32
+    CTAs/SM, 16x16 at 3 and 4, and the one-barrier-per-plane 16x16 at 3) and two
+    march lengths: the shapes agree to FP32
     rounding and each is within 1e-5 of the FP64 oracle normwise after 5
     steps."""
     import paper_2606_26268_b300 as R
@@ -264,7 +265,7 @@ def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
     nvar = r0.get_launch()[2]
     dt = r0.dt()
     r0.close()
-    assert nvar == 4
+    assert nvar == 6
     o = run_oracle(p, 5, dt=dt)
     nE, ne = np.linalg.norm(o["E"]), np.linalg.norm(o["e"])
     ref = None
@@ -280,7 +281,7 @@ def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
             if ref is None:
                 ref = out
             else:
-                assert_shapes_agree(out, ref, (v, chunk))
+                assert_shapes_agree(out, ref, (v, chunk), p.n)
             err = (np.linalg.norm(g["E"] - o["E"]) / nE,
                    np.linalg.norm(g["F"][:p.ncomp] - o["F"][:p.ncomp]) / nE,
                    np.linalg.norm(g["e"] - o["e"]) / ne)
@@ -297,9 +298,16 @@ def test_launch_shapes_agree_and_tuning_keeps_the_state(precision, ndim, n):
     ref = None
     r0 = R.from_problem(p, precision)
     nvar = r0.get_launch()[2]
+    r0_dt = r0.dt()
     r0.close()
     assert nvar >= 3
     tol = 1e-13 if precision == "fp64" else 2e-6
+    spread = (0.0, 0.0)
+    if precision == "split":
+        # random flux directions cell by cell: f-fix and limiter switches
+        # everywhere, so the problem amplifies rounding (about 100-fold in
+        # three steps); the shapes agree within that
+        spread = oracle_spread(rounded(p, np.float32), 3, r0_dt)
     for v in range(nvar):
         for chunk in (0, 7, 16):
             r = R.from_problem(p, precision)
@@ -312,7 +320,7 @@ def test_launch_shapes_agree_and_tuning_keeps_the_state(precision, ndim, n):
             elif precision == "fp64":
                 np.testing.assert_allclose(out, ref, rtol=tol, atol=0)
             else:
-                assert_shapes_agree(out, ref, (v, chunk))
+                assert_shapes_agree(out, ref, (v, chunk), p.n, spread)
     r = R.from_problem(p, precision)
     before = r.read("E").copy()
     st0 = r.stats()
@@ -473,7 +481,7 @@ def test_rk2_split_and_launch_shapes():
     q.integrator = "rk2"
     q.implicit_mode = "newton"
     ref = None
-    for v in (0, 5, 7, 9):
+    for v in (0, 5, 7, 9, 10, 11, 12):
         r = R.from_problem(q, "split", newton_rtol=1e-7)
         r.set_launch(v, 0)
         r.step(3)
@@ -483,7 +491,7 @@ def test_rk2_split_and_launch_shapes():
         if ref is None:
             ref = E
         else:
-            assert_shapes_agree(E, ref, v)
+            assert_shapes_agree(E, ref, v, q.n)
 
 
 # ---------------------------------------------------------------------------
