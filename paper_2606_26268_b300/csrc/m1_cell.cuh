@@ -95,7 +95,7 @@ __device__ __forceinline__ void coupling_features(const CoupleParams& p, float r
 // deposit of Sect. 2.9 when the context has them; the default step kernels,
 // which such contexts do not use, compile both out.
 template <class P, bool GEN = true>
-__device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, long long ic,
+__device__ __forceinline__ CoupleOutT<typename P::T> couple_cell(const StepArgs<P>& a, long long ic,
                                                  typename P::S rho_s, typename P::S e_s,
                                                  typename P::T kp, typename P::T Es, float T0,
                                                  bool once, double T1 = 0.0) {
@@ -121,13 +121,15 @@ __device__ __forceinline__ CoupleOut couple_cell(const StepArgs<P>& a, long long
 
 // Bookkeeping and stores of the cell at padded index ic with unpadded
 // coordinates ci, given its coupling result co.  Us = (E*, F*) after
-// transport (E* already floored).
+// transport (E* already floored).  ghosts = false: the caller knows the cell
+// lies at least two cells from every boundary, so it feeds no ghost copy.
 template <class P, int NDIM, int NC, bool GEN = true>
 __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, const int (&ci)[3],
                                             typename P::T (&Us)[4], typename P::S rho_s,
                                             typename P::S e_s, typename P::T kp,
                                             typename P::T chi, const typename P::T (&mom)[3],
-                                            const CoupleOut& co, Counters& c) {
+                                            const CoupleOutT<typename P::T>& co, Counters& c,
+                                            bool ghosts = true) {
   using S = typename P::S;
   using T = typename P::T;
   const StepDims& Dm = a.dim;
@@ -147,7 +149,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
       unsigned int slot = atomicAdd(a.log_count, 1u);
       if (slot < a.log_cap)
         reinterpret_cast<float4*>(a.log)[slot] =
-            make_float4(x1, x2, float(log(co.Tnew / double(Tn))), glin);
+            make_float4(x1, x2, float(log(double(co.Tnew) / double(Tn))), glin);
     }
   }
   T En = Us[0] + T(co.dE);
@@ -248,6 +250,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
   // ghost copies: wrapped (periodic), edge (outflow), mirrored with the
   // normal components negated (reflective), F only (LTE: E, e held); the
   // FIXED sides hold their boundary state
+  if (!ghosts) return;
 #pragma unroll
   for (int d = 0; d < NDIM; ++d) {
     const int n = Dm.n[d];

@@ -137,11 +137,19 @@ __device__ __forceinline__ bool fix_face(T (&uf)[4], const T (&uc)[4], T nc2, T 
     const T Ef2 = Ef * Ef;
     keep = (nf2 <= Ef2) && (nf2 > (nc2 * (inv_Ec * inv_Ec)) * Ef2);
   }
-  if (!keep) {
-    T r = (sizeof(T) == 8) ? Ef / Ec : Ef * inv_Ec;
-    uf[1] = uc[1] * r;
-    if (NC > 1) uf[2] = uc[2] * r;
-    if (NC > 2) uf[3] = uc[3] * r;
+  if constexpr (sizeof(T) == 8) {
+    if (!keep) {
+      T r = Ef / Ec;
+      uf[1] = uc[1] * r;
+      if (NC > 1) uf[2] = uc[2] * r;
+      if (NC > 2) uf[3] = uc[3] * r;
+    }
+  } else {
+    // selects rather than a branch: lanes of a warp disagree often
+    const T r = Ef * inv_Ec;
+    uf[1] = keep ? uf[1] : uc[1] * r;
+    if (NC > 1) uf[2] = keep ? uf[2] : uc[2] * r;
+    if (NC > 2) uf[3] = keep ? uf[3] : uc[3] * r;
   }
   return !keep;
 }
@@ -443,14 +451,19 @@ struct CoupleParams {
   int a_is_one;  // a_R == 1 (code units): the emission term needs no scaling
 };
 
-struct CoupleOut {
-  double dE;     // E^{n+1} - E*
-  double Tnew;   // T^{n+1} of the solve
+// Result of the coupling of one cell, in the precision of the transport
+// (double for the FP64 form, float for the split form, whose T^{n+1} and
+// E^{n+1} - E* are stored in float).
+template <class R>
+struct CoupleOutT {
+  R dE;          // E^{n+1} - E*
+  R Tnew;        // T^{n+1} of the solve
   int iters;
   int fallback;  // restarted from T^n
   int noconv;
   int conv1;     // single solve only: it already passes the Newton convergence test
 };
+using CoupleOut = CoupleOutT<double>;
 
 // Increments of the 2x2 system of Eq. (implicit_matrix) with T^4 linearised
 // about Tk.  With D = E* - a Tk^4, det = (1 + g_r) C_v + 4 g a Tk^3 and
@@ -558,11 +571,11 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
 // Split precision: the T^4 emission term, the residual E* - a Tk^4 and the
 // Newton numerator are formed in double; det and the final products, whose
 // terms are all positive, in float.
-__device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float rho, float e,
+__device__ __forceinline__ CoupleOutT<float> couple_split(const CoupleParams& p, float rho, float e,
                                                   float kp, float Es, float T0f,
                                                   bool once = false, float sq = 0.f,
                                                   bool absorb = false, float T1f = 0.f) {
-  CoupleOut o{};
+  CoupleOutT<float> o{};
   float Cv = rho * p.f_cvfac;
   float invCv = rcp_approx(Cv);
   float Tf = e * invCv;
@@ -570,8 +583,8 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
   float g = p.f_dtc * kp * rho;
   float c1 = (1.f + gr) * Cv;
   if (absorb) {  // absorption only: E^{n+1} = E* / (1 + g_r)
-    o.dE = double(-Es * gr * rcp_approx(1.f + gr));
-    o.Tnew = double(Tf);
+    o.dE = -Es * gr * rcp_approx(1.f + gr);
+    o.Tnew = Tf;
     o.iters = 1;
     o.conv1 = 1;
     return o;
@@ -593,10 +606,10 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
       dT += (1.f + gr) * h;
       dE += gr * 4.f * aT3 * h;
     }
-    o.Tnew = double(Tf + dT);
-    o.dE = double(dE);
+    o.Tnew = Tf + dT;
+    o.dE = dE;
     o.iters = 1;
-    o.conv1 = fabsf(dT) <= p.f_rtol * float(o.Tnew);
+    o.conv1 = fabsf(dT) <= p.f_rtol * o.Tnew;
     return o;
   }
   double Tn = double(Tf);
@@ -641,9 +654,9 @@ __device__ __forceinline__ CoupleOut couple_split(const CoupleParams& p, float r
     int used = ok ? it : (it > maxit ? maxit : it);
     o.iters += used;
     if (ok || attempt == 1) {
-      o.Tnew = Tnew;
+      o.Tnew = float(Tnew);
       float inner = float(4.0 * aT3 * (double(Cv) * (Tn - Tk) + double(sq)) - double(Cv) * D);
-      o.dE = double(gr * inner * rcp_approx(det));
+      o.dE = gr * inner * rcp_approx(det);
       o.noconv = ok ? 0 : 1;
       return o;
     }

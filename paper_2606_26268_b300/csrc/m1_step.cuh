@@ -626,7 +626,7 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       // it does not already converge go to the queue pass, which iterates
       // (from T^n or the learned guess) without holding back this warp.
       bool queued = false;
-      CoupleOut co;
+      CoupleOutT<T> co;
       if (a.queue_cap) {
         co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;

@@ -306,7 +306,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       const S rho_m = sl0[FR * BOXP + own], e_m = sl0[FE * BOXP + own];
       const int ci[3] = {cx, cy, m};
       bool queued = false;
-      CoupleOut co;
+      CoupleOutT<T> co;
       if (a.queue_cap) {
         co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;

@@ -41,9 +41,11 @@ struct Tma2Tile {
 
 // Plane rings: E and F of a plane in one of kTma2RingEF slots, rho and e in
 // one of kTma2RingRE slots (rho and e of a plane are needed one plane later
-// than its E and F, and are released one plane earlier).
+// than its E and F, and are released one plane earlier).  One mbarrier per
+// E/F slot tracks the E/F of plane k together with the rho/e of plane k - 1,
+// which the same iteration needs first.
 constexpr int kTma2RingEF = 4;
-constexpr int kTma2RingRE = 3;
+constexpr int kTma2RingRE = 4;
 
 template <int NC, int TX, int TY>
 constexpr size_t tma2_smem_bytes() {
@@ -128,7 +130,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   float* const s_ef =
       reinterpret_cast<float*>(s_dyn + ((128u - (smem_addr(s_dyn) & 127u)) & 127u));
   float* const s_re = s_ef + RF * SLOT_EF;
-  __shared__ __align__(8) unsigned long long s_bar[RF + RR];  // E/F slots, then rho/e slots
+  __shared__ __align__(8) unsigned long long s_bar[RF];  // E/F of plane k and rho/e of k - 1
   __shared__ T s_tau[TY + 2][TX + 2];   // [row + 1][col + 1], rows/cols -1 .. TY/TX
   __shared__ T s_hx[NV][TY][TX + 1];    // upper x state of column c at [c + 1], c = -1 .. TX-1
   __shared__ T s_hy[NV][TY + 1][TX];    // upper y state of row k at [k + 1], k = -1 .. TY-1
@@ -154,6 +156,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   const long long base = (long long)min(cx + 2, Dm.pn[0] - 1) + (long long)py * Dm.sy;
   const long long ms = Dm.sz;
   const bool in_col = cx < Dm.n[0] && cy < Dm.n[1];
+  // a column at least two cells from the x and y boundaries feeds ghost
+  // copies only near the z boundaries
+  const bool xy_inner = cx >= 2 && cx < Dm.n[0] - 2 && cy >= 2 && cy < Dm.n[1] - 2;
   const T chat = a.chat;
   // The face fluxes and signal speeds are formed in units of chat (the
   // solver called with chat = 1) and the divergence takes dt chat.
@@ -167,39 +172,35 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   auto HLO = [&](int d, int ip) -> T { return even(d) ? T(-0.5) : tabv(G, d, TAB_HLO, ip); };
   auto ALO = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_ALO, ip); };
   auto AHI = [&](int d, int ip) -> T { return UNI ? a.uni_inv[d] : tabv(G, d, TAB_AHI, ip); };
+  static_assert((RF & (RF - 1)) == 0 && (RR & (RR - 1)) == 0, "power-of-two rings");
   // E/F of plane j in slot j % RF; rho/e of plane j >= 1 in slot (j - 1) % RR
   // (plane 0 is read for its E and F only).
-  auto slot = [&](int j) -> const float* { return s_ef + (j % RF) * SLOT_EF; };
-  auto rslot = [&](int j) -> const float* { return s_re + ((j - 1) % RR) * SLOT_RE; };
-  int ef_issued = -1, re_issued = 0;
-  auto issue_ef = [&](int j) {  // thread 0: E and F of plane j
-    ef_issued = j;
-    unsigned long long* bar = &s_bar[j % RF];
-    float* dst = s_ef + (j % RF) * SLOT_EF;
-    mbar_arrive_expect_tx(bar, TX_EF);
-    const int z = m0 + j;  // padded z of plane m0 - 2 + j
+  auto slot = [&](int j) -> const float* { return s_ef + (j & (RF - 1)) * SLOT_EF; };
+  auto rslot = [&](int j) -> const float* { return s_re + ((j - 1) & (RR - 1)) * SLOT_RE; };
+  int issued = -1;
+  auto issue = [&](int k) {  // thread 0: E/F of plane k and rho/e of plane k - 1 (k >= 2)
+    issued = k;
+    unsigned long long* bar = &s_bar[k & (RF - 1)];
+    float* dst = s_ef + (k & (RF - 1)) * SLOT_EF;
+    mbar_arrive_expect_tx(bar, k >= 2 ? TX_EF + TX_RE : TX_EF);
+    const int z = m0 + k;  // padded z of plane m0 - 2 + k
 #pragma unroll
     for (int f = 0; f < NV; ++f) tma_load_3d(dst + f * BOXP, &tm.m[f], x0, y0, z, bar);
-  };
-  auto issue_re = [&](int j) {  // thread 0: rho and e of plane j >= 1
-    re_issued = j;
-    unsigned long long* bar = &s_bar[RF + (j - 1) % RR];
-    float* dst = s_re + ((j - 1) % RR) * SLOT_RE;
-    mbar_arrive_expect_tx(bar, TX_RE);
-    const int z = m0 + j;
-    tma_load_3d(dst, &tm.m[FR], x0, y0, z, bar);
-    tma_load_3d(dst + BOXP, &tm.m[FE], x0, y0, z, bar);
+    if (k >= 2) {
+      float* rdst = s_re + ((k - 2) & (RR - 1)) * SLOT_RE;
+      tma_load_3d(rdst, &tm.m[FR], x0, y0, z - 1, bar);
+      tma_load_3d(rdst + BOXP, &tm.m[FE], x0, y0, z - 1, bar);
+    }
   };
   bool ok = true;
-  auto wait_bar = [&](unsigned long long* bar, uint32_t par) {
+  // plane k's E/F and plane k - 1's rho/e
+  auto wait = [&](int k) {
+    unsigned long long* bar = &s_bar[k & (RF - 1)];
+    const uint32_t par = uint32_t((k / RF) & 1);
     if (!(a.wait_polls ? mbar_test(bar, par, a.wait_polls) : mbar_wait(bar, par, kWaitLimit))) {
       ok = false;
       s_abort = 1;
     }
-  };
-  auto wait = [&](int j) { wait_bar(&s_bar[j % RF], uint32_t((j / RF) & 1)); };
-  auto wait_re = [&](int j) {
-    wait_bar(&s_bar[RF + (j - 1) % RR], uint32_t(((j - 1) / RR) & 1));
   };
   auto state_at = [&](const float* sl, int idx, T (&u)[4]) {
     u[0] = sl[idx];
@@ -208,16 +209,14 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   };
 
   if (tid == 0) {
-    for (int s = 0; s < RF + RR; ++s) mbar_init(&s_bar[s], 1);
+    for (int s = 0; s < RF; ++s) mbar_init(&s_bar[s], 1);
     mbar_fence_init();
     s_abort = 0;
   }
   counters_reset(s_red, tid);
   __syncthreads();
-  if (tid == 0) {
-    for (int j = 0; j < RF && j <= jlast; ++j) issue_ef(j);
-    for (int j = 1; j <= RR && j <= jlast - 1; ++j) issue_re(j);
-  }
+  if (tid == 0)
+    for (int k = 0; k < RF && k <= jlast; ++k) issue(k);
 
   Counters cnt;
   T q[3][4], hiS[4], zlo[4], zhi[4];
@@ -226,9 +225,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   for (int v = 0; v < 4; ++v) zlo[v] = zhi[v] = hiS[v] = T(0);
 
   // prologue: planes m0-2 .. m0+1 (j = 0..3) for the face m0 - 1/2
-  for (int j = 0; j < 4; ++j) wait(j);
-  wait_re(1);
-  wait_re(2);
+  for (int j = 0; j < 4; ++j) wait(j);  // E/F of planes 0 .. 3, rho/e of 1 and 2
   {
     T qm2[4], qm1[4];
     state_at(slot(0), own, qm2);
@@ -261,7 +258,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   __syncthreads();
   if (tid == 0 && RF <= jlast) {
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    issue_ef(RF);
+    issue(RF);
   }
 
   // halo face state of this thread (last three warps): item h of
@@ -289,8 +286,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   for (int m = m0; m < m1; ++m) {
     const int j = m - m0 + 2;  // plane m
     const long long ic = base + (long long)(m + 2) * ms;
-    wait(j + 2);
-    wait_re(j + 1);
+    wait(j + 2);  // E/F of plane j + 2, rho/e of plane j + 1
     const float* sl0 = slot(j);
     const float* rl0 = rslot(j);
     const float* rl1 = rslot(j + 1);
@@ -350,12 +346,12 @@ __global__ void __launch_bounds__(TX * TY, MINB)
                                          chi_n);
     __syncthreads();
     if (s_abort) break;
-    // plane j - 1 was last read in iteration m - 1 (or the prologue): its
-    // slots take the E/F of plane j + 3 and the rho/e of plane j + 2
-    if (tid == 0 && (j + 3 <= jlast || j + 2 <= jlast - 1)) {
+    // the E/F of plane j - 1 (last read in iteration m - 1 or the prologue)
+    // and the rho/e of plane j - 2 are no longer read: their slots take the
+    // E/F of plane j + 3 and the rho/e of plane j + 2
+    if (tid == 0 && j + 3 <= jlast) {
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-      if (j + 3 <= jlast) issue_ef(j + 3);
-      if (j + 2 <= jlast - 1) issue_re(j + 2);
+      issue(j + 3);
     }
 
     // --- phase 2: HLL fluxes of the lower x and y faces (and upper tile faces)
@@ -525,7 +521,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       const S rho_m = rl0[own], e_m = rl0[BOXP + own];
       const int ci[3] = {cx, cy, m};
       bool queued = false;
-      CoupleOut co;
+      CoupleOutT<T> co;
       if (a.queue_cap) {
         co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;
@@ -552,7 +548,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       } else {
         co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
-      if (!queued) finish_cell<P, NDIM, NC, GEN>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+      if (!queued)
+        finish_cell<P, NDIM, NC, GEN>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt,
+                                      !xy_inner || m < 2 || m >= Dm.n[2] - 2);
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
@@ -573,10 +571,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   if (s_abort && tid == 0) {
     // let the copies still in flight land (bounded) before the CTA exits
     // (the last phase issued on each slot: the earlier ones completed first)
-    for (int j = ef_issued - RF + 1 > 0 ? ef_issued - RF + 1 : 0; j <= ef_issued; ++j)
-      mbar_wait(&s_bar[j % RF], uint32_t((j / RF) & 1), kWaitLimit);
-    for (int j = re_issued - RR + 1 > 1 ? re_issued - RR + 1 : 1; j <= re_issued; ++j)
-      mbar_wait(&s_bar[RF + (j - 1) % RR], uint32_t(((j - 1) / RR) & 1), kWaitLimit);
+    for (int k = issued - RF + 1 > 0 ? issued - RF + 1 : 0; k <= issued; ++k)
+      mbar_wait(&s_bar[k & (RF - 1)], uint32_t((k / RF) & 1), kWaitLimit);
   }
   counters_flush<P>(a, cnt, s_red, tid);
 }

@@ -227,7 +227,7 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
       }
       const int ci[3] = {cx, m, 0};
       bool queued = false;
-      CoupleOut co;
+      CoupleOutT<T> co;
       if (a.queue_cap) {
         co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, true);
         queued = !co.conv1;

@@ -56,7 +56,7 @@ __device__ __forceinline__ void queue_load(const StepArgs<P>& a, long long ic, Q
 template <class P, int NDIM, int NC>
 __device__ __forceinline__ void queue_solve(const StepArgs<P>& a, QueuedCell<P>& c, float T0,
                                             Counters& cnt) {
-  const CoupleOut co =
+  const auto co =
       couple_cell<P>(a, c.ic, c.rho, c.e, c.kp, c.Us[0], T0, false, double(c.T1));
   finish_cell<P, NDIM, NC>(a, c.ic, c.ci, c.Us, c.rho, c.e, c.kp, c.chi, c.mom, co, cnt);
 }

@@ -1367,7 +1367,15 @@ extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, f
       cudaStreamSynchronize(c->stream) != cudaSuccess)
     return RAD_ECUDA;
   std::vector<int> chunks;
-  if (c->ndim == 3) chunks = {8, 16, 32, 64, 128};
+  if (c->ndim == 3) {
+    // and the march length of every march count up to 40: the CTAs of the
+    // last marches, launched last, are the short ones, and the length sets
+    // how much of the GPU the last wave leaves idle
+    chunks = {8, 16, 32, 64, 128};
+    for (int nb = 2; nb <= 40 && nb <= c->n[2]; ++nb) chunks.push_back((c->n[2] + nb - 1) / nb);
+    std::sort(chunks.begin(), chunks.end());
+    chunks.erase(std::unique(chunks.begin(), chunks.end()), chunks.end());
+  }
   else if (c->ndim == 2) chunks = {8, 16, 32, 64, 128, 256};
   else chunks = {1};
   const int nmarch = c->ndim == 3 ? c->n[2] : (c->ndim == 2 ? c->n[1] : 1);

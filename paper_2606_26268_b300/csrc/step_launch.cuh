@@ -5,7 +5,6 @@
 #include "m1_step.cuh"
 #include "m1_step_tma.cuh"
 #include "m1_step_tma2.cuh"
-#include "m1_step_tma3.cuh"
 #include "m1_strip2d.cuh"
 #include "step_launch.h"
 
@@ -78,38 +77,17 @@ cudaError_t launch_tma2(StepArgs<P> a, const void* tma, cudaStream_t s, int chun
   return cudaGetLastError();
 }
 
-template <class P, int NC, bool UNI, int TX, int TY, int MINB, bool GEN, int GEOM = kCart,
-          bool UYZ = false>
-cudaError_t launch_tma3(StepArgs<P> a, const void* tma, cudaStream_t s, int chunk) {
-  if (!tma) return cudaErrorInvalidValue;
-  const int* n = a.dim.n;
-  a.chunk = chunk > 0 ? chunk : 32;
-  if (a.chunk > n[2]) a.chunk = n[2];
-  constexpr size_t smem = tma3_smem_bytes<NC, TX, TY>();
-  auto kern = step_tma3_kernel<P, NC, UNI, TX, TY, MINB, GEN, GEOM, UYZ>;
-  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  if (e != cudaSuccess) return e;
-  TmaMaps maps;
-  std::memcpy(&maps, tma, sizeof(maps));
-  dim3 grid((n[0] + TX - 1) / TX, (n[1] + TY - 1) / TY, (n[2] + a.chunk - 1) / a.chunk);
-  kern<<<grid, dim3(TX, TY), smem, s>>>(a, maps);
-  return cudaGetLastError();
-}
-
 // CTA shapes.  3D: 32x8 (2 or 3 CTAs/SM), 32x16, 64x8, and for the split
 // precision on Cartesian grids the TMA-staged 32x8 with overlapping tiles
 // (variants 4, 5) and with non-overlapping tiles (6, 7), and the TMA-staged
-// non-overlapping 16x16 (8, 9, 10), at 2, 3 or 4 CTAs/SM, and the
-// one-barrier-per-plane kernel with 16x16 and 32x8 tiles at 3 CTAs/SM (11,
-// 12); 2D rows of 128, 256
+// non-overlapping 16x16 (8, 9), each at 2 or 3 CTAs/SM; 2D rows of 128, 256
 // or 64 threads, rows of 64 and 128 threads held to 80 registers (24 warps
 // per SM; variants 3, 4), and in the default form one warp per strip of 31
 // columns with the row exchanged by shuffles (variants 5, 6: 24 or 16
 // strips per SM); 1D: 128.  Curvilinear 3D
 // grids in the split precision: the default shape, the TMA-staged
-// non-overlapping 32x8 at 2 or 3 CTAs/SM (variants 1, 2), 16x16 at 3 or 4
-// (variants 3, 4) and the one-barrier-per-plane 16x16 at 3 (variant 5); other
-// curvilinear
+// non-overlapping 32x8 at 2 or 3 CTAs/SM (variants 1, 2) and 16x16 at 3
+// (variant 3); other curvilinear
 // grids the default shape only.  The general form (GEN: face options,
 // absorption only, irradiation, evolved gas) has the TMA-staged shapes only
 // when it keeps the default face scheme (TMA_OK).  UYZ: directions 1 and 2
@@ -120,8 +98,8 @@ struct Shapes {
   static constexpr bool tma = TMA_OK && P::kSplit && GEOM == kCart && NDIM == 3;
   static constexpr bool tma_curv = TMA_OK && P::kSplit && GEOM != kCart && NDIM == 3;
   static constexpr int count =
-      tma_curv ? 6
-               : ((GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 13 : 4) : (GEN ? 5 : 7)));
+      tma_curv ? 4
+               : ((GEOM != kCart || NDIM == 1) ? 1 : (NDIM == 3 ? (tma ? 10 : 4) : (GEN ? 5 : 7)));
   static cudaError_t launch(const void* vargs, const void* maps, cudaStream_t s, int variant,
                             int chunk) {
     const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
@@ -131,8 +109,6 @@ struct Shapes {
         if (variant == 1) return launch_tma2<P, NC, UNI, 32, 8, 2, GEN, GEOM, UYZ>(a, maps, s, chunk);
         if (variant == 2) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN, GEOM, UYZ>(a, maps, s, chunk);
         if (variant == 3) return launch_tma2<P, NC, UNI, 16, 16, 3, GEN, GEOM, UYZ>(a, maps, s, chunk);
-        if (variant == 4) return launch_tma2<P, NC, UNI, 16, 16, 4, GEN, GEOM, UYZ>(a, maps, s, chunk);
-        if (variant == 5) return launch_tma3<P, NC, UNI, 16, 16, 3, GEN, GEOM, UYZ>(a, maps, s, chunk);
         return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 2, GEN>(a, s, chunk);
       }
       if constexpr (tma) {
@@ -142,9 +118,6 @@ struct Shapes {
         if (variant == 7) return launch_tma2<P, NC, UNI, 32, 8, 3, GEN>(a, maps, s, chunk);
         if (variant == 8) return launch_tma2<P, NC, UNI, 16, 16, 2, GEN>(a, maps, s, chunk);
         if (variant == 9) return launch_tma2<P, NC, UNI, 16, 16, 3, GEN>(a, maps, s, chunk);
-        if (variant == 10) return launch_tma2<P, NC, UNI, 16, 16, 4, GEN>(a, maps, s, chunk);
-        if (variant == 11) return launch_tma3<P, NC, UNI, 16, 16, 3, GEN>(a, maps, s, chunk);
-        if (variant == 12) return launch_tma3<P, NC, UNI, 32, 8, 3, GEN>(a, maps, s, chunk);
       }
       if constexpr (count > 1) {
         if (variant == 1) return launch_shape<P, 3, GEOM, NC, UNI, 32, 8, 3, GEN>(a, s, chunk);
@@ -184,22 +157,18 @@ LaunchEntry entry() {
       e.tma_box[v][0] = Tma2Tile<32, 8>::BX;
       e.tma_box[v][1] = Tma2Tile<32, 8>::BY;
     }
-    for (int v = 8; v < 12; ++v) {
+    for (int v = 8; v < 10; ++v) {
       e.tma_box[v][0] = Tma2Tile<16, 16>::BX;
       e.tma_box[v][1] = Tma2Tile<16, 16>::BY;
     }
-    e.tma_box[12][0] = Tma2Tile<32, 8>::BX;
-    e.tma_box[12][1] = Tma2Tile<32, 8>::BY;
   }
   if constexpr (Sh::tma_curv) {
     for (int v = 1; v < 3; ++v) {
       e.tma_box[v][0] = Tma2Tile<32, 8>::BX;
       e.tma_box[v][1] = Tma2Tile<32, 8>::BY;
     }
-    for (int v = 3; v < 6; ++v) {
-      e.tma_box[v][0] = Tma2Tile<16, 16>::BX;
-      e.tma_box[v][1] = Tma2Tile<16, 16>::BY;
-    }
+    e.tma_box[3][0] = Tma2Tile<16, 16>::BX;
+    e.tma_box[3][1] = Tma2Tile<16, 16>::BY;
   }
   return e;
 }

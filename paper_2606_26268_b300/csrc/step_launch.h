@@ -10,7 +10,7 @@
 typedef cudaError_t (*LaunchFn)(const void* args, const void* tma, cudaStream_t stream,
                                 int variant, int chunk);
 
-constexpr int kMaxVariants = 13;
+constexpr int kMaxVariants = 10;
 
 struct LaunchEntry {
   LaunchFn fn;

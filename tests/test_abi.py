@@ -178,10 +178,10 @@ def test_general_form_offers_the_right_launch_shapes(R):
         L.rad_destroy(c2)
         return nv.value
 
-    assert shapes() == 13
-    assert shapes(hydro=1) == 13
-    assert shapes(irradiation=1) == 13
-    assert shapes(implicit_mode=R.RAD_ABSORPTION_ONLY) == 13
+    assert shapes() == 10
+    assert shapes(hydro=1) == 10
+    assert shapes(irradiation=1) == 10
+    assert shapes(implicit_mode=R.RAD_ABSORPTION_ONLY) == 10
     assert shapes(reconstruction=R.RAD_LIMO3) == 4
     assert shapes(face_fix=R.RAD_FIX_PLUTO, hydro=1) == 4
 
@@ -189,8 +189,7 @@ def test_general_form_offers_the_right_launch_shapes(R):
 @pytest.mark.parametrize("geometry", [1, 2])
 def test_curvilinear_grids_offer_the_tma_staged_shapes_in_the_split_form(R, geometry):
     """Split 3D cylindrical and spherical grids: the register-tiled shape and
-    the TMA-staged non-overlapping 32x8 at 2 and 3 CTAs/SM, 16x16 at 3 and 4, and the
-    one-barrier-per-plane 16x16 at 3; FP64, or a face
+    the TMA-staged non-overlapping 32x8 at 2 and 3 CTAs/SM and 16x16 at 3; FP64, or a face
     option of Sect. 2.5: the register-tiled shape only."""
     L = R.lib()
     g, xs = _grid(R, (16, 16, 16), 3, lo=(1.0, 0.5, 0.0), hi=(2.0, 2.5, 1.0))
@@ -207,8 +206,8 @@ def test_curvilinear_grids_offer_the_tma_staged_shapes_in_the_split_form(R, geom
         L.rad_destroy(c2)
         return nv.value
 
-    assert shapes(precision=R.RAD_FP32_SPLIT) == 6
-    assert shapes(precision=R.RAD_FP32_SPLIT, irradiation=1) == 6
+    assert shapes(precision=R.RAD_FP32_SPLIT) == 4
+    assert shapes(precision=R.RAD_FP32_SPLIT, irradiation=1) == 4
     assert shapes(precision=R.RAD_FP32_SPLIT, reconstruction=R.RAD_LIMO3) == 1
     assert shapes(precision=R.RAD_FP64) == 1
 

@@ -2,10 +2,8 @@
 transport, the coupling of Sect. 2.8 iterated by Newton with rtol 1e-7 from
 the learned guess (trained by the benchmark's own routine on logged solves
 of the 2D non-equilibrium box, gate 1e-2, evaluated on the tensor cores in
-the queue pass), the TMA-staged non-overlapping step kernels (launch
-variants 11 and 12: one barrier per plane, 16 x 16 and 32 x 8 tiles; 9, 7
-and 6: two barriers per plane, 16 x 16 and 32 x 8 tiles; marches of 16 and 8
-cells), on a
+the queue pass), the TMA-staged non-overlapping step kernel (launch variants
+9, 7 and 6: 16 x 16 and 32 x 8 tiles, marches of 19, 16 and 8 cells), on a
 hot-sphere box that spans several full tiles and a ragged tail in x and y
 and several march chunks in z."""
 import argparse
@@ -73,7 +71,7 @@ def _run(s, launch, nsteps, guess=True):
     return out
 
 
-@pytest.mark.parametrize("launch", [(11, 16), (12, 16), (9, 16), (7, 16), (6, 8)])
+@pytest.mark.parametrize("launch", [(9, 19), (9, 16), (7, 16), (6, 8)])
 def test_headline_form_one_step_matches_the_oracle_cell_by_cell(setup, launch):
     """One step: every cell within FP32 rounding of the converged FP64
     coupling (per-cell relative error of E and e below 1e-5; F against E),
@@ -92,7 +90,7 @@ def test_headline_form_one_step_matches_the_oracle_cell_by_cell(setup, launch):
     assert np.max(np.abs(g["e"] - h["e"]) / h["e"]) <= 1e-6
 
 
-@pytest.mark.parametrize("launch", [(11, 16), (9, 16), (7, 16), (6, 8)])
+@pytest.mark.parametrize("launch", [(9, 19), (9, 16), (7, 16), (6, 8)])
 def test_headline_form_100_steps_within_the_problems_own_sensitivity(setup, launch):
     """100 steps: normwise and per-cell errors against the FP64 oracle within
     20x the oracle's own response to 1e-7 input perturbations of E, rho and

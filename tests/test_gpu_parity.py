@@ -255,8 +255,7 @@ def _curvilinear_case(which):
 def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
     """Split 3D cylindrical and spherical grids on every offered shape (the
     register-tiled one, the TMA-staged non-overlapping 32x8 tiles at 2 and 3
-    CTAs/SM, 16x16 at 3 and 4, and the one-barrier-per-plane 16x16 at 3) and two
-    march lengths: the shapes agree to FP32
+    CTAs/SM and 16x16 at 3) and two march lengths: the shapes agree to FP32
     rounding and each is within 1e-5 of the FP64 oracle normwise after 5
     steps."""
     import paper_2606_26268_b300 as R
@@ -265,7 +264,7 @@ def test_curvilinear_tma_staged_shapes_match_the_oracle(which):
     nvar = r0.get_launch()[2]
     dt = r0.dt()
     r0.close()
-    assert nvar == 6
+    assert nvar == 4
     o = run_oracle(p, 5, dt=dt)
     nE, ne = np.linalg.norm(o["E"]), np.linalg.norm(o["e"])
     ref = None
@@ -329,7 +328,11 @@ def test_launch_shapes_agree_and_tuning_keeps_the_state(precision, ndim, n):
     np.testing.assert_array_equal(r.read("E"), before)
     assert r.stats() == st0
     r.step(3)
-    np.testing.assert_allclose(r.read("E").astype(np.float64), ref, rtol=tol, atol=0)
+    out = r.read("E").astype(np.float64)
+    if precision == "fp64":
+        np.testing.assert_allclose(out, ref, rtol=tol, atol=0)
+    else:  # the tuned shape is any of the shapes compared above
+        assert_shapes_agree(out, ref, ("tuned", v, c), p.n, spread)
     r.close()
 
 
@@ -481,7 +484,7 @@ def test_rk2_split_and_launch_shapes():
     q.integrator = "rk2"
     q.implicit_mode = "newton"
     ref = None
-    for v in (0, 5, 7, 9, 10, 11, 12):
+    for v in (0, 5, 7, 9):
         r = R.from_problem(q, "split", newton_rtol=1e-7)
         r.set_launch(v, 0)
         r.step(3)
