@@ -121,10 +121,12 @@ __device__ __forceinline__ CoupleOutT<typename P::T> couple_cell(const StepArgs<
 
 // Bookkeeping and stores of the cell at padded index ic with unpadded
 // coordinates ci, given its coupling result co.  Us = (E*, F*) after
-// transport (E* already floored).  ghosts = false: the caller knows the cell
-// lies at least two cells from every boundary, so it feeds no ghost copy.
-template <class P, int NDIM, int NC, bool GEN = true>
-__device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, const int (&ci)[3],
+// transport (E* already floored); I, the type of ic, may be a 32-bit index
+// where every padded array has fewer than 2^31 cells.  ghosts = false: the
+// caller knows the cell lies at least two cells from every boundary, so it
+// feeds no ghost copy.
+template <class P, int NDIM, int NC, bool GEN = true, class I = long long>
+__device__ __forceinline__ void finish_cell(const StepArgs<P>& a, I ic, const int (&ci)[3],
                                             typename P::T (&Us)[4], typename P::S rho_s,
                                             typename P::S e_s, typename P::T kp,
                                             typename P::T chi, const typename P::T (&mom)[3],
@@ -273,7 +275,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, long long ic, 
       else
         src = lo ? 0 : n - 1;
       if (src != i) continue;
-      const long long ig = ic + (long long)(gpos - i) * stride;
+      const long long ig = (long long)ic + (long long)(gpos - i) * stride;
       if constexpr (GEN) {
         if (a.rho_avg) a.rho_avg[ig] = S(rfin);
         if (gas_held) {

@@ -78,6 +78,16 @@ __device__ __forceinline__ int face_states(const T (&um)[4], const T (&uc)[4], c
   return fix_face<T, NC>(lo, uc, n2c, invc) + fix_face<T, NC>(hi, uc, n2c, invc);
 }
 
+__device__ __forceinline__ float4 f4_of(const float (&u)[4]) {
+  return make_float4(u[0], u[1], u[2], u[3]);
+}
+__device__ __forceinline__ void f4_to(float4 v, float (&u)[4]) {
+  u[0] = v.x;
+  u[1] = v.y;
+  u[2] = v.z;
+  u[3] = v.w;
+}
+
 // One of the two states (the upper if `upper`), for the halo ring.
 template <class T, int NC, bool UNI>
 __device__ __forceinline__ void face_state1(const T (&um)[4], const T (&uc)[4], const T (&up)[4],
@@ -124,7 +134,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   constexpr uint32_t TX_RE = 2u * BX * BY * sizeof(float);
   static_assert(TL::NHALO <= 96 && NT >= 160, "halo states on the last three warps");
   static_assert(TL::NEXTRA <= 64, "upper tile faces on the first two warps");
-  static_assert(NC >= 2, "the upper y faces take the x solver with F_x and F_y exchanged");
+  static_assert(NC == 3, "float4 states; the upper y faces take the x solver with F_x, F_y exchanged");
 
   extern __shared__ unsigned char s_dyn[];
   float* const s_ef =
@@ -132,12 +142,13 @@ __global__ void __launch_bounds__(TX * TY, MINB)
   float* const s_re = s_ef + RF * SLOT_EF;
   __shared__ __align__(8) unsigned long long s_bar[RF];  // E/F of plane k and rho/e of k - 1
   __shared__ T s_tau[TY + 2][TX + 2];   // [row + 1][col + 1], rows/cols -1 .. TY/TX
-  __shared__ T s_hx[NV][TY][TX + 1];    // upper x state of column c at [c + 1], c = -1 .. TX-1
-  __shared__ T s_hy[NV][TY + 1][TX];    // upper y state of row k at [k + 1], k = -1 .. TY-1
-  __shared__ T s_lx[NV][TY];            // lower x state of column TX
-  __shared__ T s_ly[NV][TX];            // lower y state of row TY
-  __shared__ T s_fx[NV][TY][TX + 1];    // x face c - 1/2 at [c], c = 0 .. TX
-  __shared__ T s_fy[NV][TY + 1][TX];    // y face k - 1/2 at [k], k = 0 .. TY
+  // states and fluxes as float4 (E, F0, F1, F2): one shared-memory access each
+  __shared__ float4 s_hx[TY][TX + 1];  // upper x state of column c at [c + 1], c = -1 .. TX-1
+  __shared__ float4 s_hy[TY + 1][TX];  // upper y state of row k at [k + 1], k = -1 .. TY-1
+  __shared__ float4 s_lx[TY];          // lower x state of column TX
+  __shared__ float4 s_ly[TX];          // lower y state of row TY
+  __shared__ float4 s_fx[TY][TX + 1];  // x face c - 1/2 at [c], c = 0 .. TX
+  __shared__ float4 s_fy[TY + 1][TX];  // y face k - 1/2 at [k], k = 0 .. TY
   __shared__ unsigned long long s_red[ST_N];
   __shared__ int s_abort;
 
@@ -285,7 +296,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
   for (int m = m0; m < m1; ++m) {
     const int j = m - m0 + 2;  // plane m
-    const long long ic = base + (long long)(m + 2) * ms;
+    // 32-bit cell index: the TMA-staged shapes run only where a padded array
+    // has fewer than 2^31 cells
+    const unsigned int ic = unsigned(base) + unsigned(m + 2) * unsigned(ms);
     wait(j + 2);  // E/F of plane j + 2, rho/e of plane j + 1
     const float* sl0 = slot(j);
     const float* rl0 = rslot(j);
@@ -309,11 +322,8 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       nf += face_states<T, NC, U1>(um, q[0], up, IXC(1, py - 1), IXC(1, py), HLO(1, py),
                                     HHI(1, py), n2_own, inv_own, loy, hy);
       if (in_col) cnt.fix += nf;
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        s_hx[v][ty][tx + 1] = hx[v];
-        s_hy[v][ty + 1][tx] = hy[v];
-      }
+      s_hx[ty][tx + 1] = f4_of(hx);
+      s_hy[ty + 1][tx] = f4_of(hy);
     }
     s_tau[ty + 1][tx + 1] = tau_m;
     if (has_h) {
@@ -324,19 +334,17 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       const int d = h_x ? 0 : 1;
       face_state1<T, NC, UNI>(um, uc, up, IXC(d, h_p - 1), IXC(d, h_p),
                               h_hi ? HHI(d, h_p) : HLO(d, h_p), h_hi, st);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) {
-        if (h_x) {
-          if (h_hi)
-            s_hx[v][h_rc][0] = st[v];
-          else
-            s_lx[v][h_rc] = st[v];
-        } else {
-          if (h_hi)
-            s_hy[v][0][h_rc] = st[v];
-          else
-            s_ly[v][h_rc] = st[v];
-        }
+      const float4 s4 = f4_of(st);
+      if (h_x) {
+        if (h_hi)
+          s_hx[h_rc][0] = s4;
+        else
+          s_lx[h_rc] = s4;
+      } else {
+        if (h_hi)
+          s_hy[0][h_rc] = s4;
+        else
+          s_ly[h_rc] = s4;
       }
       T kp, chi;
       s_tau[h_row - 1][h_col - 1] = cell_tau<P, NDIM, GEOM, UNI>(
@@ -356,58 +364,41 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
     // --- phase 2: HLL fluxes of the lower x and y faces (and upper tile faces)
     {
-      T uL[4] = {0, 0, 0, 0}, f[4];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) uL[v] = s_hx[v][ty][tx];
+      T uL[4], f[4];
+      f4_to(s_hx[ty][tx], uL);
       riemann<T, NC, 0>(uL, lox, T(1), T(0.5) * (s_tau[ty + 1][tx] + s_tau[ty + 1][tx + 1]), f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) s_fx[v][ty][tx] = f[v];
-#pragma unroll
-      for (int v = 0; v < NV; ++v) uL[v] = s_hy[v][ty][tx];
+      s_fx[ty][tx] = f4_of(f);
+      f4_to(s_hy[ty][tx], uL);
       riemann<T, NC, 1>(uL, loy, T(1), T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]), f);
-#pragma unroll
-      for (int v = 0; v < NV; ++v) s_fy[v][ty][tx] = f[v];
+      s_fy[ty][tx] = f4_of(f);
     }
     if (has_e) {
       // x faces (rows e < TY) and y faces (columns e - TY) share one call of
       // the x solver: a y face enters with F_x and F_y exchanged, and its
       // flux leaves with them exchanged back, so a warp holding both kinds
       // does not run the solver twice
-      T uL[4] = {0, 0, 0, 0}, uR[4] = {0, 0, 0, 0}, f[4];
       const int c = e - TY;
+      float4 l4, r4;
       T tau_e;
       if (e_x) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) {
-          uL[v] = s_hx[v][e][TX];
-          uR[v] = s_lx[v][e];
-        }
+        l4 = s_hx[e][TX];
+        r4 = s_lx[e];
         tau_e = T(0.5) * (s_tau[e + 1][TX] + s_tau[e + 1][TX + 1]);
       } else {
-        uL[0] = s_hy[0][TY][c];
-        uR[0] = s_ly[0][c];
-        uL[1] = s_hy[2][TY][c];
-        uR[1] = s_ly[2][c];
-        uL[2] = s_hy[1][TY][c];
-        uR[2] = s_ly[1][c];
-#pragma unroll
-        for (int v = 3; v < NV; ++v) {
-          uL[v] = s_hy[v][TY][c];
-          uR[v] = s_ly[v][c];
-        }
+        l4 = s_hy[TY][c];
+        r4 = s_ly[c];
+        l4 = make_float4(l4.x, l4.z, l4.y, l4.w);
+        r4 = make_float4(r4.x, r4.z, r4.y, r4.w);
         tau_e = T(0.5) * (s_tau[TY][c + 1] + s_tau[TY + 1][c + 1]);
       }
+      T uL[4], uR[4], f[4];
+      f4_to(l4, uL);
+      f4_to(r4, uR);
       riemann<T, NC, 0>(uL, uR, T(1), tau_e, f);
-      if (e_x) {
-#pragma unroll
-        for (int v = 0; v < NV; ++v) s_fx[v][e][TX] = f[v];
-      } else {
-        s_fy[0][TY][c] = f[0];
-        s_fy[1][TY][c] = f[2];
-        s_fy[2][TY][c] = f[1];
-#pragma unroll
-        for (int v = 3; v < NV; ++v) s_fy[v][TY][c] = f[v];
-      }
+      if (e_x)
+        s_fx[e][TX] = f4_of(f);
+      else
+        s_fy[TY][c] = make_float4(f[0], f[2], f[1], f[3]);
     }
     // march face m + 1/2 from the column registers
     T hiN[4];
@@ -440,6 +431,11 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     if (in_col) {
       const T (&u)[4] = q[0];
       T Us[4];
+      T fxl[4], fxh[4], fyl[4], fyh[4];
+      f4_to(s_fx[ty][tx], fxl);
+      f4_to(s_fx[ty][tx + 1], fxh);
+      f4_to(s_fy[ty][tx], fyl);
+      f4_to(s_fy[ty + 1][tx], fyh);
       if constexpr (GEOM == kCart && NV == 4) {  // flux divergence on packed pairs
         const float2 mx = make_float2(-AHI(0, px), -AHI(0, px)), px_ = make_float2(ALO(0, px), ALO(0, px));
         const float2 my = make_float2(-AHI(1, py), -AHI(1, py)), py_ = make_float2(ALO(1, py), ALO(1, py));
@@ -448,10 +444,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         const float2 dt2 = make_float2(dtc, dtc);
 #pragma unroll
         for (int h = 0; h < 4; h += 2) {
-          float2 d = f2_mul(mx, make_float2(s_fx[h][ty][tx + 1], s_fx[h + 1][ty][tx + 1]));
-          d = f2_fma(px_, make_float2(s_fx[h][ty][tx], s_fx[h + 1][ty][tx]), d);
-          d = f2_fma(my, make_float2(s_fy[h][ty + 1][tx], s_fy[h + 1][ty + 1][tx]), d);
-          d = f2_fma(py_, make_float2(s_fy[h][ty][tx], s_fy[h + 1][ty][tx]), d);
+          float2 d = f2_mul(mx, make_float2(fxh[h], fxh[h + 1]));
+          d = f2_fma(px_, make_float2(fxl[h], fxl[h + 1]), d);
+          d = f2_fma(my, make_float2(fyh[h], fyh[h + 1]), d);
+          d = f2_fma(py_, make_float2(fyl[h], fyl[h + 1]), d);
           d = f2_fma(mz, make_float2(zhi[h], zhi[h + 1]), d);
           d = f2_fma(pz, make_float2(zlo[h], zlo[h + 1]), d);
           const float2 us = f2_fma(dt2, d, make_float2(u[h], u[h + 1]));
@@ -466,10 +462,10 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         {
           const T alo = ALO(0, px), ahi = AHI(0, px);
 #pragma unroll
-          for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fx[v][ty][tx + 1] - alo * s_fx[v][ty][tx];
+          for (int v = 0; v < NV; ++v) dU[v] -= ahi * fxh[v] - alo * fxl[v];
           if constexpr (GEOM != kCart) {
             constexpr int PH = GEOM == kCyl ? 2 : 3;  // the phi component
-            const T fhi = s_fx[PH][ty][tx + 1], flo = s_fx[PH][ty][tx];
+            const T fhi = fxh[PH], flo = fxl[PH];
             dU[PH] += ahi * fhi - alo * flo;
             dU[PH] -= tabv(G, 0, TAB_AMHI, px) * fhi - tabv(G, 0, TAB_AMLO, px) * flo;
           }
@@ -482,9 +478,9 @@ __global__ void __launch_bounds__(TX * TY, MINB)
             ahi *= met0;
           }
 #pragma unroll
-          for (int v = 0; v < NV; ++v) dU[v] -= ahi * s_fy[v][ty + 1][tx] - alo * s_fy[v][ty][tx];
+          for (int v = 0; v < NV; ++v) dU[v] -= ahi * fyh[v] - alo * fyl[v];
           if constexpr (GEOM == kSph) {
-            const T fhi = s_fy[3][ty + 1][tx], flo = s_fy[3][ty][tx];
+            const T fhi = fyh[3], flo = fyl[3];
             dU[3] += ahi * fhi - alo * flo;
             dU[3] -= met0 * (tabv(G, 1, TAB_AMHI, py) * fhi - tabv(G, 1, TAB_AMLO, py) * flo);
           }

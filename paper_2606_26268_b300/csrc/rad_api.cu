@@ -930,6 +930,8 @@ static const void* tma_maps(rad_ctx* c, int variant, int in_buf, int rho_buf = -
   if (variant < 0 || variant >= kMaxVariants) return nullptr;
   const int bx = c->launch.tma_box[variant][0], by = c->launch.tma_box[variant][1];
   if (bx <= 0 || c->esize != 4 || c->ndim != 3 || c->nc != 3 || !c->ws) return nullptr;
+  // the staged kernels index cells with 32 bits
+  if ((long long)c->dims.pn[0] * c->dims.pn[1] * c->dims.pn[2] >= (1ll << 31)) return nullptr;
   for (const TmaSet& t : c->tma)
     if (t.bx == bx && t.by == by) return rho_buf < 0 ? t.maps[in_buf] : t.gas[in_buf][rho_buf];
   EncodeTiledFn enc = encode_tiled();
