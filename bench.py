@@ -36,10 +36,11 @@ UNIT = "cell updates/s"
 # written once; halos, tables and ghost layers excluded)
 BYTES_PER_CELL = {("split", 3): 68, ("fp64", 3): 136, ("split", 2): 52, ("fp64", 2): 104}
 PRECISION_DETAIL = {
-    "split": "FP32 storage and transport; in the coupling the emission term a T^4, the residual "
-             "E* - a T^4 and the Newton numerator in FP64, the determinant, its reciprocal and "
-             "the increments of T and E in FP32; learned guess: hidden layers bf16 x bf16 -> FP32 "
-             "on the tensor cores",
+    "split": "FP32 storage and transport; in the coupling the residual E* - a T^4 of the single "
+             "solve within one FP32 rounding of exact (compensated FP32 products), a T^4, the "
+             "residual and the numerator of the Newton iterations in FP64, the determinant, its "
+             "reciprocal and the increments of T and E in FP32; learned guess: hidden layers "
+             "bf16 x bf16 -> FP32 on the tensor cores",
     "fp64": "FP64 throughout"}
 
 

@@ -76,8 +76,11 @@ typedef enum {
 } rad_bc;
 typedef enum { RAD_OPAC_CONST = 0, RAD_OPAC_POWERLAW = 1, RAD_OPAC_TABLE = 2 } rad_opac_kind;
 /* Precision.  RAD_FP32_SPLIT stores and transports in FP32.  In the
- * coupling it forms the emission term a T^4 and the residual E* - a T^4 in
- * FP64 (and, when iterating, the numerator of the Newton update); the other
+ * coupling it forms the residual E* - a T^4 of the single linearised solve
+ * to within one FP32 rounding of its exact value (compensated FP32: T^2 and
+ * T^4 carried with their exact FMA remainders, a_R as a pair of floats), as
+ * an FP64 evaluation rounded to FP32 would; when iterating (Newton), a T^4,
+ * the residual and the numerator of the update are FP64.  The other
  * products of the linearised solve (a T^3, the determinant and its
  * reciprocal, the increments of T and E) are FP32.  It forms f = |F|/E from
  * E^2 and |F|^2 in FP32, so E (and e_floor) must keep E^2 a normal float

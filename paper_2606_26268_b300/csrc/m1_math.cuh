@@ -2,9 +2,10 @@
 // (device code, sm_103a).  Two precision policies:
 //   Fp64  : storage, transport and coupling in double, IEEE division/sqrt;
 //   Split : float storage and transport (MUFU approximations of rcp, rsqrt,
-//           sqrt, ex2, lg2), the coupling's T^4 term and E - a T^4 residual
-//           in double, the remaining well-conditioned coupling products in
-//           float.
+//           sqrt, ex2, lg2); the coupling's E - a T^4 residual to within one
+//           float rounding (compensated float in the single solve, double in
+//           the Newton iterations), the remaining well-conditioned coupling
+//           products in float.
 #pragma once
 #include <cstdint>
 
@@ -448,6 +449,7 @@ struct CoupleParams {
   int absorb;  // absorption only: E^{n+1} = E* / (1 + g_r), no emission (general form)
   // float copies for the split-precision path
   float f_dtchat, f_dtc, f_cvfac, f_a, f_rtol;
+  float f_a_lo;  // a_R - f_a in float: (f_a, f_a_lo) carries a_R to about 48 bits
   int a_is_one;  // a_R == 1 (code units): the emission term needs no scaling
 };
 
@@ -568,9 +570,10 @@ __device__ __forceinline__ CoupleOut couple_fp64(const CoupleParams& p, double r
   return o;
 }
 
-// Split precision: the T^4 emission term, the residual E* - a Tk^4 and the
-// Newton numerator are formed in double; det and the final products, whose
-// terms are all positive, in float.
+// Split precision: the residual E* - a T^4 of the single solve in
+// compensated float (within one float rounding of exact), the T^4 term, the
+// residual and the numerator of the Newton iterations in double; det and the
+// final products, whose terms are all positive, in float.
 __device__ __forceinline__ CoupleOutT<float> couple_split(const CoupleParams& p, float rho, float e,
                                                   float kp, float Es, float T0f,
                                                   bool once = false, float sq = 0.f,
@@ -590,11 +593,24 @@ __device__ __forceinline__ CoupleOutT<float> couple_split(const CoupleParams& p,
     return o;
   }
   if (!p.newton || once) {
-    // the T^4 emission term and E* - a T^4 in double: T^2 of a float is
-    // exact in double, so this is two roundings from exact
-    double T2 = double(Tf) * double(Tf);
-    double aT2 = p.a_is_one ? T2 : p.a_rad * T2;
-    float D = float(fma(-aT2, T2, double(Es)));
+    // E* - a T^4 without cancellation and without the (slow) FP64 pipe:
+    // T^2 = t2 + t2e and t2^2 = t4 + t4e exactly (the FMA remainders), so
+    // a T^4 = a (t4 + l4) with l4 = t4e + t2e (2 t2 + t2e) to about 2^-48
+    // relative, and with a = f_a + f_a_lo the residual E* - a T^4 comes out
+    // within one float rounding of its exact value, as from an FP64
+    // evaluation rounded to float
+    const float t2 = Tf * Tf;
+    const float t2e = fmaf(Tf, Tf, -t2);
+    const float t4 = t2 * t2;
+    const float l4 = fmaf(t2e, fmaf(2.f, t2, t2e), fmaf(t2, t2, -t4));
+    float D;
+    if (p.a_is_one) {
+      D = (Es - t4) - l4;
+    } else {
+      const float h = p.f_a * t4;
+      const float he = fmaf(p.f_a, t4, -h);
+      D = (Es - h) - fmaf(p.f_a, l4, fmaf(p.f_a_lo, t4, he));
+    }
     float aT3 = p.f_a * Tf * Tf * Tf;
     float det = c1 + 4.f * g * aT3;
     const float rdet = rcp_approx(det);

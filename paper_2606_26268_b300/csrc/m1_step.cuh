@@ -284,6 +284,10 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
   const int gm = MARCH ? Dm.g[MA] : 0;
   const bool in_col = cx < Dm.n[0] && (!TILE_Y || cy < Dm.n[1]);
   const bool upd_col = in_col && tx <= TX - 2 && (!TILE_Y || ty <= TY - 2);
+  // a column at least two cells from the boundaries of its tile directions
+  // feeds ghost copies only near the ends of the march
+  const bool col_inner =
+      cx >= 2 && cx < Dm.n[0] - 2 && (!TILE_Y || (cy >= 2 && cy < Dm.n[1] - 2));
   // In the split precision the face fluxes and signal speeds are formed in
   // units of chat (the flux functions take fchat = 1) and the divergence
   // is scaled by dt chat; in FP64 they carry chat as the oracle does.
@@ -653,7 +657,9 @@ __device__ __forceinline__ void step_tile(const StepArgs<P>& a, int bx, int by, 
       } else {
         co = couple_cell<P, GEN>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
-      if (!queued) finish_cell<P, NDIM, NC, GEN>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+      if (!queued)
+        finish_cell<P, NDIM, NC, GEN>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt,
+                                      !col_inner || (MARCH && (m < 2 || m >= Dm.n[MA] - 2)));
     }
     if constexpr (MARCH) {
 #pragma unroll

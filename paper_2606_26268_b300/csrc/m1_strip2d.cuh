@@ -40,6 +40,9 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
   const long long ms = Dm.sy;
   const int gm = Dm.g[1];
   const bool upd_col = cx < Dm.n[0] && k <= 30;
+  // a column at least two cells from the x boundaries feeds ghost copies
+  // only near the y boundaries
+  const bool x_inner = cx >= 2 && cx < Dm.n[0] - 2;
   // In the split precision the face fluxes and signal speeds are formed in
   // units of chat (the flux functions take fchat = 1) and the divergence
   // is scaled by dt chat; in FP64 they carry chat as the oracle does.
@@ -255,7 +258,8 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
         co = couple_cell<P, false>(a, ic, rho_m, e_m, kp_m, Us[0], 0.f, false);
       }
       if (!queued)
-        finish_cell<P, NDIM, NC, false>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt);
+        finish_cell<P, NDIM, NC, false>(a, ic, ci, Us, rho_m, e_m, kp_m, chi_m, mom, co, cnt,
+                                        !x_inner || m < 2 || m >= Dm.n[1] - 2);
     }
 #pragma unroll
     for (int v = 0; v < 4; ++v) {

@@ -862,6 +862,7 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   cp.f_dtc = float(dt * c->par.c);
   cp.f_cvfac = float(cp.cvfac);
   cp.f_a = float(c->par.a_rad);
+  cp.f_a_lo = float(c->par.a_rad - double(cp.f_a));
   cp.f_rtol = float(c->par.newton_rtol);
   cp.a_is_one = c->par.a_rad == 1.0;
   a.chat = T(c->par.chat);
