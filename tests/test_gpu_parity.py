@@ -216,6 +216,34 @@ def test_split_turbulent_nonequilibrium_box():
     assert err["E"] <= 2e-3, err
 
 
+def test_split_single_solve_residual_near_equilibrium_gas_dominated():
+    """Sect. 2.8 single solve where E* - a T^4 cancels: E = a T^4 (1 + 1e-4 d),
+    the gas holding ~1e6 times the radiation energy, strong absorption (the
+    step moves E by ~1.6e-2), and a radiation constant that no float holds
+    exactly (a_R = 0.7e-6, carried as a float pair by the split form's
+    compensated residual).  With det >= (1 + g_r) C_v an error dD in the
+    residual moves E^{n+1} by at most dD, so the residual is good to float
+    rounding of a T^4 when E per cell stays within FP32 transport rounding
+    of the FP64 oracle: 1e-5 after one step."""
+    p = W.random_smooth("cartesian", (40, 24, 20), 3, seed=2024, bc="periodic", ncomp=3,
+                        fmax=0.1, opacity={"kind": "const", "kappa_p": 3e3, "kappa_r": 1.0,
+                                           "sigma": 0.0})
+    p.a_rad = 0.7e-6
+    d = np.random.default_rng(7).standard_normal(p.N)
+    p.E = p.a_rad * np.asarray(p.T) ** 4 * (1.0 + 1e-4 * d)
+    p.F = np.asarray(p.F) * 1e-6 * np.mean(p.E) / np.mean(np.abs(p.F) + 1e-300)
+    q = rounded(p, np.float32)
+    g = run_gpu(q, 1, "split")
+    o = run_oracle(q, 1, dt=g["dt"])
+    assert g["status"] == 0
+    cv_t = np.asarray(q.rho) * np.asarray(q.T) / (q.mu * (q.gamma_gas - 1.0))
+    assert np.median(cv_t / o["E"]) > 1e5  # gas-dominated, as intended
+    moved = np.median(np.abs(o["E"] - q.E) / q.E)
+    assert moved > 1e-6  # the coupling does move E
+    err = np.max(np.abs(g["E"] - o["E"]) / o["E"])
+    assert err <= 1e-5, (err, moved)
+
+
 def test_split_hot_sphere_within_the_problems_own_sensitivity():
     """The hot-sphere box amplifies perturbations: the FP64 oracle itself moves
     by ~1e-3 (normwise) after 100 steps when its inputs are perturbed by 1e-7.
