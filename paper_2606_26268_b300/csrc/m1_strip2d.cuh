@@ -4,18 +4,43 @@
 // that a row needs no barrier.
 //
 // The arithmetic per cell is that of step_tile (m1_step.cuh) for NDIM = 2:
-// lane k owns column x0 + k and computes the x face x0 + k - 1/2 from the four
-// cells around it (face4); lanes 0..30 update their cell with their own face
-// and the face of the lane to their right, so strips overlap by one column
-// (31 updated columns per strip).  The cells left of the strip (x0 - 2,
-// x0 - 1) and right of it (x0 + 32) are loaded by lanes 0, 1 and 31, a row
-// ahead, and passed on by shuffles.  The march face and the cell update
-// follow step_tile.  Default form (no face options, absorption-only
-// coupling or irradiation deposit).
+// lane k owns column x0 + k, reconstructs its cell's two x face states once
+// (its neighbours' states by shuffles), passes the upper one to lane k + 1
+// and computes the x face x0 + k - 1/2 from the upper state of lane k - 1
+// and its own lower state; lanes 0..30 update their cell with their own
+// face and the face of the lane to their right, so strips overlap by one
+// column (31 updated columns per strip).  The cells left of the strip
+// (x0 - 2, x0 - 1, whose upper state and optical depth the face x0 - 1/2
+// needs) are loaded by lane 0 and the cell right of it (x0 + 32) by lane 31,
+// a row ahead.  The march face and the cell update follow step_tile.
+// Default form (no face options, absorption-only coupling or irradiation
+// deposit).
 #pragma once
 #include "m1_step.cuh"
 
 namespace m1 {
+
+// Lower (lo) and upper (hi) x face states of cell uc between um and up,
+// each fixed with the cell's own centre; returns how many the fix replaced.
+template <class T, int NC, bool UNI>
+__device__ __forceinline__ int face_states_x(const T (&um)[4], const T (&uc)[4], const T (&up)[4],
+                                             T ixl, T ixr, T hl, T hh, T n2c, T invc,
+                                             T (&lo)[4], T (&hi)[4]) {
+  constexpr int NV = 1 + NC;
+  if constexpr (UNI && sizeof(T) == 4) {
+    uni_states<T, NV>(um, uc, up, lo, hi);
+  } else {
+    T dl[4], dr[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      dl[q] = (uc[q] - um[q]) * ixl;
+      dr[q] = (up[q] - uc[q]) * ixr;
+    }
+    plm_state<T, NV>(dl, dr, uc, hl, lo);
+    plm_state<T, NV>(dl, dr, uc, hh, hi);
+  }
+  return fix_face<T, NC>(lo, uc, n2c, invc) + fix_face<T, NC>(hi, uc, n2c, invc);
+}
 
 template <class P, int NC, bool UNI>
 __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int by) {
@@ -102,20 +127,20 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
     if (upd_col) cnt.fix += nfh;
   }
 
-  // the strip's outside cells: lane 0 column x0 - 2, lane 1 column x0 - 1
-  // (whose optical depth the face x0 - 1/2 needs), lane 31 column x0 + 32
-  const bool has_halo = k <= 1 || k == 31;
-  const int hxs = k == 0 ? -2 : (k == 1 ? -1 : 32);
-  const int hx = min(max(x0 + hxs + Dm.g[0], 0), Dm.pn[0] - 1);
-  T hu[4] = {0, 0, 0, 0};
+  // the strip's outside cells: lane 0 columns x0 - 2 (ha) and x0 - 1 (hb,
+  // with its rho and e), lane 31 column x0 + 32 (hb)
+  const int hxa = min(max(x0 - 2 + Dm.g[0], 0), Dm.pn[0] - 1);
+  const int hxb = min(max(x0 + (k == 0 ? -1 : 32) + Dm.g[0], 0), Dm.pn[0] - 1);
+  T ha[4] = {0, 0, 0, 0}, hb[4] = {0, 0, 0, 0};
   S hrho = S(1), he = S(1);
   auto load_halo = [&](int m) {
-    if (has_halo) {
-      const long long ih = hx + (long long)(m + gm) * ms;
-      load_state<S, NC>(a.in, ih, hu);
-      if (k == 1) {
-        hrho = __ldg(a.rho + ih);
-        he = __ldg(a.in.e + ih);
+    if (k == 0 || k == 31) {
+      const long long ib = hxb + (long long)(m + gm) * ms;
+      load_state<S, NC>(a.in, ib, hb);
+      if (k == 0) {
+        load_state<S, NC>(a.in, hxa + (long long)(m + gm) * ms, ha);
+        hrho = __ldg(a.rho + ib);
+        he = __ldg(a.in.e + ib);
       }
     }
   };
@@ -135,48 +160,45 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
 #pragma unroll
       for (int v = 0; v < NC; ++v) mom[v] = T(__ldg(a.in.m[v] + ic));
     }
-    // the row around this lane's column, from its neighbours and the
-    // outside cells
-    T um2[4], um1[4], up1[4];
+    // the row around this lane's column: its neighbours by shuffles, the
+    // outside cells from lanes 0 and 31
+    T um1[4], up1[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) {
       if (v < NV) {
-        const T own = q[0][v], hv = hu[v];
+        const T own = q[0][v];
         const T sU1 = __shfl_up_sync(FULL, own, 1);
-        const T sU2 = __shfl_up_sync(FULL, own, 2);
         const T sD1 = __shfl_down_sync(FULL, own, 1);
-        const T h0 = __shfl_sync(FULL, hv, 0);
-        const T h1 = __shfl_sync(FULL, hv, 1);
-        const T h31 = __shfl_sync(FULL, hv, 31);
-        um1[v] = k >= 1 ? sU1 : h1;
-        um2[v] = k >= 2 ? sU2 : (k == 1 ? h1 : h0);
-        up1[v] = k <= 30 ? sD1 : h31;
+        um1[v] = k >= 1 ? sU1 : hb[v];
+        up1[v] = k <= 30 ? sD1 : hb[v];
       } else {
-        um1[v] = um2[v] = up1[v] = T(0);
+        um1[v] = up1[v] = T(0);
       }
     }
-    T htau = T(0);
-    if (k == 1) {
+    // the two x face states of this lane's cell, fixed with its centre
+    T lox[4], hix[4];
+    const int nfx = face_states_x<T, NC, UNI>(um1, q[0], up1, IXC(0, px - 1), IXC(0, px),
+                                              HLO(0, px), HHI(0, px), n2_own, inv_own, lox, hix);
+    if (upd_col) cnt.fix += nfx;
+    // the upper state and optical depth of the column left of each lane's
+    // face: lane k - 1's, or for lane 0 the outside column x0 - 1
+    T uL[4];
+#pragma unroll
+    for (int v = 0; v < 4; ++v) uL[v] = __shfl_up_sync(FULL, hix[v], 1);
+    T tL = __shfl_up_sync(FULL, tau_m, 1);
+    if (k == 0) {
+      T lo0[4];
+      face_states_x<T, NC, UNI>(ha, hb, q[0], IXC(0, px - 2), IXC(0, px - 1), HLO(0, px - 1),
+                                HHI(0, px - 1), flux2<T, NC>(hb), Ops<T>::rcp(hb[0]), lo0, uL);
       T kp, chi;
-      htau = cell_tau<P, NDIM, GEOM, UNI>(a, hrho, he, min(hx, G.len[0] - 1), m + gm, 0, kp, chi);
+      tL = cell_tau<P, NDIM, GEOM, UNI>(a, hrho, he, min(hxb, G.len[0] - 1), m + gm, 0, kp, chi);
     }
-    const T tU = __shfl_up_sync(FULL, tau_m, 1);
-    const T tH = __shfl_sync(FULL, htau, 1);
     if (m + 1 < m1) load_halo(m + 1);
     tau_n = cell_tau<P, NDIM, GEOM, UNI>(a, rho_n, e_n, px, m + 1 + gm, 0, kp_n, chi_n);
 
     // x face (column - 1/2)
     T fx[4];
-    {
-      const T tau = T(0.5) * ((k >= 1 ? tU : tH) + tau_m);
-      const int nf = face4<T, NC, 0, UNI>(um2, um1, q[0], up1, IXC(0, px - 2), IXC(0, px - 1),
-                                          IXC(0, px), HHI(0, px - 1), HLO(0, px), tau, fchat,
-                                          inv_own, n2_own, fx);
-      // fixed states of updated cells: the lower one of this cell, the upper
-      // one of the cell to the left
-      if (upd_col) cnt.fix += nf >> 1;
-      if (k >= 1 && cx - 1 < Dm.n[0]) cnt.fix += nf & 1;
-    }
+    riemann<T, NC, 0>(uL, lox, fchat, T(0.5) * (tL + tau_m), fx);
     T fhi[4];
 #pragma unroll
     for (int v = 0; v < 4; ++v) fhi[v] = __shfl_down_sync(FULL, fx[v], 1);
