@@ -52,7 +52,9 @@ typedef enum {
   RAD_ENONPHYS = 4,     /* non-physical input or state (E <= 0, |F| > E, NaN) */
   RAD_ENOCONV = 5,      /* the coupling iteration did not converge in some cell */
   RAD_ETIMEOUT = 6,     /* a bounded device wait ran out */
-  RAD_EUNSUPPORTED = 7  /* valid request this build does not implement */
+  RAD_EUNSUPPORTED = 7, /* valid request this build does not implement */
+  RAD_EBOUNDS = 8       /* debug build only: a device-side index check failed (the
+                           access was skipped, the state that step left is not valid) */
 } rad_status;
 
 typedef enum { RAD_CARTESIAN = 0, RAD_CYLINDRICAL = 1, RAD_SPHERICAL = 2 } rad_geometry;
@@ -352,6 +354,18 @@ rad_status rad_get_launch(const rad_ctx *ctx, int *variant, int *chunk, int *nva
  * stays usable.  Not in the paper: it exists so that the timeout path can be
  * exercised without a fault.  Errors: RAD_EINVAL. */
 rad_status rad_set_wait_limit(rad_ctx *ctx, unsigned int polls);
+
+/* Debug build (librad_debug.so, built with RAD_DEBUG_CHECKS): every store
+ * of the step kernels and the gas step checks its cell index against the
+ * padded arrays; a failed check sets a flag that the next rad_sync returns
+ * as RAD_EBOUNDS, and the access is skipped (no trap).  Not in the paper: it
+ * stands in for a memory checker.  rad_debug_check_index runs one such
+ * check on the context's stream, on E of the current state at cell `index`
+ * of the padded layout (rewriting the value it holds when the index is in
+ * range), so that the check itself can be exercised; release builds do
+ * nothing and return RAD_EUNSUPPORTED.  Errors: RAD_EINVAL, RAD_ENOMEM,
+ * RAD_ECUDA. */
+rad_status rad_debug_check_index(rad_ctx *ctx, long long index);
 
 /* Autotuner: times `reps` steps of every (shape, chunk) candidate on the
  * current state without advancing it (each trial recomputes the same step

@@ -15,10 +15,12 @@ from typing import Optional
 import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "_lib", "librad.so")
+# RAD_DEBUG=1: the debug build (device-side index checks, RAD_EBOUNDS)
+LIB_PATH = os.path.join(_HERE, "_lib", "librad_debug.so" if os.environ.get("RAD_DEBUG") == "1"
+                        else "librad.so")
 
 RAD_OK, RAD_EINVAL, RAD_ENOMEM, RAD_ECUDA, RAD_ENONPHYS, RAD_ENOCONV, RAD_ETIMEOUT, \
-    RAD_EUNSUPPORTED = range(8)
+    RAD_EUNSUPPORTED, RAD_EBOUNDS = range(9)
 RAD_CARTESIAN, RAD_CYLINDRICAL, RAD_SPHERICAL = range(3)
 RAD_BC_OUTFLOW, RAD_BC_PERIODIC, RAD_BC_REFLECTIVE, RAD_BC_FIXED, RAD_BC_LTE = range(5)
 RAD_OPAC_CONST, RAD_OPAC_POWERLAW, RAD_OPAC_TABLE = range(3)
@@ -80,7 +82,8 @@ EXPORTS = ["rad_default_params", "rad_create", "rad_workspace_size", "rad_bind_w
            "rad_read", "rad_set_gas_host_async", "rad_set_rad_host_async",
            "rad_read_host_async", "rad_sync", "rad_dt", "rad_get_stats", "rad_reset_stats",
            "rad_launches_per_step", "rad_profile_begin", "rad_profile_end",
-           "rad_set_launch", "rad_get_launch", "rad_set_wait_limit", "rad_tune",
+           "rad_set_launch", "rad_get_launch", "rad_set_wait_limit", "rad_debug_check_index",
+           "rad_tune",
            "rad_mlp_nparam", "rad_mlp_set", "rad_mlp_get", "rad_mlp_init", "rad_mlp_train",
            "rad_mlp_grad", "rad_mlp_predict", "rad_mlp_predict_tc", "rad_log_bind",
            "rad_log_count",
@@ -130,6 +133,7 @@ def lib() -> C.CDLL:
     L.rad_profile_end.argtypes = [vp, P(C.c_float), P(C.c_float), P(C.c_int)]
     L.rad_set_launch.argtypes = [vp, C.c_int, C.c_int]
     L.rad_set_wait_limit.argtypes = [vp, C.c_uint]
+    L.rad_debug_check_index.argtypes = [vp, C.c_longlong]
     L.rad_get_launch.argtypes = [vp, P(C.c_int), P(C.c_int), P(C.c_int)]
     L.rad_tune.argtypes = [vp, C.c_int, P(C.c_int), P(C.c_int), P(C.c_float)]
     L.rad_mlp_nparam.argtypes = []
@@ -388,6 +392,11 @@ class Rad:
 
     def set_launch(self, variant: int, chunk: int = 0):
         check(lib().rad_set_launch(self.ctx, int(variant), int(chunk)), "rad_set_launch")
+
+    def debug_check_index(self, index: int) -> int:
+        """rad_debug_check_index (the debug build's index check on cell
+        `index` of the padded layout); returns the status code."""
+        return lib().rad_debug_check_index(self.ctx, int(index))
 
     def set_wait_limit(self, polls: int):
         """Bound of the staged-plane waits (0: the default)."""

@@ -369,6 +369,7 @@ extern "C" rad_status rad_batch_set_graph(rad_batch* b, int use_graph) {
 }
 
 extern "C" rad_status rad_batch_step(rad_batch* b, const double* dt, int nsteps) {
+  NvtxRange nvtx_range("rad_batch_step");
   if (!b || nsteps < 0) return RAD_EINVAL;
   if (!b->ws) return RAD_ENOMEM;
   for (const rad_ctx* m : b->g) {
@@ -408,6 +409,7 @@ extern "C" rad_status rad_batch_sync(rad_batch* b) {
     return RAD_ECUDA;
   if (word && cudaMemsetAsync(b->ws + b->off_status, 0, sizeof(int), b->stream) != cudaSuccess)
     return RAD_ECUDA;
+  if (word & STATUS_BOUNDS) return RAD_EBOUNDS;
   if (word & STATUS_TIMEOUT) return RAD_ETIMEOUT;
   if (word & STATUS_NONPHYS) return RAD_ENONPHYS;
   if (word & STATUS_NOCONV) return RAD_ENOCONV;
@@ -469,6 +471,7 @@ extern "C" rad_status rad_batch_get_launch(const rad_batch* b, int* variant, int
 // step into the members' spare buffers.  Restores the counters and the status
 // word and keeps the fastest pair.
 extern "C" rad_status rad_batch_tune(rad_batch* b, int reps, int* variant, int* chunk, float* ms) {
+  NvtxRange nvtx_range("rad_batch_tune");
   if (!b || reps < 1) return RAD_EINVAL;
   if (!b->ws) return RAD_ENOMEM;
   for (const rad_ctx* m : b->g)

@@ -3,6 +3,7 @@
 // (batch_api.cu).  Not part of the public ABI.
 #pragma once
 #include <cuda.h>
+#include <nvtx3/nvToolsExt.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -13,6 +14,15 @@
 #include "mlp_launch.h"
 #include "rad.h"
 #include "step_launch.h"
+
+// NVTX range over one host entry point (header-only NVTX v3: a no-op unless a
+// profiler is attached), so that profiles show the library's calls.
+struct NvtxRange {
+  explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+  ~NvtxRange() { nvtxRangePop(); }
+  NvtxRange(const NvtxRange&) = delete;
+  NvtxRange& operator=(const NvtxRange&) = delete;
+};
 
 // Tensor maps of the TMA-staged step for one box shape: per state buffer (up to 3),
 // E, F0..F2, rho and e (the order of the kernel's TmaMaps).

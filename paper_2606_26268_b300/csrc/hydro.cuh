@@ -34,6 +34,7 @@ struct HydroArgs {
   T inv_gm1;         // 1 / (Gamma - 1)
   T uni_inv[3];      // 1 / h per direction (uniform grids)
   T bcT[3][2];       // gas temperature of the fixed and LTE sides
+  int* status;       // status word (the debug build's index checks)
 };
 
 // Conserved state and physical flux along D of a primitive state.
@@ -385,10 +386,14 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
 #pragma unroll
       for (int v = 0; v < NC; ++v) k2 += U[1 + v] * U[1 + v];
       const T en = U[4] - T(0.5) * k2 * Ops<T>::rcp(U[0]);
-      h.rho_out[ic] = S(U[0]);
-      h.e_out[ic] = S(en);
+      // (the debug build skips the stores of a cell whose index fails its check)
+      const bool store_ok = index_ok((long long)ic, padded_cells(Dm), h.status);
+      if (store_ok) {
+        h.rho_out[ic] = S(U[0]);
+        h.e_out[ic] = S(en);
 #pragma unroll
-      for (int v = 0; v < NC; ++v) h.m_out[v][ic] = S(U[1 + v]);
+        for (int v = 0; v < NC; ++v) h.m_out[v][ic] = S(U[1 + v]);
+      }
       // ghost copies of rho* and e* (the optical depths of the radiation
       // step read them): wrapped, edge or mirrored; the fixed and LTE sides
       // take the edge density and e = C_v T_b
@@ -397,7 +402,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
       for (int d = 0; d < NDIM; ++d) {
         const int n = Dm.n[d];
         const int i = ci[d];
-        if (i >= 2 && i < n - 2) continue;
+        if (!store_ok || (i >= 2 && i < n - 2)) continue;
         const long long stride = d == 0 ? 1ll : (d == 1 ? Dm.sy : Dm.sz);
 #pragma unroll
         for (int gslot = 0; gslot < 4; ++gslot) {
@@ -413,6 +418,7 @@ __global__ void __launch_bounds__(TX * TY, (TX * TY >= 256 && P::kSplit) ? 3 : 1
             src = lo ? 0 : n - 1;
           if (src != i) continue;
           const long long ig = ic + (long long)(gpos - i) * stride;
+          if (!index_ok(ig, padded_cells(Dm), h.status)) continue;
           h.rho_out[ig] = S(U[0]);
           const bool held = bc == BC_FIXED || bc == BC_LTE;
           h.e_out[ig] = S(held ? h.cvfac * U[0] * h.bcT[d][lo ? 0 : 1] : en);

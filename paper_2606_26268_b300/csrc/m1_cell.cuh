@@ -242,6 +242,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, I ic, const in
   }
   if (!(En > T(0)) || !(en == en) || !(en > T(0))) atomicOr(a.status, STATUS_NONPHYS);
   // stores: own cell and the ghost copies it feeds
+  if (!index_ok((long long)ic, padded_cells(Dm), a.status)) return;
   a.out.E[ic] = S(En);
 #pragma unroll
   for (int v = 0; v < NC; ++v) {
@@ -276,6 +277,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, I ic, const in
         src = lo ? 0 : n - 1;
       if (src != i) continue;
       const long long ig = (long long)ic + (long long)(gpos - i) * stride;
+      if (!index_ok(ig, padded_cells(Dm), a.status)) continue;
       if constexpr (GEN) {
         if (a.rho_avg) a.rho_avg[ig] = S(rfin);
         if (gas_held) {

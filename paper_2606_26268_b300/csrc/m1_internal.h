@@ -75,7 +75,30 @@ enum {
   ST_N
 };
 
-enum { STATUS_NOCONV = 1, STATUS_NONPHYS = 2, STATUS_TIMEOUT = 4 };
+enum { STATUS_NOCONV = 1, STATUS_NONPHYS = 2, STATUS_TIMEOUT = 4, STATUS_BOUNDS = 8 };
+
+// Index check of the debug build (compiled with RAD_DEBUG_CHECKS, the
+// library librad_debug.so): an index outside [0, n) sets STATUS_BOUNDS in
+// the status word, which the next rad_sync returns as RAD_EBOUNDS, and the
+// caller skips the access; there is no trap.  Release builds compile the
+// check to `true`.
+__device__ __forceinline__ bool index_ok(long long i, long long n, int* status) {
+#ifdef RAD_DEBUG_CHECKS
+  if (i >= 0 && i < n) return true;
+  atomicOr(status, STATUS_BOUNDS);
+  return false;
+#else
+  (void)i;
+  (void)n;
+  (void)status;
+  return true;
+#endif
+}
+
+// Cells of one padded field array.
+__host__ __device__ __forceinline__ long long padded_cells(const StepDims& d) {
+  return (long long)d.pn[0] * d.pn[1] * d.pn[2];
+}
 
 template <class P>
 struct StepArgs {

@@ -529,7 +529,7 @@ __global__ void __launch_bounds__(TX * TY, MINB)
         base_slot = __shfl_sync(mask, base_slot, leader);
         if (queued) {
           unsigned int qs = base_slot + __popc(want & ((1u << (tid & 31)) - 1u));
-          if (qs < a.queue_cap) {
+          if (qs < a.queue_cap && index_ok((long long)ic, padded_cells(a.dim), a.status)) {
             a.queue[qs] = ic;
             a.stash.E[ic] = S(Us[0]);
             // the single solve's T^{n+1}: the queue pass continues from it

@@ -264,7 +264,7 @@ __device__ __forceinline__ void step_strip2d(const StepArgs<P>& a, int bx, int b
         base_slot = __shfl_sync(mask, base_slot, leader);
         if (queued) {
           const unsigned int slot = base_slot + __popc(want & ((1u << k) - 1u));
-          if (slot < a.queue_cap) {
+          if (slot < a.queue_cap && index_ok((long long)ic, padded_cells(a.dim), a.status)) {
             a.queue[slot] = ic;
             a.stash.E[ic] = S(Us[0]);
             // the single solve's T^{n+1}: the queue pass continues from it

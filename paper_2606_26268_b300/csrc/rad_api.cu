@@ -27,11 +27,12 @@ static const char* kMsg[] = {"ok",
                              "non-physical input or state",
                              "coupling iteration did not converge",
                              "bounded device wait ran out",
-                             "unsupported request"};
+                             "unsupported request",
+                             "device-side index check failed (debug build)"};
 
 extern "C" const char* rad_strerror(rad_status s) {
   int i = int(s);
-  if (i < 0 || i > 7) return "unknown status";
+  if (i < 0 || i > 8) return "unknown status";
   return kMsg[i];
 }
 
@@ -185,6 +186,7 @@ static bool misaligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p)
 
 extern "C" rad_status rad_create(const rad_grid* grid, int geometry, const rad_opacity* opacity,
                                  const rad_params* params, rad_ctx** out) {
+  NvtxRange nvtx_range("rad_create");
   if (!grid || !opacity || !params || !out) return RAD_EINVAL;
   if (grid->ndim < 1 || grid->ndim > 3) return RAD_EINVAL;
   if (geometry < 0 || geometry > 2) return RAD_EINVAL;
@@ -719,6 +721,7 @@ static rad_status set_gas_t(rad_ctx* c, const void* rho, const void* v, const vo
 
 extern "C" rad_status rad_set_gas(rad_ctx* c, const void* rho, const void* v, const void* T,
                                   int on_device) {
+  NvtxRange nvtx_range("rad_set_gas");
   if (!c || !rho || !v || !T) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   return c->esize == 8 ? set_gas_t<double>(c, rho, v, T, on_device)
@@ -773,6 +776,7 @@ extern "C" rad_status rad_set_irradiation(rad_ctx* c, const void* q, int on_devi
 }
 
 extern "C" rad_status rad_set_rad(rad_ctx* c, const void* E, const void* F, int on_device) {
+  NvtxRange nvtx_range("rad_set_rad");
   if (!c || !E || !F) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   return c->esize == 8 ? set_rad_t<double>(c, E, F, on_device)
@@ -1008,6 +1012,7 @@ static cudaError_t enqueue_gas(rad_ctx* c, double dt, int in_buf, int rho_buf) {
   }
   h.rho = static_cast<const S*>(rho_ptr(c, in_buf));
   h.e = static_cast<const S*>(state_ptr(c, in_buf, 4));
+  h.status = reinterpret_cast<int*>(c->ws + c->off_status);
   h.rho_out = static_cast<S*>(rho_ptr(c, rho_buf));
   h.e_out = reinterpret_cast<S*>(c->ws + c->off_gas_e);
   for (int q = 0; q < 3; ++q) {
@@ -1087,6 +1092,7 @@ static rad_status enqueue_pass(rad_ctx* c, double dt, int in_buf, int out_buf,
 }
 
 extern "C" rad_status rad_step(rad_ctx* c, double dt, int nsteps) {
+  NvtxRange nvtx_range("rad_step");
   if (!c || nsteps < 0) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
@@ -1245,6 +1251,7 @@ extern "C" rad_status rad_mlp_grad(rad_ctx* c, const float* dev_records, size_t 
 
 extern "C" rad_status rad_mlp_train(rad_ctx* c, const float* dev_records, size_t n, int epochs,
                                     int batch, float lr, uint64_t seed, float* final_loss) {
+  NvtxRange nvtx_range("rad_mlp_train");
   if (!c || !dev_records || n == 0 || epochs < 0 || batch < 1 || !(lr > 0.f) ||
       n > (size_t(1) << 40) || misaligned16(dev_records))
     return RAD_EINVAL;
@@ -1340,6 +1347,31 @@ extern "C" rad_status rad_set_launch(rad_ctx* c, int variant, int chunk) {
   return RAD_OK;
 }
 
+// One index check of the debug build on E of the current state.
+__global__ void debug_check_kernel(float* E32, double* E64, long long i, long long n,
+                                   int* status) {
+  if (index_ok(i, n, status)) {
+    if (E32) E32[i] = E32[i];
+    if (E64) E64[i] = E64[i];
+  }
+}
+
+extern "C" rad_status rad_debug_check_index(rad_ctx* c, long long index) {
+  if (!c) return RAD_EINVAL;
+#ifdef RAD_DEBUG_CHECKS
+  if (!c->ws) return RAD_ENOMEM;
+  void* E = state_ptr(c, c->cur, 0);
+  debug_check_kernel<<<1, 1, 0, c->stream>>>(c->esize == 4 ? static_cast<float*>(E) : nullptr,
+                                             c->esize == 8 ? static_cast<double*>(E) : nullptr,
+                                             index, padded_cells(c->dims),
+                                             reinterpret_cast<int*>(c->ws + c->off_status));
+  return cudaGetLastError() == cudaSuccess ? RAD_OK : RAD_ECUDA;
+#else
+  (void)index;
+  return RAD_EUNSUPPORTED;
+#endif
+}
+
 extern "C" rad_status rad_set_wait_limit(rad_ctx* c, unsigned int polls) {
   if (!c) return RAD_EINVAL;
   c->wait_polls = polls;
@@ -1358,6 +1390,7 @@ extern "C" rad_status rad_get_launch(const rad_ctx* c, int* variant, int* chunk,
 // advancing it (the step is recomputed from the same input buffer), keeps
 // the fastest, and restores the counters and the status word.
 extern "C" rad_status rad_tune(rad_ctx* c, int reps, int* variant, int* chunk, float* ms) {
+  NvtxRange nvtx_range("rad_tune");
   if (!c || reps < 1) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   if (!c->have_gas || !c->have_rad) return RAD_EINVAL;
@@ -1454,6 +1487,7 @@ static rad_status take_status(rad_ctx* c) {
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return RAD_ECUDA;
   const int st = w[0] | w[1];
   if (st) cudaMemsetAsync(c->ws + c->off_status, 0, sizeof(w), c->stream);
+  if (st & STATUS_BOUNDS) return RAD_EBOUNDS;
   if (st & STATUS_TIMEOUT) return RAD_ETIMEOUT;
   if (st & STATUS_NONPHYS) return RAD_ENONPHYS;
   if (st & STATUS_NOCONV) return RAD_ENOCONV;
@@ -1504,6 +1538,7 @@ static rad_status read_t(rad_ctx* c, int field, void* dst, int dev) {
 }
 
 extern "C" rad_status rad_read(rad_ctx* c, int field, void* dst, size_t bytes, int on_device) {
+  NvtxRange nvtx_range("rad_read");
   if (!c || !dst || field < 0 || field > 5) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   int ncomp = (field == RAD_FIELD_F || field == RAD_FIELD_M) ? c->par.ncomp : 1;
@@ -1592,6 +1627,7 @@ static rad_status async_upload(rad_ctx* c, const void* const* src, const size_t*
 
 extern "C" rad_status rad_set_gas_host_async(rad_ctx* c, const void* rho, const void* v,
                                              const void* T) {
+  NvtxRange nvtx_range("rad_set_gas_host_async");
   if (!c || !rho || !v || !T) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   rad_status st = async_setup(c);
@@ -1611,6 +1647,7 @@ extern "C" rad_status rad_set_gas_host_async(rad_ctx* c, const void* rho, const 
 }
 
 extern "C" rad_status rad_set_rad_host_async(rad_ctx* c, const void* E, const void* F) {
+  NvtxRange nvtx_range("rad_set_rad_host_async");
   if (!c || !E || !F) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   rad_status st = async_setup(c);
@@ -1629,6 +1666,7 @@ extern "C" rad_status rad_set_rad_host_async(rad_ctx* c, const void* E, const vo
 }
 
 extern "C" rad_status rad_read_host_async(rad_ctx* c, int field, void* dst, size_t bytes) {
+  NvtxRange nvtx_range("rad_read_host_async");
   if (!c || !dst || field < 0 || field > 5) return RAD_EINVAL;
   if (!c->ws) return RAD_ENOMEM;
   const int ncomp = (field == RAD_FIELD_F || field == RAD_FIELD_M) ? c->par.ncomp : 1;

@@ -240,3 +240,26 @@ def test_record_pointers_off_a_16_byte_boundary_are_refused(R):
 def test_wait_limit_setter_validates_its_context(R):
     L = R.lib()
     assert L.rad_set_wait_limit(None, 1) == R.RAD_EINVAL
+
+
+def test_debug_build_exports_the_same_entry_points_and_the_release_build_refuses_the_check(R):
+    """The debug build (librad_debug.so, RAD_DEBUG_CHECKS) exports every
+    function include/rad.h declares; its index check reports RAD_EBOUNDS,
+    which rad_strerror names.  The release build compiles the checks out and
+    answers rad_debug_check_index with RAD_EUNSUPPORTED, on the host."""
+    from paper_2606_26268_b300 import build
+    lib = build.build(debug=True)
+    D = C.CDLL(lib)
+    for name in declared_functions():
+        assert hasattr(D, name), name
+    L = R.lib()
+    L.rad_strerror.restype = C.c_char_p
+    assert b"index check" in L.rad_strerror(R.RAD_EBOUNDS)
+    g, xs = _grid(R)
+    o = R.rad_opacity()
+    p = R.default_params()
+    ctx = C.c_void_p()
+    assert L.rad_create(C.byref(g), 0, C.byref(o), C.byref(p), C.byref(ctx)) == R.RAD_OK
+    assert L.rad_debug_check_index(ctx, 0) == R.RAD_EUNSUPPORTED
+    assert L.rad_debug_check_index(None, 0) == R.RAD_EINVAL
+    L.rad_destroy(ctx)
