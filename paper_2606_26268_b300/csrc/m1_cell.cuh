@@ -240,7 +240,7 @@ __device__ __forceinline__ void finish_cell(const StepArgs<P>& a, I ic, const in
     }
     en = eg - ka;
   }
-  if (!(En > T(0)) || !(en == en) || !(en > T(0))) atomicOr(a.status, STATUS_NONPHYS);
+  if (!(En > T(0) && en > T(0))) atomicOr(a.status, STATUS_NONPHYS);  // also NaN
   // stores: own cell and the ghost copies it feeds
   if (!index_ok((long long)ic, padded_cells(Dm), a.status)) return;
   a.out.E[ic] = S(En);

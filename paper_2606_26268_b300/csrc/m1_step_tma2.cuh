@@ -304,11 +304,6 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     const float* rl0 = rslot(j);
     const float* rl1 = rslot(j + 1);
     state_at(slot(j + 2), own, q[2]);
-    T mom[3] = {0, 0, 0};
-    if (in_col) {
-#pragma unroll
-      for (int v = 0; v < NC; ++v) mom[v] = T(__ldg(a.in.m[v] + ic));
-    }
     // --- phase 1: face states of the own cell (x and y) and of the halo
     T lox[4], loy[4];
     {
@@ -429,6 +424,11 @@ __global__ void __launch_bounds__(TX * TY, MINB)
 
     // update of the own cell
     if (in_col) {
+      // the gas momentum is loaded here rather than with the plane: three
+      // registers fewer across both phases
+      T mom[3] = {0, 0, 0};
+#pragma unroll
+      for (int v = 0; v < NC; ++v) mom[v] = T(__ldg(a.in.m[v] + ic));
       const T (&u)[4] = q[0];
       T Us[4];
       T fxl[4], fxh[4], fyl[4], fyh[4];
