@@ -272,27 +272,15 @@ __global__ void __launch_bounds__(TX * TY, MINB)
     issue(RF);
   }
 
-  // halo face state of this thread (last three warps): item h of
-  //   [0, TY): upper x of column -1, row h       [TY, 2TY): lower x of column TX
-  //   [2TY, 2TY+TX): upper y of row -1, col c    [2TY+TX, 2TY+2TX): lower y of row TY
-  const int h = tid - (NT - 96);
-  const bool has_h = h >= 0 && h < TL::NHALO;
-  const bool h_x = h < 2 * TY;                    // x-direction item
-  const bool h_hi = h_x ? h < TY : h < 2 * TY + TX;  // upper state wanted
-  const int h_rc = h_x ? (h < TY ? h : h - TY) : (h < 2 * TY + TX ? h - 2 * TY : h - 2 * TY - TX);
-  // smem position of the item's cell, its neighbours' stride, table indices
-  const int h_row = h_x ? h_rc + 2 : (h_hi ? 1 : TY + 2);
-  const int h_col = h_x ? (h_hi ? 1 : TX + 2) : h_rc + 2;
-  const int h_idx = h_row * BX + h_col;
-  const int h_step = h_x ? 1 : BX;
-  const int h_px = min(x0 + h_col, G.len[0] - 1);
-  const int h_py = min(y0 + h_row, G.len[1] - 1);
-  const int h_p = h_x ? h_px : h_py;  // padded index along the item's direction
-  // upper tile face of this thread (first two warps): x face TX - 1/2 of
-  // row e (e < TY) or y face TY - 1/2 of column e - TY
-  const int e = tid;
-  const bool has_e = e < TL::NEXTRA;
-  const bool e_x = e < TY;
+  // The halo item and the upper tile face of a thread are recomputed from
+  // its index where they are used, not kept in registers across the march:
+  // the index is read by an asm statement that is not hoisted out of the loop.
+  auto fresh_tid = [&]() -> int {
+    unsigned int x, y;
+    asm volatile("mov.u32 %0, %%tid.x;" : "=r"(x));
+    asm volatile("mov.u32 %0, %%tid.y;" : "=r"(y));
+    return int(x + TX * y);
+  };
 
   for (int m = m0; m < m1; ++m) {
     const int j = m - m0 + 2;  // plane m
@@ -321,7 +309,23 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       s_hy[ty + 1][tx] = f4_of(hy);
     }
     s_tau[ty + 1][tx + 1] = tau_m;
-    if (has_h) {
+    // halo face state of this thread (the last three warps): item h of
+    //   [0, TY): upper x of column -1, row h       [TY, 2TY): lower x of column TX
+    //   [2TY, 2TY+TX): upper y of row -1, col c    [2TY+TX, 2TY+2TX): lower y of row TY
+    const int h = fresh_tid() - (NT - 96);
+    if (h >= 0 && h < TL::NHALO) {
+      const bool h_x = h < 2 * TY;                       // x-direction item
+      const bool h_hi = h_x ? h < TY : h < 2 * TY + TX;  // upper state wanted
+      const int h_rc =
+          h_x ? (h < TY ? h : h - TY) : (h < 2 * TY + TX ? h - 2 * TY : h - 2 * TY - TX);
+      // smem position of the item's cell, its neighbours' stride, table indices
+      const int h_row = h_x ? h_rc + 2 : (h_hi ? 1 : TY + 2);
+      const int h_col = h_x ? (h_hi ? 1 : TX + 2) : h_rc + 2;
+      const int h_idx = h_row * BX + h_col;
+      const int h_step = h_x ? 1 : BX;
+      const int h_px = min(x0 + h_col, G.len[0] - 1);
+      const int h_py = min(y0 + h_row, G.len[1] - 1);
+      const int h_p = h_x ? h_px : h_py;  // padded index along the item's direction
       T uc[4], um[4], up[4], st[4];
       state_at(sl0, h_idx, uc);
       state_at(sl0, h_idx - h_step, um);
@@ -367,7 +371,11 @@ __global__ void __launch_bounds__(TX * TY, MINB)
       riemann<T, NC, 1>(uL, loy, T(1), T(0.5) * (s_tau[ty][tx + 1] + s_tau[ty + 1][tx + 1]), f);
       s_fy[ty][tx] = f4_of(f);
     }
-    if (has_e) {
+    // upper tile face of this thread (the first two warps): x face TX - 1/2
+    // of row e (e < TY) or y face TY - 1/2 of column e - TY
+    const int e = fresh_tid();
+    if (e < TL::NEXTRA) {
+      const bool e_x = e < TY;
       // x faces (rows e < TY) and y faces (columns e - TY) share one call of
       // the x solver: a y face enters with F_x and F_y exchanged, and its
       // flux leaves with them exchanged back, so a warp holding both kinds
