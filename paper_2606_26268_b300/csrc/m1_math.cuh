@@ -204,10 +204,11 @@ __device__ __forceinline__ void state_flux(const T (&u)[4], T chat, T (&flux)[4]
     lp = (fc + z) / s;
     lm = (fc - z) / s;
   } else {
-    // A denormal |F|^2 is treated as zero flux: the flush-to-zero rsqrt would
-    // turn it into an infinite 1/|F|, and the closure depends on the
-    // direction of F only at O(f^2).
-    T rn = nF2 > T(1e-37) ? rsqrt_approx(nF2) : T(0);
+    // |F|^2 is clamped to 1e-37 under the rsqrt: the flush-to-zero rsqrt
+    // would turn a denormal or zero |F|^2 into an infinite 1/|F|.  F = 0
+    // still gives zero f and zero direction terms, and below the clamp the
+    // closure depends on the direction of F only at O(f^2).
+    T rn = rsqrt_approx(fmaxf(nF2, T(1e-37)));
     T nF = nF2 * rn;
     f = nF * invE;
     f = f > T(1) ? T(1) : f;
@@ -371,6 +372,9 @@ struct OpacityDev {
   int linear_rho;              // powerlaw with a = 1, b = 0 (kappa = k0 rho)
   // float copies for the split-precision path (no double conversions there)
   float f_kp, f_chi0, f_k0, f_a, f_b, f_kmin, f_kmax, f_s1, f_lrho0, f_lT0, f_sr, f_sT;
+  // log2 of C_v / rho = 1 / (mu (Gamma - 1)), and b_T times it and a_rho - b_T, for
+  // the opacities from (rho, e) without forming T
+  float f_lcv, f_blcv, f_amb;
 };
 
 // Opacities per unit mass at (rho, T): kp (Planck), chi = kappa_R + sigma.
@@ -425,6 +429,43 @@ __device__ __forceinline__ void opacity(const OpacityDev& o, float rho, float T,
     const float kLog10_2 = 0.30102999566398120f;
     float xr = (lg2_approx(rho) * kLog10_2 - o.f_lrho0) * o.f_sr;
     float xt = (lg2_approx(T) * kLog10_2 - o.f_lT0) * o.f_sT;
+    xr = fminf(fmaxf(xr, 0.f), float(o.nrho - 1));
+    xt = fminf(fmaxf(xt, 0.f), float(o.nT - 1));
+    int ir = min(int(xr), o.nrho - 2), it = min(int(xt), o.nT - 2);
+    float wr = xr - ir, wt = xt - it;
+    const float* t = o.tab32 + it * o.nrho + ir;
+    float l00 = __ldg(t), l10 = __ldg(t + 1), l01 = __ldg(t + o.nrho), l11 = __ldg(t + o.nrho + 1);
+    float lk = (1.f - wr) * ((1.f - wt) * l00 + wt * l01) + wr * ((1.f - wt) * l10 + wt * l11);
+    k = ex2_approx(lk * 3.32192809488736235f);
+  }
+  kp = k;
+  chi = k * o.f_s1;
+}
+
+// The same opacities at (rho, T = e / (rho C_v/rho)) from log2 T = log2 e -
+// log2 rho - log2 (C_v/rho), in float: no reciprocal and no T (the power law
+// k0 rho^a T^b = k0 2^((a - b) log2 rho + b log2 e - b log2 (C_v/rho))).
+__device__ __forceinline__ void opacity_re(const OpacityDev& o, float rho, float e, float& kp,
+                                           float& chi) {
+  if (o.kind == 0) {
+    kp = o.f_kp;
+    chi = o.f_chi0;
+    return;
+  }
+  float k;
+  if (o.kind == 1) {
+    if (o.linear_rho) {
+      k = o.f_k0 * rho;
+    } else {
+      k = o.f_k0 * ex2_approx(fmaf(o.f_amb, lg2_approx(rho), fmaf(o.f_b, lg2_approx(e), -o.f_blcv)));
+    }
+    k = k < o.f_kmin ? o.f_kmin : k;
+    k = k > o.f_kmax ? o.f_kmax : k;
+  } else {
+    const float kLog10_2 = 0.30102999566398120f;
+    const float lr = lg2_approx(rho);
+    float xr = (lr * kLog10_2 - o.f_lrho0) * o.f_sr;
+    float xt = ((lg2_approx(e) - lr - o.f_lcv) * kLog10_2 - o.f_lT0) * o.f_sT;
     xr = fminf(fmaxf(xr, 0.f), float(o.nrho - 1));
     xt = fminf(fmaxf(xt, 0.f), float(o.nT - 1));
     int ir = min(int(xr), o.nrho - 2), it = min(int(xt), o.nT - 2);

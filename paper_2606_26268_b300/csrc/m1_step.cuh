@@ -57,12 +57,10 @@ __device__ __forceinline__ typename P::T cell_tau(const StepArgs<P>& a, typename
                                                   typename P::T& kp, typename P::T& chi) {
   using T = typename P::T;
   T r = T(rho);
-  T Temp;
   if constexpr (sizeof(T) == 8)
-    Temp = T(e) / (r * T(a.cp.cvfac));
+    opacity(a.opac, r, T(e) / (r * T(a.cp.cvfac)), kp, chi);
   else
-    Temp = T(e) * rcp_approx(r * a.cp.f_cvfac);
-  opacity(a.opac, r, Temp, kp, chi);
+    opacity_re(a.opac, r, T(e), kp, chi);
   if constexpr (UNI) return r * chi * a.uni_h;
   return r * chi * cell_hmax<T, NDIM, GEOM>(a.geo, p0, p1, p2);
 }

@@ -42,12 +42,10 @@ __device__ __forceinline__ void queue_load(const StepArgs<P>& a, long long ic, Q
   c.rho = a.rho[ic];
   c.e = a.in.e[ic];
   T rr = T(c.rho);
-  T Temp;
   if constexpr (sizeof(T) == 8)
-    Temp = T(c.e) / (rr * T(a.cp.cvfac));
+    opacity(a.opac, rr, T(c.e) / (rr * T(a.cp.cvfac)), c.kp, c.chi);
   else
-    Temp = T(c.e) * rcp_approx(rr * a.cp.f_cvfac);
-  opacity(a.opac, rr, Temp, c.kp, c.chi);
+    opacity_re(a.opac, rr, T(c.e), c.kp, c.chi);
 }
 
 // The Newton iteration continued from the single solve's T1, or from the

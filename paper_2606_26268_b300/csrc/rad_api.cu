@@ -849,6 +849,12 @@ static void fill_args(rad_ctx* c, StepArgs<P>& a, double dt, int in_buf, int out
   od.f_lT0 = float(o.lT0);
   od.f_sr = float(od.sr);
   od.f_sT = float(od.sT);
+  {
+    const double lcv = std::log2(1.0 / (c->par.mu * (c->par.gamma_gas - 1.0)));
+    od.f_lcv = float(lcv);
+    od.f_blcv = float(o.b_T * lcv);
+    od.f_amb = float(o.a_rho - o.b_T);
+  }
   CoupleParams& cp = a.cp;
   cp.dt = dt;
   cp.chat = c->par.chat;
