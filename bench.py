@@ -587,7 +587,11 @@ def run_ours(args):
         rd = R.from_problem(pd, args.precision, device=dev, implicit_mode=implicit, **extra)
         if theta is not None:
             rd.mlp_set(theta)
-        tv = rd.tune(2)
+        if args.disk_launch:
+            tv = tuple(int(x) for x in args.disk_launch.split(","))
+            rd.set_launch(*tv)
+        else:
+            tv = rd.tune(2)
         dtd = rd.dt()
         msd, perd, ktd = time_steps(rd, torch, 10, 3, dtd)
         std_ = rd.stats()
@@ -821,6 +825,8 @@ def main():
     ap.add_argument("--launch", default="", help="variant,chunk (skips the autotuner)")
     ap.add_argument("--batch-launch", default="",
                     help="variant,chunk of the batched form (skips its autotuner)")
+    ap.add_argument("--disk-launch", default="",
+                    help="variant,chunk of the spherical disk form (skips its autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
