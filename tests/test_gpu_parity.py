@@ -244,6 +244,51 @@ def test_split_single_solve_residual_near_equilibrium_gas_dominated():
     assert err <= 1e-5, (err, moved)
 
 
+@pytest.mark.parametrize("mode", ["once", "newton"])
+@pytest.mark.parametrize("opac", ["kramers", "powerlaw_general", "table"])
+def test_split_opacities_through_the_coupling(opac, mode):
+    """Sect. 2.8 opacities kappa(rho, T) of the split form, which takes
+    log2 T = log2 e - log2 rho - log2 (C_v/rho) instead of forming T: with
+    E uniform and F = 0 the transport leaves E and F unchanged, so a step
+    moves E by the coupling alone, at rates set by each cell's opacity.  rho
+    and T span decades (the power laws' clip and the table's edges are
+    reached).  Over the cells where the coupling moves E by more than 1e-3 E,
+    E^{n+1} - E^n agrees with the FP64 oracle normwise to 5e-5 in the single
+    solve and 2e-4 when both iterate to 1e-10 (the float coefficients of the
+    split form's iteration move its root by float rounding), and per cell to
+    5e-3 and 2e-2 (float storage of E^{n+1} and of T near equilibrium).  The
+    oracle with kappa raised by 1e-3 moves it by 1.2e-4 to 4.4e-4 normwise
+    and 1e-3 per cell; a wrong exponent, constant or sign moves it by orders
+    more."""
+    if opac == "kramers":
+        o = {"kind": "powerlaw", "k0": 2.0, "a_rho": 1.0, "b_T": -3.5, "kmin": 1e-3, "kmax": 1e3}
+    elif opac == "powerlaw_general":
+        o = {"kind": "powerlaw", "k0": 2.0, "a_rho": 0.5, "b_T": -2.0, "kmin": 1e-3, "kmax": 1e3}
+    else:
+        o = _opacity("table")
+    p = W.random_smooth("cartesian", (40, 23, 37), 3, seed=91, bc="periodic", opacity=o, ncomp=3)
+    rng = np.random.default_rng(5)
+    p.rho = np.exp(1.5 * rng.standard_normal(p.N))
+    p.T = np.exp(0.8 * rng.standard_normal(p.N))
+    p.E = np.full(p.N, float(np.mean(p.a_rad * p.T ** 4)))
+    p.F = np.zeros((3, p.N))
+    p.implicit_mode = mode
+    if mode == "newton":
+        p.newton_rtol = 1e-10
+    q = rounded(p, np.float32)
+    g = run_gpu(q, 1, "split")
+    o_ = run_oracle(q, 1, dt=g["dt"])
+    assert g["status"] == 0
+    E0 = np.asarray(q.E)
+    dg, do = g["E"] - E0, o_["E"] - E0
+    sel = np.abs(do) > 1e-3 * E0
+    assert sel.mean() > 0.2, sel.mean()  # the coupling moves E in much of the box
+    norm = np.linalg.norm(dg[sel] - do[sel]) / np.linalg.norm(do[sel])
+    cell = np.max(np.abs(dg[sel] - do[sel]) / np.abs(do[sel]))
+    assert norm <= (5e-5 if mode == "once" else 2e-4), (norm, cell)
+    assert cell <= (5e-3 if mode == "once" else 2e-2), (norm, cell)
+
+
 def test_split_hot_sphere_within_the_problems_own_sensitivity():
     """The hot-sphere box amplifies perturbations: the FP64 oracle itself moves
     by ~1e-3 (normwise) after 100 steps when its inputs are perturbed by 1e-7.
