@@ -91,16 +91,36 @@ __global__ void __launch_bounds__(TC_ROWS)
   __shared__ unsigned long long s_red[ST_N];
   // the network's shared state only when it is used
   __shared__ typename std::conditional<MLP, TcMlpSmem, int>::type s_tc;
+  __shared__ unsigned int s_wsum[TC_ROWS / 32];
   const int tid = threadIdx.x;
-  if (tid == 0) {
-    unsigned int acc = 0;
-    s_off[0] = 0;
-    for (int g = 0; g < count; ++g) {
-      acc += min(counts[g], args[g].queue_cap);
-      s_off[g + 1] = acc;
+  // prefix sums of the queue lengths, TC_ROWS grids at a time: each thread
+  // loads one grid's length and the block scans them (warp shuffles, then
+  // the warp totals), so the loads are not one thread's chain over all grids
+  {
+    const int lane = tid & 31, w = tid >> 5;
+    unsigned int carry = 0;
+    if (tid == 0) s_off[0] = 0;
+    for (int g0 = 0; g0 < count; g0 += TC_ROWS) {
+      const int g = g0 + tid;
+      unsigned int v = g < count ? min(counts[g], args[g].queue_cap) : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned int t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+      }
+      if (lane == 31) s_wsum[w] = v;
+      __syncthreads();
+      unsigned int before = 0, all = 0;
+#pragma unroll
+      for (int k = 0; k < TC_ROWS / 32; ++k) {
+        before += k < w ? s_wsum[k] : 0u;
+        all += s_wsum[k];
+      }
+      if (g < count) s_off[g + 1] = carry + before + v;
+      carry += all;
+      __syncthreads();  // s_wsum is rewritten by the next group
     }
   }
-  __syncthreads();
   const unsigned int total = s_off[count];
   const unsigned int first = blockIdx.x * TC_ROWS;
   if (first >= total) return;  // no queued cell for this block

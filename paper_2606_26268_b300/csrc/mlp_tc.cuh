@@ -124,10 +124,26 @@ __device__ __forceinline__ void tc_store_row(unsigned char* tile, int r, const f
 // (hidden weights as bf16 operand tiles), the completion barrier and the
 // TMEM columns (allocated by warp 0).  Ends with a barrier.
 __device__ __forceinline__ void tc_mlp_setup(TcMlpSmem& s, const float* __restrict__ w, int tid) {
-  for (int i = tid; i < MLP_H * MLP_H; i += TC_ROWS) {
-    const int n = i / MLP_H, k = i % MLP_H;
-    *reinterpret_cast<__nv_bfloat16*>(s.w2 + tc_offset(n, k)) = __float2bfloat16_rn(w[MLP_W2 + i]);
-    *reinterpret_cast<__nv_bfloat16*>(s.w3 + tc_offset(n, k)) = __float2bfloat16_rn(w[MLP_W3 + i]);
+  // element i = tid + TC_ROWS j of each hidden matrix, 2 U loads in flight
+  // per round: a load, convert and store per element in turn would wait for
+  // every load in sequence
+  constexpr int PER = MLP_H * MLP_H / TC_ROWS, U = 8;
+  static_assert(PER % U == 0, "whole rounds");
+#pragma unroll 1
+  for (int j0 = 0; j0 < PER; j0 += U) {
+    float v2[U], v3[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      v2[u] = __ldg(w + MLP_W2 + tid + TC_ROWS * (j0 + u));
+      v3[u] = __ldg(w + MLP_W3 + tid + TC_ROWS * (j0 + u));
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int i = tid + TC_ROWS * (j0 + u);
+      const int n = i / MLP_H, k = i % MLP_H;
+      *reinterpret_cast<__nv_bfloat16*>(s.w2 + tc_offset(n, k)) = __float2bfloat16_rn(v2[u]);
+      *reinterpret_cast<__nv_bfloat16*>(s.w3 + tc_offset(n, k)) = __float2bfloat16_rn(v3[u]);
+    }
   }
   for (int i = tid; i < 2 * MLP_H; i += TC_ROWS) s.w1[i] = w[MLP_W1 + i];
   if (tid < MLP_H) {
