@@ -613,7 +613,11 @@ def run_ours(args):
                 "l2": "state 55 MB (split) / 109 MB (FP64) per buffer, inside the 126 MB L2"}
         for prec, n2 in (("split", 50), ("fp64", 10)):
             r2d = R.from_problem(p2, prec, device=dev, implicit_mode="once")
-            tv2 = r2d.tune(2)
+            if prec == "split" and args.launch_2d:
+                tv2 = tuple(int(x) for x in args.launch_2d.split(","))
+                r2d.set_launch(*tv2)
+            else:
+                tv2 = r2d.tune(2)
             dt2 = r2d.dt()
             ms2, _, kt2 = time_steps(r2d, torch, n2, 3, dt2)
             st2 = r2d.sync()
@@ -827,6 +831,8 @@ def main():
                     help="variant,chunk of the batched form (skips its autotuner)")
     ap.add_argument("--disk-launch", default="",
                     help="variant,chunk of the spherical disk form (skips its autotuner)")
+    ap.add_argument("--2d-launch", dest="launch_2d", default="",
+                    help="variant,chunk of the split 2D box form (skips its autotuner)")
     args = ap.parse_args()
     if args.warmup < 3 and args.impl == "ours":
         args.warmup = 3
