@@ -43,7 +43,7 @@ __global__ void __launch_bounds__(128) queue_pass_kernel(const __grid_constant__
 // tensor cores (rows of cells below the gate are ignored), and each gated
 // cell starts its Newton iteration from T^n exp(output).
 template <class P, int NDIM, int NC>
-__global__ void __launch_bounds__(TC_ROWS) queue_pass_tc_kernel(const __grid_constant__ StepArgs<P> a) {
+__global__ void __launch_bounds__(TC_ROWS, 5) queue_pass_tc_kernel(const __grid_constant__ StepArgs<P> a) {
   __shared__ TcMlpSmem s;
   __shared__ unsigned long long s_red[ST_N];
   const unsigned int count = min(*a.queue_count, a.queue_cap);
@@ -80,7 +80,7 @@ template <class P, int NDIM, int NC>
 cudaError_t launch_queue_pass(const void* vargs, cudaStream_t s) {
   const StepArgs<P>& a = *static_cast<const StepArgs<P>*>(vargs);
   if (a.mlp_w)
-    queue_pass_tc_kernel<P, NDIM, NC><<<148 * 4, TC_ROWS, 0, s>>>(a);
+    queue_pass_tc_kernel<P, NDIM, NC><<<148 * 5, TC_ROWS, 0, s>>>(a);
   else
     queue_pass_kernel<P, NDIM, NC><<<148 * 4, 128, 0, s>>>(a);
   return cudaGetLastError();

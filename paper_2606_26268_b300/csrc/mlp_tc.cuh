@@ -30,7 +30,7 @@ constexpr int TC_ROWS = 128;                       // samples per product
 constexpr uint32_t TC_LBO = 128, TC_SBO = 1024;    // bytes, see above
 constexpr uint32_t TC_A_BYTES = TC_ROWS * MLP_H * 2;  // 16 KB
 constexpr uint32_t TC_W_BYTES = MLP_H * MLP_H * 2;    // 8 KB
-constexpr uint32_t TC_TMEM_COLS = 128;  // allocation (power of 2 >= 32); the products use 64
+constexpr uint32_t TC_TMEM_COLS = 64;  // allocation (power of 2 >= 32): the N = 64 accumulators
 
 // Instruction descriptor of tcgen05.mma kind::f16: D in F32 (bits 4-5 = 1),
 // A and B in BF16 (bits 7-9 = 1, 10-12 = 1), both K-major (bits 15, 16 = 0),
