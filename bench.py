@@ -686,9 +686,10 @@ def run_ours(args):
     if not args.skip_batch:
         batched = run_batched(args, R, torch, dev, theta, hbm, world)
 
-    # --- CPU baseline: the oracle on the host cores, bounded sample ---------
+    # --- CPU baseline: the oracle on the host cores, bounded sample (one
+    # process on one GPU only: a multi-rank line carries none) --------------
     cpu = None
-    if rank == 0 and not args.skip_cpu:
+    if rank == 0 and world == 1 and not args.skip_cpu:
         cpu = cpu_baseline(prob, dt, args.cpu_seconds)
 
     if rank == 0:
